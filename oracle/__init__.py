@@ -1,0 +1,138 @@
+"""ctypes wrapper of the plain FP64 CPU oracle (``pop_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg are its only users.  The product
+library never imports, links or runs it, and the two share no code.
+
+``build()`` compiles ``liboracle.so`` next to this file with gcc (OpenMP when
+the compiler has it).  Functions mirror the C entry points one to one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pop_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+FLAG_INVALID_LAMBDA = 1
+FLAG_ZERO_EVENT = 2
+FLAG_LOW_NEFF = 4
+FLAG_ZERO_XI = 32
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc; returns the path of the shared library."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", _LIB + ".tmp"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + ["-lm"], check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d, i64, i32, p = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        for name in ("pop_oracle_p_m1", "pop_oracle_p_chi", "pop_oracle_p_z"):
+            getattr(lib, name).argtypes = [d, p]
+            getattr(lib, name).restype = d
+        lib.pop_oracle_p_q.argtypes = [d, d, p]
+        lib.pop_oracle_p_q.restype = d
+        lib.pop_oracle_p_tilt.argtypes = [d, d, p]
+        lib.pop_oracle_p_tilt.restype = d
+        lib.pop_oracle_z_norm.argtypes = [d]
+        lib.pop_oracle_z_norm.restype = d
+        lib.pop_oracle_p_theta.argtypes = [p, i32, p]
+        lib.pop_oracle_p_theta.restype = d
+        lib.pop_oracle_lambda_valid.argtypes = [p, i32]
+        lib.pop_oracle_lambda_valid.restype = i32
+        lib.pop_oracle_loglik.argtypes = [i64, p, i32, p, p, i64, i64, p, p, i64, i32, p, i32, p, p, p, p]
+        lib.pop_oracle_loglik.restype = i32
+        lib.pop_oracle_max_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _lam(L):
+    a = np.ascontiguousarray(L, dtype=np.float64)
+    if a.shape[-1] < 12:
+        a = np.concatenate([a, np.ones(12 - a.shape[-1])])
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def p_m1(m1, L):
+    a = _lam(L)
+    return _load().pop_oracle_p_m1(float(m1), _ptr(a))
+
+
+def p_q(q, m1, L):
+    a = _lam(L)
+    return _load().pop_oracle_p_q(float(q), float(m1), _ptr(a))
+
+
+def p_chi(x, L):
+    a = _lam(L)
+    return _load().pop_oracle_p_chi(float(x), _ptr(a))
+
+
+def p_tilt(c1, c2, L):
+    a = _lam(L)
+    return _load().pop_oracle_p_tilt(float(c1), float(c2), _ptr(a))
+
+
+def p_z(z, L):
+    a = _lam(L)
+    return _load().pop_oracle_p_z(float(z), _ptr(a))
+
+
+def z_norm(kappa):
+    return _load().pop_oracle_z_norm(float(kappa))
+
+
+def p_theta(theta, L):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    a = _lam(L)
+    return _load().pop_oracle_p_theta(_ptr(th), th.shape[-1], _ptr(a))
+
+
+def lambda_valid(L):
+    a = np.ascontiguousarray(L, dtype=np.float64)
+    return bool(_load().pop_oracle_lambda_valid(_ptr(a), a.shape[-1]))
+
+
+def max_threads():
+    return _load().pop_oracle_max_threads()
+
+
+def loglik(catalog, injections, lambdas, nthreads=0):
+    """ln L, ln xi, N_eff and flags for each row of ``lambdas`` [K, P]."""
+    lam = np.ascontiguousarray(np.atleast_2d(lambdas), dtype=np.float64)
+    K, P = lam.shape
+    off = np.ascontiguousarray(catalog.offsets, dtype=np.int64)
+    th = np.ascontiguousarray(catalog.theta, dtype=np.float64)
+    pr = np.ascontiguousarray(catalog.prior, dtype=np.float64)
+    ith = np.ascontiguousarray(injections.theta, dtype=np.float64)
+    pd = np.ascontiguousarray(injections.p_draw, dtype=np.float64)
+    out = np.empty(K), np.empty(K), np.empty(K), np.empty(K, np.uint32)
+    rc = _load().pop_oracle_loglik(len(off) - 1, _ptr(off), th.shape[1], _ptr(th), _ptr(pr),
+                                   ith.shape[0], int(injections.n_draw), _ptr(ith), _ptr(pd),
+                                   K, P, _ptr(lam), int(nthreads),
+                                   _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(out[3]))
+    if rc != 0:
+        raise ValueError("oracle rejected the input sizes")
+    return out

@@ -1,0 +1,252 @@
+/*
+ * Plain, slow FP64 CPU oracle of the population likelihood.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline / reference leg may load this library.  The GPU
+ * library shares no code, header, table or constant with this file.
+ *
+ * What it computes (paper, Sec. "Population acceleration"):
+ *
+ *   ln L(Lambda) = sum_i ln[ (1/n_i) sum_j p(theta_ij | Lambda) / pi(theta_ij) ]
+ *                  - N ln xi(Lambda)
+ *
+ * The product over events of sums of reweighted posterior samples is the
+ * "recycling" estimate of Eq. (poplike).  The -N ln xi term is what the rate
+ * factor R^N exp(-R VT) of the first equation of that section leaves after R is
+ * marginalised under a 1/R prior: int R^(N-1) exp(-R VT) dR = Gamma(N) VT^-N,
+ * with VT proportional to xi.  The 1/n_i factor (a mean instead of the paper's
+ * plain sum) only shifts ln L by a Lambda-independent constant.
+ *
+ * The selection term is the Monte Carlo integral over found injections that
+ * the same section mentions (its cost grows with the number of events):
+ *   xi(Lambda) = (1/N_draw) sum_{k found} p(theta_k | Lambda) / p_draw(theta_k).
+ *
+ * The population density p(theta|Lambda) (the section cites the mass, spin
+ * magnitude and spin orientation models without writing them out) is the
+ * product of
+ *   p(m1)      = (1-lam) PL(m1; -alpha, mmin, mmax) + lam N_T(m1; mpp, sigpp, [mmin, mmax])
+ *   p(q | m1)  = (1+beta) q^beta / (1 - (mmin/m1)^(1+beta))   on q in [mmin/m1, 1]
+ *   p(a)       = Beta(a; alpha_chi, beta_chi) for a1 and a2
+ *   p(c1, c2)  = (1-xi_t)/4 + xi_t G(c1) G(c2), G = normal(1, sigma_t) truncated to [-1, 1]
+ *   p(z)       = (1+z)^(kappa-1) z^2 / I(kappa) on [0, 2], I by a 1024-node trapezoid
+ * Support is closed except mmin < m1 (m1 = mmin would leave q a single point);
+ * the q test is fl64(q*m1) >= mmin.
+ *
+ * Every density is evaluated directly per sample with libm (pow, exp, log,
+ * erf, lgamma, expm1).  There is no blocking, fusion or reordering.
+ * It is built with -ffp-contract=off so that q*m1 rounds once, as stated.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Result flags (bit values are the library's public interface). */
+#define OR_FLAG_INVALID_LAMBDA 1u
+#define OR_FLAG_ZERO_EVENT 2u
+#define OR_FLAG_LOW_NEFF 4u
+#define OR_FLAG_ZERO_XI 32u
+
+/* Lambda indices, in the order of the C-ABI. */
+enum { P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_LAM, P_MPP, P_SIGPP, P_ACHI, P_BCHI, P_XIT, P_SIGT, P_KAPPA };
+
+static const double SQRT2 = 1.4142135623730950488;
+static const double SQRT2PI = 2.5066282746310005024;
+
+/* Validity of a Lambda point (outside it ln L = -inf, flagged). */
+int pop_oracle_lambda_valid(const double* L, int n_params)
+{
+    for (int p = 0; p < n_params; ++p)
+        if (!isfinite(L[p])) return 0;
+    if (!(L[P_MMIN] > 0.0) || !(L[P_MMIN] < L[P_MMAX])) return 0;
+    if (!(L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0)) return 0;
+    if (!(L[P_SIGPP] > 0.0) || !(L[P_SIGT] > 0.0)) return 0;
+    if (!(L[P_ACHI] > 0.0) || !(L[P_BCHI] > 0.0)) return 0;
+    if (!(L[P_XIT] >= 0.0 && L[P_XIT] <= 1.0)) return 0;
+    return 1;
+}
+
+/* Power law x^-alpha normalised on [a, b]; the alpha = 1 limit is 1/(x ln(b/a)). */
+static double powerlaw_pdf(double x, double alpha, double a, double b)
+{
+    if (alpha == 1.0) return 1.0 / (x * log(b / a));
+    return pow(x, -alpha) * (1.0 - alpha) / (pow(b, 1.0 - alpha) - pow(a, 1.0 - alpha));
+}
+
+/* Normal(mu, sigma) truncated to [a, b]; normalisation by erf. */
+static double truncnorm_pdf(double x, double mu, double sigma, double a, double b)
+{
+    double z = 0.5 * (erf((b - mu) / (SQRT2 * sigma)) - erf((a - mu) / (SQRT2 * sigma)));
+    double g = exp(-0.5 * (x - mu) * (x - mu) / (sigma * sigma)) / (SQRT2PI * sigma);
+    return g / z;
+}
+
+/* Primary mass density on mmin < m1 <= mmax. */
+double pop_oracle_p_m1(double m1, const double* L)
+{
+    double mmin = L[P_MMIN], mmax = L[P_MMAX], lam = L[P_LAM];
+    if (!(m1 > mmin && m1 <= mmax)) return 0.0;
+    double pl = powerlaw_pdf(m1, L[P_ALPHA], mmin, mmax);
+    double pp = lam > 0.0 ? truncnorm_pdf(m1, L[P_MPP], L[P_SIGPP], mmin, mmax) : 0.0;
+    return (1.0 - lam) * pl + lam * pp;
+}
+
+/* Mass-ratio density q^beta on [mmin/m1, 1].  The normalisation
+ * 1 - (mmin/m1)^(1+beta) is evaluated as -expm1((1+beta) ln(mmin/m1)), the same
+ * number without cancellation; beta = -1 is the 1/(q ln(m1/mmin)) limit. */
+double pop_oracle_p_q(double q, double m1, const double* L)
+{
+    double beta = L[P_BETA], mmin = L[P_MMIN];
+    if (!(q * m1 >= mmin && q <= 1.0)) return 0.0;
+    if (beta == -1.0) return 1.0 / (q * log(m1 / mmin));
+    double norm = -expm1((1.0 + beta) * log(mmin / m1));
+    return (1.0 + beta) * pow(q, beta) / norm;
+}
+
+/* Beta(alpha_chi, beta_chi) density of one spin magnitude (pow: 0^0 = 1). */
+double pop_oracle_p_chi(double a, const double* L)
+{
+    double ac = L[P_ACHI], bc = L[P_BCHI];
+    if (!(a >= 0.0 && a <= 1.0)) return 0.0;
+    double lnB = lgamma(ac) + lgamma(bc) - lgamma(ac + bc);
+    return pow(a, ac - 1.0) * pow(1.0 - a, bc - 1.0) / exp(lnB);
+}
+
+/* Aligned/isotropic tilt mixture of the two cosines. */
+double pop_oracle_p_tilt(double c1, double c2, const double* L)
+{
+    double xit = L[P_XIT], sig = L[P_SIGT];
+    if (!(c1 >= -1.0 && c1 <= 1.0 && c2 >= -1.0 && c2 <= 1.0)) return 0.0;
+    double g1 = truncnorm_pdf(c1, 1.0, sig, -1.0, 1.0);
+    double g2 = truncnorm_pdf(c2, 1.0, sig, -1.0, 1.0);
+    return (1.0 - xit) / 4.0 + xit * g1 * g2;
+}
+
+/* Trapezoid rule for (1+z)^(kappa-1) z^2 on 1024 equispaced nodes of [0, 2]. */
+double pop_oracle_z_norm(double kappa)
+{
+    const int n = 1024;
+    double h = 2.0 / (n - 1), s = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double z = 2.0 * k / (n - 1);
+        double f = pow(1.0 + z, kappa - 1.0) * z * z;
+        s += (k == 0 || k == n - 1) ? 0.5 * f : f;
+    }
+    return s * h;
+}
+
+double pop_oracle_p_z(double z, const double* L)
+{
+    if (!(z >= 0.0 && z <= 2.0)) return 0.0;
+    return pow(1.0 + z, L[P_KAPPA] - 1.0) * z * z / pop_oracle_z_norm(L[P_KAPPA]);
+}
+
+/* p(theta | Lambda) for one sample (n_dims 6: m1,q,a1,a2,c1,c2; 7 adds z). */
+double pop_oracle_p_theta(const double* th, int n_dims, const double* L)
+{
+    double p = pop_oracle_p_m1(th[0], L);
+    if (p == 0.0) return 0.0;
+    p *= pop_oracle_p_q(th[1], th[0], L);
+    p *= pop_oracle_p_chi(th[2], L) * pop_oracle_p_chi(th[3], L);
+    p *= pop_oracle_p_tilt(th[4], th[5], L);
+    if (n_dims == 7) p *= pop_oracle_p_z(th[6], L);
+    return p;
+}
+
+/* The same with a precomputed redshift normalisation (one trapezoid per Lambda). */
+static double p_theta_znorm(const double* th, int n_dims, const double* L, double znorm)
+{
+    double p = pop_oracle_p_m1(th[0], L);
+    if (p == 0.0) return 0.0;
+    p *= pop_oracle_p_q(th[1], th[0], L);
+    p *= pop_oracle_p_chi(th[2], L) * pop_oracle_p_chi(th[3], L);
+    p *= pop_oracle_p_tilt(th[4], th[5], L);
+    if (n_dims == 7) {
+        double z = th[6];
+        if (!(z >= 0.0 && z <= 2.0)) return 0.0;
+        p *= pow(1.0 + z, L[P_KAPPA] - 1.0) * z * z / znorm;
+    }
+    return p;
+}
+
+/*
+ * ln L for K Lambda points.
+ *   offsets[n_events+1] (CSR), theta[offsets[n] * n_dims], prior[offsets[n]]
+ *   inj_theta[n_found * n_dims], p_draw[n_found], n_draw >= n_found
+ *   lambda[K * n_params], n_params = 11 + (n_dims == 7)
+ * Outputs (any but out_lnL may be NULL): ln L, ln xi, N_eff, flags.
+ * Returns 0, or -1 on inconsistent sizes.
+ */
+int pop_oracle_loglik(int64_t n_events, const int64_t* offsets, int n_dims,
+                      const double* theta, const double* prior,
+                      int64_t n_found, int64_t n_draw, const double* inj_theta, const double* p_draw,
+                      int64_t K, int n_params, const double* lambda, int nthreads,
+                      double* out_lnL, double* out_lnxi, double* out_neff, uint32_t* out_flags)
+{
+    if (n_events < 1 || (n_dims != 6 && n_dims != 7) || n_params != 11 + (n_dims == 7) ||
+        n_draw < n_found || n_draw < 1 || K < 0 || !out_lnL)
+        return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t k = 0; k < K; ++k) {
+        const double* L = lambda + k * n_params;
+        uint32_t flags = 0;
+        double lnL, lnxi = 0.0, neff = 0.0;
+        if (!pop_oracle_lambda_valid(L, n_params)) {
+            flags |= OR_FLAG_INVALID_LAMBDA;
+            lnL = -INFINITY;
+        } else {
+            double znorm = n_dims == 7 ? pop_oracle_z_norm(L[P_KAPPA]) : 1.0;
+            /* Selection term and its effective sample count. */
+            double sw = 0.0, sw2 = 0.0;
+            for (int64_t j = 0; j < n_found; ++j) {
+                double w = p_theta_znorm(inj_theta + j * n_dims, n_dims, L, znorm) / p_draw[j];
+                sw += w;
+                sw2 += w * w;
+            }
+            double xi = sw / (double)n_draw;
+            double var = sw2 / ((double)n_draw * (double)n_draw) - xi * xi / (double)n_draw;
+            neff = var > 0.0 ? xi * xi / var : INFINITY;
+            /* Recycled per-event Monte Carlo integrals. */
+            double sum_ln = 0.0;
+            for (int64_t i = 0; i < n_events; ++i) {
+                double s = 0.0;
+                int64_t n_i = offsets[i + 1] - offsets[i];
+                for (int64_t j = offsets[i]; j < offsets[i + 1]; ++j)
+                    s += p_theta_znorm(theta + j * n_dims, n_dims, L, znorm) / prior[j];
+                if (s == 0.0) flags |= OR_FLAG_ZERO_EVENT;
+                sum_ln += log(s / (double)n_i);
+            }
+            if (xi == 0.0) {
+                flags |= OR_FLAG_ZERO_XI;
+                lnL = -INFINITY;
+                lnxi = -INFINITY;
+                neff = 0.0;
+            } else {
+                lnxi = log(xi);
+                lnL = (flags & OR_FLAG_ZERO_EVENT) ? -INFINITY : sum_ln - (double)n_events * lnxi;
+            }
+            if (neff < 4.0 * (double)n_events) flags |= OR_FLAG_LOW_NEFF;
+        }
+        out_lnL[k] = lnL;
+        if (out_lnxi) out_lnxi[k] = lnxi;
+        if (out_neff) out_neff[k] = neff;
+        if (out_flags) out_flags[k] = flags;
+    }
+    return 0;
+}
+
+/* Threads the OpenMP runtime would use (1 without OpenMP). */
+int pop_oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
