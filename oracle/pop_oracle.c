@@ -95,14 +95,17 @@ double pop_oracle_p_m1(double m1, const double* L)
 }
 
 /* Mass-ratio density q^beta on [mmin/m1, 1].  The normalisation
- * 1 - (mmin/m1)^(1+beta) is evaluated as -expm1((1+beta) ln(mmin/m1)), the same
- * number without cancellation; beta = -1 is the 1/(q ln(m1/mmin)) limit. */
+ * 1 - (mmin/m1)^(1+beta) is evaluated as -expm1((1+beta) ln(mmin/m1)) with
+ * ln(mmin/m1) = log1p((mmin - m1)/m1): the same numbers without cancellation
+ * (mmin - m1 is exact when m1 is near mmin, where the density is largest);
+ * beta = -1 is the 1/(q ln(m1/mmin)) limit. */
 double pop_oracle_p_q(double q, double m1, const double* L)
 {
     double beta = L[P_BETA], mmin = L[P_MMIN];
     if (!(q * m1 >= mmin && q <= 1.0)) return 0.0;
-    if (beta == -1.0) return 1.0 / (q * log(m1 / mmin));
-    double norm = -expm1((1.0 + beta) * log(mmin / m1));
+    double ln_ratio = log1p((mmin - m1) / m1);
+    if (beta == -1.0) return 1.0 / (q * -ln_ratio);
+    double norm = -expm1((1.0 + beta) * ln_ratio);
     return (1.0 + beta) * pow(q, beta) / norm;
 }
 

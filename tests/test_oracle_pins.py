@@ -97,15 +97,19 @@ def test_mass_ratio_integrates_to_one(oracle, beta, m1):
     assert oracle.p_q(q, m1, L) / oracle.p_q(1.0, m1, L) == pytest.approx(q ** beta, rel=1e-13)
 
 
-def test_mass_ratio_near_degenerate_support(oracle):
-    # m1 a hair above mmin: the support shrinks to [mmin/m1, 1]; the density must
-    # still integrate to one (catches 1 - x^(1+beta) cancellation).
-    L = _lam(beta=1.3)
-    m1 = L[2] * (1.0 + 1e-9)
-    lo = L[2] / m1
-    width = 1.0 - lo
-    val = oracle.p_q(1.0, m1, L) * width
-    assert val == pytest.approx(1.0, rel=1e-6)
+@pytest.mark.parametrize("beta", [-1.0, 0.0, 1.3, 2.0])
+@pytest.mark.parametrize("eps", [1e-13, 1e-9, 1e-6, 1e-3, 0.1])
+def test_mass_ratio_near_degenerate_support(oracle, beta, eps):
+    """m1 a hair above mmin: the q support shrinks to [mmin/m1, 1] and the density
+    at q = 1 grows like 1/(1 - mmin/m1).  Pinned against the closed form in
+    50-digit arithmetic (catches 1 - x^(1+beta) and ln(mmin/m1) cancellation)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    L = _lam(beta=beta)
+    m1 = float(np.nextafter(L[2] * (1.0 + eps), np.inf))
+    r = mp.mpf(L[2]) / mp.mpf(m1)
+    exact = 1 / (-mp.log(r)) if beta == -1.0 else (1 + mp.mpf(beta)) / (1 - r ** (1 + mp.mpf(beta)))
+    assert oracle.p_q(1.0, m1, L) == pytest.approx(float(exact), rel=1e-14)
 
 
 @pytest.mark.parametrize("ac,bc", [(2.0, 5.0), (1.0, 1.0), (1.0, 3.0), (3.7, 2.2), (0.6, 1.4)])
