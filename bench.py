@@ -1,0 +1,301 @@
+"""Throughput of the population likelihood on GB300.
+
+Workload: 1000 events x 4096 posterior samples each (dense), 10^7 injection
+draws (about 1.1e6 found), batches of K = 1024 Lambda points, the mass + spin
+model; synthetic, seeded data shaped like a catalog (no real posteriors
+offline).  One step = one pop_loglik over the K-batch: per-Lambda prologue,
+sample weights for every (sample, Lambda) and (injection, Lambda) pair,
+per-event segmented sums, selection term, finalise.  The headline form is
+plain FP64; the FP32 form is timed in the same run and reported under
+"forms".  The feature arrays (375 MB FP64, 208 MB FP32) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank evaluates its own K-batch (replicas, weak scaling);
+rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1904_02863_gb300 import synth  # noqa: E402
+
+METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
+WORKLOAD = "c2_f64_catalog"
+
+# Algorithmic FP64-pipe operations per (sample, Lambda) pair of the weight
+# kernel: 15 add/mul/fma + 3 exp (9 each) + 1 expm1 (10) + 1 reciprocal (4);
+# +1 fma for the squared weight on injection pairs.
+FP64_OPS_PER_PAIR = 56
+FP64_OPS_PER_INJ_PAIR = 57
+# GB300: 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2070 MHz
+# over 152 SMs); peak op rate = 2 * SMs * clock.
+FP64_LANES_PER_SM = 2
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--oracle-lambdas", type=int, default=32, help="Lambda rows in the CPU sample")
+    return p.parse_args()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(cat, inj, lam, n_rows):
+    import oracle
+    cores = host_cores()
+    sub = lam[:n_rows]
+    t0 = time.perf_counter()
+    oracle.loglik(cat, inj, sub, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_rows / dt, "unit": "evals/s", "cores": min(cores, n_rows), "kind": "oracle",
+            "sample": f"{n_rows} Lambda rows of the same workload (full 1000x4096 catalog and "
+                      f"{inj.n_found} found injections per row), FP64, OpenMP over Lambda",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: rank 0 only."""
+    if rank != 0:
+        return
+    cat, inj, lam = synth.make_workload(WORKLOAD)
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    rows = max(1, min(args.oracle_lambdas, 64))
+    for _ in range(min(args.warmup, 1)):
+        oracle.loglik(cat, inj, lam[:min(rows, cores)], nthreads=cores)
+    times = []
+    for s in range(args.steps):
+        sub = lam[(s * rows) % 1024:][:rows]
+        t0 = time.perf_counter()
+        oracle.loglik(cat, inj, sub, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = rows * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "events": 1000, "samples_per_event": 4096,
+                                            "n_draw": 10**7, "n_found": inj.n_found, "K": 1024,
+                                            "step_sample_rows": rows},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": min(cores, rows), "kind": "oracle",
+                             "sample": f"{rows} Lambda rows per step of the full workload"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line, default=_jsonable), flush=True)
+
+
+def _jsonable(o):
+    if isinstance(o, np.integer):
+        return int(o)
+    if isinstance(o, np.floating):
+        return float(o)
+    raise TypeError(type(o).__name__)
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1904_02863_gb300 import binding as B
+    from paper_1904_02863_gb300 import build
+    build.build()
+
+    cat, inj, _ = synth.make_workload(WORKLOAD)
+    K = 1024
+    lam = synth.make_lambdas(K, 11, seed=synth.seed_for(2, 2) + 7919 * rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    like = B.Likelihood(local, stream).load(cat, inj)
+    dev_lam = torch.from_numpy(lam).cuda()
+    outs = [torch.empty(K, dtype=torch.float64, device="cuda") for _ in range(3)] + \
+           [torch.empty(K, dtype=torch.int32, device="cuda")]
+
+    def timed(mode):
+        for _ in range(args.warmup):
+            B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wms = []
+        start.record(stream)
+        for _ in range(args.steps):
+            B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+            wms.append(B.pop_last_kernel_ms(like.ctx)[0])
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(start.elapsed_time(stop), world)
+        return ms, statistics.mean(wms)
+
+    with Clocks(local) as clk:
+        ms64, w64 = timed(B.POP_MODE_F64)
+        ms32, w32 = timed(B.POP_MODE_F32)
+
+    # End to end through the public API with pinned host buffers.
+    h_lam = torch.from_numpy(lam).pin_memory()
+    h_out = [torch.empty(K, dtype=torch.float64).pin_memory() for _ in range(3)] + \
+            [torch.empty(K, dtype=torch.int32).pin_memory()]
+    B.pop_loglik(like.ctx, h_lam, B.POP_MODE_F64, out=h_out)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        B.pop_loglik(like.ctx, h_lam, B.POP_MODE_F64, out=h_out)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+
+    n_ev_pairs = cat.offsets[-1] * K
+    n_inj_pairs = inj.n_found * K
+    ops = n_ev_pairs * FP64_OPS_PER_PAIR + n_inj_pairs * FP64_OPS_PER_INJ_PAIR
+    clocks = clk.summary()
+    peak_tops = FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12  # FP64 pipe ops/s (FMA = 1 op)
+    achieved_tops = ops / (w64 * 1e-3) / 1e12
+    value = world * K * args.steps / (ms64 * 1e-3)
+    value32 = world * K * args.steps / (ms32 * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events": 1000, "samples_per_event": 4096, "n_draw": 10**7,
+                   "n_found": inj.n_found, "K": K, "mode": "POP_MODE_F64", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (375 MB FP64 features)",
+                   "tiling_f64": B.pop_get_tiling(like.ctx, B.POP_MODE_F64),
+                   "tiling_f32": B.pop_get_tiling(like.ctx, B.POP_MODE_F32)},
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (FP64 pipe)",
+                     "frac": achieved_tops / peak_tops, "traffic": None,
+                     "kernel": "weight_f64_kernel", "weight_ms": w64,
+                     "ops_per_launch": ops, "peak_basis": "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz"},
+        "e2e": {"value": world * K * args.steps / e2e_s, "unit": "evals/s",
+                "h2d_bytes_per_step": int(lam.nbytes), "d2h_bytes_per_step": int(K * (8 * 3 + 4))},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "forms": {"f32": {"value": value32, "unit": "evals/s", "ms_per_step": ms32 / args.steps,
+                          "weight_ms": w32, "dtype": "f32"}},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
+    like.close()
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * pop.h — C-ABI of libpop.so, the GB300 (sm_103a) population-likelihood library.
+ *
+ * Method (paper "Parallelized Inference for Gravitational-Wave Astronomy",
+ * Sec. "Population acceleration"): for a batch of population hyper-parameters
+ * Lambda the library returns
+ *
+ *     ln L(Lambda) = sum_i ln[ (1/n_i) sum_j p(theta_ij | Lambda) / pi(theta_ij) ] - N ln xi(Lambda)
+ *
+ * The inner sum is the "recycling" Monte Carlo integral of Eq. (poplike) over
+ * the n_i posterior samples theta_ij of event i, each divided by the prior pi
+ * of the single-event analysis.  The -N ln xi term is the rate factor
+ * R^N exp(-R VT(Lambda)) of the first equation of that section with R
+ * marginalised under a 1/R prior (VT proportional to xi).  xi(Lambda) is the
+ * Monte Carlo selection integral over found injections that the same section
+ * describes:  xi = (1/N_draw) sum_{k found} p(theta_k | Lambda) / p_draw(theta_k).
+ *
+ * The population density p(theta | Lambda) is the product of
+ *   primary mass   (1-lam) PL(m1; -alpha, [mmin, mmax]) + lam N(m1; mpp, sigpp) truncated to [mmin, mmax]
+ *   mass ratio     (1+beta) q^beta / (1 - (mmin/m1)^(1+beta)) on [mmin/m1, 1]   (beta = -1: 1/(q ln(m1/mmin)))
+ *   spin sizes     Beta(a1; alpha_chi, beta_chi) Beta(a2; alpha_chi, beta_chi)
+ *   spin tilts     (1-xi_t)/4 + xi_t G(cos t1) G(cos t2), G = N(1, sigma_t) truncated to [-1, 1]
+ *   redshift       (1+z)^(kappa-1) z^2 / I(kappa) on [0, 2], I = 1024-node trapezoid   (optional)
+ * with support mmin < m1 <= mmax, fl64(q*m1) >= mmin, q <= 1, a in [0,1],
+ * cos in [-1,1], z in [0,2]; the weight is 0 outside it.
+ *
+ * Conventions for every entry point:
+ *   - returns a pop_status (0 = POP_OK); errors never abort the process and a
+ *     failing call leaves the context as it was (pop_last_error has the text);
+ *   - sample coordinates theta are row-major [n, n_dims], n_dims = 6
+ *     (m1, q, a1, a2, cos t1, cos t2) or 7 (+ z);
+ *   - Lambda rows are row-major [K, n_params], n_params = 11
+ *     (alpha, beta, mmin, mmax, lam, mpp, sigpp, alpha_chi, beta_chi, xi_t, sigma_t)
+ *     or 12 (+ kappa), and n_params must equal 11 + (n_dims == 7);
+ *   - `mem` says where caller pointers live (POP_MEM_HOST or POP_MEM_DEVICE);
+ *     all data is copied, the caller keeps ownership of its buffers;
+ *   - one context drives one GPU on one stream; calls on a context are not
+ *     thread-safe.  There is no CPU fallback: without a usable GPU,
+ *     pop_create fails with POP_ECUDA.
+ */
+#ifndef POP_H
+#define POP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pop_ctx pop_ctx;
+
+typedef enum {
+    POP_OK = 0,
+    POP_EINVAL = -1,    /* bad argument or malformed input */
+    POP_ENOMEM = -2,    /* device or pinned-host allocation failed */
+    POP_ECUDA = -3,     /* CUDA runtime error (text in pop_last_error) */
+    POP_ESTATE = -4,    /* events/injections not loaded, or surrogate not trained */
+    POP_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    POP_ENUMERIC = -6   /* surrogate gate failed; Monte Carlo xi was used */
+} pop_status;
+
+/* Storage of the packed per-sample features (bit mask, both may be kept). */
+enum { POP_STORE_F64 = 1, POP_STORE_F32 = 2 };
+
+/* Arithmetic of pop_loglik.
+ *   POP_MODE_F64: FP64 everywhere (needs POP_STORE_F64 features).
+ *   POP_MODE_F32: FP32 sample weights with compensated per-thread sums; FP64
+ *                 per-Lambda constants, partial combines, per-event log,
+ *                 cross-event sum and xi (needs POP_STORE_F32 features).
+ *   POP_MODE_F32_SURROGATE: as POP_MODE_F32, with ln xi from the trained MLP
+ *                 and Monte Carlo xi only for the Lambda the gate rejects. */
+enum { POP_MODE_F64 = 0, POP_MODE_F32 = 1, POP_MODE_F32_SURROGATE = 2 };
+
+enum { POP_MEM_HOST = 0, POP_MEM_DEVICE = 1 };
+
+/* Per-Lambda result flags (out_flags).  ln L = -inf is a legitimate value,
+ * not an error; NaN is never returned. */
+enum {
+    POP_FLAG_INVALID_LAMBDA = 1u,  /* Lambda outside the model's domain: ln L = -inf */
+    POP_FLAG_ZERO_EVENT = 2u,      /* some event has sum_j w_ij = 0: ln L = -inf */
+    POP_FLAG_LOW_NEFF = 4u,        /* injection effective sample count < 4 N */
+    POP_FLAG_SURROGATE_USED = 8u,  /* ln xi came from the surrogate */
+    POP_FLAG_MC_FALLBACK = 16u,    /* surrogate rejected, Monte Carlo xi used */
+    POP_FLAG_ZERO_XI = 32u         /* xi = 0 (no found injection has weight): ln L = -inf */
+};
+
+/* Create a context on CUDA device `device` that issues all work on `stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * legacy default stream).  *out receives the context; destroy it with
+ * pop_destroy.  Fails with POP_ECUDA when no usable GPU is present. */
+int pop_create(pop_ctx** out, int device, void* stream);
+
+/* Free every device and host buffer of the context.  NULL is accepted. */
+int pop_destroy(pop_ctx* ctx);
+
+/* Text of the last error on `ctx` (or of the last pop_create failure when ctx
+ * is NULL).  Valid until the next call on the same context. */
+const char* pop_last_error(const pop_ctx* ctx);
+
+/* Static name of a pop_status value. */
+const char* pop_status_string(int status);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int pop_version(void);
+
+/* Host-only validation of a CSR event layout, without a context or a GPU:
+ * n_events >= 1, offsets[0] = 0, offsets non-decreasing with every n_i >= 1,
+ * n_dims in {6, 7}.  Writes a message into msg[msg_len] (may be NULL). */
+int pop_validate_events(int64_t n_events, const int64_t* offsets, int n_dims, char* msg, int msg_len);
+
+/* Load the per-event posterior samples (paper: the N x n_i sample arrays are
+ * moved to the GPU once; Sec. "Population acceleration").
+ *   offsets[n_events+1]  int64, host memory always, CSR row starts (dense
+ *                        [N, S] data is offsets[i] = i*S)
+ *   theta[offsets[N] * n_dims], prior[offsets[N]] (pi > 0, finite) in `mem`
+ *   storage              POP_STORE_F64 and/or POP_STORE_F32
+ * A one-time pack kernel turns the samples into per-sample features
+ * (log-masses, summed spin logs, tilt distance, -ln pi) in FP64 and stores
+ * them in the requested precision(s).  Replaces previously loaded events.
+ * POP_EINVAL on malformed offsets, non-finite theta or pi <= 0. */
+int pop_load_events(pop_ctx* ctx, int64_t n_events, const int64_t* offsets, int n_dims,
+                    const double* theta, const double* prior, int storage, int mem);
+
+/* Load the found injections of the selection term (same section: Monte Carlo
+ * integral over found injections).
+ *   theta[n_found * n_dims], p_draw[n_found] (> 0, finite) in `mem`
+ *   n_draw = number of draws, found and missed (n_draw >= n_found >= 1).
+ * n_dims must equal that of the loaded events (load events first). */
+int pop_load_injections(pop_ctx* ctx, int64_t n_found, int64_t n_draw, int n_dims,
+                        const double* theta, const double* p_draw, int storage, int mem);
+
+/* Evaluate ln L for K Lambda points.
+ *   lambda[K * n_params] in `mem`; out_lnL[K] required; out_lnxi[K] (ln xi),
+ *   out_neff[K] (injection effective sample count xi^2 / Var[xi]) and
+ *   out_flags[K] may be NULL; all outputs in `mem`.
+ * With POP_MEM_DEVICE the call is asynchronous on the context stream; with
+ * POP_MEM_HOST it returns after the results are in the host buffers.
+ * K may be 0.  Scratch grows to the largest K seen and is reused. */
+int pop_loglik(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int mode,
+               double* out_lnL, double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem);
+
+/* Tiling of the persistent weight kernel for `mode` (POP_MODE_F64 or
+ * POP_MODE_F32): Lambda points per work item (1, 2, 4, 8, 16 or 32), threads
+ * per block (128, 256 or 512) and resident blocks per SM (0 = occupancy
+ * maximum).  Takes effect at the next pop_loglik. */
+int pop_set_tiling(pop_ctx* ctx, int mode, int lambda_tile, int block_threads, int blocks_per_sm);
+
+/* Read back the tiling in use for `mode` (any pointer may be NULL). */
+int pop_get_tiling(pop_ctx* ctx, int mode, int* lambda_tile, int* block_threads, int* blocks_per_sm);
+
+/* Autotune the tiling of `mode` on the loaded data for batches of K Lambda
+ * (times every candidate with CUDA events on the context stream and keeps the
+ * fastest).  When cache_path is non-NULL the choice is read from / appended to
+ * that text file, keyed by device name, mode, and data shape. */
+int pop_autotune(pop_ctx* ctx, int mode, int64_t K, const char* cache_path);
+
+/* Use CUDA-graph replay for pop_loglik (1, default) or direct launches (0). */
+int pop_set_graphs(pop_ctx* ctx, int enable);
+
+/* Duration in milliseconds of the weight kernel of the last pop_loglik
+ * (CUDA events around it on the context stream; waits for that call). */
+int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POP_H */

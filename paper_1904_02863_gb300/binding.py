@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libpop.so (include/pop.h), same names as the C-ABI.
+
+Argument marshalling only: every step of the likelihood runs in the library's
+CUDA kernels.  Host inputs are numpy arrays (passed with POP_MEM_HOST); device
+inputs are torch CUDA tensors (passed by pointer with POP_MEM_DEVICE).  torch
+supplies device memory and the stream, nothing else.  There is no fallback:
+if libpop.so is missing or no GPU is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpop.so")
+
+POP_OK, POP_EINVAL, POP_ENOMEM, POP_ECUDA, POP_ESTATE, POP_ETIMEOUT, POP_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
+POP_STORE_F64, POP_STORE_F32 = 1, 2
+POP_MODE_F64, POP_MODE_F32, POP_MODE_F32_SURROGATE = 0, 1, 2
+POP_MEM_HOST, POP_MEM_DEVICE = 0, 1
+POP_FLAG_INVALID_LAMBDA, POP_FLAG_ZERO_EVENT, POP_FLAG_LOW_NEFF = 1, 2, 4
+POP_FLAG_SURROGATE_USED, POP_FLAG_MC_FALLBACK, POP_FLAG_ZERO_XI = 8, 16, 32
+
+# Every symbol include/pop.h declares (checked by the CPU test suite).
+EXPORTS = (
+    "pop_create", "pop_destroy", "pop_last_error", "pop_status_string", "pop_version",
+    "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
+    "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
+)
+
+
+class PopError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpop.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run __graft_entry__.build() (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "pop_create": (i32, [ctypes.POINTER(vp), i32, vp]),
+        "pop_destroy": (i32, [vp]),
+        "pop_last_error": (ctypes.c_char_p, [vp]),
+        "pop_status_string": (ctypes.c_char_p, [i32]),
+        "pop_version": (i32, []),
+        "pop_validate_events": (i32, [i64, vp, i32, ctypes.c_char_p, i32]),
+        "pop_load_events": (i32, [vp, i64, vp, i32, vp, vp, i32, i32]),
+        "pop_load_injections": (i32, [vp, i64, i64, i32, vp, vp, i32, i32]),
+        "pop_loglik": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp, i32]),
+        "pop_set_tiling": (i32, [vp, i32, i32, i32, i32]),
+        "pop_get_tiling": (i32, [vp, i32, vp, vp, vp]),
+        "pop_autotune": (i32, [vp, i32, i64, ctypes.c_char_p]),
+        "pop_set_graphs": (i32, [vp, i32]),
+        "pop_last_kernel_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().pop_status_string(status).decode()
+    except Exception:
+        return str(status)
+
+
+def _check(ctx, rc):
+    if rc != POP_OK:
+        msg = load_library().pop_last_error(ctx)
+        raise PopError(rc, msg.decode() if msg else "")
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _arg(x, dtype):
+    """(pointer, mem, keepalive) of a numpy array or a torch CUDA tensor."""
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.uint32: torch.int32, np.int64: torch.int64}[dtype]
+        if not x.is_contiguous() or x.dtype != want:
+            raise TypeError(f"tensor arguments must be contiguous tensors of {want}")
+        return ctypes.c_void_p(x.data_ptr()), POP_MEM_DEVICE if x.is_cuda else POP_MEM_HOST, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST, a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+def pop_version() -> int:
+    return load_library().pop_version()
+
+
+def pop_validate_events(n_events, offsets, n_dims):
+    """Host-only CSR check; returns (status, message)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    buf = ctypes.create_string_buffer(256)
+    rc = load_library().pop_validate_events(int(n_events), off.ctypes.data_as(ctypes.c_void_p), int(n_dims), buf, 256)
+    return rc, buf.value.decode()
+
+
+def pop_create(device: int = 0, stream=None):
+    ctx = ctypes.c_void_p()
+    rc = load_library().pop_create(ctypes.byref(ctx), int(device), _stream_ptr(stream))
+    _check(None, rc)
+    return ctx
+
+
+def pop_destroy(ctx):
+    _check(ctx, load_library().pop_destroy(ctx))
+
+
+def pop_last_error(ctx) -> str:
+    return load_library().pop_last_error(ctx).decode()
+
+
+def pop_load_events(ctx, offsets, theta, prior, storage=POP_STORE_F64 | POP_STORE_F32):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    tp, mem, k1 = _arg(theta, np.float64)
+    pp, mem2, k2 = _arg(prior, np.float64)
+    if mem != mem2:
+        raise TypeError("theta and prior must both be host arrays or both device tensors")
+    n_dims = int(theta.shape[1])
+    _check(ctx, load_library().pop_load_events(ctx, len(off) - 1, off.ctypes.data_as(ctypes.c_void_p), n_dims,
+                                               tp, pp, int(storage), mem))
+
+
+def pop_load_injections(ctx, n_draw, theta, p_draw, storage=POP_STORE_F64 | POP_STORE_F32):
+    tp, mem, k1 = _arg(theta, np.float64)
+    pp, mem2, k2 = _arg(p_draw, np.float64)
+    if mem != mem2:
+        raise TypeError("theta and p_draw must both be host arrays or both device tensors")
+    _check(ctx, load_library().pop_load_injections(ctx, int(theta.shape[0]), int(n_draw), int(theta.shape[1]),
+                                                   tp, pp, int(storage), mem))
+
+
+def pop_loglik(ctx, lambdas, mode=POP_MODE_F64, out=None):
+    """ln L, ln xi, N_eff, flags for each row of ``lambdas``.
+
+    numpy input -> numpy outputs (synchronous).  torch CUDA input -> torch CUDA
+    outputs (asynchronous on the context stream); ``out`` may supply them.
+    """
+    lp, mem, keep = _arg(lambdas, np.float64)
+    K, P = int(lambdas.shape[0]), int(lambdas.shape[1])
+    if out is not None:
+        ptrs = [_arg(r, dt)[0] for r, dt in zip(out, (np.float64, np.float64, np.float64, np.uint32))]
+        _check(ctx, load_library().pop_loglik(ctx, K, P, lp, int(mode), *ptrs, mem))
+        return out
+    if mem == POP_MEM_HOST:
+        res = (np.empty(K), np.empty(K), np.empty(K), np.empty(K, np.uint32))
+        ptrs = [r.ctypes.data_as(ctypes.c_void_p) for r in res]
+    else:
+        import torch
+        dev = lambdas.device
+        res = (torch.empty(K, dtype=torch.float64, device=dev), torch.empty(K, dtype=torch.float64, device=dev),
+                      torch.empty(K, dtype=torch.float64, device=dev), torch.empty(K, dtype=torch.int32, device=dev))
+        ptrs = [ctypes.c_void_p(r.data_ptr()) for r in res]
+    _check(ctx, load_library().pop_loglik(ctx, K, P, lp, int(mode), *ptrs, mem))
+    return res
+
+
+def pop_set_tiling(ctx, mode, lambda_tile, block_threads, blocks_per_sm=0):
+    _check(ctx, load_library().pop_set_tiling(ctx, int(mode), int(lambda_tile), int(block_threads), int(blocks_per_sm)))
+
+
+def pop_get_tiling(ctx, mode):
+    t, b, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load_library().pop_get_tiling(ctx, int(mode), ctypes.byref(t), ctypes.byref(b), ctypes.byref(s)))
+    return t.value, b.value, s.value
+
+
+def pop_autotune(ctx, mode, K, cache_path=None):
+    cp = cache_path.encode() if cache_path else None
+    _check(ctx, load_library().pop_autotune(ctx, int(mode), int(K), cp))
+    return pop_get_tiling(ctx, mode)
+
+
+def pop_set_graphs(ctx, enable: bool):
+    _check(ctx, load_library().pop_set_graphs(ctx, 1 if enable else 0))
+
+
+def pop_last_kernel_ms(ctx):
+    w, t = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, load_library().pop_last_kernel_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, t.value
+
+
+# ------------------------------------------------------------------ convenience
+class Likelihood:
+    """One context: load a catalog and injections once, evaluate many Lambda batches."""
+
+    def __init__(self, device=0, stream=None):
+        if stream is None:
+            import torch
+            torch.cuda.set_device(device)
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.ctx = pop_create(device, stream)
+
+    def load(self, catalog, injections, storage=POP_STORE_F64 | POP_STORE_F32):
+        pop_load_events(self.ctx, catalog.offsets, catalog.theta, catalog.prior, storage)
+        pop_load_injections(self.ctx, injections.n_draw, injections.theta, injections.p_draw, storage)
+        return self
+
+    def __call__(self, lambdas, mode=POP_MODE_F64):
+        return pop_loglik(self.ctx, lambdas, mode)
+
+    def close(self):
+        if self.ctx:
+            pop_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,679 @@
+// Host runtime behind the C-ABI of include/pop.h: the context, device buffers,
+// input validation, the one-time pack, CUDA-graph replay of
+// prologue -> weight -> finalise, and the tiling autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "pop.h"
+#include "pop_internal.h"
+
+using namespace pop;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int CHUNK_LEN = 4096;  // samples per work chunk (events are split at this length)
+constexpr int64_t ALIGN_ELEMS = 64;
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// RAII device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { reset(); }
+    void reset()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n)
+    {
+        reset();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    void swap(DevBuf& o)
+    {
+        std::swap(p, o.p);
+        std::swap(bytes, o.bytes);
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// One packed sample set (events or injections) in either or both precisions.
+struct SampleSet {
+    int64_t n = 0;
+    int64_t stride = 0;
+    int n_dims = 0;
+    int storage = 0;
+    DevBuf f64, f32, m2;
+    void swap(SampleSet& o)
+    {
+        std::swap(n, o.n);
+        std::swap(stride, o.stride);
+        std::swap(n_dims, o.n_dims);
+        std::swap(storage, o.storage);
+        f64.swap(o.f64);
+        f32.swap(o.f32);
+        m2.swap(o.m2);
+    }
+};
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t k_cap = -1;
+    uint64_t version = 0;
+    Tiling tiling{};
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        k_cap = -1;
+    }
+};
+
+}  // namespace
+
+struct pop_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;  // created here when the caller passed the legacy default stream
+    std::string err;
+    int sm_count = 0;
+    std::string device_name;
+
+    SampleSet ev, inj;
+    std::vector<int64_t> h_offsets;
+    DevBuf d_offsets;        // int64 [N+1]
+    int64_t n_draw = 0;
+
+    // Work chunks: event chunks first, then injection chunks.
+    DevBuf d_chunks, d_ecb;  // Chunk [n_chunks], int32 [N+1]
+    int32_t n_chunks = 0, n_ev_chunks = 0;
+    bool chunks_dirty = true;
+    uint64_t version = 1;    // bumped whenever buffers the graphs point at change
+
+    // Per-call scratch, sized for K_cap Lambda points.
+    int64_t k_cap = 0;
+    int n_params_cap = 12;
+    DevBuf d_lambda, d_c64, d_c32, d_part, d_part2, d_lnL, d_lnxi, d_neff, d_flags, d_K;
+    int32_t part_chunks = -1, part_inj = -1;
+
+    Tiling tiling[2] = {{8, 256, 0}, {16, 256, 0}};
+    bool use_graphs = true;
+    Graph graph[2];
+    cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
+    bool timed = false;
+    int64_t last_K = 0;
+    int last_params = 0;
+};
+
+namespace {
+
+int fail(pop_ctx* c, int status, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return status;
+}
+
+int cuda_fail(pop_ctx* c, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? POP_ENOMEM : POP_ECUDA, m);
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+bool valid_mem(int mem) { return mem == POP_MEM_HOST || mem == POP_MEM_DEVICE; }
+
+cudaMemcpyKind in_kind(int mem) { return mem == POP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind out_kind(int mem) { return mem == POP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+__global__ void set_k_kernel(int64_t* dK, int64_t K) { *dK = K; }
+
+// Pack theta/prior (host or device) into a new SampleSet.
+int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const double* prior, int storage,
+                 int mem, SampleSet& out, const char* what)
+{
+    out.n = n;
+    out.n_dims = n_dims;
+    out.storage = storage;
+    out.stride = round_up(std::max<int64_t>(n, 1), ALIGN_ELEMS);
+    const double* th = theta;
+    const double* pr = prior;
+    DevBuf tmp_th, tmp_pr, bad;
+    if (mem == POP_MEM_HOST) {
+        CK(tmp_th.alloc(sizeof(double) * n * n_dims), "cudaMalloc(theta staging)");
+        CK(tmp_pr.alloc(sizeof(double) * n), "cudaMalloc(prior staging)");
+        CK(cudaMemcpyAsync(tmp_th.p, theta, sizeof(double) * n * n_dims, cudaMemcpyHostToDevice, c->stream),
+           "copy theta");
+        CK(cudaMemcpyAsync(tmp_pr.p, prior, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "copy prior");
+        th = tmp_th.as<double>();
+        pr = tmp_pr.as<double>();
+    }
+    CK(bad.alloc(sizeof(unsigned long long)), "cudaMalloc(flag)");
+    CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned long long), c->stream), "memset");
+    if (storage & POP_STORE_F64) {
+        CK(out.f64.alloc(sizeof(double) * F_COUNT64 * out.stride), "cudaMalloc(f64 features)");
+        CK(launch_pack_f64(th, pr, n, n_dims, out.f64.as<double>(), out.stride, bad.as<unsigned long long>(),
+                           c->stream), "pack_f64");
+    }
+    if (storage & POP_STORE_F32) {
+        CK(out.f32.alloc(sizeof(float) * F_COUNT32 * out.stride), "cudaMalloc(f32 features)");
+        CK(out.m2.alloc(sizeof(double) * out.stride), "cudaMalloc(m2)");
+        CK(launch_pack_f32(th, pr, n, n_dims, out.f32.as<float>(), out.m2.as<double>(), out.stride,
+                           bad.as<unsigned long long>(), c->stream), "pack_f32");
+    }
+    unsigned long long h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad.p, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream), "copy flag");
+    CK(cudaStreamSynchronize(c->stream), "pack sync");
+    if (h_bad) {
+        char m[160];
+        snprintf(m, sizeof m, "%s: %llu samples with non-finite coordinates or a prior/p_draw <= 0", what, h_bad);
+        return fail(c, POP_EINVAL, m);
+    }
+    return POP_OK;
+}
+
+// (Re)build the chunk table from the loaded events and injections.
+int build_chunks(pop_ctx* c)
+{
+    if (!c->chunks_dirty) return POP_OK;
+    std::vector<Chunk> ch;
+    std::vector<int32_t> ecb(c->h_offsets.size());
+    const int64_t N = (int64_t)c->h_offsets.size() - 1;
+    for (int64_t i = 0; i < N; ++i) {
+        ecb[i] = (int32_t)ch.size();
+        for (int64_t s = c->h_offsets[i]; s < c->h_offsets[i + 1]; s += CHUNK_LEN)
+            ch.push_back(Chunk{s, (int32_t)std::min<int64_t>(CHUNK_LEN, c->h_offsets[i + 1] - s), 0});
+    }
+    ecb[N] = (int32_t)ch.size();
+    const int32_t n_ev = (int32_t)ch.size();
+    for (int64_t s = 0; s < c->inj.n; s += CHUNK_LEN)
+        ch.push_back(Chunk{s, (int32_t)std::min<int64_t>(CHUNK_LEN, c->inj.n - s), 1});
+    if (ch.size() > (size_t)INT32_MAX / 2) return fail(c, POP_EINVAL, "too many work chunks");
+    DevBuf dch, decb;
+    CK(dch.alloc(sizeof(Chunk) * ch.size()), "cudaMalloc(chunks)");
+    CK(decb.alloc(sizeof(int32_t) * ecb.size()), "cudaMalloc(ecb)");
+    CK(cudaMemcpyAsync(dch.p, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice, c->stream), "copy chunks");
+    CK(cudaMemcpyAsync(decb.p, ecb.data(), sizeof(int32_t) * ecb.size(), cudaMemcpyHostToDevice, c->stream),
+       "copy ecb");
+    CK(cudaStreamSynchronize(c->stream), "chunk sync");
+    c->d_chunks.swap(dch);
+    c->d_ecb.swap(decb);
+    c->n_chunks = (int32_t)ch.size();
+    c->n_ev_chunks = n_ev;
+    c->chunks_dirty = false;
+    c->version++;
+    return POP_OK;
+}
+
+// Scratch for K Lambda points (grows only).
+int ensure_scratch(pop_ctx* c, int64_t K)
+{
+    const int32_t n_inj = c->n_chunks - c->n_ev_chunks;
+    if (K <= c->k_cap && c->part_chunks == c->n_chunks && c->part_inj == n_inj) return POP_OK;
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(K, c->k_cap), 64);
+    DevBuf lam, c64, c32, part, part2, lnL, lnxi, neff, flags, dK;
+    CK(lam.alloc(sizeof(double) * cap * 12), "cudaMalloc(lambda)");
+    CK(c64.alloc(sizeof(LamF64) * cap), "cudaMalloc(consts64)");
+    CK(c32.alloc(sizeof(LamF32) * cap), "cudaMalloc(consts32)");
+    CK(part.alloc(sizeof(double) * cap * c->n_chunks), "cudaMalloc(partials)");
+    CK(part2.alloc(sizeof(double) * cap * std::max<int32_t>(n_inj, 1)), "cudaMalloc(partials2)");
+    CK(lnL.alloc(sizeof(double) * cap), "cudaMalloc(lnL)");
+    CK(lnxi.alloc(sizeof(double) * cap), "cudaMalloc(lnxi)");
+    CK(neff.alloc(sizeof(double) * cap), "cudaMalloc(neff)");
+    CK(flags.alloc(sizeof(uint32_t) * cap), "cudaMalloc(flags)");
+    CK(dK.alloc(sizeof(int64_t)), "cudaMalloc(K)");
+    if (c->d_lambda.p)  // keep the last Lambda batch (the autotuner reuses it)
+        CK(cudaMemcpyAsync(lam.p, c->d_lambda.p, std::min(lam.bytes, c->d_lambda.bytes), cudaMemcpyDeviceToDevice,
+                           c->stream), "copy lambda");
+    c->d_lambda.swap(lam);
+    c->d_c64.swap(c64);
+    c->d_c32.swap(c32);
+    c->d_part.swap(part);
+    c->d_part2.swap(part2);
+    c->d_lnL.swap(lnL);
+    c->d_lnxi.swap(lnxi);
+    c->d_neff.swap(neff);
+    c->d_flags.swap(flags);
+    c->d_K.swap(dK);
+    c->k_cap = cap;
+    c->part_chunks = c->n_chunks;
+    c->part_inj = n_inj;
+    c->version++;
+    return POP_OK;
+}
+
+int grid_size(pop_ctx* c, int mode)
+{
+    const Tiling& t = c->tiling[mode];
+    const void* fn = mode == POP_MODE_F64 ? weight_f64_fn(t, c->ev.n_dims == 7) : weight_f32_fn(t, c->ev.n_dims == 7);
+    int occ = 0;
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t.block_threads, 0) != cudaSuccess) occ = 1;
+    if (t.blocks_per_sm > 0) occ = std::min(occ, t.blocks_per_sm);
+    return std::max(1, occ) * c->sm_count;
+}
+
+// Enqueue prologue -> weight -> finalise for the K stored in d_K.
+int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturing)
+{
+    // Inside a capture the timing events must become external event-record
+    // nodes, or the replayed graph would never record them.
+    const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    const int m = mode == POP_MODE_F64 ? 0 : 1;
+    WorkDesc wd{c->d_chunks.as<Chunk>(), c->n_chunks, c->n_ev_chunks, c->ev.n_dims == 7};
+    CK(cudaEventRecordWithFlags(c->ev_t0, c->stream, rec), "event");
+    CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
+                       c->d_c32.as<LamF32>(), c->stream), "prologue");
+    CK(cudaEventRecordWithFlags(c->ev_w0, c->stream, rec), "event");
+    if (m == 0) {
+        FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
+        CK(launch_weight_f64(c->tiling[0], grid, e, j, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
+                             c->d_part.as<double>(), c->d_part2.as<double>(), c->stream), "weight_f64");
+    } else {
+        FeatF32 e{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
+        FeatF32 j{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
+        CK(launch_weight_f32(c->tiling[1], grid, e, j, wd, c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(),
+                             c->d_part.as<double>(), c->d_part2.as<double>(), c->stream), "weight_f32");
+    }
+    CK(cudaEventRecordWithFlags(c->ev_w1, c->stream, rec), "event");
+    CK(launch_finalise(c->d_part.as<double>(), c->d_part2.as<double>(), c->d_ecb.as<int32_t>(),
+                       c->d_offsets.as<int64_t>(), c->ev.n == 0 ? 0 : (int64_t)c->h_offsets.size() - 1,
+                       c->n_chunks, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
+                       c->k_cap, c->d_lnL.as<double>(), c->d_lnxi.as<double>(), c->d_neff.as<double>(),
+                       c->d_flags.as<uint32_t>(), c->stream), "finalise");
+    CK(cudaEventRecordWithFlags(c->ev_t1, c->stream, rec), "event");
+    return POP_OK;
+}
+
+int run_pipeline(pop_ctx* c, int mode, int n_params)
+{
+    const int m = mode == POP_MODE_F64 ? 0 : 1;
+    const int grid = grid_size(c, m);
+    if (!c->use_graphs) return enqueue_pipeline(c, mode, n_params, grid, false);
+    Graph& g = c->graph[m];
+    const Tiling& t = c->tiling[m];
+    const bool stale = !g.exec || g.k_cap != c->k_cap || g.version != c->version || g.tiling.lambda_tile != t.lambda_tile ||
+                       g.tiling.block_threads != t.block_threads || g.tiling.blocks_per_sm != t.blocks_per_sm ||
+                       c->last_params != n_params;
+    if (stale) {
+        g.reset();
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int rc = enqueue_pipeline(c, mode, n_params, grid, true);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (rc != POP_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        CK(e, "end capture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e, "graph instantiate");
+        g.k_cap = c->k_cap;
+        g.version = c->version;
+        g.tiling = t;
+    }
+    CK(cudaGraphLaunch(g.exec, c->stream), "graph launch");
+    return POP_OK;
+}
+
+bool tiling_ok(int mode, const Tiling& t)
+{
+    return (mode == POP_MODE_F64 ? weight_f64_fn(t, false) : weight_f32_fn(t, false)) != nullptr &&
+           t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32;
+}
+
+}  // namespace
+
+// ============================================================== C-ABI
+extern "C" {
+
+int pop_version(void) { return 10000; }
+
+const char* pop_status_string(int s)
+{
+    switch (s) {
+        case POP_OK: return "POP_OK";
+        case POP_EINVAL: return "POP_EINVAL";
+        case POP_ENOMEM: return "POP_ENOMEM";
+        case POP_ECUDA: return "POP_ECUDA";
+        case POP_ESTATE: return "POP_ESTATE";
+        case POP_ETIMEOUT: return "POP_ETIMEOUT";
+        case POP_ENUMERIC: return "POP_ENUMERIC";
+        default: return "POP_UNKNOWN";
+    }
+}
+
+const char* pop_last_error(const pop_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int pop_create(pop_ctx** out, int device, void* stream)
+{
+    pop_ctx* c = nullptr;
+    if (!out) return fail(nullptr, POP_EINVAL, "pop_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return fail(nullptr, POP_ECUDA, std::string("pop_create: no CUDA device (") + cudaGetErrorString(e) + ")");
+    if (device < 0 || device >= n) return fail(nullptr, POP_EINVAL, "pop_create: device index out of range");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, POP_ECUDA, std::string("pop_create: ") + cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail(nullptr, POP_ECUDA, std::string("pop_create: ") + cudaGetErrorString(e));
+    if (prop.major < 10) return fail(nullptr, POP_ECUDA, "pop_create: the library is built for sm_103a (GB300)");
+    c = new pop_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (!c->stream) {
+        // The legacy default stream cannot be captured into a graph; a blocking
+        // stream keeps the same ordering with respect to it.
+        e = cudaStreamCreate(&c->stream);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(nullptr, POP_ECUDA, std::string("pop_create: ") + cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->device_name = prop.name;
+    cudaEvent_t* evs[] = {&c->ev_t0, &c->ev_w0, &c->ev_w1, &c->ev_t1};
+    for (cudaEvent_t* ev : evs) {
+        e = cudaEventCreate(ev);
+        if (e != cudaSuccess) {
+            pop_destroy(c);
+            return fail(nullptr, POP_ECUDA, std::string("pop_create: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = c;
+    return POP_OK;
+}
+
+int pop_destroy(pop_ctx* c)
+{
+    if (!c) return POP_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (Graph& g : c->graph) g.reset();
+    cudaEvent_t evs[] = {c->ev_t0, c->ev_w0, c->ev_w1, c->ev_t1};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return POP_OK;
+}
+
+int pop_validate_events(int64_t n_events, const int64_t* offsets, int n_dims, char* msg, int msg_len)
+{
+    auto say = [&](const char* m) {
+        if (msg && msg_len > 0) snprintf(msg, (size_t)msg_len, "%s", m);
+        return POP_EINVAL;
+    };
+    if (n_events < 1) return say("n_events must be >= 1");
+    if (!offsets) return say("offsets is NULL");
+    if (n_dims != 6 && n_dims != 7) return say("n_dims must be 6 or 7");
+    if (offsets[0] != 0) return say("offsets[0] must be 0");
+    for (int64_t i = 0; i < n_events; ++i)
+        if (offsets[i + 1] <= offsets[i]) return say("every event needs >= 1 sample (offsets strictly increasing)");
+    if (offsets[n_events] > ((int64_t)1 << 40)) return say("too many samples");
+    if (msg && msg_len > 0) msg[0] = 0;
+    return POP_OK;
+}
+
+int pop_load_events(pop_ctx* c, int64_t n_events, const int64_t* offsets, int n_dims, const double* theta,
+                    const double* prior, int storage, int mem)
+{
+    if (!c) return POP_EINVAL;
+    char m[200];
+    if (pop_validate_events(n_events, offsets, n_dims, m, sizeof m) != POP_OK)
+        return fail(c, POP_EINVAL, std::string("pop_load_events: ") + m);
+    if (!theta || !prior) return fail(c, POP_EINVAL, "pop_load_events: theta/prior is NULL");
+    if (storage < 1 || storage > 3) return fail(c, POP_EINVAL, "pop_load_events: storage must be F64, F32 or both");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_load_events: bad mem");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int64_t n = offsets[n_events];
+    SampleSet s;
+    int rc = pack_samples(c, n, n_dims, theta, prior, storage, mem, s, "pop_load_events");
+    if (rc != POP_OK) return rc;
+    DevBuf doff;
+    CK(doff.alloc(sizeof(int64_t) * (n_events + 1)), "cudaMalloc(offsets)");
+    CK(cudaMemcpyAsync(doff.p, offsets, sizeof(int64_t) * (n_events + 1), cudaMemcpyHostToDevice, c->stream),
+       "copy offsets");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    c->ev.swap(s);
+    c->d_offsets.swap(doff);
+    c->h_offsets.assign(offsets, offsets + n_events + 1);
+    if (c->inj.n && c->inj.n_dims != n_dims) {  // stale injections of another layout
+        SampleSet none;
+        c->inj.swap(none);
+        c->n_draw = 0;
+    }
+    c->chunks_dirty = true;
+    c->version++;
+    return POP_OK;
+}
+
+int pop_load_injections(pop_ctx* c, int64_t n_found, int64_t n_draw, int n_dims, const double* theta,
+                        const double* p_draw, int storage, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (c->ev.n == 0) return fail(c, POP_ESTATE, "pop_load_injections: load events first");
+    if (n_found < 1 || n_draw < n_found) return fail(c, POP_EINVAL, "pop_load_injections: need n_draw >= n_found >= 1");
+    if (n_dims != c->ev.n_dims) return fail(c, POP_EINVAL, "pop_load_injections: n_dims differs from the events");
+    if (!theta || !p_draw) return fail(c, POP_EINVAL, "pop_load_injections: theta/p_draw is NULL");
+    if (storage < 1 || storage > 3) return fail(c, POP_EINVAL, "pop_load_injections: bad storage");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_load_injections: bad mem");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    SampleSet s;
+    int rc = pack_samples(c, n_found, n_dims, theta, p_draw, storage, mem, s, "pop_load_injections");
+    if (rc != POP_OK) return rc;
+    c->inj.swap(s);
+    c->n_draw = n_draw;
+    c->chunks_dirty = true;
+    c->version++;
+    return POP_OK;
+}
+
+int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_lnL,
+               double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (c->ev.n == 0 || c->inj.n == 0) return fail(c, POP_ESTATE, "pop_loglik: load events and injections first");
+    if (K < 0) return fail(c, POP_EINVAL, "pop_loglik: K < 0");
+    if (n_params != 11 + (c->ev.n_dims == 7))
+        return fail(c, POP_EINVAL, "pop_loglik: n_params must be 11 (12 with redshift samples)");
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32 && mode != POP_MODE_F32_SURROGATE)
+        return fail(c, POP_EINVAL, "pop_loglik: bad mode");
+    if (mode == POP_MODE_F32_SURROGATE) return fail(c, POP_ESTATE, "pop_loglik: surrogate not trained");
+    const int need = mode == POP_MODE_F64 ? POP_STORE_F64 : POP_STORE_F32;
+    if (!(c->ev.storage & need) || !(c->inj.storage & need))
+        return fail(c, POP_ESTATE, "pop_loglik: the loaded storage does not include this mode's precision");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_loglik: bad mem");
+    if (K == 0) return POP_OK;
+    if (!lambda || !out_lnL) return fail(c, POP_EINVAL, "pop_loglik: lambda/out_lnL is NULL");
+    if (K > (1LL << 24)) return fail(c, POP_EINVAL, "pop_loglik: K too large");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    int rc = build_chunks(c);
+    if (rc != POP_OK) return rc;
+    rc = ensure_scratch(c, K);
+    if (rc != POP_OK) return rc;
+    CK(cudaMemcpyAsync(c->d_lambda.p, lambda, sizeof(double) * K * n_params, in_kind(mem), c->stream), "copy lambda");
+    set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
+    CK(cudaGetLastError(), "set K");
+    rc = run_pipeline(c, mode, n_params);
+    if (rc != POP_OK) return rc;
+    c->last_params = n_params;
+    c->last_K = K;
+    c->timed = true;
+    CK(cudaMemcpyAsync(out_lnL, c->d_lnL.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnL");
+    if (out_lnxi) CK(cudaMemcpyAsync(out_lnxi, c->d_lnxi.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnxi");
+    if (out_neff) CK(cudaMemcpyAsync(out_neff, c->d_neff.p, sizeof(double) * K, out_kind(mem), c->stream), "copy neff");
+    if (out_flags)
+        CK(cudaMemcpyAsync(out_flags, c->d_flags.p, sizeof(uint32_t) * K, out_kind(mem), c->stream), "copy flags");
+    if (mem == POP_MEM_HOST) CK(cudaStreamSynchronize(c->stream), "sync");
+    return POP_OK;
+}
+
+int pop_set_tiling(pop_ctx* c, int mode, int lambda_tile, int block_threads, int blocks_per_sm)
+{
+    if (!c) return POP_EINVAL;
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32) return fail(c, POP_EINVAL, "pop_set_tiling: bad mode");
+    Tiling t{lambda_tile, block_threads, blocks_per_sm};
+    if (!tiling_ok(mode, t)) return fail(c, POP_EINVAL, "pop_set_tiling: unsupported tiling");
+    c->tiling[mode] = t;
+    return POP_OK;
+}
+
+int pop_get_tiling(pop_ctx* c, int mode, int* lambda_tile, int* block_threads, int* blocks_per_sm)
+{
+    if (!c) return POP_EINVAL;
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32) return fail(c, POP_EINVAL, "pop_get_tiling: bad mode");
+    const Tiling& t = c->tiling[mode];
+    if (lambda_tile) *lambda_tile = t.lambda_tile;
+    if (block_threads) *block_threads = t.block_threads;
+    if (blocks_per_sm) *blocks_per_sm = t.blocks_per_sm;
+    return POP_OK;
+}
+
+int pop_set_graphs(pop_ctx* c, int enable)
+{
+    if (!c) return POP_EINVAL;
+    c->use_graphs = enable != 0;
+    return POP_OK;
+}
+
+int pop_last_kernel_ms(pop_ctx* c, double* weight_ms, double* total_ms)
+{
+    if (!c) return POP_EINVAL;
+    if (!c->timed) return fail(c, POP_ESTATE, "pop_last_kernel_ms: no pop_loglik yet");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaEventSynchronize(c->ev_t1), "event sync");
+    float w = 0.f, t = 0.f;
+    CK(cudaEventElapsedTime(&w, c->ev_w0, c->ev_w1), "elapsed");
+    CK(cudaEventElapsedTime(&t, c->ev_t0, c->ev_t1), "elapsed");
+    if (weight_ms) *weight_ms = w;
+    if (total_ms) *total_ms = t;
+    return POP_OK;
+}
+
+int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
+{
+    if (!c) return POP_EINVAL;
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32) return fail(c, POP_EINVAL, "pop_autotune: bad mode");
+    if (c->ev.n == 0 || c->inj.n == 0) return fail(c, POP_ESTATE, "pop_autotune: load events and injections first");
+    if (c->last_K < 1 || K < 1 || K > c->last_K)
+        return fail(c, POP_ESTATE, "pop_autotune: needs a previous pop_loglik with at least K Lambda points");
+    const int need = mode == POP_MODE_F64 ? POP_STORE_F64 : POP_STORE_F32;
+    if (!(c->ev.storage & need) || !(c->inj.storage & need))
+        return fail(c, POP_ESTATE, "pop_autotune: the loaded storage does not include this mode's precision");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    char key[512];
+    snprintf(key, sizeof key, "%s|mode=%d|chunks=%d|ev_chunks=%d|K=%lld|dims=%d", c->device_name.c_str(), mode,
+             c->n_chunks, c->n_ev_chunks, (long long)K, c->ev.n_dims);
+    for (char* p = key; *p; ++p)
+        if (*p == ' ') *p = '_';
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        Tiling best{};
+        bool found = false;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k;
+            Tiling t{};
+            if (ls >> k >> t.lambda_tile >> t.block_threads >> t.blocks_per_sm && k == key && tiling_ok(mode, t)) {
+                best = t;
+                found = true;
+            }
+        }
+        if (found) {
+            c->tiling[mode] = best;
+            return POP_OK;
+        }
+    }
+    const int tiles64[] = {1, 2, 4, 8, 16};
+    const int tiles32[] = {2, 4, 8, 16, 32};
+    const int threads[] = {128, 256, 512};
+    const Tiling saved = c->tiling[mode];
+    const int n_params = c->last_params;
+    int rc = build_chunks(c);
+    if (rc != POP_OK) return rc;
+    rc = ensure_scratch(c, K);
+    if (rc != POP_OK) return rc;
+    set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
+    CK(cudaGetLastError(), "set K");
+    CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
+                       c->d_c32.as<LamF32>(), c->stream), "prologue");
+    float best_ms = 1e30f;
+    Tiling best = saved;
+    WorkDesc wd{c->d_chunks.as<Chunk>(), c->n_chunks, c->n_ev_chunks, c->ev.n_dims == 7};
+    for (int ti = 0; ti < 5; ++ti) {
+        for (int nt : threads) {
+            Tiling t{mode == POP_MODE_F64 ? tiles64[ti] : tiles32[ti], nt, 0};
+            c->tiling[mode] = t;
+            const int grid = grid_size(c, mode);
+            float ms[3];
+            for (int r = -1; r < 3; ++r) {
+                CK(cudaEventRecord(c->ev_w0, c->stream), "event");
+                cudaError_t e;
+                if (mode == POP_MODE_F64) {
+                    FeatF64 ev{c->ev.f64.as<double>(), c->ev.stride}, ij{c->inj.f64.as<double>(), c->inj.stride};
+                    e = launch_weight_f64(t, grid, ev, ij, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
+                                          c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
+                } else {
+                    FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
+                    FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
+                    e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(),
+                                          c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
+                }
+                if (e != cudaSuccess) {
+                    c->tiling[mode] = saved;
+                    return cuda_fail(c, e, "autotune launch");
+                }
+                CK(cudaEventRecord(c->ev_w1, c->stream), "event");
+                CK(cudaEventSynchronize(c->ev_w1), "event sync");
+                if (r >= 0) CK(cudaEventElapsedTime(&ms[r], c->ev_w0, c->ev_w1), "elapsed");
+            }
+            std::sort(ms, ms + 3);
+            if (ms[1] < best_ms) {
+                best_ms = ms[1];
+                best = t;
+            }
+        }
+    }
+    c->tiling[mode] = best;
+    c->timed = false;
+    if (cache_path) {
+        std::ofstream out(cache_path, std::ios::app);
+        out << key << " " << best.lambda_tile << " " << best.block_threads << " " << best.blocks_per_sm << "\n";
+    }
+    return POP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal types shared by the host runtime (pop_api.cu) and the kernels
+// (pop_kernels.cu).  Nothing here is part of the public C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pop.h"
+
+namespace pop {
+
+// Lambda parameter indices in the C-ABI row order.
+enum { P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_LAM, P_MPP, P_SIGPP, P_ACHI, P_BCHI, P_XIT, P_SIGT, P_KAPPA };
+
+// Packed per-sample feature rows (structure of arrays, row r at base + r*stride).
+// FP64 layout rows: natural logs.  FP32 layout rows: base-2 logs (so every
+// exponential is one ex2), and m2 kept in a separate FP64 row for the exact
+// q-support test.
+enum { F_LM1, F_M1, F_LQ, F_SA, F_SB, F_DC, F_NLPI, F_LZ1, F_M2, F_INVM1, F_COUNT64 = 10 };
+// FP32 layout: the same first eight rows, then the low part of log2 m1
+// (log2 m1 = row F_LM1 + row F32_LM1LO to ~1e-15), so that the q
+// normalisation (1+beta) log2(mmin/m1) keeps its relative accuracy as m1 -> mmin.
+enum { F32_LM1LO = 8, F_COUNT32 = 9 };
+
+// Sentinel for ln 0 in the spin-magnitude and z logs: finite, so that a zero
+// exponent gives 0 * sentinel = 0 (0^0 = 1) and a positive one underflows.
+constexpr double LOG_ZERO = -1e30;
+
+// Per-Lambda constants of the FP64 weight (natural-log units).
+struct alignas(16) LamF64 {
+    int64_t mmin_bits;   // bit pattern of mmin (+inf when Lambda is invalid)
+    int64_t mmax_bits;   // bit pattern of mmax
+    double nalpha;       // -alpha
+    double cpl;          // ln|1+beta| - 2 ln B - ln I + ln((1-lam) C_pl)
+    double mu;           // mpp
+    double nh;           // -1 / (2 sigpp^2)
+    double cg;           // ln|1+beta| - 2 ln B - ln I + ln(lam C_g)
+    double beta;         // q exponent
+    double ac, bc;       // alpha_chi - 1, beta_chi - 1
+    double km1;          // kappa - 1 (0 without redshift)
+    double b1;           // 1 + beta
+    double mmin;         // mmin (for (mmin - m1)/m1 near the lower mass edge)
+    double lmmin;        // ln mmin
+    double nht;          // -1 / (2 sigma_t^2)
+    double ct;           // ln(xi_t C_t^2)
+    double t0;           // (1 - xi_t) / 4
+    int32_t beta_m1;     // beta == -1: q normalisation is ln(m1/mmin)
+    int32_t valid;
+};
+
+// Per-Lambda constants of the FP32 weight (base-2 units).
+struct alignas(16) LamF32 {
+    int64_t mmin_bits;   // FP64 bit pattern of mmin, for the exact m2 >= mmin test
+    float thr_lo;        // largest float <= mmin   (m1 > mmin  <=>  m1_f32 > thr_lo)
+    float thr_hi;        // largest float <= mmax   (m1 <= mmax <=>  m1_f32 <= thr_hi)
+    float nalpha, cpl, mu, nh, cg, beta, ac, bc, km1;
+    // q normalisation exponent u = b1 ((lmmin - lm1) + (lmmin_lo - lm1_lo)) in base 2,
+    // evaluated as fma(b1, lmmin - lm1, fma(nb1, lm1_lo, b1lmmin_lo)); with
+    // beta = -1, b1 = 1 and the normalisation is -u.
+    float b1, nb1, lmmin, b1lmmin_lo;
+    float nht, ct, t0;
+    int32_t beta_m1;
+    int32_t valid;
+};
+
+// One work chunk: a contiguous run of samples of one event, or of injections.
+struct Chunk {
+    int64_t start;       // first sample in its feature block
+    int32_t len;         // samples in the chunk (>= 1)
+    int32_t inj;         // 0 = event chunk, 1 = injection chunk
+};
+
+struct FeatF64 {
+    const double* base;  // [F_COUNT64][stride]
+    int64_t stride;
+};
+
+struct FeatF32 {
+    const float* base;   // [F_COUNT32][stride]
+    const double* m2;    // [stride]
+    int64_t stride;
+};
+
+// Everything the weight kernel needs about the loaded data.
+struct WorkDesc {
+    const Chunk* chunks;     // [n_chunks]: event chunks first, then injection chunks
+    int32_t n_chunks;
+    int32_t n_ev_chunks;
+    int32_t has_z;
+};
+
+// Launch-time options of the weight kernels.
+struct Tiling {
+    int lambda_tile;     // Lambda points per work item
+    int block_threads;   // threads per block
+    int blocks_per_sm;   // 0 = occupancy maximum
+};
+
+// ---------------------------------------------------------------- kernel launchers
+// All launch on `s` and return the launch error (cudaSuccess when queued).
+cudaError_t launch_pack_f64(const double* theta, const double* prior, int64_t n, int n_dims,
+                            double* feat, int64_t stride, unsigned long long* bad, cudaStream_t s);
+cudaError_t launch_pack_f32(const double* theta, const double* prior, int64_t n, int n_dims,
+                            float* feat, double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s);
+cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params,
+                            LamF64* c64, LamF32* c32, cudaStream_t s);
+cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd,
+                              const LamF64* lam, const int64_t* dK, double* part, double* part2,
+                              cudaStream_t s);
+cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
+                              const LamF32* lam, const int64_t* dK, double* part, double* part2,
+                              cudaStream_t s);
+cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ev_chunk_begin,
+                            const int64_t* offsets, int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks,
+                            int64_t n_draw, const LamF64* lam, const int64_t* dK, int64_t K_cap,
+                            double* lnL, double* lnxi, double* neff, uint32_t* flags, cudaStream_t s);
+
+// Kernel function of a tiling (nullptr when that instantiation does not exist).
+const void* weight_f64_fn(const Tiling& t, bool has_z);
+const void* weight_f32_fn(const Tiling& t, bool has_z);
+
+}  // namespace pop

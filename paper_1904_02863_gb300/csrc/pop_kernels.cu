@@ -1,0 +1,359 @@
+// One-time pack kernels, the per-Lambda prologue and the finalise kernel.
+//
+// Paper, Sec. "Population acceleration": the N x n_i sample arrays go to the
+// GPU once (pack), the population model is evaluated for every sample and
+// Lambda (weight kernels, separate files), then the per-event sums, their
+// logarithms and the cross-event sum are formed on the device and only the
+// log-likelihood comes back (finalise).
+#include <math.h>
+
+#include "pop_internal.h"
+
+namespace pop {
+
+namespace {
+
+constexpr double SQRT2 = 1.4142135623730950488;
+constexpr double SQRT2PI = 2.5066282746310005024;
+constexpr double LN2 = 0.69314718055994530942;
+constexpr double LOG2E = 1.4426950408889634074;
+constexpr int Z_NODES = 1024;  // redshift normalisation: trapezoid on 1024 nodes of [0, 2]
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+// Reads one sample; returns false when the inputs are not usable at all
+// (non-finite, or pi <= 0), true otherwise.  `live` is false when the sample
+// lies outside the Lambda-independent part of the support.
+struct RawSample {
+    double m1, q, a1, a2, c1, c2, z, pi;
+};
+
+__device__ __forceinline__ bool read_sample(const double* theta, const double* prior, int64_t j, int nd,
+                                            bool round_f32, RawSample& s, bool& live)
+{
+    const double* th = theta + j * nd;
+    s.m1 = th[0]; s.q = th[1]; s.a1 = th[2]; s.a2 = th[3]; s.c1 = th[4]; s.c2 = th[5];
+    s.z = nd == 7 ? th[6] : 1.0;
+    s.pi = prior[j];
+    if (round_f32) {  // FP32 storage: the raw inputs are quantised first
+        s.m1 = (double)(float)s.m1; s.q = (double)(float)s.q; s.a1 = (double)(float)s.a1;
+        s.a2 = (double)(float)s.a2; s.c1 = (double)(float)s.c1; s.c2 = (double)(float)s.c2;
+        s.z = (double)(float)s.z; s.pi = (double)(float)s.pi;
+    }
+    bool ok = finite_d(s.m1) && finite_d(s.q) && finite_d(s.a1) && finite_d(s.a2) && finite_d(s.c1) &&
+              finite_d(s.c2) && finite_d(s.z) && finite_d(s.pi) && s.pi > 0.0;
+    live = ok && s.m1 > 0.0 && s.q > 0.0 && s.q <= 1.0 && s.a1 >= 0.0 && s.a1 <= 1.0 && s.a2 >= 0.0 &&
+           s.a2 <= 1.0 && s.c1 >= -1.0 && s.c1 <= 1.0 && s.c2 >= -1.0 && s.c2 <= 1.0 && s.z >= 0.0 && s.z <= 2.0;
+    return ok;
+}
+
+__device__ __forceinline__ double log_or_zero(double x) { return x > 0.0 ? log(x) : LOG_ZERO; }
+
+__global__ void pack_f64_kernel(const double* __restrict__ theta, const double* __restrict__ prior, int64_t n,
+                                int nd, double* __restrict__ feat, int64_t stride, unsigned long long* bad)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        RawSample s;
+        bool live;
+        if (!read_sample(theta, prior, j, nd, false, s, live)) atomicAdd(bad, 1ull);
+        double f[F_COUNT64] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (live) {
+            f[F_LM1] = log(s.m1);
+            f[F_M1] = s.m1;
+            f[F_INVM1] = 1.0 / s.m1;
+            f[F_LQ] = log(s.q);
+            f[F_SA] = (s.a1 > 0.0 && s.a2 > 0.0) ? log(s.a1) + log(s.a2) : LOG_ZERO;
+            f[F_SB] = (s.a1 < 1.0 && s.a2 < 1.0) ? log(1.0 - s.a1) + log(1.0 - s.a2) : LOG_ZERO;
+            f[F_DC] = (s.c1 - 1.0) * (s.c1 - 1.0) + (s.c2 - 1.0) * (s.c2 - 1.0);
+            f[F_NLPI] = -log(s.pi);
+            if (nd == 7) {
+                f[F_NLPI] = s.z > 0.0 ? f[F_NLPI] + 2.0 * log(s.z) : LOG_ZERO;
+                f[F_LZ1] = log1p(s.z);
+            }
+            f[F_M2] = __dmul_rn(s.q, s.m1);  // one rounding, as the support test is defined
+        }
+#pragma unroll
+        for (int r = 0; r < F_COUNT64; ++r) feat[r * stride + j] = f[r];
+    }
+}
+
+__global__ void pack_f32_kernel(const double* __restrict__ theta, const double* __restrict__ prior, int64_t n,
+                                int nd, float* __restrict__ feat, double* __restrict__ m2, int64_t stride,
+                                unsigned long long* bad)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        RawSample s;
+        bool live;
+        if (!read_sample(theta, prior, j, nd, true, s, live)) atomicAdd(bad, 1ull);
+        float f[F_COUNT32] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        double mm = 0.0;
+        if (live) {
+            const double l2m1 = log2(s.m1);
+            f[F_LM1] = (float)l2m1;
+            f[F32_LM1LO] = (float)(l2m1 - (double)f[F_LM1]);
+            f[F_M1] = (float)s.m1;  // exact: m1 is already a float
+            f[F_LQ] = (float)log2(s.q);
+            f[F_SA] = (s.a1 > 0.0 && s.a2 > 0.0) ? (float)(log2(s.a1) + log2(s.a2)) : (float)LOG_ZERO;
+            f[F_SB] = (s.a1 < 1.0 && s.a2 < 1.0) ? (float)(log2(1.0 - s.a1) + log2(1.0 - s.a2)) : (float)LOG_ZERO;
+            f[F_DC] = (float)((s.c1 - 1.0) * (s.c1 - 1.0) + (s.c2 - 1.0) * (s.c2 - 1.0));
+            double nl = -log2(s.pi);
+            if (nd == 7) {
+                nl = s.z > 0.0 ? nl + 2.0 * log2(s.z) : LOG_ZERO;
+                f[F_LZ1] = (float)(log1p(s.z) * LOG2E);
+            }
+            f[F_NLPI] = (float)nl;
+            mm = __dmul_rn(s.q, s.m1);  // exact: product of two floats fits in 53 bits
+        }
+#pragma unroll
+        for (int r = 0; r < F_COUNT32; ++r) feat[r * stride + j] = f[r];
+        m2[j] = mm;
+    }
+}
+
+__device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
+
+// Per-Lambda constants.  One warp per Lambda: the lanes share the 1024-node
+// redshift trapezoid, lane 0 does the rest.
+__global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
+                                LamF64* __restrict__ c64, LamF32* __restrict__ c32)
+{
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= *dK) return;
+    const double* L = lambda + k * n_params;
+    const bool has_z = n_params == 12;
+
+    // I(kappa) = trapezoid of (1+z)^(kappa-1) z^2 on z_k = 2k/1023.
+    double zs = 0.0;
+    if (has_z) {
+        const double km1 = L[P_KAPPA] - 1.0;
+        for (int i = lane; i < Z_NODES; i += 32) {
+            double z = 2.0 * i / (Z_NODES - 1);
+            double f = exp(km1 * log1p(z)) * z * z;
+            zs += (i == 0 || i == Z_NODES - 1) ? 0.5 * f : f;
+        }
+        for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
+        zs *= 2.0 / (Z_NODES - 1);
+    }
+    if (lane != 0) return;
+
+    bool valid = true;
+    for (int p = 0; p < n_params; ++p) valid = valid && finite_d(L[p]);
+    const double alpha = L[P_ALPHA], beta = L[P_BETA], mmin = L[P_MMIN], mmax = L[P_MMAX];
+    const double lam = L[P_LAM], mu = L[P_MPP], sig = L[P_SIGPP], ach = L[P_ACHI], bch = L[P_BCHI];
+    const double xit = L[P_XIT], sigt = L[P_SIGT];
+    valid = valid && mmin > 0.0 && mmin < mmax && lam >= 0.0 && lam <= 1.0 && sig > 0.0 && sigt > 0.0 &&
+            ach > 0.0 && bch > 0.0 && xit >= 0.0 && xit <= 1.0;
+
+    LamF64 c;
+    LamF32 f;
+    if (!valid) {
+        c = LamF64{};
+        c.mmin_bits = dbits(INFINITY);
+        c.mmax_bits = dbits(INFINITY);
+        c.valid = 0;
+        f = LamF32{};
+        f.mmin_bits = c.mmin_bits;
+        f.thr_lo = INFINITY;
+        f.thr_hi = INFINITY;
+        f.valid = 0;
+        c64[k] = c;
+        c32[k] = f;
+        return;
+    }
+    const double lmmin = log(mmin), lmmax = log(mmax);
+    // Power law: C_pl = (1-alpha) / (mmax^(1-alpha) - mmin^(1-alpha)), in logs.
+    double ln_cpl;
+    if (alpha == 1.0) {
+        ln_cpl = -log(lmmax - lmmin);
+    } else {
+        const double oma = 1.0 - alpha;
+        ln_cpl = log(fabs(oma)) - oma * lmmin - log(fabs(expm1(oma * (lmmax - lmmin))));
+    }
+    // Truncated Gaussian on [mmin, mmax]: C_g = 1 / (sigma sqrt(2 pi) Z_m).
+    const double zm = 0.5 * (erf((mmax - mu) / (SQRT2 * sig)) - erf((mmin - mu) / (SQRT2 * sig)));
+    const double ln_cg = log(lam) - log(sig * SQRT2PI * zm);
+    const double ln_beta = lgamma(ach) + lgamma(bch) - lgamma(ach + bch);
+    const double b1 = 1.0 + beta;
+    const int beta_m1 = b1 == 0.0;
+    const double ln_qn = beta_m1 ? 0.0 : log(fabs(b1));
+    const double ln_iz = has_z ? log(zs) : 0.0;
+    const double common = ln_qn - 2.0 * ln_beta - ln_iz;
+    // Tilt: C_t = 1 / (sigma_t sqrt(2 pi) * erf(sqrt2 / sigma_t) / 2).
+    const double ln_ct = -log(sigt * SQRT2PI * 0.5 * erf(SQRT2 / sigt));
+
+    c.mmin_bits = dbits(mmin);
+    c.mmax_bits = dbits(mmax);
+    c.nalpha = -alpha;
+    c.cpl = common + log1p(-lam) + ln_cpl;
+    c.mu = mu;
+    c.nh = -0.5 / (sig * sig);
+    c.cg = common + ln_cg;
+    c.beta = beta;
+    c.ac = ach - 1.0;
+    c.bc = bch - 1.0;
+    c.km1 = has_z ? L[P_KAPPA] - 1.0 : 0.0;
+    c.b1 = b1;
+    c.mmin = mmin;
+    c.lmmin = lmmin;
+    c.nht = -0.5 / (sigt * sigt);
+    c.ct = log(xit) + 2.0 * ln_ct;
+    c.t0 = 0.25 * (1.0 - xit);
+    c.beta_m1 = beta_m1;
+    c.valid = 1;
+    c64[k] = c;
+
+    // FP32 copy in base-2 units.  With beta = -1 the q normalisation ln(m1/mmin)
+    // is formed from base-2 logs, so 1/ln 2 joins the constant.
+    const double fix = beta_m1 ? -log(LN2) : 0.0;
+    f.mmin_bits = c.mmin_bits;
+    f.thr_lo = __double2float_rd(mmin);
+    f.thr_hi = __double2float_rd(mmax);
+    f.nalpha = (float)c.nalpha;
+    f.cpl = (float)((c.cpl + fix) * LOG2E);
+    f.mu = (float)mu;
+    f.nh = (float)(c.nh * LOG2E);
+    f.cg = (float)((c.cg + fix) * LOG2E);
+    f.beta = (float)beta;
+    f.ac = (float)c.ac;
+    f.bc = (float)c.bc;
+    f.km1 = (float)c.km1;
+    const double b1f = beta_m1 ? 1.0 : b1;
+    const double l2mmin = log2(mmin);
+    f.lmmin = (float)l2mmin;
+    f.b1 = (float)b1f;
+    f.nb1 = (float)-b1f;
+    f.b1lmmin_lo = (float)(b1f * (l2mmin - (double)f.lmmin));
+    f.nht = (float)(c.nht * LOG2E);
+    f.ct = (float)(c.ct * LOG2E);
+    f.t0 = (float)c.t0;
+    f.beta_m1 = beta_m1;
+    f.valid = 1;
+    c32[k] = f;
+}
+
+// Deterministic block sum (fixed shuffle tree, then warps in order).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < NT / 32; ++i) s += sh[i];
+    return s;
+}
+
+constexpr int FIN_THREADS = 256;
+
+// ln L = sum_i ln(S_i / n_i) - N ln xi, plus ln xi, N_eff and flags.
+__global__ void __launch_bounds__(FIN_THREADS)
+finalise_kernel(const double* __restrict__ part, const double* __restrict__ part2,
+                const int32_t* __restrict__ ecb, const int64_t* __restrict__ off, int64_t n_events,
+                int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw, const LamF64* __restrict__ lam,
+                const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags)
+{
+    __shared__ double sh[FIN_THREADS / 32];
+    const int64_t k = blockIdx.x;
+    if (k >= *dK) return;
+    if (!lam[k].valid) {
+        if (threadIdx.x == 0) {
+            lnL[k] = -INFINITY;
+            lnxi[k] = 0.0;
+            neff[k] = 0.0;
+            flags[k] = POP_FLAG_INVALID_LAMBDA;
+        }
+        return;
+    }
+    const double* pk = part + k * (int64_t)n_chunks;
+    double s_ln = 0.0, zero = 0.0;
+    for (int64_t i = threadIdx.x; i < n_events; i += FIN_THREADS) {
+        double S = 0.0;
+        for (int32_t c = ecb[i]; c < ecb[i + 1]; ++c) S += pk[c];
+        if (S == 0.0) zero = 1.0;
+        else s_ln += log(S / (double)(off[i + 1] - off[i]));
+    }
+    const int32_t n_inj = n_chunks - n_ev_chunks;
+    const double* p2 = part2 + k * (int64_t)n_inj;
+    double sw = 0.0, sw2 = 0.0;
+    for (int32_t c = threadIdx.x; c < n_inj; c += FIN_THREADS) {
+        sw += pk[n_ev_chunks + c];
+        sw2 += p2[c];
+    }
+    s_ln = block_sum<FIN_THREADS>(s_ln, sh);
+    zero = block_sum<FIN_THREADS>(zero, sh);
+    sw = block_sum<FIN_THREADS>(sw, sh);
+    sw2 = block_sum<FIN_THREADS>(sw2, sh);
+    if (threadIdx.x != 0) return;
+    uint32_t fl = 0;
+    const double nd = (double)n_draw;
+    const double xi = sw / nd;
+    const double var = sw2 / (nd * nd) - xi * xi / nd;
+    double ne = var > 0.0 ? xi * xi / var : INFINITY;
+    double out, lx;
+    if (zero > 0.0) fl |= POP_FLAG_ZERO_EVENT;
+    if (xi == 0.0) {
+        fl |= POP_FLAG_ZERO_XI;
+        out = -INFINITY;
+        lx = -INFINITY;
+        ne = 0.0;
+    } else {
+        lx = log(xi);
+        out = (fl & POP_FLAG_ZERO_EVENT) ? -INFINITY : s_ln - (double)n_events * lx;
+    }
+    if (ne < 4.0 * (double)n_events) fl |= POP_FLAG_LOW_NEFF;
+    lnL[k] = out;
+    lnxi[k] = lx;
+    neff[k] = ne;
+    flags[k] = fl;
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 65535LL * 32) b = 65535LL * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_pack_f64(const double* theta, const double* prior, int64_t n, int n_dims, double* feat,
+                            int64_t stride, unsigned long long* bad, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    pack_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, n, n_dims, feat, stride, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_f32(const double* theta, const double* prior, int64_t n, int n_dims, float* feat,
+                            double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    pack_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, n, n_dims, feat, m2, stride, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params, LamF64* c64,
+                            LamF32* c32, cudaStream_t s)
+{
+    if (K_cap <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)((K_cap * 32 + threads - 1) / threads);
+    prologue_kernel<<<blocks, threads, 0, s>>>(lambda, dK, n_params, c64, c32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,
+                            int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
+                            const LamF64* lam, const int64_t* dK, int64_t K_cap, double* lnL, double* lnxi,
+                            double* neff, uint32_t* flags, cudaStream_t s)
+{
+    if (K_cap <= 0) return cudaSuccess;
+    finalise_kernel<<<(unsigned)K_cap, FIN_THREADS, 0, s>>>(part, part2, ecb, off, n_events, n_chunks, n_ev_chunks,
+                                                            n_draw, lam, dK, lnL, lnxi, neff, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace pop

@@ -1,0 +1,203 @@
+// FP64 sample-weight kernel with per-(event chunk, Lambda) segmented sums.
+//
+// Paper, Sec. "Population acceleration": evaluating the population model for
+// every posterior sample is the embarrassingly parallel hot loop of the
+// recycled likelihood, Eq. (poplike).  Here one persistent grid walks work
+// items (chunk of one event's samples or of the injections) x (tile of T
+// Lambda points).  Every thread keeps one sample's features in registers and
+// evaluates its weight for the T Lambda points of the tile, whose constants
+// sit in shared memory; the block then reduces the T partial sums in a fixed
+// order (shuffle tree, then warps in order) and writes one FP64 partial per
+// (Lambda, chunk) — no atomics, bit-reproducible.
+//
+// w(theta) = [exp(aE + cpl - alpha ln m1) + exp(aE + cg - (m1-mu)^2/(2 sig^2))]
+//            * [(1-xi_t)/4 + exp(ct - dc/(2 sig_t^2))] / |expm1((1+beta) ln(mmin/m1))|
+// with aE = -ln pi + beta ln q + (alpha_chi-1)(ln a1 + ln a2) + (beta_chi-1)(ln(1-a1) + ln(1-a2))
+//          [+ (kappa-1) ln(1+z)], and every Lambda-only factor folded into cpl, cg, ct.
+#include <math.h>
+
+#include "pop_internal.h"
+
+namespace pop {
+
+namespace {
+
+struct F64Sample {
+    double lm1, m1, lq, sa, sb, dc, nlpi, lz1, invm1;
+    int64_t m1b, m2b;  // bit patterns of m1, m2 (non-negative doubles compare as integers)
+};
+
+// |bits(m1) - bits(mmin)| below 2^46 means m1/mmin - 1 is below ~2^-6.
+constexpr long long NEAR_EDGE_BITS = 1LL << 46;
+
+// log1p(t) for |t| < 2^-5 from its Taylor series to t^12 (truncation < 1e-19
+// relative).
+__device__ __forceinline__ double log1p_near0(double t)
+{
+    double p = -1.0 / 12;
+    p = fma(p, t, 1.0 / 11);
+    p = fma(p, t, -1.0 / 10);
+    p = fma(p, t, 1.0 / 9);
+    p = fma(p, t, -1.0 / 8);
+    p = fma(p, t, 1.0 / 7);
+    p = fma(p, t, -1.0 / 6);
+    p = fma(p, t, 1.0 / 5);
+    p = fma(p, t, -1.0 / 4);
+    p = fma(p, t, 1.0 / 3);
+    p = fma(p, t, -1.0 / 2);
+    p = fma(p, t, 1.0);
+    return p * t;
+}
+
+template <bool HAS_Z>
+__device__ __forceinline__ void load_f64(const FeatF64& F, int64_t s, F64Sample& x)
+{
+    const double* b = F.base;
+    const int64_t st = F.stride;
+    x.lm1 = __ldg(b + F_LM1 * st + s);
+    x.m1 = __ldg(b + F_M1 * st + s);
+    x.lq = __ldg(b + F_LQ * st + s);
+    x.sa = __ldg(b + F_SA * st + s);
+    x.sb = __ldg(b + F_SB * st + s);
+    x.dc = __ldg(b + F_DC * st + s);
+    x.nlpi = __ldg(b + F_NLPI * st + s);
+    x.lz1 = HAS_Z ? __ldg(b + F_LZ1 * st + s) : 0.0;
+    x.invm1 = __ldg(b + F_INVM1 * st + s);
+    x.m1b = __double_as_longlong(x.m1);
+    x.m2b = __double_as_longlong(__ldg(b + F_M2 * st + s));
+}
+
+template <bool HAS_Z>
+__device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c)
+{
+    // Support: mmin < m1 <= mmax and fl64(q m1) >= mmin, compared on bit patterns.
+    const bool in = (x.m1b > c.mmin_bits) & (x.m1b <= c.mmax_bits) & (x.m2b >= c.mmin_bits);
+    double aE = fma(c.beta, x.lq, x.nlpi);
+    aE = fma(c.ac, x.sa, aE);
+    aE = fma(c.bc, x.sb, aE);
+    if (HAS_Z) aE = fma(c.km1, x.lz1, aE);
+    const double e1 = exp(fma(c.nalpha, x.lm1, aE + c.cpl));
+    const double d = x.m1 - c.mu;
+    const double e2 = exp(fma(c.nh * d, d, aE + c.cg));
+    // ln(mmin/m1) for the q normalisation.  Within ~3% of the lower edge the
+    // log difference would cancel, so it is log1p((mmin - m1)/m1) by its series
+    // (mmin - m1 is exact there); the test runs on bit patterns (integer pipe).
+    double lr = c.lmmin - x.lm1;
+    if (llabs(x.m1b - c.mmin_bits) < NEAR_EDGE_BITS) lr = log1p_near0(x.invm1 * (c.mmin - x.m1));
+    const double den = c.beta_m1 ? -lr : fabs(expm1(c.b1 * lr));
+    const double tt = c.t0 + exp(fma(c.nht, x.dc, c.ct));
+    const double w = (e1 + e2) * tt / den;
+    return in ? w : 0.0;
+}
+
+template <int T, int NT, bool HAS_Z>
+__global__ void __launch_bounds__(NT)
+weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict__ lam,
+                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
+{
+    __shared__ LamF64 sl[T];
+    __shared__ double red[NT / 32][T];
+    __shared__ double red2[NT / 32][T];
+    const int64_t K = *dK;
+    const int64_t n_tiles = (K + T - 1) / T;
+    const int64_t n_items = (int64_t)wd.n_chunks * n_tiles;
+    const int n_inj_chunks = wd.n_chunks - wd.n_ev_chunks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int c = (int)(item / n_tiles);
+        const int64_t k0 = (item - (int64_t)c * n_tiles) * T;
+        const int tn = (int)(K - k0 < T ? K - k0 : T);
+        __syncthreads();  // the previous item is done with sl / red
+        {
+            constexpr int W = (int)(sizeof(LamF64) / 8);
+            double* dst = reinterpret_cast<double*>(sl);
+            for (int i = threadIdx.x; i < T * W; i += NT) {
+                const int l = i / W;
+                const int64_t src = k0 + (l < tn ? l : tn - 1);
+                dst[i] = reinterpret_cast<const double*>(lam + src)[i - l * W];
+            }
+        }
+        __syncthreads();
+        const Chunk ch = wd.chunks[c];
+        const FeatF64 F = ch.inj ? inj : ev;
+        double acc[T], acc2[T];
+#pragma unroll
+        for (int l = 0; l < T; ++l) acc[l] = acc2[l] = 0.0;
+        for (int j = threadIdx.x; j < ch.len; j += NT) {
+            F64Sample x;
+            load_f64<HAS_Z>(F, ch.start + j, x);
+#pragma unroll
+            for (int l = 0; l < T; ++l) {
+                const double w = weight_f64<HAS_Z>(x, sl[l]);
+                acc[l] += w;
+                if (ch.inj) acc2[l] = fma(w, w, acc2[l]);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < T; ++l) {
+            double v = acc[l], v2 = acc2[l];
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (ch.inj) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+            }
+            if (lane == 0) {
+                red[warp][l] = v;
+                red2[warp][l] = v2;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < tn) {
+            const int l = threadIdx.x;
+            double s = 0.0, s2 = 0.0;
+            for (int w = 0; w < NT / 32; ++w) {
+                s += red[w][l];
+                s2 += red2[w][l];
+            }
+            part[(k0 + l) * wd.n_chunks + c] = s;
+            if (ch.inj) part2[(k0 + l) * n_inj_chunks + (c - wd.n_ev_chunks)] = s2;
+        }
+    }
+}
+
+template <int T, int NT>
+const void* pick_f64(bool has_z)
+{
+    return has_z ? (const void*)weight_f64_kernel<T, NT, true> : (const void*)weight_f64_kernel<T, NT, false>;
+}
+
+template <int NT>
+const void* pick_f64_t(int T, bool has_z)
+{
+    switch (T) {
+        case 1: return pick_f64<1, NT>(has_z);
+        case 2: return pick_f64<2, NT>(has_z);
+        case 4: return pick_f64<4, NT>(has_z);
+        case 8: return pick_f64<8, NT>(has_z);
+        case 16: return pick_f64<16, NT>(has_z);
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+const void* weight_f64_fn(const Tiling& t, bool has_z)
+{
+    switch (t.block_threads) {
+        case 128: return pick_f64_t<128>(t.lambda_tile, has_z);
+        case 256: return pick_f64_t<256>(t.lambda_tile, has_z);
+        case 512: return pick_f64_t<512>(t.lambda_tile, has_z);
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam,
+                              const int64_t* dK, double* part, double* part2, cudaStream_t s)
+{
+    const void* fn = weight_f64_fn(t, wd.has_z != 0);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, 0, s);
+}
+
+}  // namespace pop
