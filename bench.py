@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--oracle-lambdas", type=int, default=32, help="Lambda rows in the CPU sample")
+    p.add_argument("--events", type=int, default=1000, help="events (a smaller catalog for profiling captures)")
+    p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
+    p.add_argument("--mode", default="both", choices=["both", "f64", "f32"])
     return p.parse_args()
 
 
@@ -215,8 +218,10 @@ def main():
     from paper_1904_02863_gb300 import build
     build.build()
 
-    cat, inj, _ = synth.make_workload(WORKLOAD)
-    K = 1024
+    scale = args.events / 1000.0
+    cat, inj, _ = synth.make_workload(WORKLOAD, scale=scale)
+    workload = WORKLOAD if args.events == 1000 else f"{WORKLOAD}_events{args.events}"
+    K = args.K
     lam = synth.make_lambdas(K, 11, seed=synth.seed_for(2, 2) + 7919 * rank)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -244,49 +249,57 @@ def main():
         ms = max_over_ranks(start.elapsed_time(stop), world)
         return ms, statistics.mean(wms)
 
+    head = B.POP_MODE_F32 if args.mode == "f32" else B.POP_MODE_F64
     with Clocks(local) as clk:
-        ms64, w64 = timed(B.POP_MODE_F64)
-        ms32, w32 = timed(B.POP_MODE_F32)
+        ms_h, w_h = timed(head)
+        if args.mode == "both":
+            ms32, w32 = timed(B.POP_MODE_F32)
 
     # End to end through the public API with pinned host buffers.
     h_lam = torch.from_numpy(lam).pin_memory()
     h_out = [torch.empty(K, dtype=torch.float64).pin_memory() for _ in range(3)] + \
             [torch.empty(K, dtype=torch.int32).pin_memory()]
-    B.pop_loglik(like.ctx, h_lam, B.POP_MODE_F64, out=h_out)
+    B.pop_loglik(like.ctx, h_lam, head, out=h_out)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        B.pop_loglik(like.ctx, h_lam, B.POP_MODE_F64, out=h_out)
+        B.pop_loglik(like.ctx, h_lam, head, out=h_out)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
 
-    n_ev_pairs = cat.offsets[-1] * K
-    n_inj_pairs = inj.n_found * K
-    ops = n_ev_pairs * FP64_OPS_PER_PAIR + n_inj_pairs * FP64_OPS_PER_INJ_PAIR
+    n_ev_pairs = int(cat.offsets[-1]) * K
+    n_inj_pairs = int(inj.n_found) * K
     clocks = clk.summary()
-    peak_tops = FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12  # FP64 pipe ops/s (FMA = 1 op)
-    achieved_tops = ops / (w64 * 1e-3) / 1e12
-    value = world * K * args.steps / (ms64 * 1e-3)
-    value32 = world * K * args.steps / (ms32 * 1e-3)
+    value = world * K * args.steps / (ms_h * 1e-3)
+    if head == B.POP_MODE_F64:
+        ops = n_ev_pairs * FP64_OPS_PER_PAIR + n_inj_pairs * FP64_OPS_PER_INJ_PAIR
+        peak_tops = FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12  # FP64 pipe ops/s (FMA = 1 op)
+        achieved_tops = ops / (w_h * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (FP64 pipe)",
+                    "frac": achieved_tops / peak_tops, "traffic": None, "kernel": "weight_f64_kernel",
+                    "weight_ms": w_h, "ops_per_launch": ops,
+                    "peak_basis": "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz"}
+    else:
+        roofline = {"bound": "alu", "kernel": "weight_f32_kernel", "weight_ms": w_h}
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events": 1000, "samples_per_event": 4096, "n_draw": 10**7,
-                   "n_found": inj.n_found, "K": K, "mode": "POP_MODE_F64", "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (375 MB FP64 features)",
+        "warmup": args.warmup, "ms_per_step": ms_h / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if head == B.POP_MODE_F64 else "f32", "data": "synthetic",
+        "config": {"workload": workload, "events": cat.n_events, "samples_per_event": 4096,
+                   "n_draw": int(inj.n_draw), "n_found": int(inj.n_found), "K": K,
+                   "mode": "POP_MODE_F64" if head == B.POP_MODE_F64 else "POP_MODE_F32",
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (FP64 features 80 B/sample)",
                    "tiling_f64": B.pop_get_tiling(like.ctx, B.POP_MODE_F64),
                    "tiling_f32": B.pop_get_tiling(like.ctx, B.POP_MODE_F32)},
-        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (FP64 pipe)",
-                     "frac": achieved_tops / peak_tops, "traffic": None,
-                     "kernel": "weight_f64_kernel", "weight_ms": w64,
-                     "ops_per_launch": ops, "peak_basis": "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz"},
+        "roofline": roofline,
         "e2e": {"value": world * K * args.steps / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(lam.nbytes), "d2h_bytes_per_step": int(K * (8 * 3 + 4))},
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
-        "forms": {"f32": {"value": value32, "unit": "evals/s", "ms_per_step": ms32 / args.steps,
-                          "weight_ms": w32, "dtype": "f32"}},
     }
+    if args.mode == "both":
+        line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
+                                 "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
     like.close()
