@@ -161,6 +161,44 @@ int pop_set_graphs(pop_ctx* ctx, int enable);
  * (CUDA events around it on the context stream; waits for that call). */
 int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
 
+/* Bytes of the scratch array that pop_loglik_f64_noalloc uses (16 MiB). */
+#define POP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* ln L in FP64 (as pop_loglik with POP_MODE_F64) without allocating anything.
+ *
+ * The paper has no counterpart: this is an interface for callers that cannot
+ * call cudaMalloc — code whose device memory all belongs to an outer pool or
+ * framework, or a sampler loop that must not allocate or free while it runs.
+ * There is no context: the caller passes every input and output as a device
+ * pointer it owns, and the library calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Scratch (per-Lambda constants and per-(Lambda, event)
+ * partial sums) lives in one static device array of POP_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads libpop.so holds until the process exits.
+ *
+ *   device, stream   CUDA device index and cudaStream_t (NULL = legacy stream)
+ *   offsets[n_events+1]  int64 CSR row starts (device); n_samples = offsets[N]
+ *   theta[n_samples * n_dims], prior[n_samples]              (device, as pop_load_events)
+ *   inj_theta[n_found * n_dims], p_draw[n_found], n_draw     (device, as pop_load_injections)
+ *   lambda[K * n_params]                                     (device, as pop_loglik)
+ *   out_lnL, out_lnxi, out_neff (double[K]), out_flags (uint32[K])  (device, all required)
+ *   msg[msg_len]     host buffer for the error text (may be NULL)
+ *
+ * The scratch needed is about K * 8 * (n_events + 2 * ceil(n_found / 4096))
+ * + K * 256 bytes; a call above POP_NOALLOC_SCRATCH_BYTES fails with
+ * POP_EINVAL before any GPU work (split the Lambda batch).  Malformed offsets,
+ * non-finite samples and prior/p_draw <= 0 give POP_EINVAL after the kernels
+ * ran (outputs then undefined).  The call is synchronous: it returns after the
+ * outputs are written.  The first call on a device looks up the array's device
+ * address (module load and symbol lookup), so make that first call before any
+ * stream capture.  All calls share the one array and each call rewrites every
+ * scratch word it reads, so nothing carries over from the previous call; calls
+ * that overlap on the GPU (other threads or streams) race on it. */
+int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events, const int64_t* offsets,
+                           int64_t n_samples, int n_dims, const double* theta, const double* prior,
+                           int64_t n_found, int64_t n_draw, const double* inj_theta, const double* p_draw,
+                           int64_t K, int n_params, const double* lambda, double* out_lnL, double* out_lnxi,
+                           double* out_neff, uint32_t* out_flags, char* msg, int msg_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,9 @@ EXPORTS = (
     "pop_create", "pop_destroy", "pop_last_error", "pop_status_string", "pop_version",
     "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
     "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
+    "pop_loglik_f64_noalloc",
 )
+POP_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class PopError(RuntimeError):
@@ -64,6 +66,8 @@ def load_library(path: str = LIB_PATH):
         "pop_autotune": (i32, [vp, i32, i64, ctypes.c_char_p]),
         "pop_set_graphs": (i32, [vp, i32]),
         "pop_last_kernel_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
+        "pop_loglik_f64_noalloc": (i32, [i32, vp, i64, vp, i64, i32, vp, vp, i64, i64, vp, vp, i64, i32, vp,
+                                         vp, vp, vp, vp, ctypes.c_char_p, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -206,6 +210,26 @@ def pop_last_kernel_ms(ctx):
     w, t = ctypes.c_double(), ctypes.c_double()
     _check(ctx, load_library().pop_last_kernel_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
     return w.value, t.value
+
+
+def pop_loglik_f64_noalloc(offsets, theta, prior, n_draw, inj_theta, p_draw, lambdas, out, device=0, stream=None):
+    """FP64 ln L with no device allocation by the library (see include/pop.h).
+
+    Every argument but ``n_draw`` is a contiguous CUDA tensor the caller owns
+    (offsets int64, the rest float64; ``out`` = (lnL, lnxi, neff, flags int32),
+    each of length K).  Synchronous; raises PopError on failure.
+    """
+    ptr = lambda t, dt: _arg(t, dt)[0]
+    msg = ctypes.create_string_buffer(512)
+    rc = load_library().pop_loglik_f64_noalloc(
+        int(device), _stream_ptr(stream), int(offsets.shape[0]) - 1, ptr(offsets, np.int64), int(theta.shape[0]),
+        int(theta.shape[1]), ptr(theta, np.float64), ptr(prior, np.float64), int(inj_theta.shape[0]), int(n_draw),
+        ptr(inj_theta, np.float64), ptr(p_draw, np.float64), int(lambdas.shape[0]), int(lambdas.shape[1]),
+        ptr(lambdas, np.float64), ptr(out[0], np.float64), ptr(out[1], np.float64), ptr(out[2], np.float64),
+        ptr(out[3], np.uint32), msg, 512)
+    if rc != POP_OK:
+        raise PopError(rc, msg.value.decode())
+    return out
 
 
 # ------------------------------------------------------------------ convenience
