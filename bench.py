@@ -250,6 +250,10 @@ def main():
         return ms, statistics.mean(wms)
 
     head = B.POP_MODE_F32 if args.mode == "f32" else B.POP_MODE_F64
+    # Tiling from the autotuner (FP64 on the first 64 Lambda rows: its launches are long).
+    for mode in ([head] if args.mode != "both" else [B.POP_MODE_F64, B.POP_MODE_F32]):
+        B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+        B.pop_autotune(like.ctx, mode, min(K, 64) if mode == B.POP_MODE_F64 else K)
     with Clocks(local) as clk:
         ms_h, w_h = timed(head)
         if args.mode == "both":

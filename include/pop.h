@@ -161,6 +161,13 @@ int pop_set_graphs(pop_ctx* ctx, int enable);
  * (CUDA events around it on the context stream; waits for that call). */
 int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
 
+/* Diagnostic: evaluate the FP64 weight kernel's own device functions on x[n]
+ * and write y[n] (both in `mem`): fn 0 = exp (Tang's table-driven method,
+ * 2048-entry table; 0 below x = -707, +inf above 709.7), fn 1 = expm1, fn 2 =
+ * reciprocal of a positive normal x (hardware seed + one cubic Newton step).
+ * The test suite checks them against libm and CUDA's functions. */
+int pop_math_check(pop_ctx* ctx, int fn, int64_t n, const double* x, double* y, int mem);
+
 /* Bytes of the scratch array that pop_loglik_f64_noalloc uses (16 MiB). */
 #define POP_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "pop_create", "pop_destroy", "pop_last_error", "pop_status_string", "pop_version",
     "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
     "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
-    "pop_loglik_f64_noalloc",
+    "pop_loglik_f64_noalloc", "pop_math_check",
 )
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "pop_last_kernel_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
         "pop_loglik_f64_noalloc": (i32, [i32, vp, i64, vp, i64, i32, vp, vp, i64, i64, vp, vp, i64, i32, vp,
                                          vp, vp, vp, vp, ctypes.c_char_p, i32]),
+        "pop_math_check": (i32, [vp, i32, i64, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +211,15 @@ def pop_last_kernel_ms(ctx):
     w, t = ctypes.c_double(), ctypes.c_double()
     _check(ctx, load_library().pop_last_kernel_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
     return w.value, t.value
+
+
+def pop_math_check(ctx, fn, x):
+    """The FP64 kernel's exp (0), expm1 (1) or reciprocal (2) evaluated on the GPU."""
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(xa)
+    _check(ctx, load_library().pop_math_check(ctx, int(fn), xa.size, xa.ctypes.data_as(ctypes.c_void_p),
+                                              y.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST))
+    return y
 
 
 def pop_loglik_f64_noalloc(offsets, theta, prior, n_draw, inj_theta, p_draw, lambdas, out, device=0, stream=None):

@@ -122,6 +122,8 @@ struct pop_ctx {
     bool use_graphs = true;
     Graph graph[2];
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
+    DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
+    ExpConsts expc{};
     bool timed = false;
     int64_t last_K = 0;
     int last_params = 0;
@@ -274,7 +276,8 @@ int grid_size(pop_ctx* c, int mode)
     const Tiling& t = c->tiling[mode];
     const void* fn = mode == POP_MODE_F64 ? weight_f64_fn(t, c->ev.n_dims == 7) : weight_f32_fn(t, c->ev.n_dims == 7);
     int occ = 0;
-    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t.block_threads, 0) != cudaSuccess) occ = 1;
+    const int dyn = mode == POP_MODE_F64 ? WEIGHT_F64_DYN_SMEM : 0;
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t.block_threads, dyn) != cudaSuccess) occ = 1;
     if (t.blocks_per_sm > 0) occ = std::min(occ, t.blocks_per_sm);
     return std::max(1, occ) * c->sm_count;
 }
@@ -294,7 +297,8 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     if (m == 0) {
         FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
         CK(launch_weight_f64(c->tiling[0], grid, e, j, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
-                             c->d_part.as<double>(), c->d_part2.as<double>(), c->stream), "weight_f64");
+                             c->d_part.as<double>(), c->d_part2.as<double>(), c->d_exptab.as<double2>(), c->expc,
+                             c->stream), "weight_f64");
     } else {
         FeatF32 e{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
         FeatF32 j{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
@@ -351,8 +355,58 @@ bool tiling_ok(int mode, const Tiling& t)
 
 }  // namespace
 
+namespace pop {
+
+// Tang's table: T_j = 2^(j/2048) = hi + lo, and ln2/2048 = l_hi + l_lo with l_hi
+// holding 31 significant bits, all from long double (extended or quad) arithmetic.
+void build_exp_table(double2* tab, ExpConsts* kc)
+{
+    for (int j = 0; j < EXP_TABLE_SIZE; ++j) {
+        const long double v = exp2l((long double)j / EXP_TABLE_SIZE);
+        const double hi = (double)v;
+        tab[j] = make_double2(hi, (double)(v - (long double)hi));
+    }
+    const long double ln2 = logl(2.0L);
+    const long double L = ln2 / EXP_TABLE_SIZE;
+    double l_hi = (double)L;
+    uint64_t bits;
+    memcpy(&bits, &l_hi, sizeof bits);
+    bits &= ~((1ull << 22) - 1);  // keep 31 significant bits: kd * l_hi is exact for |kd| < 2^21
+    memcpy(&l_hi, &bits, sizeof bits);
+    kc->inv_l = (double)(EXP_TABLE_SIZE / ln2);
+    kc->l_hi = l_hi;
+    kc->l_lo = (double)(L - (long double)l_hi);
+}
+
+}  // namespace pop
+
 // ============================================================== C-ABI
 extern "C" {
+
+int pop_math_check(pop_ctx* c, int fn, int64_t n, const double* x, double* y, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y)) || !valid_mem(mem))
+        return fail(c, POP_EINVAL, "pop_math_check: bad arguments");
+    if (n == 0) return POP_OK;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const double* dx = x;
+    double* dy = y;
+    DevBuf bx, by;
+    if (mem == POP_MEM_HOST) {
+        CK(bx.alloc(sizeof(double) * n), "cudaMalloc");
+        CK(by.alloc(sizeof(double) * n), "cudaMalloc");
+        CK(cudaMemcpyAsync(bx.p, x, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "copy x");
+        dx = bx.as<double>();
+        dy = by.as<double>();
+    }
+    CK(launch_math_check(fn, n, dx, dy, c->d_exptab.as<double2>(), c->expc, c->stream), "math_check");
+    if (mem == POP_MEM_HOST) {
+        CK(cudaMemcpyAsync(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "copy y");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+    }
+    return POP_OK;
+}
 
 int pop_version(void) { return 10000; }
 
@@ -403,6 +457,18 @@ int pop_create(pop_ctx** out, int device, void* stream)
     }
     c->sm_count = prop.multiProcessorCount;
     c->device_name = prop.name;
+    {
+        std::vector<double2> tab(EXP_TABLE_SIZE);
+        build_exp_table(tab.data(), &c->expc);
+        e = c->d_exptab.alloc(sizeof(double2) * EXP_TABLE_SIZE);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_exptab.p, tab.data(), sizeof(double2) * EXP_TABLE_SIZE, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            pop_destroy(c);
+            return fail(nullptr, e == cudaErrorMemoryAllocation ? POP_ENOMEM : POP_ECUDA,
+                        std::string("pop_create: ") + cudaGetErrorString(e));
+        }
+    }
     cudaEvent_t* evs[] = {&c->ev_t0, &c->ev_w0, &c->ev_w1, &c->ev_t1};
     for (cudaEvent_t* ev : evs) {
         e = cudaEventCreate(ev);
@@ -645,7 +711,8 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
                 if (mode == POP_MODE_F64) {
                     FeatF64 ev{c->ev.f64.as<double>(), c->ev.stride}, ij{c->inj.f64.as<double>(), c->inj.stride};
                     e = launch_weight_f64(t, grid, ev, ij, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
-                                          c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
+                                          c->d_part.as<double>(), c->d_part2.as<double>(),
+                                          c->d_exptab.as<double2>(), c->expc, c->stream);
                 } else {
                     FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
                     FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};

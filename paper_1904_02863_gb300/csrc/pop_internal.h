@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "pop.h"
+#include "pop_math.cuh"
 
 namespace pop {
 
@@ -104,9 +105,16 @@ cudaError_t launch_pack_f32(const double* theta, const double* prior, int64_t n,
                             float* feat, double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params,
                             LamF64* c64, LamF32* c32, cudaStream_t s);
+// The FP64 weight kernel keeps the 2^(j/2048) table of its exponentials in dynamic shared memory.
+constexpr int WEIGHT_F64_DYN_SMEM = EXP_TABLE_SIZE * (int)sizeof(double2);
 cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd,
                               const LamF64* lam, const int64_t* dK, double* part, double* part2,
+                              const double2* exptab, ExpConsts kc, cudaStream_t s);
+// Evaluates the FP64 weight kernel's exp (fn 0), expm1 (fn 1) or reciprocal (fn 2) on x[n].
+cudaError_t launch_math_check(int fn, int64_t n, const double* x, double* y, const double2* exptab, ExpConsts kc,
                               cudaStream_t s);
+// Host: the 2^(j/2048) table (hi, lo) and the reduction constants, in extended precision.
+void build_exp_table(double2* tab, ExpConsts* kc);
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
                               const LamF32* lam, const int64_t* dK, double* part, double* part2,
                               cudaStream_t s);

@@ -1,0 +1,99 @@
+// FP64 exponential, expm1 and reciprocal for the FP64 weight kernel.
+//
+// GB300 runs FP64 at 2 FMA lanes per SM per clock (1/64 of FP32), so the
+// weight kernel is bound by the number of FP64 instructions per pair; these
+// versions use as few as the accuracy allows and push the rest (table lookup,
+// exponent scaling, range tests) onto the integer and load pipes.
+//
+// exp / expm1: P. T. P. Tang, "Table-driven implementation of the exponential
+// function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157.
+// x is written as (2048 m + j) ln2/2048 + r with |r| <= ln2/4096, so
+// exp(x) = 2^m 2^(j/2048) e^r; 2^(j/2048) comes from a 2048-entry table held as
+// hi + lo doubles (built on the host in extended precision), e^r - 1 from its
+// Taylor series to r^3 for exp (truncation r^4/24 < 4e-17 of a result near 1)
+// and to r^4 for expm1 (whose result can be as small as r).  The reduction constant
+// ln2/2048 is split in a hi part with trailing zero bits (so kd * L_HI is exact
+// for |kd| < 2^21) and a lo part.
+//
+// exp(x) for x < -707 (results below ~1e-307) is returned as 0, and above 709.7 as +inf.
+#pragma once
+
+#include <stdint.h>
+
+namespace pop {
+
+constexpr int EXP_TABLE_BITS = 11;
+constexpr int EXP_TABLE_SIZE = 1 << EXP_TABLE_BITS;   // 2048 entries of (hi, lo)
+
+constexpr double EXP_SHIFTER = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
+
+// Reduction constants (computed once on the host from long double ln 2).
+struct ExpConsts {
+    double inv_l;   // 2048 / ln 2
+    double l_hi;    // ln 2 / 2048 rounded to 31 significant bits
+    double l_lo;    // ln 2 / 2048 - l_hi
+};
+
+// Arguments whose result (and 2^m scaling) stays a normal double.
+constexpr double EXP_X_MIN = -707.0;
+constexpr double EXP_X_MAX = 709.7;
+
+__device__ __forceinline__ int64_t bits_of(double x) { return __double_as_longlong(x); }
+
+// exp(x).  tab = [hi, lo] pairs in shared memory.
+__device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ tab, const ExpConsts& k)
+{
+    // Range tests on bit patterns (integer pipe): x < EXP_X_MIN or x > EXP_X_MAX (or -inf/+inf).
+    const int64_t b = bits_of(x);
+    const bool under = (uint64_t)b > (uint64_t)bits_of(EXP_X_MIN);  // negative and below the range
+    const bool over = b > bits_of(EXP_X_MAX);                         // positive and above the range
+    const double xs = (under | over) ? 0.0 : x;
+    const double t = fma(xs, k.inv_l, EXP_SHIFTER);
+    const int n = __double2loint(t);
+    const double kd = t - EXP_SHIFTER;
+    double r = fma(kd, -k.l_hi, xs);
+    r = fma(kd, -k.l_lo, r);
+    const double p = fma(fma(r, 1.0 / 6.0, 0.5), r * r, r);  // e^r - 1
+    const double2 tj = tab[n & (EXP_TABLE_SIZE - 1)];
+    const double res = tj.x + fma(tj.x, p, tj.y);            // 2^(j/2048) e^r in [0.99, 2.01)
+    const int m = n >> EXP_TABLE_BITS;                       // arithmetic shift: floor
+    const double scaled = __hiloint2double(__double2hiint(res) + (int)((unsigned)m << 20), __double2loint(res));
+    return under ? 0.0 : (over ? __longlong_as_double(0x7ff0000000000000LL) : scaled);
+}
+
+// expm1(u) for EXP_X_MIN <= u <= EXP_X_MAX: (2^m T_hi - 1) + 2^m (T_hi p + T_lo).  When m = j = 0
+// this is p itself, so tiny arguments keep full relative accuracy; 2^m T_hi - 1 is exact when
+// 2^m T_hi is within a factor of two of 1.
+__device__ __forceinline__ double expm1_tab(double u, const double2* __restrict__ tab, const ExpConsts& k)
+{
+    const int64_t b = bits_of(u);
+    const bool under = (uint64_t)b > (uint64_t)bits_of(EXP_X_MIN);
+    const bool over = b > bits_of(EXP_X_MAX);
+    const double us = (under | over) ? 0.0 : u;
+    const double t = fma(us, k.inv_l, EXP_SHIFTER);
+    const int n = __double2loint(t);
+    const double kd = t - EXP_SHIFTER;
+    double r = fma(kd, -k.l_hi, us);
+    r = fma(kd, -k.l_lo, r);
+    // To r^4 here: near the first table steps the result is as small as ~1.7e-4, so the
+    // truncation must be small relative to r, not to 1 (r^5/120 / r < 1e-17).
+    const double p = fma(fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5), r * r, r);
+    const double2 tj = tab[n & (EXP_TABLE_SIZE - 1)];
+    const int m = n >> EXP_TABLE_BITS;
+    const double s = __hiloint2double(__double2hiint(tj.x) + (int)((unsigned)m << 20), __double2loint(tj.x));
+    const double sc = __hiloint2double((m + 1023) << 20, 0);                                     // 2^m
+    const double res = fma(fma(tj.x, p, tj.y), sc, s - 1.0);
+    return under ? -1.0 : (over ? __longlong_as_double(0x7ff0000000000000LL) : res);
+}
+
+// 1/d for positive normal d: the hardware seed (rcp.approx.ftz.f64) refined by one cubic
+// Newton step y = y0 (1 + e + e^2), e = 1 - d y0 (error e^3).
+__device__ __forceinline__ double rcp_pos(double d)
+{
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(d));
+    const double e = fma(-d, y0, 1.0);
+    return fma(fma(e, e, e), y0, y0);
+}
+
+}  // namespace pop

@@ -2,14 +2,15 @@
 //
 // Same work decomposition as the FP64 kernel (persistent grid over
 // chunk x Lambda-tile items, features in registers, Lambda constants in shared
-// memory).  The features and constants are in base-2 log units so every
-// exponential is one ex2.approx (MUFU) and the q normalisation's reciprocal is
-// one rcp.approx.  Per (thread, Lambda) the weights are summed with Kahan
-// compensation; warps combine the (sum, compensation) pairs with an error-free
-// two-sum; only the per-warp results are widened to FP64, summed across warps
-// in a fixed order and written as FP64 partials.  The per-Lambda constants come
-// from the FP64 prologue; the per-event log and the cross-event sum are FP64
-// in the finalise kernel.
+// memory).  Each thread takes two samples per step, so one read of a Lambda's
+// constants serves two weights and the two dependency chains overlap.  The
+// features and constants are in base-2 log units so every exponential is one
+// ex2.approx (MUFU) and the q normalisation's reciprocal one rcp.approx.  Per
+// (thread, Lambda) the weights are summed with Kahan compensation; warps and
+// then the block combine the (sum, compensation) pairs with an error-free
+// two-sum, and one thread per Lambda widens the block result to FP64 for the
+// partial.  The per-Lambda constants come from the FP64 prologue; the
+// per-event log and the cross-event sum are FP64 in the finalise kernel.
 #include <math.h>
 
 #include "pop_internal.h"
@@ -33,22 +34,27 @@ __device__ __forceinline__ float rcpf(float x)
 }
 
 // 2^u - 1.  ex2(u) - 1 loses relative accuracy as u -> 0, so |u| < 1/8 uses
-// the Taylor series of e^x - 1 in x = u ln 2 to fifth order (truncation
-// below 5e-7 relative there).
+// the Taylor series of e^x - 1 in x = u ln 2 to fifth order (truncation below
+// 1e-8 relative there).  The series is evaluated only in warps where some lane
+// needs it (samples within a few percent of mmin).
 __device__ __forceinline__ float exp2m1f(float u)
 {
-    constexpr float c1 = 0.693147180559945f;   // ln2
-    constexpr float c2 = 0.240226506959101f;   // ln2^2 / 2
-    constexpr float c3 = 0.0555041086648216f;  // ln2^3 / 6
-    constexpr float c4 = 0.00961812910762848f; // ln2^4 / 24
-    constexpr float c5 = 0.00133335581464284f; // ln2^5 / 120
-    float p = fmaf(c5, u, c4);
-    p = fmaf(p, u, c3);
-    p = fmaf(p, u, c2);
-    p = fmaf(p, u, c1);
-    p *= u;
-    const float e = ex2f(u) - 1.0f;
-    return fabsf(u) < 0.125f ? p : e;
+    constexpr float c1 = 0.693147180559945f;    // ln2
+    constexpr float c2 = 0.240226506959101f;    // ln2^2 / 2
+    constexpr float c3 = 0.0555041086648216f;   // ln2^3 / 6
+    constexpr float c4 = 0.00961812910762848f;  // ln2^4 / 24
+    constexpr float c5 = 0.00133335581464284f;  // ln2^5 / 120
+    float e = ex2f(u) - 1.0f;
+    const bool small = fabsf(u) < 0.125f;
+    if (__any_sync(0xffffffffu, small)) {
+        float p = fmaf(c5, u, c4);
+        p = fmaf(p, u, c3);
+        p = fmaf(p, u, c2);
+        p = fmaf(p, u, c1);
+        p *= u;
+        e = small ? p : e;
+    }
+    return e;
 }
 
 struct F32Sample {
@@ -71,6 +77,13 @@ __device__ __forceinline__ void load_f32(const FeatF32& F, int64_t s, F32Sample&
     x.lz1 = HAS_Z ? __ldg(b + F_LZ1 * st + s) : 0.0f;
     x.lm1lo = __ldg(b + F32_LM1LO * st + s);
     x.m2b = __double_as_longlong(__ldg(F.m2 + s));
+}
+
+// A sample outside every support (m1 = 0): weight 0 for any Lambda.
+__device__ __forceinline__ void dead_f32(F32Sample& x)
+{
+    x.lm1 = x.m1 = x.lq = x.sa = x.sb = x.dc = x.nlpi = x.lz1 = x.lm1lo = 0.0f;
+    x.m2b = 0;
 }
 
 template <bool HAS_Z>
@@ -101,17 +114,22 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float w)
     s = t;
 }
 
-// Combine (s, c) pairs (value s - c) across the warp with an error-free two-sum.
+// (s, c) += (s2, c2) for compensated pairs of value s - c (error-free two-sum of the sums).
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2)
+{
+    const float S = s + s2;
+    const float bp = S - s;
+    const float e = (s - (S - bp)) + (s2 - bp);
+    c = (c + c2) - e;
+    s = S;
+}
+
 __device__ __forceinline__ void warp_combine(float& s, float& c)
 {
     for (int o = 16; o > 0; o >>= 1) {
         const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
         const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-        const float S = s + s2;
-        const float bp = S - s;
-        const float e = (s - (S - bp)) + (s2 - bp);
-        c = (c + c2) - e;
-        s = S;
+        pair_add(s, c, s2, c2);
     }
 }
 
@@ -120,9 +138,9 @@ __global__ void __launch_bounds__(NT)
 weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
                   const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
 {
+    constexpr int NW = NT / 32;
     __shared__ LamF32 sl[T];
-    __shared__ double red[NT / 32][T];
-    __shared__ double red2[NT / 32][T];
+    __shared__ float rs[NW][T], rc[NW][T], rs2[NW][T], rc2[NW][T];
     const int64_t K = *dK;
     const int64_t n_tiles = (K + T - 1) / T;
     const int64_t n_items = (int64_t)wd.n_chunks * n_tiles;
@@ -149,14 +167,22 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
         float s[T], cp[T], s2[T], cp2[T];
 #pragma unroll
         for (int l = 0; l < T; ++l) s[l] = cp[l] = s2[l] = cp2[l] = 0.0f;
-        for (int j = threadIdx.x; j < ch.len; j += NT) {
-            F32Sample x;
-            load_f32<HAS_Z>(F, ch.start + j, x);
+        // Every thread runs the same number of steps (slots past the end are dead
+        // samples), so all 32 lanes reach the warp vote inside exp2m1f together.
+        for (int base = 0; base < ch.len; base += 2 * NT) {
+            const int j = base + threadIdx.x;
+            F32Sample x0, x1;
+            if (j < ch.len) load_f32<HAS_Z>(F, ch.start + j, x0);
+            else dead_f32(x0);
+            if (j + NT < ch.len) load_f32<HAS_Z>(F, ch.start + j + NT, x1);
+            else dead_f32(x1);
 #pragma unroll
             for (int l = 0; l < T; ++l) {
-                const float w = weight_f32<HAS_Z>(x, sl[l]);
-                kahan_add(s[l], cp[l], w);
-                if (ch.inj) kahan_add(s2[l], cp2[l], w * w);
+                const LamF32 cl = sl[l];
+                const float w0 = weight_f32<HAS_Z>(x0, cl);
+                const float w1 = weight_f32<HAS_Z>(x1, cl);
+                kahan_add(s[l], cp[l], w0 + w1);
+                if (ch.inj) kahan_add(s2[l], cp2[l], fmaf(w0, w0, w1 * w1));
             }
         }
 #pragma unroll
@@ -164,20 +190,22 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
             warp_combine(s[l], cp[l]);
             if (ch.inj) warp_combine(s2[l], cp2[l]);
             if (lane == 0) {
-                red[warp][l] = (double)s[l] - (double)cp[l];
-                red2[warp][l] = (double)s2[l] - (double)cp2[l];
+                rs[warp][l] = s[l];
+                rc[warp][l] = cp[l];
+                rs2[warp][l] = s2[l];
+                rc2[warp][l] = cp2[l];
             }
         }
         __syncthreads();
-        if (threadIdx.x < tn) {
+        if (threadIdx.x < tn) {  // one thread per Lambda, all in warp 0
             const int l = threadIdx.x;
-            double a = 0.0, a2 = 0.0;
-            for (int w = 0; w < NT / 32; ++w) {
-                a += red[w][l];
-                a2 += red2[w][l];
+            float a = rs[0][l], ac = rc[0][l], b = rs2[0][l], bc = rc2[0][l];
+            for (int w = 1; w < NW; ++w) {
+                pair_add(a, ac, rs[w][l], rc[w][l]);
+                pair_add(b, bc, rs2[w][l], rc2[w][l]);
             }
-            part[(k0 + l) * wd.n_chunks + c] = a;
-            if (ch.inj) part2[(k0 + l) * n_inj_chunks + (c - wd.n_ev_chunks)] = a2;
+            part[(k0 + l) * wd.n_chunks + c] = (double)a - (double)ac;
+            if (ch.inj) part2[(k0 + l) * n_inj_chunks + (c - wd.n_ev_chunks)] = (double)b - (double)bc;
         }
     }
 }

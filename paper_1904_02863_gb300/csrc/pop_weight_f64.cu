@@ -16,6 +16,8 @@
 //          [+ (kappa-1) ln(1+z)], and every Lambda-only factor folded into cpl, cg, ct.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pop_internal.h"
 
 namespace pop {
@@ -68,7 +70,8 @@ __device__ __forceinline__ void load_f64(const FeatF64& F, int64_t s, F64Sample&
 }
 
 template <bool HAS_Z>
-__device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c)
+__device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c, const double2* __restrict__ tab,
+                                             const ExpConsts& kc)
 {
     // Support: mmin < m1 <= mmax and fl64(q m1) >= mmin, compared on bit patterns.
     const bool in = (x.m1b > c.mmin_bits) & (x.m1b <= c.mmax_bits) & (x.m2b >= c.mmin_bits);
@@ -76,28 +79,38 @@ __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c
     aE = fma(c.ac, x.sa, aE);
     aE = fma(c.bc, x.sb, aE);
     if (HAS_Z) aE = fma(c.km1, x.lz1, aE);
-    const double e1 = exp(fma(c.nalpha, x.lm1, aE + c.cpl));
+    const double e1 = exp_tab(fma(c.nalpha, x.lm1, aE + c.cpl), tab, kc);
     const double d = x.m1 - c.mu;
-    const double e2 = exp(fma(c.nh * d, d, aE + c.cg));
+    const double e2 = exp_tab(fma(c.nh * d, d, aE + c.cg), tab, kc);
     // ln(mmin/m1) for the q normalisation.  Within ~3% of the lower edge the
     // log difference would cancel, so it is log1p((mmin - m1)/m1) by its series
     // (mmin - m1 is exact there); the test runs on bit patterns (integer pipe).
     double lr = c.lmmin - x.lm1;
     if (llabs(x.m1b - c.mmin_bits) < NEAR_EDGE_BITS) lr = log1p_near0(x.invm1 * (c.mmin - x.m1));
-    const double den = c.beta_m1 ? -lr : fabs(expm1(c.b1 * lr));
-    const double tt = c.t0 + exp(fma(c.nht, x.dc, c.ct));
-    const double w = (e1 + e2) * tt / den;
+    const double den = c.beta_m1 ? -lr : fabs(expm1_tab(c.b1 * lr, tab, kc));
+    const double tt = c.t0 + exp_tab(fma(c.nht, x.dc, c.ct), tab, kc);
+    const double w = (e1 + e2) * tt * rcp_pos(den);
     return in ? w : 0.0;
+}
+
+// Copies the 2^(j/2048) table into shared memory (once per block of the persistent grid).
+template <int NT>
+__device__ __forceinline__ void load_table(double2* dst, const double2* __restrict__ src)
+{
+    for (int i = threadIdx.x; i < EXP_TABLE_SIZE; i += NT) dst[i] = src[i];
 }
 
 template <int T, int NT, bool HAS_Z>
 __global__ void __launch_bounds__(NT)
 weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict__ lam,
-                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
+                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2,
+                  const double2* __restrict__ exptab, ExpConsts kc)
 {
+    extern __shared__ double2 stab[];  // EXP_TABLE_SIZE entries (dynamic shared memory)
     __shared__ LamF64 sl[T];
     __shared__ double red[NT / 32][T];
     __shared__ double red2[NT / 32][T];
+    load_table<NT>(stab, exptab);
     const int64_t K = *dK;
     const int64_t n_tiles = (K + T - 1) / T;
     const int64_t n_items = (int64_t)wd.n_chunks * n_tiles;
@@ -129,7 +142,7 @@ weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict
             load_f64<HAS_Z>(F, ch.start + j, x);
 #pragma unroll
             for (int l = 0; l < T; ++l) {
-                const double w = weight_f64<HAS_Z>(x, sl[l]);
+                const double w = weight_f64<HAS_Z>(x, sl[l], stab, kc);
                 acc[l] += w;
                 if (ch.inj) acc2[l] = fma(w, w, acc2[l]);
             }
@@ -192,12 +205,36 @@ const void* weight_f64_fn(const Tiling& t, bool has_z)
 }
 
 cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam,
-                              const int64_t* dK, double* part, double* part2, cudaStream_t s)
+                              const int64_t* dK, double* part, double* part2, const double2* exptab,
+                              ExpConsts kc, cudaStream_t s)
 {
     const void* fn = weight_f64_fn(t, wd.has_z != 0);
     if (!fn) return cudaErrorInvalidValue;
-    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, 0, s);
+    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2, &exptab, &kc};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, WEIGHT_F64_DYN_SMEM, s);
+}
+
+namespace {
+
+__global__ void math_check_kernel(int fn, int64_t n, const double* __restrict__ x, double* __restrict__ y,
+                                  const double2* __restrict__ exptab, ExpConsts kc)
+{
+    extern __shared__ double2 stab[];
+    load_table<256>(stab, exptab);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fn == 0 ? exp_tab(x[i], stab, kc) : (fn == 1 ? expm1_tab(x[i], stab, kc) : rcp_pos(x[i]));
+}
+
+}  // namespace
+
+cudaError_t launch_math_check(int fn, int64_t n, const double* x, double* y, const double2* exptab, ExpConsts kc,
+                              cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    math_check_kernel<<<(unsigned)blocks, 256, WEIGHT_F64_DYN_SMEM, s>>>(fn, n, x, y, exptab, kc);
+    return cudaGetLastError();
 }
 
 }  // namespace pop

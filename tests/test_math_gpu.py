@@ -1,0 +1,72 @@
+"""The FP64 weight kernel's own exp, expm1 and reciprocal (Tang's table-driven
+exponential; seeded Newton reciprocal) against the host's libm (numpy), against
+CUDA's own exp (torch on the GPU), and against their error bounds."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1904_02863_gb300 import binding as B
+    from paper_1904_02863_gb300 import build
+    build.build()
+    c = B.pop_create(0)
+    yield c
+    B.pop_destroy(c)
+
+
+def ulps(a, b):
+    """|a - b| in units of the last place of b."""
+    return np.abs(a - b) / np.spacing(np.abs(b))
+
+
+def test_exp_within_one_ulp_of_libm(ctx):
+    from paper_1904_02863_gb300 import binding as B
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-700, 709, 200000), rng.uniform(-1, 1, 100000),
+                        rng.uniform(-1e-6, 1e-6, 20000), np.arange(-40, 41) * np.log(2) / 2048,
+                        [0.0, -0.0, 1e-300, -1e-300, 709.5, -706.9]])
+    y = B.pop_math_check(ctx, 0, x)
+    assert np.max(ulps(y, np.exp(x))) <= 1.0
+
+
+def test_exp_against_cuda_exp(ctx):
+    import torch
+    from paper_1904_02863_gb300 import binding as B
+    x = np.random.default_rng(2).uniform(-50, 50, 100000)
+    y = B.pop_math_check(ctx, 0, x)
+    ref = torch.exp(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.max(ulps(y, ref)) <= 2.0
+
+
+def test_exp_range_ends(ctx):
+    from paper_1904_02863_gb300 import binding as B
+    x = np.array([-707.5, -1e30, -np.inf, 710.0, 1e30, np.inf])
+    y = B.pop_math_check(ctx, 0, x)
+    np.testing.assert_array_equal(y, [0.0, 0.0, 0.0, np.inf, np.inf, np.inf])
+
+
+def test_expm1_relative_accuracy(ctx):
+    from paper_1904_02863_gb300 import binding as B
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-20, 5, 200000), rng.uniform(-1e-3, 1e-3, 100000),
+                        -np.logspace(-300, 1, 5000), np.logspace(-300, 1, 5000), [0.0]])
+    y = B.pop_math_check(ctx, 1, x)
+    ref = np.expm1(x)
+    nz = ref != 0
+    assert np.max(ulps(y[nz], ref[nz])) <= 2.0
+    assert y[~nz].tolist() == [0.0] * int((~nz).sum())
+    assert B.pop_math_check(ctx, 1, np.array([-800.0]))[0] == -1.0
+
+
+def test_reciprocal_correct_to_half_ulp_bound(ctx):
+    from paper_1904_02863_gb300 import binding as B
+    rng = np.random.default_rng(4)
+    x = np.concatenate([10 ** rng.uniform(-300, 300, 200000), rng.uniform(1e-3, 10, 100000)])
+    y = B.pop_math_check(ctx, 2, x)
+    assert np.max(ulps(y, 1.0 / x)) <= 1.0
