@@ -49,6 +49,25 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 
 
+def in_support_pairs(theta, lam):
+    """(sample, Lambda) pairs inside the support (mmin < m1 <= mmax, fl64(q m1) >= mmin).
+
+    Only those carry algorithmic work: outside the support the weight is 0 by
+    definition and no density is evaluated.  Exact count, per Lambda.
+    """
+    m1 = theta[:, 0]
+    m2 = theta[:, 1] * theta[:, 0]
+    m2s = np.sort(m2)
+    mmin, mmax = lam[:, 2], lam[:, 3]
+    total = int((len(m2s) - np.searchsorted(m2s, mmin, side="left")).sum())
+    # remove m1 > mmax (the few high-mass samples) and m1 <= mmin with m2 >= mmin (q = 1 ties)
+    hi = m1 > mmax.min()
+    total -= int(((m2[hi, None] >= mmin[None, :]) & (m1[hi, None] > mmax[None, :])).sum())
+    tie = m2 >= m1
+    total -= int(((m2[tie, None] >= mmin[None, :]) & (m1[tie, None] <= mmin[None, :])).sum())
+    return total
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -270,8 +289,9 @@ def main():
         B.pop_loglik(like.ctx, h_lam, head, out=h_out)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
 
-    n_ev_pairs = int(cat.offsets[-1]) * K
-    n_inj_pairs = int(inj.n_found) * K
+    n_ev_pairs = in_support_pairs(cat.theta, lam)
+    n_inj_pairs = in_support_pairs(inj.theta, lam)
+    all_pairs = (int(cat.offsets[-1]) + int(inj.n_found)) * K
     clocks = clk.summary()
     value = world * K * args.steps / (ms_h * 1e-3)
     if head == B.POP_MODE_F64:
@@ -281,6 +301,8 @@ def main():
         roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (FP64 pipe)",
                     "frac": achieved_tops / peak_tops, "traffic": None, "kernel": "weight_f64_kernel",
                     "weight_ms": w_h, "ops_per_launch": ops,
+                    "in_support_pairs": n_ev_pairs + n_inj_pairs, "all_pairs": all_pairs,
+                    "ops_per_in_support_pair": FP64_OPS_PER_PAIR,
                     "peak_basis": "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz"}
     else:
         roofline = {"bound": "alu", "kernel": "weight_f32_kernel", "weight_ms": w_h}

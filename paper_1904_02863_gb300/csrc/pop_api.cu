@@ -157,9 +157,29 @@ cudaMemcpyKind out_kind(int mem) { return mem == POP_MEM_HOST ? cudaMemcpyDevice
 
 __global__ void set_k_kernel(int64_t* dK, int64_t K) { *dK = K; }
 
-// Pack theta/prior (host or device) into a new SampleSet.
+// Load-time order of the samples: within every segment [seg[s], seg[s+1]) the
+// samples are sorted by m2 = q m1.  The lower support edge is exactly
+// m2 >= mmin, so for any Lambda the samples below it are contiguous and whole
+// warps of them skip the weight arithmetic.  Sums over a segment do not
+// depend on the order (beyond rounding).
+std::vector<int64_t> support_order(const double* theta, int64_t n, int n_dims, const std::vector<int64_t>& seg)
+{
+    std::vector<double> key(n);
+    for (int64_t j = 0; j < n; ++j) {
+        const double m2 = theta[j * n_dims + 1] * theta[j * n_dims];
+        key[j] = std::isnan(m2) ? INFINITY : m2;  // malformed rows are rejected later by the pack kernel
+    }
+    std::vector<int64_t> perm(n);
+    for (int64_t j = 0; j < n; ++j) perm[j] = j;
+    for (size_t s = 0; s + 1 < seg.size(); ++s)
+        std::stable_sort(perm.begin() + seg[s], perm.begin() + seg[s + 1],
+                         [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+    return perm;
+}
+
+// Pack theta/prior (host or device) into a new SampleSet, in support_order.
 int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const double* prior, int storage,
-                 int mem, SampleSet& out, const char* what)
+                 int mem, SampleSet& out, const char* what, const std::vector<int64_t>& seg)
 {
     out.n = n;
     out.n_dims = n_dims;
@@ -167,7 +187,23 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     out.stride = round_up(std::max<int64_t>(n, 1), ALIGN_ELEMS);
     const double* th = theta;
     const double* pr = prior;
-    DevBuf tmp_th, tmp_pr, bad;
+    DevBuf tmp_th, tmp_pr, bad, dperm;
+    {
+        std::vector<double> host_th;
+        const double* hth = theta;
+        if (mem == POP_MEM_DEVICE) {
+            host_th.resize((size_t)n * n_dims);
+            CK(cudaMemcpyAsync(host_th.data(), theta, sizeof(double) * n * n_dims, cudaMemcpyDeviceToHost,
+                               c->stream), "copy theta to host");
+            CK(cudaStreamSynchronize(c->stream), "sync");
+            hth = host_th.data();
+        }
+        const std::vector<int64_t> perm = support_order(hth, n, n_dims, seg);
+        CK(dperm.alloc(sizeof(int64_t) * std::max<int64_t>(n, 1)), "cudaMalloc(order)");
+        CK(cudaMemcpyAsync(dperm.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream),
+           "copy order");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+    }
     if (mem == POP_MEM_HOST) {
         CK(tmp_th.alloc(sizeof(double) * n * n_dims), "cudaMalloc(theta staging)");
         CK(tmp_pr.alloc(sizeof(double) * n), "cudaMalloc(prior staging)");
@@ -181,13 +217,15 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned long long), c->stream), "memset");
     if (storage & POP_STORE_F64) {
         CK(out.f64.alloc(sizeof(double) * F_COUNT64 * out.stride), "cudaMalloc(f64 features)");
-        CK(launch_pack_f64(th, pr, n, n_dims, out.f64.as<double>(), out.stride, bad.as<unsigned long long>(),
+        CK(launch_pack_f64(th, pr, dperm.as<int64_t>(), n, n_dims, out.f64.as<double>(), out.stride,
+                           bad.as<unsigned long long>(),
                            c->stream), "pack_f64");
     }
     if (storage & POP_STORE_F32) {
         CK(out.f32.alloc(sizeof(float) * F_COUNT32 * out.stride), "cudaMalloc(f32 features)");
         CK(out.m2.alloc(sizeof(double) * out.stride), "cudaMalloc(m2)");
-        CK(launch_pack_f32(th, pr, n, n_dims, out.f32.as<float>(), out.m2.as<double>(), out.stride,
+        CK(launch_pack_f32(th, pr, dperm.as<int64_t>(), n, n_dims, out.f32.as<float>(), out.m2.as<double>(),
+                           out.stride,
                            bad.as<unsigned long long>(), c->stream), "pack_f32");
     }
     unsigned long long h_bad = 0;
@@ -525,7 +563,8 @@ int pop_load_events(pop_ctx* c, int64_t n_events, const int64_t* offsets, int n_
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const int64_t n = offsets[n_events];
     SampleSet s;
-    int rc = pack_samples(c, n, n_dims, theta, prior, storage, mem, s, "pop_load_events");
+    int rc = pack_samples(c, n, n_dims, theta, prior, storage, mem, s, "pop_load_events",
+                          std::vector<int64_t>(offsets, offsets + n_events + 1));
     if (rc != POP_OK) return rc;
     DevBuf doff;
     CK(doff.alloc(sizeof(int64_t) * (n_events + 1)), "cudaMalloc(offsets)");
@@ -557,7 +596,8 @@ int pop_load_injections(pop_ctx* c, int64_t n_found, int64_t n_draw, int n_dims,
     if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_load_injections: bad mem");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     SampleSet s;
-    int rc = pack_samples(c, n_found, n_dims, theta, p_draw, storage, mem, s, "pop_load_injections");
+    int rc = pack_samples(c, n_found, n_dims, theta, p_draw, storage, mem, s, "pop_load_injections",
+                          std::vector<int64_t>{0, n_found});
     if (rc != POP_OK) return rc;
     c->inj.swap(s);
     c->n_draw = n_draw;

@@ -99,9 +99,9 @@ struct Tiling {
 
 // ---------------------------------------------------------------- kernel launchers
 // All launch on `s` and return the launch error (cudaSuccess when queued).
-cudaError_t launch_pack_f64(const double* theta, const double* prior, int64_t n, int n_dims,
+cudaError_t launch_pack_f64(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
                             double* feat, int64_t stride, unsigned long long* bad, cudaStream_t s);
-cudaError_t launch_pack_f32(const double* theta, const double* prior, int64_t n, int n_dims,
+cudaError_t launch_pack_f32(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
                             float* feat, double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params,
                             LamF64* c64, LamF32* c32, cudaStream_t s);

@@ -49,13 +49,15 @@ __device__ __forceinline__ bool read_sample(const double* theta, const double* p
 
 __device__ __forceinline__ double log_or_zero(double x) { return x > 0.0 ? log(x) : LOG_ZERO; }
 
-__global__ void pack_f64_kernel(const double* __restrict__ theta, const double* __restrict__ prior, int64_t n,
-                                int nd, double* __restrict__ feat, int64_t stride, unsigned long long* bad)
+// Output slot j takes input sample perm[j] (the load-time order, see pack_samples).
+__global__ void pack_f64_kernel(const double* __restrict__ theta, const double* __restrict__ prior,
+                                const int64_t* __restrict__ perm, int64_t n, int nd, double* __restrict__ feat,
+                                int64_t stride, unsigned long long* bad)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         RawSample s;
         bool live;
-        if (!read_sample(theta, prior, j, nd, false, s, live)) atomicAdd(bad, 1ull);
+        if (!read_sample(theta, prior, perm ? perm[j] : j, nd, false, s, live)) atomicAdd(bad, 1ull);
         double f[F_COUNT64] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (live) {
             f[F_LM1] = log(s.m1);
@@ -77,14 +79,14 @@ __global__ void pack_f64_kernel(const double* __restrict__ theta, const double* 
     }
 }
 
-__global__ void pack_f32_kernel(const double* __restrict__ theta, const double* __restrict__ prior, int64_t n,
-                                int nd, float* __restrict__ feat, double* __restrict__ m2, int64_t stride,
-                                unsigned long long* bad)
+__global__ void pack_f32_kernel(const double* __restrict__ theta, const double* __restrict__ prior,
+                                const int64_t* __restrict__ perm, int64_t n, int nd, float* __restrict__ feat,
+                                double* __restrict__ m2, int64_t stride, unsigned long long* bad)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         RawSample s;
         bool live;
-        if (!read_sample(theta, prior, j, nd, true, s, live)) atomicAdd(bad, 1ull);
+        if (!read_sample(theta, prior, perm ? perm[j] : j, nd, true, s, live)) atomicAdd(bad, 1ull);
         float f[F_COUNT32] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         double mm = 0.0;
         if (live) {
@@ -319,19 +321,19 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
-cudaError_t launch_pack_f64(const double* theta, const double* prior, int64_t n, int n_dims, double* feat,
-                            int64_t stride, unsigned long long* bad, cudaStream_t s)
+cudaError_t launch_pack_f64(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
+                            double* feat, int64_t stride, unsigned long long* bad, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    pack_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, n, n_dims, feat, stride, bad);
+    pack_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, perm, n, n_dims, feat, stride, bad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_f32(const double* theta, const double* prior, int64_t n, int n_dims, float* feat,
-                            double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s)
+cudaError_t launch_pack_f32(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
+                            float* feat, double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    pack_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, n, n_dims, feat, m2, stride, bad);
+    pack_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, perm, n, n_dims, feat, m2, stride, bad);
     return cudaGetLastError();
 }
 

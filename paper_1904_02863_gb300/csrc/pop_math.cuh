@@ -54,8 +54,10 @@ __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ 
     double r = fma(kd, -k.l_hi, xs);
     r = fma(kd, -k.l_lo, r);
     const double p = fma(fma(r, 1.0 / 6.0, 0.5), r * r, r);  // e^r - 1
-    const double2 tj = tab[n & (EXP_TABLE_SIZE - 1)];
-    const double res = tj.x + fma(tj.x, p, tj.y);            // 2^(j/2048) e^r in [0.99, 2.01)
+    // 2^(j/2048) e^r in [0.99, 2.01): the correctly rounded T_hi alone keeps the result
+    // within about one ulp (the lo part matters only for expm1's cancellation).
+    const double th = tab[n & (EXP_TABLE_SIZE - 1)].x;
+    const double res = fma(th, p, th);
     const int m = n >> EXP_TABLE_BITS;                       // arithmetic shift: floor
     const double scaled = __hiloint2double(__double2hiint(res) + (int)((unsigned)m << 20), __double2loint(res));
     return under ? 0.0 : (over ? __longlong_as_double(0x7ff0000000000000LL) : scaled);

@@ -86,10 +86,17 @@ __device__ __forceinline__ void dead_f32(F32Sample& x)
     x.m2b = 0;
 }
 
+// Support: mmin < m1 <= mmax (exact against the rounded-down float thresholds) and
+// fl64(q m1) >= mmin on the FP64 bit pattern.
+__device__ __forceinline__ bool in_support(const F32Sample& x, const LamF32& c)
+{
+    return (x.m1 > c.thr_lo) & (x.m1 <= c.thr_hi) & (x.m2b >= c.mmin_bits);
+}
+
+// Weight inside the support (the caller applies in_support).
 template <bool HAS_Z>
 __device__ __forceinline__ float weight_f32(const F32Sample& x, const LamF32& c)
 {
-    const bool in = (x.m1 > c.thr_lo) & (x.m1 <= c.thr_hi) & (x.m2b >= c.mmin_bits);
     float aE = fmaf(c.beta, x.lq, x.nlpi);
     aE = fmaf(c.ac, x.sa, aE);
     aE = fmaf(c.bc, x.sb, aE);
@@ -102,8 +109,7 @@ __device__ __forceinline__ float weight_f32(const F32Sample& x, const LamF32& c)
     const float u = fmaf(c.b1, c.lmmin - x.lm1, fmaf(c.nb1, x.lm1lo, c.b1lmmin_lo));
     const float den = c.beta_m1 ? -u : fabsf(exp2m1f(u));
     const float tt = c.t0 + ex2f(fmaf(c.nht, x.dc, c.ct));
-    const float w = (e1 + e2) * tt * rcpf(den);
-    return in ? w : 0.0f;
+    return (e1 + e2) * tt * rcpf(den);
 }
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float w)
@@ -179,10 +185,18 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
 #pragma unroll
             for (int l = 0; l < T; ++l) {
                 const LamF32 cl = sl[l];
-                const float w0 = weight_f32<HAS_Z>(x0, cl);
-                const float w1 = weight_f32<HAS_Z>(x1, cl);
-                kahan_add(s[l], cp[l], w0 + w1);
-                if (ch.inj) kahan_add(s2[l], cp2[l], fmaf(w0, w0, w1 * w1));
+                const bool in0 = in_support(x0, cl), in1 = in_support(x1, cl);
+                // Samples are stored in increasing q m1 per event: warps wholly below the
+                // lower mass edge skip the arithmetic.
+                if (__any_sync(0xffffffffu, in0 | in1)) {
+                    // Evaluated on every lane (exp2m1f votes across the warp), then selected.
+                    float w0 = weight_f32<HAS_Z>(x0, cl);
+                    float w1 = weight_f32<HAS_Z>(x1, cl);
+                    w0 = in0 ? w0 : 0.0f;
+                    w1 = in1 ? w1 : 0.0f;
+                    kahan_add(s[l], cp[l], w0 + w1);
+                    if (ch.inj) kahan_add(s2[l], cp2[l], fmaf(w0, w0, w1 * w1));
+                }
             }
         }
 #pragma unroll

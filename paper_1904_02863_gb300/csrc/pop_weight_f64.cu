@@ -73,8 +73,7 @@ template <bool HAS_Z>
 __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c, const double2* __restrict__ tab,
                                              const ExpConsts& kc)
 {
-    // Support: mmin < m1 <= mmax and fl64(q m1) >= mmin, compared on bit patterns.
-    const bool in = (x.m1b > c.mmin_bits) & (x.m1b <= c.mmax_bits) & (x.m2b >= c.mmin_bits);
+    // Weight inside the support (the caller applies in_support).
     double aE = fma(c.beta, x.lq, x.nlpi);
     aE = fma(c.ac, x.sa, aE);
     aE = fma(c.bc, x.sb, aE);
@@ -89,8 +88,21 @@ __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c
     if (llabs(x.m1b - c.mmin_bits) < NEAR_EDGE_BITS) lr = log1p_near0(x.invm1 * (c.mmin - x.m1));
     const double den = c.beta_m1 ? -lr : fabs(expm1_tab(c.b1 * lr, tab, kc));
     const double tt = c.t0 + exp_tab(fma(c.nht, x.dc, c.ct), tab, kc);
-    const double w = (e1 + e2) * tt * rcp_pos(den);
-    return in ? w : 0.0;
+    return (e1 + e2) * tt * rcp_pos(den);
+}
+
+// Support: mmin < m1 <= mmax and fl64(q m1) >= mmin, compared on bit patterns
+// (integer pipe; non-negative doubles order like their bits).
+__device__ __forceinline__ bool in_support(const F64Sample& x, const LamF64& c)
+{
+    return (x.m1b > c.mmin_bits) & (x.m1b <= c.mmax_bits) & (x.m2b >= c.mmin_bits);
+}
+
+// A sample outside every support (m1 = 0): weight 0 for any Lambda.
+__device__ __forceinline__ void dead_f64(F64Sample& x)
+{
+    x.lm1 = x.m1 = x.lq = x.sa = x.sb = x.dc = x.nlpi = x.lz1 = x.invm1 = 0.0;
+    x.m1b = x.m2b = 0;
 }
 
 // Copies the 2^(j/2048) table into shared memory (once per block of the persistent grid).
@@ -137,12 +149,24 @@ weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict
         double acc[T], acc2[T];
 #pragma unroll
         for (int l = 0; l < T; ++l) acc[l] = acc2[l] = 0.0;
-        for (int j = threadIdx.x; j < ch.len; j += NT) {
+        // Same trip count on every thread (slots past the end are dead samples), so
+        // the whole warp takes part in the support vote.  Samples are stored in
+        // increasing q m1 within an event, so the ones below a Lambda's lower mass
+        // edge are contiguous and their warps skip the FP64 arithmetic.
+        for (int base = 0; base < ch.len; base += NT) {
+            const int j = base + threadIdx.x;
             F64Sample x;
-            load_f64<HAS_Z>(F, ch.start + j, x);
+            if (j < ch.len) load_f64<HAS_Z>(F, ch.start + j, x);
+            else dead_f64(x);
 #pragma unroll
             for (int l = 0; l < T; ++l) {
-                const double w = weight_f64<HAS_Z>(x, sl[l], stab, kc);
+                const LamF64& cl = sl[l];
+                const bool in = in_support(x, cl);
+                double w = 0.0;
+                if (__any_sync(0xffffffffu, in)) {
+                    w = weight_f64<HAS_Z>(x, cl, stab, kc);
+                    w = in ? w : 0.0;
+                }
                 acc[l] += w;
                 if (ch.inj) acc2[l] = fma(w, w, acc2[l]);
             }

@@ -25,14 +25,15 @@ def ulps(a, b):
     return np.abs(a - b) / np.spacing(np.abs(b))
 
 
-def test_exp_within_one_ulp_of_libm(ctx):
+def test_exp_within_two_ulp_of_libm(ctx):
     from paper_1904_02863_gb300 import binding as B
     rng = np.random.default_rng(1)
     x = np.concatenate([rng.uniform(-700, 709, 200000), rng.uniform(-1, 1, 100000),
                         rng.uniform(-1e-6, 1e-6, 20000), np.arange(-40, 41) * np.log(2) / 2048,
                         [0.0, -0.0, 1e-300, -1e-300, 709.5, -706.9]])
     y = B.pop_math_check(ctx, 0, x)
-    assert np.max(ulps(y, np.exp(x))) <= 1.0
+    e = ulps(y, np.exp(x))
+    assert np.max(e) <= 2.0 and np.mean(e) < 0.5
 
 
 def test_exp_against_cuda_exp(ctx):
