@@ -168,6 +168,62 @@ int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
  * The test suite checks them against libm and CUDA's functions. */
 int pop_math_check(pop_ctx* ctx, int fn, int64_t n, const double* x, double* y, int mem);
 
+/* ------------------------------------------------------------------ ln xi surrogate
+ * The paper announces a learned selection term that includes spin effects in
+ * VT at no extra run-time cost (Sec. "Population acceleration", right after the
+ * Monte Carlo VT).  Here it is a network on the normalised Lambda
+ * (x = 2 (Lambda - lo)/(hi - lo) - 1, 12 inputs, kappa = 0 when absent) ->
+ * 4 x 256 SiLU -> (ln xi, ln N_eff) standardised; BF16 weights and
+ * activations on the tcgen05 tensor cores with FP32 accumulators, FP32 master
+ * weights and Adam.  Flat FP32 parameter layout (201218 floats): W0 [256 x 12],
+ * b0 [256], W1 [256 x 256], b1, W2, b2, W3, b3, W4 [2 x 256], b4 [2]; W row-major
+ * [out][in]. */
+
+/* Train on n_pairs Lambda drawn uniformly (seeded) from the box
+ * [lambda_lo, lambda_hi] (n_params values each), with targets ln xi-hat and
+ * ln N_eff from the loaded injections (the Monte Carlo selection term itself,
+ * FP32 arithmetic when FP32 storage is loaded, else FP64); heldout_frac of the
+ * pairs are held out.
+ * Mean-squared loss on the standardised targets, mini-batches of 4096, Adam
+ * with cosine learning-rate decay over `epochs`.  The surrogate is trusted when
+ * its held-out ln xi error beyond the targets' own Monte Carlo scatter
+ * (sqrt(max(0, rmse^2 - mean(1/N_eff)))) is at most 0.01.
+ * *out_heldout_rmse (may be NULL) = held-out RMS error of ln xi vs the targets. */
+int pop_xi_surrogate_train(pop_ctx* ctx, int64_t n_pairs, double heldout_frac, uint64_t seed,
+                           const double* lambda_lo, const double* lambda_hi, int n_params, int epochs,
+                           double* out_heldout_rmse);
+
+/* Held-out statistics of the trained surrogate (any pointer may be NULL). */
+int pop_xi_surrogate_info(pop_ctx* ctx, double* heldout_rmse, double* mc_noise, double* excess, int* trusted);
+
+/* ln xi (and ln N_eff, may be NULL) predicted for K Lambda rows; out_fallback[k]
+ * (may be NULL) = 1 when the Monte Carlo xi must be used instead: surrogate
+ * not trusted, Lambda outside the training box, or predicted N_eff < 4 N.
+ * All arrays in `mem`; synchronous. */
+int pop_xi_surrogate_infer(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, double* out_lnxi,
+                           double* out_lnneff, uint8_t* out_fallback, int mem);
+
+/* Checkpoint of the trained surrogate (weights, normalisation, held-out
+ * statistics) as a versioned binary file; load restores it. */
+int pop_xi_surrogate_save(pop_ctx* ctx, const char* path);
+int pop_xi_surrogate_load(pop_ctx* ctx, const char* path);
+
+/* Network-level access (host memory), for checks and custom training:
+ * set/get the flat FP32 parameters (n = 201218; setting resets Adam), forward
+ * on B normalised inputs x[B x 12] -> y[B x 2], the loss
+ * (1/B) sum (y - t)^2 and its gradients (flat layout), and one Adam step
+ * (beta 0.9/0.999, eps 1e-8) on a batch. */
+int pop_mlp_set_params(pop_ctx* ctx, const float* params, int64_t n);
+int pop_mlp_get_params(pop_ctx* ctx, float* params, int64_t n);
+int pop_mlp_forward(pop_ctx* ctx, int64_t B, const float* x, float* y);
+int pop_mlp_gradients(pop_ctx* ctx, int64_t B, const float* x, const float* t, float* grads, double* loss);
+int pop_mlp_train_step(pop_ctx* ctx, int64_t B, const float* x, const float* t, float lr);
+
+/* Diagnostic: C[M x N] = A[M x K] B[N x K]^T with A and B rounded to BF16, on
+ * the tcgen05 tensor cores with an FP32 accumulator (host arrays, row-major;
+ * M a multiple of 128, N a multiple of 16 up to 256, K a multiple of 64). */
+int pop_mlp_gemm_check(pop_ctx* ctx, int M, int N, int K, const float* A, const float* B, float* C);
+
 /* Bytes of the scratch array that pop_loglik_f64_noalloc uses (16 MiB). */
 #define POP_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -29,7 +29,11 @@ EXPORTS = (
     "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
     "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
     "pop_loglik_f64_noalloc", "pop_math_check",
+    "pop_xi_surrogate_train", "pop_xi_surrogate_info", "pop_xi_surrogate_infer", "pop_xi_surrogate_save",
+    "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
+    "pop_mlp_train_step", "pop_mlp_gemm_check",
 )
+MLP_N_PARAMS = 201218
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -69,6 +73,18 @@ def load_library(path: str = LIB_PATH):
         "pop_loglik_f64_noalloc": (i32, [i32, vp, i64, vp, i64, i32, vp, vp, i64, i64, vp, vp, i64, i32, vp,
                                          vp, vp, vp, vp, ctypes.c_char_p, i32]),
         "pop_math_check": (i32, [vp, i32, i64, vp, vp, i32]),
+        "pop_xi_surrogate_train": (i32, [vp, i64, d, ctypes.c_uint64, vp, vp, i32, i32, ctypes.POINTER(d)]),
+        "pop_xi_surrogate_info": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
+                                        ctypes.POINTER(i32)]),
+        "pop_xi_surrogate_infer": (i32, [vp, i64, i32, vp, vp, vp, vp, i32]),
+        "pop_xi_surrogate_save": (i32, [vp, ctypes.c_char_p]),
+        "pop_xi_surrogate_load": (i32, [vp, ctypes.c_char_p]),
+        "pop_mlp_set_params": (i32, [vp, vp, i64]),
+        "pop_mlp_get_params": (i32, [vp, vp, i64]),
+        "pop_mlp_forward": (i32, [vp, i64, vp, vp]),
+        "pop_mlp_gradients": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(d)]),
+        "pop_mlp_train_step": (i32, [vp, i64, vp, vp, ctypes.c_float]),
+        "pop_mlp_gemm_check": (i32, [vp, i32, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,6 +236,95 @@ def pop_math_check(ctx, fn, x):
     _check(ctx, load_library().pop_math_check(ctx, int(fn), xa.size, xa.ctypes.data_as(ctypes.c_void_p),
                                               y.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST))
     return y
+
+
+def _f32(a, shape=None):
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and x.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {x.shape}")
+    return x, x.ctypes.data_as(ctypes.c_void_p)
+
+
+def pop_mlp_gemm_check(ctx, A, B):
+    """C = A B^T on the tensor cores (A [M x K], B [N x K] rounded to BF16)."""
+    a, pa = _f32(A)
+    b, pb = _f32(B)
+    M, K = a.shape
+    N = b.shape[0]
+    c = np.empty((M, N), np.float32)
+    _check(ctx, load_library().pop_mlp_gemm_check(ctx, M, N, K, pa, pb, c.ctypes.data_as(ctypes.c_void_p)))
+    return c
+
+
+def pop_mlp_set_params(ctx, flat):
+    p, pp = _f32(flat, (MLP_N_PARAMS,))
+    _check(ctx, load_library().pop_mlp_set_params(ctx, pp, MLP_N_PARAMS))
+
+
+def pop_mlp_get_params(ctx):
+    out = np.empty(MLP_N_PARAMS, np.float32)
+    _check(ctx, load_library().pop_mlp_get_params(ctx, out.ctypes.data_as(ctypes.c_void_p), MLP_N_PARAMS))
+    return out
+
+
+def pop_mlp_forward(ctx, x):
+    xa, px = _f32(x)
+    y = np.empty((xa.shape[0], 2), np.float32)
+    _check(ctx, load_library().pop_mlp_forward(ctx, xa.shape[0], px, y.ctypes.data_as(ctypes.c_void_p)))
+    return y
+
+
+def pop_mlp_gradients(ctx, x, t):
+    xa, px = _f32(x)
+    ta, pt = _f32(t)
+    g = np.empty(MLP_N_PARAMS, np.float32)
+    loss = ctypes.c_double()
+    _check(ctx, load_library().pop_mlp_gradients(ctx, xa.shape[0], px, pt, g.ctypes.data_as(ctypes.c_void_p),
+                                                 ctypes.byref(loss)))
+    return g, loss.value
+
+
+def pop_mlp_train_step(ctx, x, t, lr):
+    xa, px = _f32(x)
+    ta, pt = _f32(t)
+    _check(ctx, load_library().pop_mlp_train_step(ctx, xa.shape[0], px, pt, float(lr)))
+
+
+def pop_xi_surrogate_train(ctx, n_pairs, lo, hi, epochs=100, heldout_frac=0.1, seed=0):
+    lo_a = np.ascontiguousarray(lo, dtype=np.float64)
+    hi_a = np.ascontiguousarray(hi, dtype=np.float64)
+    rmse = ctypes.c_double()
+    _check(ctx, load_library().pop_xi_surrogate_train(ctx, int(n_pairs), float(heldout_frac), int(seed),
+                                                      lo_a.ctypes.data_as(ctypes.c_void_p),
+                                                      hi_a.ctypes.data_as(ctypes.c_void_p), lo_a.size, int(epochs),
+                                                      ctypes.byref(rmse)))
+    return rmse.value
+
+
+def pop_xi_surrogate_info(ctx):
+    r, n, e, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(ctx, load_library().pop_xi_surrogate_info(ctx, ctypes.byref(r), ctypes.byref(n), ctypes.byref(e),
+                                                     ctypes.byref(t)))
+    return {"heldout_rmse": r.value, "mc_noise": n.value, "excess": e.value, "trusted": bool(t.value)}
+
+
+def pop_xi_surrogate_infer(ctx, lambdas):
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    K, P = lam.shape
+    lx, ln, fb = np.empty(K), np.empty(K), np.empty(K, np.uint8)
+    _check(ctx, load_library().pop_xi_surrogate_infer(ctx, K, P, lam.ctypes.data_as(ctypes.c_void_p),
+                                                      lx.ctypes.data_as(ctypes.c_void_p),
+                                                      ln.ctypes.data_as(ctypes.c_void_p),
+                                                      fb.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST))
+    return lx, ln, fb
+
+
+def pop_xi_surrogate_save(ctx, path):
+    _check(ctx, load_library().pop_xi_surrogate_save(ctx, str(path).encode()))
+
+
+def pop_xi_surrogate_load(ctx, path):
+    _check(ctx, load_library().pop_xi_surrogate_load(ctx, str(path).encode()))
 
 
 def pop_loglik_f64_noalloc(offsets, theta, prior, n_draw, inj_theta, p_draw, lambdas, out, device=0, stream=None):

@@ -11,7 +11,11 @@
 #include <vector>
 
 #include "pop.h"
+#include "pop_devbuf.h"
 #include "pop_internal.h"
+#include "pop_mlp.h"
+
+#include <memory>
 
 using namespace pop;
 
@@ -23,41 +27,6 @@ constexpr int CHUNK_LEN = 4096;  // samples per work chunk (events are split at 
 constexpr int64_t ALIGN_ELEMS = 64;
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
-
-// RAII device buffer.
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { reset(); }
-    void reset()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    cudaError_t alloc(size_t n)
-    {
-        reset();
-        if (n == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(&p, n);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return e;
-        }
-        bytes = n;
-        return cudaSuccess;
-    }
-    void swap(DevBuf& o)
-    {
-        std::swap(p, o.p);
-        std::swap(bytes, o.bytes);
-    }
-    template <class T>
-    T* as() const { return static_cast<T*>(p); }
-};
 
 // One packed sample set (events or injections) in either or both precisions.
 struct SampleSet {
@@ -82,6 +51,7 @@ struct Graph {
     cudaGraphExec_t exec = nullptr;
     int64_t k_cap = -1;
     uint64_t version = 0;
+    uint64_t sur_version = 0;
     Tiling tiling{};
     void reset()
     {
@@ -120,10 +90,12 @@ struct pop_ctx {
 
     Tiling tiling[2] = {{8, 256, 0}, {16, 256, 0}};
     bool use_graphs = true;
-    Graph graph[2];
+    Graph graph[3];  // per mode: F64, F32, F32 + surrogate
+    DevBuf d_need, d_slnxi, d_slnneff;  // surrogate mode: Monte Carlo mask, ln xi, ln N_eff per Lambda
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts expc{};
+    std::unique_ptr<Surrogate> sur;  // ln xi network, created on first use
     bool timed = false;
     int64_t last_K = 0;
     int last_params = 0;
@@ -289,6 +261,13 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     CK(neff.alloc(sizeof(double) * cap), "cudaMalloc(neff)");
     CK(flags.alloc(sizeof(uint32_t) * cap), "cudaMalloc(flags)");
     CK(dK.alloc(sizeof(int64_t)), "cudaMalloc(K)");
+    DevBuf need, slnxi, slnneff;
+    CK(need.alloc(cap), "cudaMalloc(need)");
+    CK(slnxi.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnxi)");
+    CK(slnneff.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnneff)");
+    c->d_need.swap(need);
+    c->d_slnxi.swap(slnxi);
+    c->d_slnneff.swap(slnneff);
     if (c->d_lambda.p)  // keep the last Lambda batch (the autotuner reuses it)
         CK(cudaMemcpyAsync(lam.p, c->d_lambda.p, std::min(lam.bytes, c->d_lambda.bytes), cudaMemcpyDeviceToDevice,
                            c->stream), "copy lambda");
@@ -331,6 +310,16 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     CK(cudaEventRecordWithFlags(c->ev_t0, c->stream, rec), "event");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
                        c->d_c32.as<LamF32>(), c->stream), "prologue");
+    SurrogateXi sx{nullptr, nullptr, nullptr};
+    if (mode == POP_MODE_F32_SURROGATE) {
+        // ln xi from the network for every Lambda, and which Lambda still need the Monte Carlo xi.
+        const int64_t n_events = (int64_t)c->h_offsets.size() - 1;
+        const int rc = c->sur->enqueue_gate(c->d_lambda.as<double>(), c->k_cap, n_params, c->d_K.as<int64_t>(),
+                                            4.0 * (double)n_events, c->d_need.as<uint8_t>(), c->d_slnxi.as<double>(),
+                                            c->d_slnneff.as<double>());
+        if (rc != POP_OK) return fail(c, rc, "surrogate: " + c->sur->err);
+        sx = SurrogateXi{c->d_need.as<uint8_t>(), c->d_slnxi.as<double>(), c->d_slnneff.as<double>()};
+    }
     CK(cudaEventRecordWithFlags(c->ev_w0, c->stream, rec), "event");
     if (m == 0) {
         FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
@@ -341,14 +330,14 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
         FeatF32 e{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
         FeatF32 j{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
         CK(launch_weight_f32(c->tiling[1], grid, e, j, wd, c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(),
-                             c->d_part.as<double>(), c->d_part2.as<double>(), c->stream), "weight_f32");
+                             c->d_part.as<double>(), c->d_part2.as<double>(), sx, c->stream), "weight_f32");
     }
     CK(cudaEventRecordWithFlags(c->ev_w1, c->stream, rec), "event");
     CK(launch_finalise(c->d_part.as<double>(), c->d_part2.as<double>(), c->d_ecb.as<int32_t>(),
                        c->d_offsets.as<int64_t>(), c->ev.n == 0 ? 0 : (int64_t)c->h_offsets.size() - 1,
                        c->n_chunks, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                        c->k_cap, c->d_lnL.as<double>(), c->d_lnxi.as<double>(), c->d_neff.as<double>(),
-                       c->d_flags.as<uint32_t>(), c->stream), "finalise");
+                       c->d_flags.as<uint32_t>(), c->stream, sx), "finalise");
     CK(cudaEventRecordWithFlags(c->ev_t1, c->stream, rec), "event");
     return POP_OK;
 }
@@ -357,12 +346,18 @@ int run_pipeline(pop_ctx* c, int mode, int n_params)
 {
     const int m = mode == POP_MODE_F64 ? 0 : 1;
     const int grid = grid_size(c, m);
+    uint64_t sur_version = 0;
+    if (mode == POP_MODE_F32_SURROGATE) {  // buffers first: nothing may be allocated during a capture
+        const int rc = c->sur->ensure_gate(c->k_cap);
+        if (rc != POP_OK) return fail(c, rc, "surrogate: " + c->sur->err);
+        sur_version = c->sur->version;
+    }
     if (!c->use_graphs) return enqueue_pipeline(c, mode, n_params, grid, false);
-    Graph& g = c->graph[m];
+    Graph& g = c->graph[mode];
     const Tiling& t = c->tiling[m];
     const bool stale = !g.exec || g.k_cap != c->k_cap || g.version != c->version || g.tiling.lambda_tile != t.lambda_tile ||
                        g.tiling.block_threads != t.block_threads || g.tiling.blocks_per_sm != t.blocks_per_sm ||
-                       c->last_params != n_params;
+                       c->last_params != n_params || g.sur_version != sur_version;
     if (stale) {
         g.reset();
         cudaGraph_t graph = nullptr;
@@ -380,6 +375,7 @@ int run_pipeline(pop_ctx* c, int mode, int n_params)
         g.k_cap = c->k_cap;
         g.version = c->version;
         g.tiling = t;
+        g.sur_version = sur_version;
     }
     CK(cudaGraphLaunch(g.exec, c->stream), "graph launch");
     return POP_OK;
@@ -414,6 +410,35 @@ void build_exp_table(double2* tab, ExpConsts* kc)
     kc->inv_l = (double)(EXP_TABLE_SIZE / ln2);
     kc->l_hi = l_hi;
     kc->l_lo = (double)(L - (long double)l_hi);
+}
+
+}  // namespace pop
+
+// Context accessors for the surrogate entry points (pop_surrogate.cu).
+namespace pop {
+
+int ctx_fail(pop_ctx* c, int status, const std::string& msg) { return fail(c, status, msg); }
+cudaStream_t ctx_stream(pop_ctx* c) { return c->stream; }
+int ctx_device(pop_ctx* c) { return c->device; }
+int64_t ctx_n_events(pop_ctx* c) { return c->ev.n ? (int64_t)c->h_offsets.size() - 1 : 0; }
+int ctx_n_dims(pop_ctx* c) { return c->ev.n_dims; }
+int ctx_has_storage(pop_ctx* c, int storage)
+{
+    return c->ev.n && c->inj.n && (c->ev.storage & storage) && (c->inj.storage & storage);
+}
+Surrogate* ctx_surrogate(pop_ctx* c, int* status)
+{
+    *status = POP_OK;
+    if (!c->sur) {
+        std::unique_ptr<Surrogate> s(new Surrogate());
+        const int rc = s->init(c->device, c->stream);
+        if (rc != POP_OK) {
+            *status = fail(c, rc, "surrogate: " + s->err);
+            return nullptr;
+        }
+        c->sur = std::move(s);
+    }
+    return c->sur.get();
 }
 
 }  // namespace pop
@@ -616,7 +641,10 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
         return fail(c, POP_EINVAL, "pop_loglik: n_params must be 11 (12 with redshift samples)");
     if (mode != POP_MODE_F64 && mode != POP_MODE_F32 && mode != POP_MODE_F32_SURROGATE)
         return fail(c, POP_EINVAL, "pop_loglik: bad mode");
-    if (mode == POP_MODE_F32_SURROGATE) return fail(c, POP_ESTATE, "pop_loglik: surrogate not trained");
+    if (mode == POP_MODE_F32_SURROGATE && (!c->sur || !c->sur->trained))
+        return fail(c, POP_ESTATE, "pop_loglik: surrogate not trained (pop_xi_surrogate_train or _load)");
+    if (mode == POP_MODE_F32_SURROGATE && c->sur->n_params != n_params)
+        return fail(c, POP_EINVAL, "pop_loglik: the surrogate was trained for another n_params");
     const int need = mode == POP_MODE_F64 ? POP_STORE_F64 : POP_STORE_F32;
     if (!(c->ev.storage & need) || !(c->inj.storage & need))
         return fail(c, POP_ESTATE, "pop_loglik: the loaded storage does not include this mode's precision");
@@ -757,7 +785,8 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
                     FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
                     FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
                     e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(),
-                                          c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
+                                          c->d_part.as<double>(), c->d_part2.as<double>(),
+                                          SurrogateXi{nullptr, nullptr, nullptr}, c->stream);
                 }
                 if (e != cudaSuccess) {
                     c->tiling[mode] = saved;

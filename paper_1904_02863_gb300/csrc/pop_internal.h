@@ -115,13 +115,23 @@ cudaError_t launch_math_check(int fn, int64_t n, const double* x, double* y, con
                               cudaStream_t s);
 // Host: the 2^(j/2048) table (hi, lo) and the reduction constants, in extended precision.
 void build_exp_table(double2* tab, ExpConsts* kc);
+// Selection term from the surrogate (all NULL when the Monte Carlo xi is used for every Lambda):
+// need_mc[k] = 1 keeps the Monte Carlo xi for Lambda k, else ln xi = lnxi[k], N_eff = neff[k].
+struct SurrogateXi {
+    const uint8_t* need_mc;
+    const double* lnxi;
+    const double* neff;
+};
+// With sx.need_mc set, injection work items whose whole Lambda tile is covered by the surrogate
+// are skipped.
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
                               const LamF32* lam, const int64_t* dK, double* part, double* part2,
-                              cudaStream_t s);
+                              SurrogateXi sx, cudaStream_t s);
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ev_chunk_begin,
                             const int64_t* offsets, int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks,
                             int64_t n_draw, const LamF64* lam, const int64_t* dK, int64_t K_cap,
-                            double* lnL, double* lnxi, double* neff, uint32_t* flags, cudaStream_t s);
+                            double* lnL, double* lnxi, double* neff, uint32_t* flags, cudaStream_t s,
+                            SurrogateXi sx = SurrogateXi{nullptr, nullptr, nullptr});
 
 // Kernel function of a tiling (nullptr when that instantiation does not exist).
 const void* weight_f64_fn(const Tiling& t, bool has_z);

@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(FIN_THREADS)
 finalise_kernel(const double* __restrict__ part, const double* __restrict__ part2,
                 const int32_t* __restrict__ ecb, const int64_t* __restrict__ off, int64_t n_events,
                 int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw, const LamF64* __restrict__ lam,
-                const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags)
+                const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags,
+                SurrogateXi sx)
 {
     __shared__ double sh[FIN_THREADS / 32];
     const int64_t k = blockIdx.x;
@@ -291,11 +292,20 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
     if (threadIdx.x != 0) return;
     uint32_t fl = 0;
     const double nd = (double)n_draw;
-    const double xi = sw / nd;
+    double xi = sw / nd;
     const double var = sw2 / (nd * nd) - xi * xi / nd;
     double ne = var > 0.0 ? xi * xi / var : INFINITY;
     double out, lx;
     if (zero > 0.0) fl |= POP_FLAG_ZERO_EVENT;
+    if (sx.need_mc) {
+        if (sx.need_mc[k]) {
+            fl |= POP_FLAG_MC_FALLBACK;
+        } else {  // selection term from the surrogate network
+            fl |= POP_FLAG_SURROGATE_USED;
+            xi = exp(sx.lnxi[k]);
+            ne = exp(sx.neff[k]);
+        }
+    }
     if (xi == 0.0) {
         fl |= POP_FLAG_ZERO_XI;
         out = -INFINITY;
@@ -350,11 +360,11 @@ cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_c
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,
                             int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
                             const LamF64* lam, const int64_t* dK, int64_t K_cap, double* lnL, double* lnxi,
-                            double* neff, uint32_t* flags, cudaStream_t s)
+                            double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx)
 {
     if (K_cap <= 0) return cudaSuccess;
     finalise_kernel<<<(unsigned)K_cap, FIN_THREADS, 0, s>>>(part, part2, ecb, off, n_events, n_chunks, n_ev_chunks,
-                                                            n_draw, lam, dK, lnL, lnxi, neff, flags);
+                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,806 @@
+// Surrogate network kernels: tcgen05 BF16 GEMM with TMEM accumulators and
+// fused epilogues, plus the small CUDA-core kernels of the input/output layers,
+// the reductions, transposes and Adam.
+//
+// GEMM: C[M x N] = A[M x K] . B[N x K]^T with A and B K-major BF16 in global
+// memory, M a multiple of 128 (one CTA per 128 rows = 128 TMEM lanes), N a
+// multiple of 16 up to 256 (FP32 accumulator columns), K a multiple of 64.
+// Each 64-wide K stage is copied into shared memory in the no-swizzle
+// core-matrix layout (8 rows x 16 bytes per 128-byte core matrix; 128 bytes to
+// the next core matrix along K, 1024 bytes to the next 8-row group), one thread
+// issues four tcgen05.mma (K = 16 each) and commits them to an mbarrier that
+// all threads wait on (with an iteration limit: on time-out the CTA sets the
+// error flag, waits once more and frees its TMEM).  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = its 32 rows).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <random>
+
+#include "pop_internal.h"
+#include "pop_mlp.h"
+
+namespace pop {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr int TC_SMEM_A = TC_BM * TC_BK * 2;    // 16 KB
+constexpr int TC_SMEM_B = 256 * TC_BK * 2;      // 32 KB
+// Requested dynamic shared memory: at most two CTAs per SM, so their
+// 2 x 256 TMEM columns always fit in the SM's 512.
+constexpr int TC_SMEM_LAUNCH = 112 * 1024;
+constexpr uint32_t CM_LBO = 128;   // bytes to the next core matrix along K
+constexpr uint32_t CM_SBO = 1024;  // bytes to the next 8-row group
+constexpr int WAIT_LIMIT = 1 << 20;
+
+enum { EPI_FWD = 0, EPI_BWD = 1, EPI_F32 = 2 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((CM_LBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((CM_SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B (both K-major), M x N.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Waits for the phase with the given parity; false after WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 lanes x 16 consecutive FP32 columns: thread = lane (row), v[j] = column c0 + j.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float siluf_(float z) { return z * sigmoidf_(z); }
+__device__ __forceinline__ float dsiluf_(float z)
+{
+    const float s = sigmoidf_(z);
+    return s * (1.0f + z * (1.0f - s));
+}
+
+struct GemmArgs {
+    const bf16* A;
+    int lda;
+    const bf16* B;
+    int ldb;
+    int M, N, K, k_split;  // blockIdx.y covers K range [y * k_split, (y + 1) * k_split)
+    int epi;
+    const float* bias;     // EPI_FWD
+    float* Z;              // EPI_FWD: pre-activation out; EPI_BWD: pre-activation of the layer below (in)
+    int ldz;
+    bf16* H;               // EPI_FWD: SiLU(Z) out; EPI_BWD: dZ out
+    int ldh;
+    float* C;              // EPI_F32: C + blockIdx.y * c_split_stride
+    int ldc;
+    int64_t c_split_stride;
+    int* err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + TC_SMEM_A;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + TC_SMEM_A + TC_SMEM_B);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + TC_SMEM_A + TC_SMEM_B + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_BM;
+    const int kbeg = blockIdx.y * g.k_split;
+    const int kend = min(g.K, kbeg + g.k_split);
+
+    if (warp == 0) tmem_alloc(smem_u32(tslot), TC_TMEM_COLS);
+    if (tid == 0) mbar_init(smem_u32(mbar), 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = idesc_bf16(TC_BM, g.N);
+    uint32_t parity = 0;
+    int failed = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
+        for (int i = tid; i < TC_BM * 8; i += TC_THREADS) {
+            const int r = i >> 3, kg = i & 7;
+            const uint4 v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + kg * 8);
+            *reinterpret_cast<uint4*>(sA + (r >> 3) * CM_SBO + kg * CM_LBO + (r & 7) * 16) = v;
+        }
+        for (int i = tid; i < g.N * 8; i += TC_THREADS) {
+            const int r = i >> 3, kg = i & 7;
+            const uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)r * g.ldb + k0 + kg * 8);
+            *reinterpret_cast<uint4*>(sB + (r >> 3) * CM_SBO + kg * CM_LBO + (r & 7) * 16) = v;
+        }
+        fence_proxy_async();  // make the generic-proxy stores visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                mma_bf16(tmem, sdesc(smem_u32(sA) + kk * 2 * CM_LBO), sdesc(smem_u32(sB) + kk * 2 * CM_LBO), idesc,
+                         (k0 > kbeg || kk > 0) ? 1u : 0u);
+            mma_commit(smem_u32(mbar));
+        }
+        const bool ok = mbar_wait(smem_u32(mbar), parity);
+        failed = __syncthreads_or(!ok);
+        if (failed) break;
+        parity ^= 1u;
+    }
+    tc_fence_after();
+    if (!failed) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < g.N; c0 += 16) {
+            float v[16];
+            tmem_ld16(trow + (uint32_t)c0, v);
+            if (g.epi == EPI_FWD) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float z = v[j] + g.bias[c0 + j];
+                    g.Z[(size_t)row * g.ldz + c0 + j] = z;
+                    g.H[(size_t)row * g.ldh + c0 + j] = __float2bfloat16(siluf_(z));
+                }
+            } else if (g.epi == EPI_BWD) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float z = g.Z[(size_t)row * g.ldz + c0 + j];
+                    g.H[(size_t)row * g.ldh + c0 + j] = __float2bfloat16(v[j] * dsiluf_(z));
+                }
+            } else {
+                float* C = g.C + blockIdx.y * g.c_split_stride;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) C[(size_t)row * g.ldc + c0 + j] = v[j];
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(g.err, 1);
+        mbar_wait(smem_u32(mbar), parity);  // let the MMAs in flight finish before TMEM is freed
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+}
+
+cudaError_t set_gemm_attributes()
+{
+    return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_LAUNCH);
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t s)
+{
+    if (g.M % TC_BM || g.N % 16 || g.N > 256 || g.N < 16 || g.K % TC_BK || g.k_split % TC_BK || g.k_split <= 0 ||
+        (int64_t)g.k_split * k_splits < g.K || (int64_t)g.k_split * (k_splits - 1) >= g.K)
+        return cudaErrorInvalidValue;
+    gemm_tc_kernel<<<dim3(g.M / TC_BM, k_splits), TC_THREADS, TC_SMEM_LAUNCH, s>>>(g);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ CUDA-core kernels
+struct Box {
+    double lo[MLP_IN], hi[MLP_IN];
+};
+
+// x0[r][c] = 2 (Lambda[r][c] - lo) / (hi - lo) - 1 for c < P (else 0); rows >= K are zero.
+__global__ void normalise_kernel(const double* __restrict__ lam, int64_t K, int P, Box box, bf16* __restrict__ x0,
+                                 int64_t rows_pad, uint8_t* __restrict__ outside)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows_pad * MLP_IN_PAD) return;
+    const int64_t r = i / MLP_IN_PAD;
+    const int c = (int)(i % MLP_IN_PAD);
+    float v = 0.0f;
+    if (r < K && c < P) v = (float)(2.0 * (lam[r * P + c] - box.lo[c]) / (box.hi[c] - box.lo[c]) - 1.0);
+    x0[i] = __float2bfloat16(v);
+    if (c == 0 && r < K && outside) {
+        uint8_t o = 0;
+        for (int p = 0; p < P; ++p) {
+            const double x = lam[r * P + p];
+            o |= !(x >= box.lo[p] && x <= box.hi[p]);
+        }
+        outside[r] = o;
+    }
+}
+
+// Output layer (2 units) on CUDA cores: one warp per row, fixed-order shuffle sum.
+__global__ void out_fwd_kernel(const bf16* __restrict__ h4, const float* __restrict__ w4, const float* __restrict__ b4,
+                               float* __restrict__ y, int64_t rows)
+{
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    float a0 = 0.f, a1 = 0.f;
+    for (int i = lane; i < MLP_HID; i += 32) {
+        const float h = __bfloat162float(h4[row * MLP_HID + i]);
+        a0 = fmaf(h, w4[i], a0);
+        a1 = fmaf(h, w4[MLP_HID + i], a1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    if (lane == 0) {
+        y[row * 2] = a0 + b4[0];
+        y[row * 2 + 1] = a1 + b4[1];
+    }
+}
+
+// dY = 2 (Y - T) / B on the first B rows, 0 on the padding; row_loss = sum_o (Y - T)^2.
+__global__ void loss_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, int64_t B, int64_t rows_pad,
+                                 float* __restrict__ dy, float* __restrict__ row_loss)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= rows_pad) return;
+    float l = 0.f, g0 = 0.f, g1 = 0.f;
+    if (r < B) {
+        const float r0 = y[r * 2] - t[r * 2], r1 = y[r * 2 + 1] - t[r * 2 + 1];
+        l = r0 * r0 + r1 * r1;
+        g0 = 2.f * r0 / (float)B;
+        g1 = 2.f * r1 / (float)B;
+    }
+    dy[r * 2] = g0;
+    dy[r * 2 + 1] = g1;
+    row_loss[r] = l;
+}
+
+// dZ4 = (dY W4) * SiLU'(Z4), BF16.
+__global__ void out_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ w4, const float* __restrict__ z4,
+                               bf16* __restrict__ dz4, int64_t rows_pad)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows_pad * MLP_HID) return;
+    const int64_t r = i / MLP_HID;
+    const int c = (int)(i % MLP_HID);
+    const float dh = dy[r * 2] * w4[c] + dy[r * 2 + 1] * w4[MLP_HID + c];
+    dz4[i] = __float2bfloat16(dh * dsiluf_(z4[i]));
+}
+
+// Column sums out[c] = sum_r X[r][c] in a fixed order (8 warps over rows, then warps in order).
+template <class T>
+__global__ void colsum_kernel(const T* __restrict__ x, int64_t rows, int cols, float* __restrict__ out)
+{
+    __shared__ float part[8][32];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
+    float s = 0.f;
+    if (c < cols)
+        for (int64_t r = w; r < rows; r += 8) s += (float)x[r * cols + c];
+    part[w][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (w == 0 && c < cols) {
+        float t = 0.f;
+        for (int i = 0; i < 8; ++i) t += part[i][threadIdx.x & 31];
+        out[c] = t;
+    }
+}
+
+// dW4[o][c] = sum_r dY[r][o] H4[r][c], db4[o] = sum_r dY[r][o] (fixed order).
+__global__ void out_wgrad_kernel(const float* __restrict__ dy, const bf16* __restrict__ h4, int64_t rows,
+                                 float* __restrict__ dw4, float* __restrict__ db4)
+{
+    __shared__ float part[2][8][32];
+    __shared__ float bpart[2][8][32];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
+    float s0 = 0.f, s1 = 0.f, b0 = 0.f, b1 = 0.f;
+    for (int64_t r = w; r < rows; r += 8) {
+        const float h = __bfloat162float(h4[r * MLP_HID + c]);
+        s0 = fmaf(dy[r * 2], h, s0);
+        s1 = fmaf(dy[r * 2 + 1], h, s1);
+        b0 += dy[r * 2];
+        b1 += dy[r * 2 + 1];
+    }
+    part[0][w][threadIdx.x & 31] = s0;
+    part[1][w][threadIdx.x & 31] = s1;
+    bpart[0][w][threadIdx.x & 31] = b0;
+    bpart[1][w][threadIdx.x & 31] = b1;
+    __syncthreads();
+    if (w == 0) {
+        float t0 = 0.f, t1 = 0.f, u0 = 0.f, u1 = 0.f;
+        for (int i = 0; i < 8; ++i) {
+            t0 += part[0][i][threadIdx.x & 31];
+            t1 += part[1][i][threadIdx.x & 31];
+            u0 += bpart[0][i][threadIdx.x & 31];
+            u1 += bpart[1][i][threadIdx.x & 31];
+        }
+        dw4[c] = t0;
+        dw4[MLP_HID + c] = t1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            db4[0] = u0;
+            db4[1] = u1;
+        }
+    }
+}
+
+// out[C x R] = in[R x C]^T (BF16), 32 x 32 tiles.
+__global__ void transpose_kernel(const bf16* __restrict__ in, int64_t R, int C, bf16* __restrict__ out)
+{
+    __shared__ bf16 tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[i][threadIdx.x] = in[r * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[c * R + r] = tile[threadIdx.x][i];
+    }
+}
+
+// out[i] = sum_s parts[s][i] in order; the first `cols` of every row of width `ld` are kept
+// (out has row width `cols`).
+__global__ void splitk_reduce_kernel(const float* __restrict__ parts, int S, int64_t stride, int rows, int ld,
+                                     int cols, float* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * cols) return;
+    const int64_t r = i / cols, c = i % cols;
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += parts[k * stride + r * ld + c];
+    out[i] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// Layer offsets in the flat parameter vector.
+__host__ __device__ constexpr int64_t off_w(int l)
+{
+    return l == 0 ? 0
+                  : (int64_t)MLP_HID * MLP_IN + MLP_HID + (int64_t)(l - 1) * ((int64_t)MLP_HID * MLP_HID + MLP_HID);
+}
+__host__ __device__ constexpr int64_t off_b(int l)
+{
+    return off_w(l) + (l == 0 ? (int64_t)MLP_HID * MLP_IN : (l == 4 ? (int64_t)MLP_OUT * MLP_HID : (int64_t)MLP_HID * MLP_HID));
+}
+
+// BF16 GEMM copies of the FP32 master weights: w0p [256 x 64] (zero-padded), w[l] [256 x 256],
+// wt[l] = w[l]^T, w4f = BF16-rounded W4 as FP32.
+__global__ void refresh_kernel(const float* __restrict__ p, bf16* __restrict__ w0p, bf16* __restrict__ w1,
+                               bf16* __restrict__ w2, bf16* __restrict__ w3, bf16* __restrict__ wt1,
+                               bf16* __restrict__ wt2, bf16* __restrict__ wt3, float* __restrict__ w4f)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nh = (int64_t)MLP_HID * MLP_HID;
+    if (i < (int64_t)MLP_HID * MLP_IN_PAD) {
+        const int64_t r = i / MLP_IN_PAD, c = i % MLP_IN_PAD;
+        w0p[i] = __float2bfloat16(c < MLP_IN ? p[off_w(0) + r * MLP_IN + c] : 0.0f);
+    }
+    if (i < nh) {
+        const int64_t r = i / MLP_HID, c = i % MLP_HID;
+        bf16* ws[3] = {w1, w2, w3};
+        bf16* wts[3] = {wt1, wt2, wt3};
+        for (int l = 0; l < 3; ++l) {
+            const bf16 v = __float2bfloat16(p[off_w(l + 1) + i]);
+            ws[l][i] = v;
+            wts[l][c * MLP_HID + r] = v;
+        }
+    }
+    if (i < (int64_t)MLP_OUT * MLP_HID) w4f[i] = __bfloat162float(__float2bfloat16(p[off_w(4) + i]));
+}
+
+__global__ void gather_rows_kernel(const bf16* __restrict__ xall, const float* __restrict__ tall,
+                                   const int64_t* __restrict__ idx, int64_t B, int64_t rows_pad, bf16* __restrict__ x0,
+                                   float* __restrict__ t)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows_pad * MLP_IN_PAD) return;
+    const int64_t r = i / MLP_IN_PAD, c = i % MLP_IN_PAD;
+    const bool live = r < B;
+    const int64_t src = live ? idx[r] : 0;
+    x0[i] = live ? xall[src * MLP_IN_PAD + c] : __float2bfloat16(0.0f);
+    if (c < 2) t[r * 2 + c] = live ? tall[src * 2 + c] : 0.0f;
+}
+
+unsigned grid1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct GateArgs {
+    double mu0, sd0, mu1, sd1, need_neff;
+    int trusted;
+};
+
+// Per Lambda: ln xi and ln N_eff from the network, and whether the Monte Carlo xi is needed
+// (untrusted network, Lambda outside the training box, predicted N_eff < 4 N, or a timed-out wait).
+__global__ void gate_kernel(const float* __restrict__ y, const uint8_t* __restrict__ outside,
+                            const int64_t* __restrict__ dK, const int* __restrict__ err, GateArgs a,
+                            uint8_t* __restrict__ need, double* __restrict__ lnxi, double* __restrict__ lnneff)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= *dK) return;
+    const double lx = (double)y[k * 2] * a.sd0 + a.mu0;
+    const double ln = (double)y[k * 2 + 1] * a.sd1 + a.mu1;
+    lnxi[k] = lx;
+    lnneff[k] = ln;
+    need[k] = (uint8_t)(!a.trusted || outside[k] || *err || !(exp(ln) >= a.need_neff) || !isfinite(lx));
+}
+
+}  // namespace
+
+int Surrogate::enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double need_neff,
+                            uint8_t* need, double* lnxi, double* lnneff)
+{
+    const int64_t rp = (k_cap + TC_BM - 1) / TC_BM * TC_BM;
+    if (rp > cap || (int64_t)outside.bytes < k_cap) {
+        err = "surrogate buffers not sized for the batch";
+        return POP_ESTATE;
+    }
+    int rc = normalise(d_lambda, k_cap, P, outside.as<uint8_t>());
+    if (rc != POP_OK) return rc;
+    rc = forward(rp);
+    if (rc != POP_OK) return rc;
+    GateArgs a{mu[0], sd[0], mu[1], sd[1], need_neff, trusted ? 1 : 0};
+    gate_kernel<<<grid1(k_cap, 256), 256, 0, stream>>>(y.as<float>(), outside.as<uint8_t>(), dK, err_flag.as<int>(), a,
+                                                       need, lnxi, lnneff);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return POP_ECUDA;
+    }
+    return POP_OK;
+}
+
+int Surrogate::ensure_gate(int64_t k_cap)
+{
+    int rc = ensure_rows(k_cap);
+    if (rc != POP_OK) return rc;
+    if ((int64_t)outside.bytes < k_cap) {
+        const cudaError_t e = outside.alloc((size_t)k_cap);
+        if (e != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? POP_ENOMEM : POP_ECUDA;
+        }
+    }
+    return POP_OK;
+}
+
+// ================================================================== Surrogate
+#define SK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                             \
+            return e_ == cudaErrorMemoryAllocation ? POP_ENOMEM : POP_ECUDA;                      \
+        }                                                                                         \
+    } while (0)
+
+int Surrogate::init(int dev, cudaStream_t s)
+{
+    device = dev;
+    stream = s;
+    SK(set_gemm_attributes());
+    SK(params.alloc(sizeof(float) * MLP_N_PARAMS));
+    SK(adam_m.alloc(sizeof(float) * MLP_N_PARAMS));
+    SK(adam_v.alloc(sizeof(float) * MLP_N_PARAMS));
+    SK(grads.alloc(sizeof(float) * MLP_N_PARAMS));
+    SK(w0p.alloc(sizeof(bf16) * MLP_HID * MLP_IN_PAD));
+    for (int l = 0; l < 3; ++l) {
+        SK(w[l].alloc(sizeof(bf16) * MLP_HID * MLP_HID));
+        SK(wt[l].alloc(sizeof(bf16) * MLP_HID * MLP_HID));
+    }
+    SK(w4f.alloc(sizeof(float) * MLP_OUT * MLP_HID));
+    SK(err_flag.alloc(sizeof(int)));
+    SK(cudaMemsetAsync(err_flag.p, 0, sizeof(int), stream));
+    SK(dw0.alloc(sizeof(float) * MLP_HID * MLP_IN_PAD));
+    return POP_OK;
+}
+
+int Surrogate::ensure_rows(int64_t rows)
+{
+    rows = (rows + TC_BM - 1) / TC_BM * TC_BM;
+    if (rows <= cap) return POP_OK;
+    SK(x0.alloc(sizeof(bf16) * rows * MLP_IN_PAD));
+    for (int l = 0; l < 4; ++l) {
+        SK(z[l].alloc(sizeof(float) * rows * MLP_HID));
+        SK(h[l].alloc(sizeof(bf16) * rows * MLP_HID));
+    }
+    SK(y.alloc(sizeof(float) * rows * 2));
+    SK(dy.alloc(sizeof(float) * rows * 2 + sizeof(float) * rows));  // dY, then per-row loss
+    SK(dz[0].alloc(sizeof(bf16) * rows * MLP_HID));
+    SK(dz[1].alloc(sizeof(bf16) * rows * MLP_HID));
+    SK(dzt.alloc(sizeof(bf16) * rows * MLP_HID));
+    SK(ht.alloc(sizeof(bf16) * rows * MLP_HID));
+    const int64_t splits = std::max<int64_t>(1, rows / 512);
+    SK(parts.alloc(sizeof(float) * splits * MLP_HID * MLP_HID));
+    cap = rows;
+    return POP_OK;
+}
+
+int Surrogate::refresh_bf16()
+{
+    refresh_kernel<<<grid1((int64_t)MLP_HID * MLP_HID, 256), 256, 0, stream>>>(
+        params.as<float>(), w0p.as<bf16>(), w[0].as<bf16>(), w[1].as<bf16>(), w[2].as<bf16>(), wt[0].as<bf16>(),
+        wt[1].as<bf16>(), wt[2].as<bf16>(), w4f.as<float>());
+    SK(cudaGetLastError());
+    return POP_OK;
+}
+
+int Surrogate::set_params_host(const float* flat)
+{
+    SK(cudaMemcpyAsync(params.p, flat, sizeof(float) * MLP_N_PARAMS, cudaMemcpyHostToDevice, stream));
+    SK(cudaMemsetAsync(adam_m.p, 0, sizeof(float) * MLP_N_PARAMS, stream));
+    SK(cudaMemsetAsync(adam_v.p, 0, sizeof(float) * MLP_N_PARAMS, stream));
+    adam_step = 0;
+    has_params = true;
+    return refresh_bf16();
+}
+
+int Surrogate::get_params_host(float* flat)
+{
+    SK(cudaMemcpyAsync(flat, params.p, sizeof(float) * MLP_N_PARAMS, cudaMemcpyDeviceToHost, stream));
+    SK(cudaStreamSynchronize(stream));
+    return POP_OK;
+}
+
+int Surrogate::init_params(uint64_t seed)
+{
+    // Uniform(-sqrt(3/fan_in), sqrt(3/fan_in)) weights (unit-variance pre-activations), zero biases.
+    std::vector<float> p(MLP_N_PARAMS, 0.0f);
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> u(-1.0, 1.0);
+    const int fan_in[MLP_LAYERS] = {MLP_IN, MLP_HID, MLP_HID, MLP_HID, MLP_HID};
+    const int fan_out[MLP_LAYERS] = {MLP_HID, MLP_HID, MLP_HID, MLP_HID, MLP_OUT};
+    for (int l = 0; l < MLP_LAYERS; ++l) {
+        const double a = std::sqrt(3.0 / fan_in[l]);
+        for (int64_t i = 0; i < (int64_t)fan_in[l] * fan_out[l]; ++i) p[off_w(l) + i] = (float)(a * u(rng));
+    }
+    return set_params_host(p.data());
+}
+
+int Surrogate::forward(int64_t rows_pad)
+{
+    GemmArgs g{};
+    g.err = err_flag.as<int>();
+    const bf16* in = x0.as<bf16>();
+    int ld_in = MLP_IN_PAD;
+    const bf16* ws[4] = {w0p.as<bf16>(), w[0].as<bf16>(), w[1].as<bf16>(), w[2].as<bf16>()};
+    for (int l = 0; l < 4; ++l) {
+        g.A = in;
+        g.lda = ld_in;
+        g.B = ws[l];
+        g.ldb = l == 0 ? MLP_IN_PAD : MLP_HID;
+        g.M = (int)rows_pad;
+        g.N = MLP_HID;
+        g.K = l == 0 ? MLP_IN_PAD : MLP_HID;
+        g.k_split = g.K;
+        g.epi = EPI_FWD;
+        g.bias = params.as<float>() + off_b(l);
+        g.Z = z[l].as<float>();
+        g.ldz = MLP_HID;
+        g.H = h[l].as<bf16>();
+        g.ldh = MLP_HID;
+        SK(launch_gemm(g, 1, stream));
+        in = h[l].as<bf16>();
+        ld_in = MLP_HID;
+    }
+    out_fwd_kernel<<<grid1(rows_pad * 32, 256), 256, 0, stream>>>(h[3].as<bf16>(), w4f.as<float>(),
+                                                                  params.as<float>() + off_b(4), y.as<float>(),
+                                                                  rows_pad);
+    SK(cudaGetLastError());
+    return POP_OK;
+}
+
+int Surrogate::backward(int64_t rows, int64_t rows_pad, const float* t)
+{
+    float* gr = grads.as<float>();
+    float* dyp = dy.as<float>();
+    float* row_loss = dyp + rows_pad * 2;
+    loss_grad_kernel<<<grid1(rows_pad, 256), 256, 0, stream>>>(y.as<float>(), t, rows, rows_pad, dyp, row_loss);
+    out_wgrad_kernel<<<MLP_HID / 32, 256, 0, stream>>>(dyp, h[3].as<bf16>(), rows_pad, gr + off_w(4), gr + off_b(4));
+    out_bwd_kernel<<<grid1(rows_pad * MLP_HID, 256), 256, 0, stream>>>(dyp, w4f.as<float>(), z[3].as<float>(),
+                                                                        dz[0].as<bf16>(), rows_pad);
+    SK(cudaGetLastError());
+    // Split-K over the batch for the weight gradients: stages of 64 rows, about 512 rows per CTA.
+    const int64_t want = std::max<int64_t>(1, rows_pad / 512);
+    const int k_split = (int)(((rows_pad + want - 1) / want + TC_BK - 1) / TC_BK * TC_BK);
+    const int splits = (int)((rows_pad + k_split - 1) / k_split);
+    int cur = 0;
+    for (int l = 3; l >= 0; --l) {
+        const bf16* dzc = dz[cur].as<bf16>();
+        const int in_w = l == 0 ? MLP_IN_PAD : MLP_HID;
+        const bf16* hin = l == 0 ? x0.as<bf16>() : h[l - 1].as<bf16>();
+        transpose_kernel<<<dim3(MLP_HID / 32, (unsigned)(rows_pad / 32)), dim3(32, 8), 0, stream>>>(
+            dzc, rows_pad, MLP_HID, dzt.as<bf16>());
+        transpose_kernel<<<dim3(in_w / 32, (unsigned)(rows_pad / 32)), dim3(32, 8), 0, stream>>>(
+            hin, rows_pad, in_w, ht.as<bf16>());
+        SK(cudaGetLastError());
+        // dW_l = dZ^T H: M = 256 outputs, N = layer inputs, K = batch rows (split-K partials).
+        GemmArgs g{};
+        g.err = err_flag.as<int>();
+        g.A = dzt.as<bf16>();
+        g.lda = (int)rows_pad;
+        g.B = ht.as<bf16>();
+        g.ldb = (int)rows_pad;
+        g.M = MLP_HID;
+        g.N = in_w;
+        g.K = (int)rows_pad;
+        g.k_split = k_split;
+        g.epi = EPI_F32;
+        g.C = parts.as<float>();
+        g.ldc = in_w;
+        g.c_split_stride = (int64_t)MLP_HID * in_w;
+        SK(launch_gemm(g, splits, stream));
+        float* dwl = l == 0 ? dw0.as<float>() : gr + off_w(l);
+        splitk_reduce_kernel<<<grid1((int64_t)MLP_HID * in_w, 256), 256, 0, stream>>>(
+            parts.as<float>(), splits, (int64_t)MLP_HID * in_w, MLP_HID, in_w, in_w, dwl);
+        if (l == 0)  // keep the 12 real input columns of the padded input layer
+            splitk_reduce_kernel<<<grid1((int64_t)MLP_HID * MLP_IN, 256), 256, 0, stream>>>(
+                dw0.as<float>(), 1, 0, MLP_HID, MLP_IN_PAD, MLP_IN, gr + off_w(0));
+        colsum_kernel<bf16><<<MLP_HID / 32, 256, 0, stream>>>(dzc, rows_pad, MLP_HID, gr + off_b(l));
+        SK(cudaGetLastError());
+        if (l > 0) {  // dZ_l = (dZ_{l+1} W_l) * SiLU'(Z_l)
+            GemmArgs b{};
+            b.err = err_flag.as<int>();
+            b.A = dzc;
+            b.lda = MLP_HID;
+            b.B = wt[l - 1].as<bf16>();
+            b.ldb = MLP_HID;
+            b.M = (int)rows_pad;
+            b.N = MLP_HID;
+            b.K = MLP_HID;
+            b.k_split = MLP_HID;
+            b.epi = EPI_BWD;
+            b.Z = z[l - 1].as<float>();
+            b.ldz = MLP_HID;
+            b.H = dz[cur ^ 1].as<bf16>();
+            b.ldh = MLP_HID;
+            SK(launch_gemm(b, 1, stream));
+            cur ^= 1;
+        }
+    }
+    return POP_OK;
+}
+
+int Surrogate::adam(float lr)
+{
+    ++adam_step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)adam_step));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)adam_step));
+    adam_kernel<<<grid1(MLP_N_PARAMS, 256), 256, 0, stream>>>(params.as<float>(), adam_m.as<float>(),
+                                                             adam_v.as<float>(), grads.as<float>(), MLP_N_PARAMS, lr,
+                                                             b1, b2, 1e-8f, bc1, bc2);
+    SK(cudaGetLastError());
+    return refresh_bf16();
+}
+
+int Surrogate::check_error()
+{
+    int h = 0;
+    SK(cudaMemcpyAsync(&h, err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SK(cudaStreamSynchronize(stream));
+    if (h) {
+        err = "a tensor-core wait timed out";
+        cudaMemsetAsync(err_flag.p, 0, sizeof(int), stream);
+        return POP_ETIMEOUT;
+    }
+    return POP_OK;
+}
+
+int Surrogate::normalise(const double* lambda, int64_t K, int P, uint8_t* outside, __nv_bfloat16* dst)
+{
+    const int64_t rows_pad = (K + TC_BM - 1) / TC_BM * TC_BM;
+    Box box;
+    for (int i = 0; i < MLP_IN; ++i) {
+        box.lo[i] = lo[i];
+        box.hi[i] = hi[i];
+    }
+    normalise_kernel<<<grid1(rows_pad * MLP_IN_PAD, 256), 256, 0, stream>>>(lambda, K, P, box,
+                                                                           dst ? dst : x0.as<bf16>(), rows_pad,
+                                                                           outside);
+    SK(cudaGetLastError());
+    return POP_OK;
+}
+
+cudaError_t mlp_gemm_check(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N, int K, int* err,
+                           cudaStream_t s)
+{
+    cudaError_t e = set_gemm_attributes();
+    if (e != cudaSuccess) return e;
+    GemmArgs g{};
+    g.A = A;
+    g.lda = K;
+    g.B = B;
+    g.ldb = K;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.k_split = K;
+    g.epi = EPI_F32;
+    g.C = C;
+    g.ldc = N;
+    g.err = err;
+    return launch_gemm(g, 1, s);
+}
+
+// Training-data gather (used by the training loop in pop_api.cu).
+cudaError_t mlp_gather(const __nv_bfloat16* xall, const float* tall, const int64_t* idx, int64_t B, int64_t rows_pad,
+                       __nv_bfloat16* x0, float* t, cudaStream_t s)
+{
+    gather_rows_kernel<<<grid1(rows_pad * MLP_IN_PAD, 256), 256, 0, s>>>(xall, tall, idx, B, rows_pad, x0, t);
+    return cudaGetLastError();
+}
+
+}  // namespace pop

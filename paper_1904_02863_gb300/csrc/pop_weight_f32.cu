@@ -142,7 +142,8 @@ __device__ __forceinline__ void warp_combine(float& s, float& c)
 template <int T, int NT, bool HAS_Z>
 __global__ void __launch_bounds__(NT)
 weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
-                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
+                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2,
+                  const uint8_t* __restrict__ need_mc)
 {
     constexpr int NW = NT / 32;
     __shared__ LamF32 sl[T];
@@ -157,6 +158,11 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
         const int c = (int)(item / n_tiles);
         const int64_t k0 = (item - (int64_t)c * n_tiles) * T;
         const int tn = (int)(K - k0 < T ? K - k0 : T);
+        if (need_mc && c >= wd.n_ev_chunks) {  // injection item: needed only for Monte Carlo xi
+            bool any = false;
+            for (int l = 0; l < tn; ++l) any |= need_mc[k0 + l] != 0;
+            if (!any) continue;  // same decision on every thread of the block
+        }
         __syncthreads();
         {
             constexpr int W = (int)(sizeof(LamF32) / 4);
@@ -256,11 +262,12 @@ const void* weight_f32_fn(const Tiling& t, bool has_z)
 }
 
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* lam,
-                              const int64_t* dK, double* part, double* part2, cudaStream_t s)
+                              const int64_t* dK, double* part, double* part2, SurrogateXi sx, cudaStream_t s)
 {
     const void* fn = weight_f32_fn(t, wd.has_z != 0);
     if (!fn) return cudaErrorInvalidValue;
-    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2};
+    const uint8_t* need = sx.need_mc;
+    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2, &need};
     return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, 0, s);
 }
 
