@@ -47,6 +47,10 @@ FP64_OPS_PER_INJ_PAIR = 57
 FP64_LANES_PER_SM = 2
 SMS = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
+# profiles/weight_f64_catalog400x4096_K64_full.md (174.22 MB / 2,077,126 units); a launch
+# reads every chunk from DRAM once, so traffic scales with the units.
+F64_DRAM_BYTES_PER_UNIT = 174.22e6 / 2077126
 
 
 def in_support_pairs(theta, lam):
@@ -186,6 +190,33 @@ def cpu_baseline(cat, inj, lam, n_rows):
             "seconds": dt}
 
 
+def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world):
+    """FP32 weights + the trained ln xi network (Monte Carlo xi only where its gate says so).
+
+    Training (2e5 Lambda from the prior box, 10% held out, targets from this
+    workload's own injections, 60 epochs) is setup, timed separately.
+    """
+    import torch
+    box = synth.LAMBDA_BOX[:11]
+    t0 = time.perf_counter()
+    B.pop_xi_surrogate_train(like.ctx, 200000, box[:, 0], box[:, 1], epochs=60, seed=synth.seed_for(2, 5))
+    train_s = time.perf_counter() - t0
+    info = B.pop_xi_surrogate_info(like.ctx)
+    ms, w = timed(B.POP_MODE_F32_SURROGATE)
+    sur = [o.clone() for o in outs]
+    B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F32, out=outs)
+    torch.cuda.synchronize()
+    used = (sur[3].cpu().numpy().view(np.uint32) & B.POP_FLAG_SURROGATE_USED) != 0
+    d = (sur[0] - outs[0]).abs().cpu().numpy()
+    fin = np.isfinite(d)
+    K = len(lam)
+    return {"value": world * K * args.steps / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / args.steps,
+            "weight_ms": w, "dtype": "f32+bf16 network", "train_seconds": train_s,
+            "heldout_rmse_lnxi": info["heldout_rmse"], "heldout_mc_noise": info["mc_noise"],
+            "trusted": info["trusted"], "surrogate_used_frac": float(used.mean()),
+            "abs_dlnL_vs_f32_mc": {"mean": float(d[fin].mean()), "max": float(d[fin].max())}}
+
+
 def run_reference(args, rank, world):
     """CPU oracle arm: rank 0 only."""
     if rank != 0:
@@ -299,7 +330,10 @@ def main():
         peak_tops = FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12  # FP64 pipe ops/s (FMA = 1 op)
         achieved_tops = ops / (w_h * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s (FP64 pipe)",
-                    "frac": achieved_tops / peak_tops, "traffic": None, "kernel": "weight_f64_kernel",
+                    "frac": achieved_tops / peak_tops,
+                    "traffic": F64_DRAM_BYTES_PER_UNIT * (int(cat.offsets[-1]) + int(inj.n_found)),
+                    "traffic_basis": "ncu dram bytes of a 400-event capture scaled by units",
+                    "kernel": "weight_f64_kernel",
                     "weight_ms": w_h, "ops_per_launch": ops,
                     "in_support_pairs": n_ev_pairs + n_inj_pairs, "all_pairs": all_pairs,
                     "ops_per_in_support_pair": FP64_OPS_PER_PAIR,
@@ -326,6 +360,7 @@ def main():
     if args.mode == "both":
         line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
                                  "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32"}}
+        line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
     like.close()
