@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1904_02863_gb300 import synth  # noqa: E402
+from paper_1904_02863_gb300 import replicas, synth  # noqa: E402
 
 METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
 WORKLOAD = "c2_f64_catalog"
@@ -150,31 +150,11 @@ class Clocks:
 
 
 def dist_setup(n_gpus):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        import torch
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
-    return rank, local, world
+    return replicas.init_from_env()
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+barrier = replicas.barrier
+max_over_ranks = replicas.max_over_ranks
 
 
 def cpu_baseline(cat, inj, lam, n_rows):
