@@ -42,7 +42,9 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        # POP_ORACLE_LIB points the pins at another build of this file (the mutation tests
+        # plant mistakes in a copy and check that the pins catch them).
+        lib = ctypes.CDLL(os.environ.get("POP_ORACLE_LIB") or build())
         d, i64, i32, p = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
         for name in ("pop_oracle_p_m1", "pop_oracle_p_chi", "pop_oracle_p_z"):
             getattr(lib, name).argtypes = [d, p]
