@@ -306,6 +306,25 @@ def test_autotune_and_cache(B, small, oracle, tmp_path):
     B.pop_set_tiling(like.ctx, B.POP_MODE_F64, 8, 256)
 
 
+def test_ragged_redshift_scale_sampled(B, oracle):
+    """The batching form at full size: 2000 ragged events (S_i ~ U{500..16000}, 1.67e7 samples),
+    redshift on, 1.97e6 injections, FP32; uneven batches replay one graph (K read on the device).
+    The oracle (on the FP32-rounded inputs) checks sampled rows of every batch."""
+    from paper_1904_02863_gb300 import synth
+    cat, inj, lam = synth.make_workload("c4_ragged_z")
+    like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F32)
+    c32, i32 = rounded(cat, inj)
+    picks = []
+    for k in (64, 200, 1000, 4096):
+        got = like(lam[:k], B.POP_MODE_F32)[0]
+        picks.append((lam[k - 1], got[k - 1]))
+    L = np.array([p[0] for p in picks])
+    ref = oracle.loglik(c32, i32, L)[0]
+    got = np.array([p[1] for p in picks])
+    assert np.max(np.abs(got - ref)) <= 0.05, np.abs(got - ref)
+    like.close()
+
+
 def test_catalog_scale_sampled(B, oracle):
     """The benchmark's workload (1000 events x 4096 samples, 1e7 draws, K = 1024) in
     its launch configuration; the oracle checks a sample of the Lambda rows."""
