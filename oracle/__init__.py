@@ -62,6 +62,8 @@ def _load():
         lib.pop_oracle_loglik.argtypes = [i64, p, i32, p, p, i64, i64, p, p, i64, i32, p, i32, p, p, p, p]
         lib.pop_oracle_loglik.restype = i32
         lib.pop_oracle_max_threads.restype = i32
+        lib.pop_oracle_xi_grid.argtypes = [i32, p, i32, p, p, i64, i32, p, p, p]
+        lib.pop_oracle_xi_grid.restype = i32
         _lib = lib
     return _lib
 
@@ -119,6 +121,21 @@ def lambda_valid(L):
 
 def max_threads():
     return _load().pop_oracle_max_threads()
+
+
+def xi_grid(m1_nodes, q_nodes, pdet, lambdas):
+    """ln xi on a regular (m1, q) grid with detection probability pdet [n_m1, n_q]; (lnxi, flags)."""
+    m1 = np.ascontiguousarray(m1_nodes, dtype=np.float64)
+    q = np.ascontiguousarray(q_nodes, dtype=np.float64)
+    pd = np.ascontiguousarray(pdet, dtype=np.float64)
+    lam = np.ascontiguousarray(np.atleast_2d(lambdas), dtype=np.float64)
+    K, P = lam.shape
+    out, fl = np.empty(K), np.empty(K, np.uint32)
+    rc = _load().pop_oracle_xi_grid(m1.size, _ptr(m1), q.size, _ptr(q), _ptr(pd), K, P, _ptr(lam), _ptr(out),
+                                    _ptr(fl))
+    if rc != 0:
+        raise ValueError("oracle rejected the grid")
+    return out, fl
 
 
 def loglik(catalog, injections, lambdas, nthreads=0):

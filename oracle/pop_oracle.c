@@ -244,6 +244,44 @@ int pop_oracle_loglik(int64_t n_events, const int64_t* offsets, int n_dims,
     return 0;
 }
 
+/*
+ * Selection term on a regular grid (Sec. "Population acceleration": VT on a
+ * regular grid, limited to low dimension, no spin effects).  With a detection
+ * probability pdet[a * n_q + b] given at the grid nodes (m1_a, q_b), the grid
+ * estimate of xi(Lambda) = int p(m1, q | Lambda) P_det(m1, q) dm1 dq is the
+ * two-dimensional trapezoid rule over the nodes:
+ *   xi_grid = sum_a sum_b wa_a wq_b p(m1_a | Lambda) p(q_b | m1_a, Lambda) pdet[a, b]
+ * with wa, wq the trapezoid weights of the (not necessarily uniform) node sets.
+ * The spin and tilt densities integrate to one and are left out.  Output: ln xi_grid
+ * (-inf when it is 0; invalid Lambda -> 0 and the returned flag bit 1).
+ */
+int pop_oracle_xi_grid(int n_m1, const double* m1, int n_q, const double* q, const double* pdet,
+                       int64_t K, int n_params, const double* lambda, double* out_lnxi, uint32_t* out_flags)
+{
+    if (n_m1 < 2 || n_q < 2 || K < 0 || !out_lnxi) return -1;
+    for (int64_t k = 0; k < K; ++k) {
+        const double* L = lambda + k * n_params;
+        if (!pop_oracle_lambda_valid(L, n_params)) {
+            out_lnxi[k] = 0.0;
+            if (out_flags) out_flags[k] = OR_FLAG_INVALID_LAMBDA;
+            continue;
+        }
+        double s = 0.0;
+        for (int a = 0; a < n_m1; ++a) {
+            double wa = 0.5 * ((a + 1 < n_m1 ? m1[a + 1] : m1[a]) - (a > 0 ? m1[a - 1] : m1[a]));
+            double pm = pop_oracle_p_m1(m1[a], L);
+            if (pm == 0.0) continue;
+            for (int b = 0; b < n_q; ++b) {
+                double wq = 0.5 * ((b + 1 < n_q ? q[b + 1] : q[b]) - (b > 0 ? q[b - 1] : q[b]));
+                s += wa * wq * pm * pop_oracle_p_q(q[b], m1[a], L) * pdet[(int64_t)a * n_q + b];
+            }
+        }
+        out_lnxi[k] = s > 0.0 ? log(s) : -INFINITY;
+        if (out_flags) out_flags[k] = s > 0.0 ? 0u : OR_FLAG_ZERO_XI;
+    }
+    return 0;
+}
+
 /* Threads the OpenMP runtime would use (1 without OpenMP). */
 int pop_oracle_max_threads(void)
 {
