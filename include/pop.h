@@ -139,6 +139,57 @@ int pop_load_injections(pop_ctx* ctx, int64_t n_found, int64_t n_draw, int n_dim
 int pop_loglik(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int mode,
                double* out_lnL, double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem);
 
+/* ------------------------------------------------------------------ grid selection term
+ * The paper evaluates VT on a regular grid with GPU acceleration, limited to a
+ * low-dimensional space without spin effects (Sec. "Population acceleration").
+ * Here the grid spans (m1, q) and the selection term is the two-dimensional
+ * trapezoid rule over its nodes:
+ *
+ *   xi_grid(Lambda) = sum_a sum_b wa_a wq_b p(m1_a | Lambda) p(q_b | m1_a, Lambda) pdet[a, b]
+ *
+ * with wa_a = (m1_{a+1} - m1_{a-1}) / 2 (one-sided at the ends, same for wq)
+ * and the mass and mass-ratio densities and supports of the population model
+ * above (the spin and redshift densities integrate to one and drop out).
+ * The spin-free grid cannot include the spin dependence of detectability; the
+ * injection term can. */
+
+/* Selection-term source of pop_loglik. */
+enum { POP_XI_INJECTIONS = 0, POP_XI_GRID = 1 };
+
+/* Load the grid: nodes m1[n_m1] and q[n_q] (finite, strictly increasing,
+ * n_m1, n_q >= 2, n_m1 * n_q <= 2^28, at least one q <= 1) and the detection
+ * probability pdet[n_m1 * n_q], row-major [a][b], finite and >= 0 at every node
+ * with q <= 1 (nodes with q > 1 only shape the weights).  All three arrays in
+ * `mem`; copied (FP64 and an FP32 copy, packed in 64-row tiles).  Replaces a
+ * previously loaded grid; synchronous.  POP_EINVAL on malformed input. */
+int pop_load_vt_grid(pop_ctx* ctx, int n_m1, const double* m1, int n_q, const double* q, const double* pdet,
+                     int mem);
+
+/* Choose the selection term of pop_loglik: POP_XI_INJECTIONS (default, needs
+ * pop_load_injections) or POP_XI_GRID (needs pop_load_vt_grid).  With the grid,
+ * pop_loglik needs no injections, returns out_neff = +inf (no Monte Carlo
+ * variance, so POP_FLAG_LOW_NEFF is never set) and rejects
+ * POP_MODE_F32_SURROGATE (which replaces the injection term). */
+int pop_set_xi_source(pop_ctx* ctx, int source);
+
+/* ln xi_grid for K Lambda rows (lambda[K * n_params], n_params 11 or 12, kappa
+ * unused), without events: out_lnxi[K] (0 for an invalid Lambda, -inf when
+ * xi_grid = 0) and out_flags[K] (may be NULL: POP_FLAG_INVALID_LAMBDA,
+ * POP_FLAG_ZERO_XI), all in `mem`; synchronous.
+ *   POP_MODE_F64: FP64 throughout.
+ *   POP_MODE_F32: FP32 pdet, q-node factors and node sums (an FP32 sum per
+ *                 32 nodes, added into an FP32 running sum); FP64 per-row
+ *                 factors, support edges and row combine.
+ * POP_ETIMEOUT when a bounded device-side wait of the contraction gave up
+ * (outputs then undefined). */
+int pop_xi_grid(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int mode, double* out_lnxi,
+                uint32_t* out_flags, int mem);
+
+/* Duration in milliseconds of the last grid evaluation (pop_xi_grid, or the
+ * grid part of pop_loglik): the node contraction kernel of the first 8192
+ * Lambda, and the whole grid term (CUDA events on the context stream). */
+int pop_xi_grid_last_ms(pop_ctx* ctx, double* contraction_ms, double* total_ms);
+
 /* Tiling of the persistent weight kernel for `mode` (POP_MODE_F64 or
  * POP_MODE_F32): Lambda points per work item (1, 2, 4, 8, 16 or 32), threads
  * per block (128, 256 or 512) and resident blocks per SM (0 = occupancy

@@ -22,6 +22,7 @@ POP_MODE_F64, POP_MODE_F32, POP_MODE_F32_SURROGATE = 0, 1, 2
 POP_MEM_HOST, POP_MEM_DEVICE = 0, 1
 POP_FLAG_INVALID_LAMBDA, POP_FLAG_ZERO_EVENT, POP_FLAG_LOW_NEFF = 1, 2, 4
 POP_FLAG_SURROGATE_USED, POP_FLAG_MC_FALLBACK, POP_FLAG_ZERO_XI = 8, 16, 32
+POP_XI_INJECTIONS, POP_XI_GRID = 0, 1
 
 # Every symbol include/pop.h declares (checked by the CPU test suite).
 EXPORTS = (
@@ -32,6 +33,7 @@ EXPORTS = (
     "pop_xi_surrogate_train", "pop_xi_surrogate_info", "pop_xi_surrogate_infer", "pop_xi_surrogate_save",
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
+    "pop_load_vt_grid", "pop_set_xi_source", "pop_xi_grid", "pop_xi_grid_last_ms",
 )
 MLP_N_PARAMS = 201218
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -85,6 +87,10 @@ def load_library(path: str = LIB_PATH):
         "pop_mlp_gradients": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(d)]),
         "pop_mlp_train_step": (i32, [vp, i64, vp, vp, ctypes.c_float]),
         "pop_mlp_gemm_check": (i32, [vp, i32, i32, i32, vp, vp, vp]),
+        "pop_load_vt_grid": (i32, [vp, i32, vp, i32, vp, vp, i32]),
+        "pop_set_xi_source": (i32, [vp, i32]),
+        "pop_xi_grid": (i32, [vp, i64, i32, vp, i32, vp, vp, i32]),
+        "pop_xi_grid_last_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +242,40 @@ def pop_math_check(ctx, fn, x):
     _check(ctx, load_library().pop_math_check(ctx, int(fn), xa.size, xa.ctypes.data_as(ctypes.c_void_p),
                                               y.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST))
     return y
+
+
+def pop_load_vt_grid(ctx, m1_nodes, q_nodes, pdet):
+    """Grid selection term: nodes and pdet [len(m1), len(q)] (numpy arrays or CUDA tensors)."""
+    mp, mem, k1 = _arg(m1_nodes, np.float64)
+    qp, mem2, k2 = _arg(q_nodes, np.float64)
+    pp, mem3, k3 = _arg(pdet, np.float64)
+    if not (mem == mem2 == mem3):
+        raise TypeError("m1, q and pdet must all be host arrays or all device tensors")
+    n1, nq = int(m1_nodes.shape[0]), int(q_nodes.shape[0])
+    if tuple(pdet.shape) != (n1, nq):
+        raise ValueError(f"pdet must have shape ({n1}, {nq})")
+    _check(ctx, load_library().pop_load_vt_grid(ctx, n1, mp, nq, qp, pp, mem))
+
+
+def pop_set_xi_source(ctx, source):
+    _check(ctx, load_library().pop_set_xi_source(ctx, int(source)))
+
+
+def pop_xi_grid(ctx, lambdas, mode=POP_MODE_F64):
+    """ln xi_grid and flags for each row of ``lambdas`` (host arrays; synchronous)."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    K, P = lam.shape
+    lx, fl = np.empty(K), np.empty(K, np.uint32)
+    _check(ctx, load_library().pop_xi_grid(ctx, K, P, lam.ctypes.data_as(ctypes.c_void_p), int(mode),
+                                           lx.ctypes.data_as(ctypes.c_void_p), fl.ctypes.data_as(ctypes.c_void_p),
+                                           POP_MEM_HOST))
+    return lx, fl
+
+
+def pop_xi_grid_last_ms(ctx):
+    w, t = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, load_library().pop_xi_grid_last_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, t.value
 
 
 def _f32(a, shape=None):

@@ -12,6 +12,7 @@
 
 #include "pop.h"
 #include "pop_devbuf.h"
+#include "pop_gridvt.h"
 #include "pop_internal.h"
 #include "pop_mlp.h"
 
@@ -96,6 +97,8 @@ struct pop_ctx {
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts expc{};
     std::unique_ptr<Surrogate> sur;  // ln xi network, created on first use
+    std::unique_ptr<GridVT> grid;    // grid selection term, created by pop_load_vt_grid
+    int xi_source = POP_XI_INJECTIONS;
     bool timed = false;
     int64_t last_K = 0;
     int last_params = 0;
@@ -306,7 +309,10 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     // nodes, or the replayed graph would never record them.
     const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     const int m = mode == POP_MODE_F64 ? 0 : 1;
-    WorkDesc wd{c->d_chunks.as<Chunk>(), c->n_chunks, c->n_ev_chunks, c->ev.n_dims == 7};
+    // With the grid selection term the injections are not part of the work list.
+    const bool use_grid = c->xi_source == POP_XI_GRID;
+    const int32_t n_items = use_grid ? c->n_ev_chunks : c->n_chunks;
+    WorkDesc wd{c->d_chunks.as<Chunk>(), n_items, c->n_ev_chunks, c->ev.n_dims == 7};
     CK(cudaEventRecordWithFlags(c->ev_t0, c->stream, rec), "event");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
                        c->d_c32.as<LamF32>(), c->stream), "prologue");
@@ -333,11 +339,15 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
                              c->d_part.as<double>(), c->d_part2.as<double>(), sx, c->stream), "weight_f32");
     }
     CK(cudaEventRecordWithFlags(c->ev_w1, c->stream, rec), "event");
+    if (use_grid)
+        CK(c->grid->enqueue(m, c->d_lambda.as<double>(), n_params, c->d_K.as<int64_t>(), c->k_cap, true, rec,
+                            c->stream), "grid selection term");
     CK(launch_finalise(c->d_part.as<double>(), c->d_part2.as<double>(), c->d_ecb.as<int32_t>(),
                        c->d_offsets.as<int64_t>(), c->ev.n == 0 ? 0 : (int64_t)c->h_offsets.size() - 1,
-                       c->n_chunks, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
+                       n_items, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                        c->k_cap, c->d_lnL.as<double>(), c->d_lnxi.as<double>(), c->d_neff.as<double>(),
-                       c->d_flags.as<uint32_t>(), c->stream, sx), "finalise");
+                       c->d_flags.as<uint32_t>(), c->stream, sx, use_grid ? c->grid->xi.as<double>() : nullptr),
+       "finalise");
     CK(cudaEventRecordWithFlags(c->ev_t1, c->stream, rec), "event");
     return POP_OK;
 }
@@ -635,7 +645,11 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
                double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem)
 {
     if (!c) return POP_EINVAL;
-    if (c->ev.n == 0 || c->inj.n == 0) return fail(c, POP_ESTATE, "pop_loglik: load events and injections first");
+    const bool use_grid = c->xi_source == POP_XI_GRID;
+    if (c->ev.n == 0) return fail(c, POP_ESTATE, "pop_loglik: load events first");
+    if (!use_grid && c->inj.n == 0) return fail(c, POP_ESTATE, "pop_loglik: load injections first");
+    if (use_grid && mode == POP_MODE_F32_SURROGATE)
+        return fail(c, POP_EINVAL, "pop_loglik: the surrogate mode replaces the injection selection term, not the grid");
     if (K < 0) return fail(c, POP_EINVAL, "pop_loglik: K < 0");
     if (n_params != 11 + (c->ev.n_dims == 7))
         return fail(c, POP_EINVAL, "pop_loglik: n_params must be 11 (12 with redshift samples)");
@@ -646,7 +660,7 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
     if (mode == POP_MODE_F32_SURROGATE && c->sur->n_params != n_params)
         return fail(c, POP_EINVAL, "pop_loglik: the surrogate was trained for another n_params");
     const int need = mode == POP_MODE_F64 ? POP_STORE_F64 : POP_STORE_F32;
-    if (!(c->ev.storage & need) || !(c->inj.storage & need))
+    if (!(c->ev.storage & need) || (!use_grid && !(c->inj.storage & need)))
         return fail(c, POP_ESTATE, "pop_loglik: the loaded storage does not include this mode's precision");
     if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_loglik: bad mem");
     if (K == 0) return POP_OK;
@@ -657,6 +671,10 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
     if (rc != POP_OK) return rc;
     rc = ensure_scratch(c, K);
     if (rc != POP_OK) return rc;
+    if (use_grid && (c->grid->k_cap < c->k_cap || c->grid->slice <= 0)) {
+        CK(c->grid->ensure(c->k_cap), "grid scratch");
+        c->version++;  // the graphs point at the grid scratch
+    }
     CK(cudaMemcpyAsync(c->d_lambda.p, lambda, sizeof(double) * K * n_params, in_kind(mem), c->stream), "copy lambda");
     set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
     CK(cudaGetLastError(), "set K");
@@ -671,6 +689,102 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
     if (out_flags)
         CK(cudaMemcpyAsync(out_flags, c->d_flags.p, sizeof(uint32_t) * K, out_kind(mem), c->stream), "copy flags");
     if (mem == POP_MEM_HOST) CK(cudaStreamSynchronize(c->stream), "sync");
+    if (use_grid && mem == POP_MEM_HOST) {
+        int bad = 0;
+        CK(c->grid->take_error(&bad, c->stream), "grid error word");
+        if (bad) return fail(c, POP_ETIMEOUT, "pop_loglik: a bounded wait of the grid contraction gave up");
+    }
+    return POP_OK;
+}
+
+int pop_load_vt_grid(pop_ctx* c, int n_m1, const double* m1, int n_q, const double* q, const double* pdet, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_load_vt_grid: bad mem");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    std::unique_ptr<GridVT> fresh;
+    GridVT* g = c->grid.get();
+    if (!g) {
+        fresh.reset(new GridVT());
+        g = fresh.get();
+    }
+    const int rc = g->load(n_m1, m1, n_q, q, pdet, mem == POP_MEM_DEVICE, c->stream);
+    if (rc != POP_OK) return fail(c, rc, g->err_msg);
+    if (fresh) c->grid = std::move(fresh);
+    c->version++;
+    return POP_OK;
+}
+
+int pop_set_xi_source(pop_ctx* c, int source)
+{
+    if (!c) return POP_EINVAL;
+    if (source != POP_XI_INJECTIONS && source != POP_XI_GRID)
+        return fail(c, POP_EINVAL, "pop_set_xi_source: source must be POP_XI_INJECTIONS or POP_XI_GRID");
+    if (source == POP_XI_GRID && !c->grid) return fail(c, POP_ESTATE, "pop_set_xi_source: load a grid first");
+    if (source != c->xi_source) {
+        c->xi_source = source;
+        c->version++;
+    }
+    return POP_OK;
+}
+
+int pop_xi_grid(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_lnxi,
+                uint32_t* out_flags, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (!c->grid) return fail(c, POP_ESTATE, "pop_xi_grid: load a grid first (pop_load_vt_grid)");
+    if (K < 0 || K > (1LL << 24)) return fail(c, POP_EINVAL, "pop_xi_grid: K out of range");
+    if (n_params != 11 && n_params != 12) return fail(c, POP_EINVAL, "pop_xi_grid: n_params must be 11 or 12");
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32) return fail(c, POP_EINVAL, "pop_xi_grid: bad mode");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_xi_grid: bad mem");
+    if (K == 0) return POP_OK;
+    if (!lambda || !out_lnxi) return fail(c, POP_EINVAL, "pop_xi_grid: lambda/out_lnxi is NULL");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    GridVT& g = *c->grid;
+    if (K > g.k_cap || g.slice <= 0) {
+        CK(g.ensure(K), "grid scratch");
+        c->version++;
+    }
+    if (K > g.k_cap_own) {
+        DevBuf l, k, x, f;
+        CK(l.alloc(sizeof(double) * K * 12), "cudaMalloc(lambda)");
+        CK(k.alloc(sizeof(int64_t)), "cudaMalloc(K)");
+        CK(x.alloc(sizeof(double) * K), "cudaMalloc(lnxi)");
+        CK(f.alloc(sizeof(uint32_t) * K), "cudaMalloc(flags)");
+        g.own_lambda.swap(l);
+        g.own_K.swap(k);
+        g.own_lnxi.swap(x);
+        g.own_flags.swap(f);
+        g.k_cap_own = K;
+    }
+    CK(cudaMemcpyAsync(g.own_lambda.p, lambda, sizeof(double) * K * n_params, in_kind(mem), c->stream), "copy lambda");
+    set_k_kernel<<<1, 1, 0, c->stream>>>(g.own_K.as<int64_t>(), K);
+    CK(cudaGetLastError(), "set K");
+    const int m = mode == POP_MODE_F64 ? 0 : 1;
+    CK(g.enqueue(m, g.own_lambda.as<double>(), n_params, g.own_K.as<int64_t>(), K, true, cudaEventRecordDefault,
+                 c->stream), "grid selection term");
+    CK(g.out_lnxi(g.own_lambda.as<double>(), n_params, g.own_K.as<int64_t>(), K, g.own_lnxi.as<double>(),
+                  g.own_flags.as<uint32_t>(), c->stream), "grid output");
+    CK(cudaMemcpyAsync(out_lnxi, g.own_lnxi.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnxi");
+    if (out_flags)
+        CK(cudaMemcpyAsync(out_flags, g.own_flags.p, sizeof(uint32_t) * K, out_kind(mem), c->stream), "copy flags");
+    int bad = 0;
+    CK(g.take_error(&bad, c->stream), "grid error word");  // synchronises the stream
+    if (bad) return fail(c, POP_ETIMEOUT, "pop_xi_grid: a bounded wait of the grid contraction gave up");
+    return POP_OK;
+}
+
+int pop_xi_grid_last_ms(pop_ctx* c, double* contraction_ms, double* total_ms)
+{
+    if (!c) return POP_EINVAL;
+    if (!c->grid || c->grid->k_cap == 0) return fail(c, POP_ESTATE, "pop_xi_grid_last_ms: no grid evaluation yet");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaEventSynchronize(c->grid->ev3), "event sync");
+    float w = 0.f, t = 0.f;
+    CK(cudaEventElapsedTime(&w, c->grid->ev1, c->grid->ev2), "elapsed");
+    CK(cudaEventElapsedTime(&t, c->grid->ev0, c->grid->ev3), "elapsed");
+    if (contraction_ms) *contraction_ms = w;
+    if (total_ms) *total_ms = t;
     return POP_OK;
 }
 

@@ -256,7 +256,7 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
                 const int32_t* __restrict__ ecb, const int64_t* __restrict__ off, int64_t n_events,
                 int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw, const LamF64* __restrict__ lam,
                 const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags,
-                SurrogateXi sx)
+                SurrogateXi sx, const double* __restrict__ grid_xi)
 {
     __shared__ double sh[FIN_THREADS / 32];
     const int64_t k = blockIdx.x;
@@ -297,6 +297,10 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
     double ne = var > 0.0 ? xi * xi / var : INFINITY;
     double out, lx;
     if (zero > 0.0) fl |= POP_FLAG_ZERO_EVENT;
+    if (grid_xi) {  // selection term from the grid: no Monte Carlo variance
+        xi = grid_xi[k];
+        ne = INFINITY;
+    }
     if (sx.need_mc) {
         if (sx.need_mc[k]) {
             fl |= POP_FLAG_MC_FALLBACK;
@@ -360,11 +364,11 @@ cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_c
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,
                             int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
                             const LamF64* lam, const int64_t* dK, int64_t K_cap, double* lnL, double* lnxi,
-                            double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx)
+                            double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx, const double* grid_xi)
 {
     if (K_cap <= 0) return cudaSuccess;
     finalise_kernel<<<(unsigned)K_cap, FIN_THREADS, 0, s>>>(part, part2, ecb, off, n_events, n_chunks, n_ev_chunks,
-                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx);
+                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx, grid_xi);
     return cudaGetLastError();
 }
 

@@ -212,6 +212,19 @@ def make_lambdas(K, n_params=11, seed=0, box=LAMBDA_BOX):
     return np.ascontiguousarray(lo + rng.random((K, n_params)) * (hi - lo))
 
 
+def campaign_pdet(m1):
+    """Detection probability of this generator's campaign: sigmoid((m1 - 20)/5), as in make_injections."""
+    return 1.0 / (1.0 + np.exp(-(np.asarray(m1, np.float64) - 20.0) / 5.0))
+
+
+def campaign_vt_grid(n_m1=3001, n_q=801, m1_range=(3.0, 100.0), q_range=(0.03, 1.0)):
+    """Regular (m1, q) grid over the injection campaign's mass range: nodes and pdet [n_m1, n_q]."""
+    m1 = np.linspace(m1_range[0], m1_range[1], n_m1)
+    q = np.linspace(q_range[0], q_range[1], n_q)
+    pdet = np.ascontiguousarray(np.broadcast_to(campaign_pdet(m1)[:, None], (n_m1, n_q)))
+    return m1, q, pdet
+
+
 def round_to_f32(x):
     """Storage quantisation of the FP32 layout: values rounded to float32, promoted back."""
     return np.asarray(x, np.float32).astype(np.float64)
