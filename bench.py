@@ -45,6 +45,7 @@ FP64_OPS_PER_INJ_PAIR = 57
 # GB300: 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2070 MHz
 # over 152 SMs); peak op rate = 2 * SMs * clock.
 FP64_LANES_PER_SM = 2
+FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
@@ -69,6 +70,26 @@ def in_support_pairs(theta, lam):
     total -= int(((m2[hi, None] >= mmin[None, :]) & (m1[hi, None] > mmax[None, :])).sum())
     tie = m2 >= m1
     total -= int(((m2[tie, None] >= mmin[None, :]) & (m1[tie, None] <= mmin[None, :])).sum())
+    return total
+
+
+def grid_support_triples(m1, q, lam):
+    """(m1 node, q node, Lambda) triples inside the support of the grid selection term:
+    mmin < m1 <= mmax, q <= 1 and fl64(q m1) >= mmin.  One FMA each is the algorithmic
+    work of the node contraction.  Exact count."""
+    nb = int(np.searchsorted(q, 1.0, side="right"))
+    qq = q[:nb]
+    total = 0
+    for L in lam:
+        mmin, mmax = L[2], L[3]
+        rows = m1[(m1 > mmin) & (m1 <= mmax)]
+        b0 = np.searchsorted(qq, mmin / rows, side="left")
+        for _ in range(2):  # the exact edge: fl64(q m1) >= mmin
+            dn = (b0 > 0) & (qq[np.maximum(b0 - 1, 0)] * rows >= mmin)
+            b0 = np.where(dn, b0 - 1, b0)
+            up = (b0 < nb) & (qq[np.minimum(b0, nb - 1)] * rows < mmin)
+            b0 = np.where(up, b0 + 1, b0)
+        total += int((nb - b0).sum())
     return total
 
 
@@ -197,6 +218,35 @@ def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world):
             "heldout_rmse_lnxi": info["heldout_rmse"], "heldout_mc_noise": info["mc_noise"],
             "trusted": info["trusted"], "surrogate_used_frac": float(used.mean()),
             "abs_dlnL_vs_f32_mc": {"mean": float(d[fin].mean()), "max": float(d[fin].max())}}
+
+
+def grid_form(B, like, lam, timed, args, world):
+    """ln L with the selection term on the dense (m1, q) campaign grid (3001 x 801
+    nodes, the paper's grid VT) instead of the injections, FP64 and FP32; the
+    grid's node contraction gets its own roofline (FP64 pipe, resp. FP32 FMA)."""
+    m1, q, pdet = synth.campaign_vt_grid()
+    B.pop_load_vt_grid(like.ctx, m1, q, pdet)
+    B.pop_set_xi_source(like.ctx, B.POP_XI_GRID)
+    triples = grid_support_triples(m1, q, lam)
+    K = len(lam)
+    out = {"grid": {"m1_nodes": int(m1.size), "q_nodes": int(q.size), "pdet": "sigmoid((m1 - 20)/5)",
+                    "in_support_triples": triples}}
+    peaks = {"f64": (FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6, "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz",
+                     "Top/s (FP64 pipe)", "gv_main_kernel<double>"),
+             "f32": (FP32_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6, "128 FP32 FMA lanes/SM/clk x 152 SMs x 2070 MHz",
+                     "Top/s (FP32 FMA)", "gv_main_kernel<float>")}
+    for name, mode in (("f64", B.POP_MODE_F64), ("f32", B.POP_MODE_F32)):
+        ms, w = timed(mode)
+        cms, tms = B.pop_xi_grid_last_ms(like.ctx)
+        peak, basis, unit, kern = peaks[name]
+        ach = triples / (cms * 1e-3)
+        out[name] = {"value": world * K * args.steps / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / args.steps,
+                     "weight_ms": w, "grid_ms": tms, "dtype": name,
+                     "roofline": {"bound": "alu", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12,
+                                  "unit": unit, "frac": ach / peak, "contraction_ms": cms,
+                                  "ops_per_launch": triples, "peak_basis": basis, "traffic": None}}
+    B.pop_set_xi_source(like.ctx, B.POP_XI_INJECTIONS)
+    return out
 
 
 def run_ragged(args, B, rank, local, world):
@@ -399,6 +449,7 @@ def main():
         line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
                                  "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32"}}
         line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
+        line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
     like.close()

@@ -8,7 +8,11 @@
 // a 4 x 4 block of (row, column) accumulators.  Chunks of 32 q nodes of the
 // packed pdet tile and of U are staged in shared memory by cp.async.bulk
 // copies that complete on an mbarrier (two stages).  Each thread computes W_a
-// and b0 of its own 16 pairs, so nothing per (row, Lambda) pair is stored.
+// and b0 of its own 16 pairs, so nothing per (row, Lambda) pair is stored:
+// in FP64 with the table-driven exp/expm1 of the FP64 weight kernel (its
+// 2^(j/2048) table sits in the stage buffers until the first copy), in FP32
+// with CUDA's exp2f/log1pf/expm1f for the FP32 form; the support decisions
+// are FP64 in both.
 // Lambda columns are placed in ascending mmin order (a counting sort per slice)
 // so that the 4 columns of a thread have nearly the same lower q edges: chunks
 // at or past every edge of the thread run unmasked, chunks below all of them
@@ -34,28 +38,46 @@ namespace pop {
 namespace {
 
 constexpr int GV_THREADS = 256;
-constexpr int GV_STAGES = 2;
+
 constexpr int GV_WAIT_LIMIT = 1 << 22;  // mbarrier polls before a wait gives up
 constexpr int GV_BUCKETS = 1024;        // mmin buckets of the column sort
 constexpr double GV_SQRT2 = 1.4142135623730950488;
 constexpr double GV_SQRT2PI = 2.5066282746310005024;
+constexpr double GV_LOG2E = 1.4426950408889634074;
 
 struct GvNodes {
-    const double* m1;    // [na]
-    const double* lnm1;  // [na]
-    const double* wa;    // [na]
-    const double* q;     // [nbp]
-    int na, nb, nbp, n_rt;
+    const double* m1;     // [na]
+    const double* lnm1;   // [na]
+    const double* invm1;  // [na]
+    const double* wa;     // [na]
+    const float* m1f;     // [na] m1 rounded to FP32 ...
+    const float* m1lf;    // [na] ... and the rest, m1 - m1f, rounded to FP32
+    const float* invm1f;  // [na]
+    const float* l2m1f;   // [na] log2 m1
+    const float* waf;     // [na]
+    const double* q;      // [nbp]
+    const double* lnq;    // [nbp]
+    const float* qf;      // [nbp]
+    const float* l2q_h;   // [nbp] log2 q as an FP32 (hi, lo) pair
+    const float* l2q_l;
+    const float* wqf;     // [nbp]
+    int na, nb, nbp;
 };
 
-// Per-column constants of the primary-mass and mass-ratio densities.
+// Per-column constants of the primary-mass and mass-ratio densities.  The
+// log-normalisations lcpl and lcg include ln|1 + beta| (0 when beta = -1).
 struct GvLam {
     double nalpha;  // exponent of m1 in the power law (-alpha)
-    double cpl;     // (1 - lam) x power-law normalisation
+    double lcpl;    // ln((1 - lam) C_pl |1 + beta|)   (-inf when lam = 1)
     double mu, nh;  // Gaussian peak: mpp and -1 / (2 sigpp^2)
-    double cg;      // lam / (sqrt(2 pi) sigpp Z), 0 when lam = 0
+    double lcg;     // ln(lam C_g |1 + beta|), C_g = 1 / (sqrt(2 pi) sigpp Z)   (-inf when lam = 0)
     double b1;      // 1 + beta
-    double mmin, mmax;
+    double beta;
+    float beta_h, beta_l;  // beta as an FP32 (hi, lo) pair
+    double mmin, lmmin;
+    long long mmin_bits, mmax_bits;  // non-negative doubles order like their bit patterns
+    float nalpha_f, l2cpl_f, nh2_f, l2cg_f, b1_f;  // FP32 form, base-2 logs
+    float mu_h, mu_l, mmin_f, mmin_l;              // mpp and mmin as FP32 (hi, lo) pairs
     int beta_m1;    // beta == -1: the q normalisation is ln(m1 / mmin)
     int live;       // a valid Lambda occupies the column
 };
@@ -73,56 +95,119 @@ __device__ void gv_consts(const double* L, int P, GvLam& c)
 {
     c.live = gv_valid(L, P);
     if (!c.live) return;
-    const double alpha = L[P_ALPHA], mmin = L[P_MMIN], mmax = L[P_MMAX], lam = L[P_LAM];
-    if (alpha == 1.0) {  // x^-1 / ln(mmax / mmin)
-        c.nalpha = -1.0;
-        c.cpl = (1.0 - lam) / log(mmax / mmin);
-    } else {
-        c.nalpha = -alpha;
-        c.cpl = (1.0 - lam) * (1.0 - alpha) / (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha));
-    }
+    const double alpha = L[P_ALPHA], beta = L[P_BETA], mmin = L[P_MMIN], mmax = L[P_MMAX], lam = L[P_LAM];
+    c.beta_m1 = beta == -1.0;
+    const double lb1 = c.beta_m1 ? 0.0 : log(fabs(1.0 + beta));
+    // Power law x^-alpha on [mmin, mmax]: ln of its normalisation (alpha = 1: 1 / ln(mmax / mmin)).
+    const double lpl = alpha == 1.0 ? -log(log(mmax / mmin))
+                                    : log((1.0 - alpha) / (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)));
+    c.nalpha = -alpha;
+    c.lcpl = log1p(-lam) + lpl + lb1;
     const double mu = L[P_MPP], sig = L[P_SIGPP];
     c.mu = mu;
     c.nh = -0.5 / (sig * sig);
     if (lam > 0.0) {
         const double z = 0.5 * (erf((mmax - mu) / (GV_SQRT2 * sig)) - erf((mmin - mu) / (GV_SQRT2 * sig)));
-        c.cg = lam / (GV_SQRT2PI * sig * z);
+        c.lcg = log(lam / (GV_SQRT2PI * sig * z)) + lb1;
     } else {
-        c.cg = 0.0;
+        c.lcg = -INFINITY;
     }
-    c.b1 = 1.0 + L[P_BETA];
-    c.beta_m1 = L[P_BETA] == -1.0;
+    c.b1 = 1.0 + beta;
+    c.beta = beta;
+    c.beta_h = (float)beta;
+    c.beta_l = (float)(beta - (double)c.beta_h);
     c.mmin = mmin;
-    c.mmax = mmax;
+    c.lmmin = log(mmin);
+    c.mmin_bits = __double_as_longlong(mmin);
+    c.mmax_bits = __double_as_longlong(mmax);
+    c.nalpha_f = (float)c.nalpha;
+    c.l2cpl_f = (float)(c.lcpl * GV_LOG2E);
+    c.nh2_f = (float)(c.nh * GV_LOG2E);
+    c.l2cg_f = (float)(c.lcg * GV_LOG2E);
+    c.b1_f = (float)c.b1;
+    c.mu_h = (float)mu;
+    c.mu_l = (float)(mu - (double)c.mu_h);
+    c.mmin_f = (float)mmin;
+    c.mmin_l = (float)(mmin - (double)c.mmin_f);
 }
 
-// W_a and b0 of one (row, column) pair.  A pair outside the mass support (or
-// with an empty q range) gets b0 = nb and contributes nothing.
-__device__ __forceinline__ void gv_pair(const GvNodes& g, const GvLam& c, int a, double& W, int& b0)
+// First q node with fl64(q_b m1) >= mmin.  The product rounds once and is
+// monotone in q, so the support in b is the suffix [b0, nb).
+// An FP32 search for thr = mmin_f / m1_f gives j.  thr is within 2^-21 of
+// x = mmin/m1 and every FP32 node within 2^-24 of its FP64 node, so a node
+// whose FP32 value is above thr (1 + 2^-18) is above x (1 + 2^-19) and passes
+// the FP64 test (which rounds once, 2^-53), and one below thr (1 - 2^-18)
+// fails it.  When both neighbours of j are that clear, j is exact; otherwise
+// (a node within ~2^-18 of the edge) the FP64 test itself moves j.
+__device__ __forceinline__ int gv_edge(const GvNodes& g, double m1, double mmin, float thr)
 {
-    W = 0.0;
-    b0 = g.nb;
-    if (!c.live) return;
-    const double m1 = g.m1[a];
-    if (!(m1 > c.mmin && m1 <= c.mmax)) return;  // also every padding row (m1 = 0)
-    double pm = c.cpl * exp(c.nalpha * g.lnm1[a]);
-    if (c.cg != 0.0) {
-        const double d = m1 - c.mu;
-        pm += c.cg * exp(c.nh * d * d);
-    }
-    // ln(mmin / m1) without cancellation: mmin - m1 is exact near the edge.
-    const double lr = log1p((c.mmin - m1) / m1);
-    const double cq = c.beta_m1 ? 1.0 / -lr : c.b1 / -expm1(c.b1 * lr);
-    W = g.wa[a] * pm * cq;
-    // First q node with fl64(q m1) >= mmin; the product rounds once, and it is
-    // monotone in q, so the support in b is the suffix [b0, nb).
     int lo = 0, hi = g.nb;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (__dmul_rn(g.q[mid], m1) >= c.mmin) hi = mid;
+        if (g.qf[mid] >= thr) hi = mid;
         else lo = mid + 1;
     }
-    b0 = lo;
+    int j = lo;
+    const bool clear_above = j == g.nb || g.qf[j] >= thr * (1.0f + 0x1p-18f);
+    const bool clear_below = j == 0 || g.qf[j - 1] < thr * (1.0f - 0x1p-18f);
+    if (clear_above && clear_below) return j;
+    while (j > 0 && __dmul_rn(g.q[j - 1], m1) >= mmin) --j;
+    while (j < g.nb && __dmul_rn(g.q[j], m1) < mmin) ++j;
+    return j;
+}
+
+// Mass support mmin < m1 <= mmax on bit patterns (every padding row has m1 = 0).
+__device__ __forceinline__ bool gv_in_mass(long long mb, const GvLam& c)
+{
+    return c.live && mb > c.mmin_bits && mb <= c.mmax_bits;
+}
+
+// W_a and b0 of one (row, column) pair, FP64: wa p(m1) (1+beta) / |expm1((1+beta) ln(mmin/m1))|
+// with the table-driven exponentials (tab in shared memory).  A pair outside the mass support
+// (or with an empty q range) gets b0 = nb and contributes nothing.
+__device__ __forceinline__ void gv_pair64(const GvNodes& g, const GvLam& c, int a, const double2* tab,
+                                          const ExpConsts& kc, double& W, int& b0)
+{
+    W = 0.0;
+    b0 = g.nb;
+    const double m1 = g.m1[a];
+    const long long mb = __double_as_longlong(m1);
+    if (!gv_in_mass(mb, c)) return;
+    const double lm = g.lnm1[a];
+    const double e1 = exp_tab(fma(c.nalpha, lm, c.lcpl), tab, kc);
+    const double d = m1 - c.mu;
+    const double e2 = exp_tab(fma(c.nh * d, d, c.lcg), tab, kc);
+    // ln(mmin/m1): the log difference, or near the edge log1p((mmin - m1)/m1) by its series
+    // (mmin - m1 is exact there).
+    double lr = c.lmmin - lm;
+    if (llabs(mb - c.mmin_bits) < NEAR_EDGE_BITS) lr = log1p_near0(g.invm1[a] * (c.mmin - m1));
+    const double den = c.beta_m1 ? -lr : fabs(expm1_tab(c.b1 * lr, tab, kc));
+    W = g.wa[a] * (e1 + e2) * rcp_pos(den);
+    b0 = gv_edge(g, m1, c.mmin, __fdividef(c.mmin_f, g.m1f[a]));
+}
+
+// The same pair in the FP32 form: base-2 exponentials and log1p/expm1 in FP32
+// (CUDA exp2f, log1pf, expm1f).  m1 - mpp and mmin - m1 come from (hi, lo) FP32
+// pairs; within ~2^-6 of the lower mass edge mmin - m1 is taken in FP64, where
+// it is exact.
+__device__ __forceinline__ void gv_pair32(const GvNodes& g, const GvLam& c, int a, float& W, int& b0)
+{
+    W = 0.0f;
+    b0 = g.nb;
+    const double m1 = g.m1[a];
+    const long long mb = __double_as_longlong(m1);
+    if (!gv_in_mass(mb, c)) return;
+    const float m1h = g.m1f[a], m1l = g.m1lf[a];
+    const float e1 = exp2f(fmaf(c.nalpha_f, g.l2m1f[a], c.l2cpl_f));
+    const float d = (m1h - c.mu_h) + (m1l - c.mu_l);
+    const float e2 = exp2f(fmaf(c.nh2_f * d, d, c.l2cg_f));
+    float t;
+    if (llabs(mb - c.mmin_bits) < NEAR_EDGE_BITS) t = (float)(g.invm1[a] * (c.mmin - m1));
+    else t = ((c.mmin_f - m1h) + (c.mmin_l - m1l)) * g.invm1f[a];
+    const float lr = log1pf(t);
+    const float den = c.beta_m1 ? -lr : fabsf(expm1f(c.b1_f * lr));
+    W = g.waf[a] * (e1 + e2) * __frcp_rn(den);
+    b0 = gv_edge(g, m1, c.mmin, __fdividef(c.mmin_f, m1h));
 }
 
 __device__ __forceinline__ int slice_count(const int64_t* dK, int64_t slice0, int S)
@@ -132,13 +217,20 @@ __device__ __forceinline__ int slice_count(const int64_t* dK, int64_t slice0, in
 }
 
 // ---------------------------------------------------------------- column sort
-// perm[r] = Lambda index of column r of the slice, ascending in mmin by
-// buckets (order inside a bucket is arbitrary); -1 in the padding columns.
+// perm[r] = Lambda index of column r of the slice (-1 in the padding).  The
+// columns go in ascending mmin by buckets, and inside every 64-column tile in
+// ascending mmax: a warp's 16 columns then share nearly the same support in
+// both m1 (dead rows are dead for the whole warp) and q.  Order inside an
+// mmin bucket is arbitrary: every column's result is independent of its position.
 __global__ void __launch_bounds__(1024)
 gv_sort_kernel(const double* __restrict__ lambda, int P, const int64_t* __restrict__ dK, int64_t slice0, int S,
                int32_t* __restrict__ perm)
 {
-    __shared__ int hist[GV_BUCKETS + 1];
+    // Dynamic shared memory: histogram [GV_BUCKETS + 1], columns [S], mmax keys [S].
+    extern __shared__ int gv_sort_smem[];
+    int* hist = gv_sort_smem;
+    int32_t* sperm = gv_sort_smem + (GV_BUCKETS + 4);
+    float* skey = reinterpret_cast<float*>(sperm + S);
     __shared__ double s_lo[32], s_hi[32];
     const int n = slice_count(dK, slice0, S);
     double lo = INFINITY, hi = -INFINITY;
@@ -173,30 +265,137 @@ gv_sort_kernel(const double* __restrict__ lambda, int P, const int64_t* __restri
     };
     for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[bucket(lambda[(slice0 + i) * P + P_MMIN])], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int b = 0; b <= GV_BUCKETS; ++b) {
-            const int h = hist[b];
-            hist[b] = s;
-            s += h;
+    // Exclusive prefix sum of the buckets by one warp: each lane scans 32 buckets,
+    // a shuffle scan gives the lane offsets; the non-finite bucket goes last.
+    static_assert(GV_BUCKETS == 32 * 32, "one warp scans the buckets");
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        int tot = 0;
+        for (int b = 32 * l; b < 32 * l + 32; ++b) tot += hist[b];
+        int incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (l >= o) incl += v;
         }
+        int run = incl - tot;
+        for (int b = 32 * l; b < 32 * l + 32; ++b) {
+            const int h = hist[b];
+            hist[b] = run;
+            run += h;
+        }
+        if (l == 31) hist[GV_BUCKETS] = run;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int pos = atomicAdd(&hist[bucket(lambda[(slice0 + i) * P + P_MMIN])], 1);
-        perm[pos] = (int32_t)(slice0 + i);
+        sperm[pos] = (int32_t)(slice0 + i);
     }
     const int npad = (n + GV_TL - 1) / GV_TL * GV_TL;
-    for (int r = n + threadIdx.x; r < npad; r += blockDim.x) perm[r] = -1;
+    for (int r = n + threadIdx.x; r < npad; r += blockDim.x) sperm[r] = -1;
+    __syncthreads();
+    // Rank by mmax inside each 64-column tile (padding and non-finite keys last, ties by
+    // position); the keys go to shared memory first, as floats (ordering only).
+    for (int r = threadIdx.x; r < npad; r += blockDim.x) {
+        const int32_t k = sperm[r];
+        const double m = k >= 0 ? lambda[(int64_t)k * P + P_MMAX] : INFINITY;
+        skey[r] = isfinite(m) ? (float)m : INFINITY;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < npad; r += blockDim.x) {
+        const int t0 = r / GV_TL * GV_TL;
+        const float kr = skey[r];
+        int rank = 0;
+        for (int u = t0; u < t0 + GV_TL; ++u) {
+            const float ku = skey[u];
+            rank += (ku < kr) || (ku == kr && u < r);
+        }
+        perm[t0 + rank] = sperm[r];
+    }
+}
+
+// Per-column constants of the slice (live = 0 for padding columns).
+__global__ void gv_lamc_kernel(const double* __restrict__ lambda, int P, const int32_t* __restrict__ perm,
+                               const int64_t* __restrict__ dK, int64_t slice0, int S, GvLam* __restrict__ lamc)
+{
+    const int n = slice_count(dK, slice0, S);
+    const int npad = (n + GV_TL - 1) / GV_TL * GV_TL;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= npad) return;
+    const int k = r < n ? perm[r] : -1;
+    GvLam c;
+    c.live = 0;
+    c.beta = 0.0;
+    if (k >= 0) gv_consts(lambda + (int64_t)k * P, P, c);
+    lamc[r] = c;
+}
+
+// ---------------------------------------------------------------- tile order
+// Launch order of the row tiles, heaviest first, so that the light tiles (near
+// the lower mass edge, above mmax, outside every support) fill the end of the
+// launch.  The work of a row tile is estimated from 16 columns spread over the
+// slice and every 4th row: the number of q nodes in the support of each (row,
+// column) pair.  Up to GV_ORDER_MAX row tiles; beyond that the order is the identity.
+constexpr int GV_ORDER_MAX = 4096;
+
+__global__ void __launch_bounds__(1024)
+gv_order_kernel(GvNodes g, const GvLam* __restrict__ lamc, const int64_t* __restrict__ dK, int64_t slice0, int S,
+                int TA, int32_t* __restrict__ rt_order)
+{
+    __shared__ float est[GV_ORDER_MAX];
+    __shared__ long long s_mmin[16], s_mmax[16];
+    __shared__ float s_thr[16];
+    const int n_rt = g.na / TA;
+    const int n = slice_count(dK, slice0, S);
+    if (n_rt > GV_ORDER_MAX || n == 0) {
+        for (int r = threadIdx.x; r < n_rt; r += blockDim.x) rt_order[r] = r;
+        return;
+    }
+    const int ns = n < 16 ? n : 16;
+    if (threadIdx.x < ns) {
+        const GvLam& c = lamc[(int)((int64_t)threadIdx.x * n / ns)];
+        s_mmin[threadIdx.x] = c.live ? c.mmin_bits : LLONG_MAX;
+        s_mmax[threadIdx.x] = c.mmax_bits;
+        s_thr[threadIdx.x] = c.mmin_f;
+    }
+    __syncthreads();
+    // Thread (rt, s): over every 4th row of row tile rt, the q nodes at or above
+    // mmin/m1 for sampled column s, from the q range (an estimate that assumes
+    // evenly spread q nodes); then a sum over the 16 columns of a half warp.
+    const float q0 = g.qf[0], qspan = g.qf[g.nb - 1] - g.qf[0];
+    for (int t0 = 0; t0 < n_rt * 16; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const int rt = t >> 4, sc = t & 15;
+        float w = 0.0f;
+        if (rt < n_rt && sc < ns) {
+#pragma unroll 4
+            for (int i = 0; i < TA; i += 4) {
+                const int a = rt * TA + i;
+                const long long mb = __double_as_longlong(__ldg(g.m1 + a));
+                if (!(mb > s_mmin[sc] && mb <= s_mmax[sc])) continue;
+                const float thr = __fdividef(s_thr[sc], __ldg(g.m1f + a));
+                const float frac = qspan > 0.0f ? fminf(fmaxf((thr - q0) / qspan, 0.0f), 1.0f) : 0.0f;
+                w += (1.0f - frac) * (float)g.nb;
+            }
+        }
+        for (int o = 8; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (sc == 0 && rt < n_rt) est[rt] = w;
+    }
+    __syncthreads();
+    for (int rt = threadIdx.x; rt < n_rt; rt += blockDim.x) {
+        const float e = est[rt];
+        int rank = 0;
+        for (int u = 0; u < n_rt; ++u) rank += (est[u] > e) || (est[u] == e && u < rt);
+        rt_order[rank] = rt;
+    }
 }
 
 // ---------------------------------------------------------------- U_b per column
 // U[lt][b][c] = wq_b q_b^beta for column r = lt * 64 + c (0 for padding
 // columns, invalid Lambda and nodes past nb).
 template <class T>
-__global__ void gv_u_kernel(GvNodes g, const double* __restrict__ wq, const double* __restrict__ lambda, int P,
-                            const int32_t* __restrict__ perm, const int64_t* __restrict__ dK, int64_t slice0, int S,
-                            T* __restrict__ U)
+__global__ void gv_u_kernel(GvNodes g, const double* __restrict__ wq, const GvLam* __restrict__ lamc,
+                            const int64_t* __restrict__ dK, int64_t slice0, int S, const double2* __restrict__ tab,
+                            ExpConsts kc, T* __restrict__ U)
 {
     const int n = slice_count(dK, slice0, S);
     const int64_t total = (int64_t)((n + GV_TL - 1) / GV_TL) * g.nbp * GV_TL;
@@ -205,13 +404,11 @@ __global__ void gv_u_kernel(GvNodes g, const double* __restrict__ wq, const doub
         const int64_t rest = t / GV_TL;
         const int b = (int)(rest % g.nbp);
         const int lt = (int)(rest / g.nbp);
-        const int r = lt * GV_TL + c;
+        const GvLam& L = lamc[lt * GV_TL + c];
         double u = 0.0;
-        const int k = r < n ? perm[r] : -1;
-        if (k >= 0 && b < g.nb) {
-            const double* L = lambda + (int64_t)k * P;
-            const double qb = g.q[b];
-            if (qb > 0.0 && gv_valid(L, P)) u = wq[b] * pow(qb, L[P_BETA]);
+        if (L.live && b < g.nb && g.q[b] > 0.0) {
+            if constexpr (sizeof(T) == 8) u = wq[b] * exp_tab(L.beta * g.lnq[b], tab, kc);
+            else u = (double)(g.wqf[b] * exp2f(fmaf(L.beta_h, g.l2q_h[b], fmaf(L.beta_h, g.l2q_l[b], L.beta_l * g.l2q_h[b]))));
         }
         U[t] = (T)u;
     }
@@ -255,84 +452,114 @@ __device__ __forceinline__ bool gv_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// Four consecutive-by-vector elements of a staged row: idx as produced by gv_lanes.
-template <class T>
-__device__ __forceinline__ void gv_load4(const T* row, int i0, T (&v)[4])
+// N consecutive elements of a staged row as 16-byte vectors (N * sizeof(T) a multiple of 16).
+template <class T, int N>
+__device__ __forceinline__ void gv_load(const T* src, T (&v)[N])
 {
-    if constexpr (sizeof(T) == 8) {  // two 16-byte vectors, 32 elements apart
-        const double2 x = *reinterpret_cast<const double2*>(row + i0);
-        const double2 y = *reinterpret_cast<const double2*>(row + i0 + 32);
-        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int h = 0; h < N / 2; ++h) {
+            const double2 x = *reinterpret_cast<const double2*>(src + 2 * h);
+            v[2 * h] = x.x;
+            v[2 * h + 1] = x.y;
+        }
     } else {
-        const float4 x = *reinterpret_cast<const float4*>(row + i0);
-        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+#pragma unroll
+        for (int h = 0; h < N / 4; ++h) {
+            const float4 x = *reinterpret_cast<const float4*>(src + 4 * h);
+            v[4 * h] = x.x;
+            v[4 * h + 1] = x.y;
+            v[4 * h + 2] = x.z;
+            v[4 * h + 3] = x.w;
+        }
     }
 }
 
 // ---------------------------------------------------------------- contraction
-// part[rt][r] = sum over the 64 rows of row tile rt of W_a sum_{b >= b0} pdet[a, b] U_b
+// Tile shapes.  RA m1 rows x 4 Lambda columns per thread; a warp is 8 x 4 threads
+// (8 RA rows x 16 consecutive columns); a CTA is 2 x 4 warps (TA = 16 RA rows x 64
+// columns).  FP64 is bound by its two-lane pipe, so small 2 x 4 thread tiles
+// (more CTAs, a shorter wave tail) cost nothing; FP32 keeps 4 x 4 tiles for
+// operand reuse and keeps more chunks in flight, two per barrier step.
+template <class T>
+struct GvCfg;
+template <>
+struct GvCfg<double> {
+    static constexpr int RA = 2, STAGES = 2, CPB = 1, MIN_BLOCKS = 3;
+};
+template <>
+struct GvCfg<float> {
+    static constexpr int RA = 4, STAGES = 4, CPB = 2, MIN_BLOCKS = 2;
+};
+template <class T>
+constexpr int gv_ta() { return 16 * GvCfg<T>::RA; }
+template <class T>
+constexpr size_t gv_dyn_smem() { return (size_t)GvCfg<T>::STAGES * GV_BC * (gv_ta<T>() + GV_TL) * sizeof(T); }
+
+// part[rt][r] = sum over the TA rows of row tile rt of W_a sum_{b >= b0} pdet[a, b] U_b
 // for every column r of Lambda tile blockIdx.y.  T = double: FP64 throughout.
 // T = float: FP32 pdet and U, FP32 sums per 32-node chunk added into an FP32
-// running sum, FP64 W and row combine.
+// running sum, FP32 row factor, FP64 row combine.
 template <class T>
-__global__ void __launch_bounds__(GV_THREADS, 2)
-gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, const double* __restrict__ lambda,
-               int P, const int32_t* __restrict__ perm, const int64_t* __restrict__ dK, int64_t slice0, int S,
-               double* __restrict__ part, int* __restrict__ err)
+__global__ void __launch_bounds__(GV_THREADS, GvCfg<T>::MIN_BLOCKS)
+gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, const GvLam* __restrict__ lamc,
+               const int32_t* __restrict__ rt_order, const int64_t* __restrict__ dK, int64_t slice0, int S,
+               const double2* __restrict__ tab_g, ExpConsts kc, double* __restrict__ part, int* __restrict__ err)
 {
-    constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte vector
-    constexpr int STAGE = GV_BC * GV_TA;   // elements of one operand chunk (GV_TA == GV_TL)
-    constexpr uint32_t CHUNK_BYTES = STAGE * sizeof(T);
-    static_assert(GV_TA == GV_TL, "square CTA tile");
+    constexpr int RA = GvCfg<T>::RA, STAGES = GvCfg<T>::STAGES, CPB = GvCfg<T>::CPB;
+    constexpr int TA = gv_ta<T>();
+    constexpr int PD_ELEMS = GV_BC * TA, U_ELEMS = GV_BC * GV_TL;  // one chunk of each operand
+    constexpr uint32_t PD_BYTES = PD_ELEMS * sizeof(T), U_BYTES = U_ELEMS * sizeof(T);
+    static_assert(STAGES % CPB == 0 && STAGES >= 2 * CPB, "whole steps in flight");
     extern __shared__ __align__(128) unsigned char gv_dyn[];
-    T* sp = reinterpret_cast<T*>(gv_dyn);  // [STAGES][BC][64] pdet
-    T* su = sp + GV_STAGES * STAGE;        // [STAGES][BC][64] U
-    __shared__ __align__(8) uint64_t bar[GV_STAGES];
+    T* sp = reinterpret_cast<T*>(gv_dyn);  // [STAGES][BC][TA] pdet
+    T* su = sp + STAGES * PD_ELEMS;        // [STAGES][BC][64] U
+    __shared__ __align__(8) uint64_t bar[STAGES];
     __shared__ GvLam lc[GV_TL];
     __shared__ int s_tmin;
-    __shared__ double red[GV_THREADS / 16][GV_TL];
+    __shared__ double red[16][GV_TL];
 
     const int n = slice_count(dK, slice0, S);
-    const int rt = blockIdx.x, lt = blockIdx.y;
+    // Linear block index -> (row tile in launch order, Lambda tile).
+    const int n_lt = S / GV_TL;
+    const int rt = rt_order[blockIdx.x / n_lt], lt = blockIdx.x % n_lt;
     if (lt * GV_TL >= n) return;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    if (tid < GV_TL) {
-        const int r = lt * GV_TL + tid;
-        const int k = r < n ? perm[r] : -1;
-        GvLam c;
-        c.live = 0;
-        if (k >= 0) gv_consts(lambda + (int64_t)k * P, P, c);
-        lc[tid] = c;
-    }
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int ty = 8 * (w >> 2) + (lane >> 2);  // 0..15
+    const int tx = 4 * (w & 3) + (lane & 3);    // 0..15
+    if (tid < GV_TL) lc[tid] = lamc[lt * GV_TL + tid];
     if (tid == 0) {
         s_tmin = INT_MAX;
-        for (int st = 0; st < GV_STAGES; ++st) gv_bar_init(gv_saddr(&bar[st]));
+        for (int st = 0; st < STAGES; ++st) gv_bar_init(gv_saddr(&bar[st]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // FP64 form: the exponential table lives in the stage buffers until the first copy.
+    const double2* tab = reinterpret_cast<const double2*>(gv_dyn);
+    if constexpr (sizeof(T) == 8) {
+        static_assert(gv_dyn_smem<T>() >= EXP_TABLE_SIZE * sizeof(double2), "the table fits the stages");
+        double2* st = reinterpret_cast<double2*>(gv_dyn);
+        for (int i = tid; i < EXP_TABLE_SIZE; i += GV_THREADS) st[i] = tab_g[i];
     }
     __syncthreads();
 
-    // This thread's rows and columns: index j -> (j / V) * 16V + t V + j % V, so
-    // that the 16-byte shared-memory reads of a quarter warp are contiguous.
-    int row[4], col[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        col[j] = (j / V) * (16 * V) + tx * V + (j % V);
-        row[j] = (j / V) * (16 * V) + ty * V + (j % V);
-    }
-    double W[4][4];
-    int b0[4][4];
+    T W[RA][4];
+    int b0[RA][4];
     int tmin = INT_MAX, tmax = -1;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RA; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            gv_pair(g, lc[col[j]], rt * GV_TA + row[i], W[i][j], b0[i][j]);
+            const int a = rt * TA + ty * RA + i;
+            if constexpr (sizeof(T) == 8) gv_pair64(g, lc[tx * 4 + j], a, tab, kc, W[i][j], b0[i][j]);
+            else gv_pair32(g, lc[tx * 4 + j], a, W[i][j], b0[i][j]);
             if (b0[i][j] < g.nb) {
                 tmin = min(tmin, b0[i][j]);
                 tmax = max(tmax, b0[i][j]);
             }
         }
     if (tmin != INT_MAX) atomicMin(&s_tmin, tmin);
+    // The table reads (generic proxy) are ordered before the bulk copies (async proxy) into the same bytes.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     double* out = part + (int64_t)rt * S + lt * GV_TL;
     if (s_tmin >= g.nb) {  // no pair of the tile has support
@@ -341,72 +568,77 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
     }
     const int nch = g.nbp / GV_BC;
     const int c0 = s_tmin / GV_BC;
-    const T* pd_tile = pd + (int64_t)rt * g.nbp * GV_TA;
+    const T* pd_tile = pd + (int64_t)rt * g.nbp * TA;
     const T* u_tile = U + (int64_t)lt * g.nbp * GV_TL;
     auto issue = [&](int c) {
-        const int st = (c - c0) % GV_STAGES;
+        const int st = (c - c0) % STAGES;
         const uint32_t b = gv_saddr(&bar[st]);
-        gv_expect_tx(b, 2 * CHUNK_BYTES);
-        gv_bulk_load(gv_saddr(sp + st * STAGE), pd_tile + (int64_t)c * STAGE, CHUNK_BYTES, b);
-        gv_bulk_load(gv_saddr(su + st * STAGE), u_tile + (int64_t)c * STAGE, CHUNK_BYTES, b);
+        gv_expect_tx(b, PD_BYTES + U_BYTES);
+        gv_bulk_load(gv_saddr(sp + st * PD_ELEMS), pd_tile + (int64_t)c * PD_ELEMS, PD_BYTES, b);
+        gv_bulk_load(gv_saddr(su + st * U_ELEMS), u_tile + (int64_t)c * U_ELEMS, U_BYTES, b);
     };
     if (tid == 0)
-        for (int c = c0; c < nch && c < c0 + GV_STAGES; ++c) issue(c);
+        for (int c = c0; c < nch && c < c0 + STAGES; ++c) issue(c);
 
-    T acc[4][4];
-    float run[4][4];  // FP32 form: running sum of the chunk sums
+    T acc[RA][4];
+    float run[RA][4];  // FP32 form: running sum of the chunk sums
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RA; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             acc[i][j] = T(0);
             run[i][j] = 0.0f;
         }
-    for (int c = c0; c < nch; ++c) {
-        const int st = (c - c0) % GV_STAGES;
-        const bool ok = gv_wait(gv_saddr(&bar[st]), (uint32_t)(((c - c0) / GV_STAGES) & 1));
+    for (int s = c0; s < nch; s += CPB) {
+        const int e = min(s + CPB, nch);
+        bool ok = true;
+        for (int c = s; c < e; ++c)
+            ok &= gv_wait(gv_saddr(&bar[(c - c0) % STAGES]), (uint32_t)(((c - c0) / STAGES) & 1));
         if (__syncthreads_or(!ok)) {
             // Give up: flag it, let the copies already issued land (bounded), leave NaN.
             if (tid == 0) {
                 atomicExch(err, 1);
-                for (int d = c; d < nch && d < c + GV_STAGES; ++d)
-                    gv_wait(gv_saddr(&bar[(d - c0) % GV_STAGES]), (uint32_t)(((d - c0) / GV_STAGES) & 1));
+                for (int d = s; d < nch && d < s + STAGES; ++d)
+                    gv_wait(gv_saddr(&bar[(d - c0) % STAGES]), (uint32_t)(((d - c0) / STAGES) & 1));
             }
             __syncthreads();
             if (tid < GV_TL) out[tid] = NAN;
             return;
         }
-        const int cb = c * GV_BC;
-        if (cb + GV_BC > tmin) {
-            const T* ps = sp + st * STAGE;
-            const T* us = su + st * STAGE;
+        for (int c = s; c < e; ++c) {
+            const int cb = c * GV_BC;
+            if (cb + GV_BC <= tmin) continue;  // below every support edge of this thread
+            const int st = (c - c0) % STAGES;
+            const T* ps = sp + st * PD_ELEMS + ty * RA;
+            const T* us = su + st * U_ELEMS + tx * 4;
+            const int bend = min(GV_BC, g.nb - cb);  // the last chunk stops at the last q node
             if (cb >= tmax) {  // every pair of the thread has support on the whole chunk
 #pragma unroll 4
-                for (int bb = 0; bb < GV_BC; ++bb) {
-                    T p[4], u[4];
-                    gv_load4(ps + bb * GV_TA, row[0], p);
-                    gv_load4(us + bb * GV_TL, col[0], u);
+                for (int bb = 0; bb < bend; ++bb) {
+                    T p[RA], u[4];
+                    gv_load(ps + bb * TA, p);
+                    gv_load(us + bb * GV_TL, u);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < RA; ++i)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) acc[i][j] = fma(p[i], u[j], acc[i][j]);
                 }
             } else {  // a support edge inside the chunk: per-pair mask
 #pragma unroll 2
-                for (int bb = 0; bb < GV_BC; ++bb) {
+                for (int bb = 0; bb < bend; ++bb) {
                     const int b = cb + bb;
-                    T p[4], u[4];
-                    gv_load4(ps + bb * GV_TA, row[0], p);
-                    gv_load4(us + bb * GV_TL, col[0], u);
+                    T p[RA], u[4];
+                    gv_load(ps + bb * TA, p);
+                    gv_load(us + bb * GV_TL, u);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < RA; ++i)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) acc[i][j] = fma(p[i], b >= b0[i][j] ? u[j] : T(0), acc[i][j]);
                 }
             }
             if constexpr (sizeof(T) == 4) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < RA; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         run[i][j] += acc[i][j];
@@ -414,39 +646,45 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
                     }
             }
         }
-        __syncthreads();  // the stage is free again
-        if (tid == 0 && c + GV_STAGES < nch) issue(c + GV_STAGES);
+        __syncthreads();  // the step's stages are free again
+        if (tid == 0)
+            for (int c = s + STAGES; c < nch && c < s + STAGES + CPB; ++c) issue(c);
     }
 
-    // Fixed-order combine: rows of the thread (i = 0..3), then the 16 row groups.
+    // Fixed-order combine: rows of the thread (i = 0..RA-1), then the 16 row groups.
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const double a = sizeof(T) == 4 ? (double)run[i][j] : (double)acc[i][j];
-            t += b0[i][j] < g.nb ? W[i][j] * a : 0.0;
+        for (int i = 0; i < RA; ++i) {
+            double v;
+            if constexpr (sizeof(T) == 4) v = (double)(W[i][j] * run[i][j]);
+            else v = W[i][j] * acc[i][j];
+            t += b0[i][j] < g.nb ? v : 0.0;
         }
-        red[ty][col[j]] = t;
+        red[ty][tx * 4 + j] = t;
     }
     __syncthreads();
     if (tid < GV_TL) {
-        double s = 0.0;
-        for (int y = 0; y < GV_THREADS / 16; ++y) s += red[y][tid];
-        out[tid] = s;
+        double sum = 0.0;
+        for (int y = 0; y < 16; ++y) sum += red[y][tid];
+        out[tid] = sum;
     }
 }
 
-// xi[k] = sum over row tiles (in order) of part[rt][r], k = perm[r].
+// xi[k] = sum over the row tiles of part[rt][r], k = perm[r]: one warp per column,
+// lane l sums row tiles l, l + 32, ... in order, then a fixed shuffle tree.
 __global__ void gv_reduce_kernel(const double* __restrict__ part, int n_rt, const int32_t* __restrict__ perm,
                                  const int64_t* __restrict__ dK, int64_t slice0, int S, double* __restrict__ xi)
 {
     const int n = slice_count(dK, slice0, S);
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double s = 0.0;
-    for (int rt = 0; rt < n_rt; ++rt) s += part[(int64_t)rt * S + r];
-    xi[perm[r]] = s;
+    const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;  // whole warps leave together
+    double sum = 0.0;
+    for (int rt = lane; rt < n_rt; rt += 32) sum += part[(int64_t)rt * S + r];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) xi[perm[r]] = sum;
 }
 
 __global__ void gv_out_kernel(const double* __restrict__ xi, const double* __restrict__ lambda, int P,
@@ -464,17 +702,18 @@ __global__ void gv_out_kernel(const double* __restrict__ xi, const double* __res
     flags[k] = x > 0.0 ? 0u : (uint32_t)POP_FLAG_ZERO_XI;
 }
 
-// pdet [n_m1][n_q] -> [n_rt][nbp][64] in FP64 and FP32 (zeros in the padding);
-// *bad = 1 when a used entry is not finite or negative.
-__global__ void gv_pack_kernel(const double* __restrict__ pdet, int n_m1, int n_q, int nb, int nbp, int n_rt,
-                               double* __restrict__ pd64, float* __restrict__ pd32, int* __restrict__ bad)
+// pdet [n_m1][n_q] -> [na / TA][nbp][TA] in T (zeros in the padding); *bad = 1
+// when a used entry is not finite or negative.
+template <class T>
+__global__ void gv_pack_kernel(const double* __restrict__ pdet, int n_m1, int n_q, int na, int nb, int nbp, int TA,
+                               T* __restrict__ out, int* __restrict__ bad)
 {
-    const int64_t total = (int64_t)n_rt * nbp * GV_TA;
+    const int64_t total = (int64_t)na * nbp;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(t % GV_TA);
-        const int64_t rest = t / GV_TA;
+        const int c = (int)(t % TA);
+        const int64_t rest = t / TA;
         const int b = (int)(rest % nbp);
-        const int a = (int)(rest / nbp) * GV_TA + c;
+        const int a = (int)(rest / nbp) * TA + c;
         double v = 0.0;
         if (a < n_m1 && b < nb) {
             v = pdet[(int64_t)a * n_q + b];
@@ -483,8 +722,7 @@ __global__ void gv_pack_kernel(const double* __restrict__ pdet, int n_m1, int n_
                 v = 0.0;
             }
         }
-        pd64[t] = v;
-        pd32[t] = (float)v;
+        out[t] = (T)v;
     }
 }
 
@@ -494,7 +732,9 @@ int blocks_for(int64_t n, int threads, int cap)
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
-size_t main_smem(int mode) { return (size_t)2 * GV_STAGES * GV_BC * GV_TA * (mode == 0 ? 8 : 4); }
+size_t main_smem(int mode) { return mode == 0 ? gv_dyn_smem<double>() : gv_dyn_smem<float>(); }
+
+size_t sort_smem(int S) { return sizeof(int) * (GV_BUCKETS + 4) + (sizeof(int32_t) + sizeof(float)) * (size_t)S; }
 
 }  // namespace
 
@@ -528,30 +768,56 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
     int nb_ = 0;
     while (nb_ < nq && hq[nb_] <= 1.0) ++nb_;
     if (nb_ == 0) return bad(POP_EINVAL, "pop_load_vt_grid: no q node <= 1");
-    const int na_ = (n1 + GV_TA - 1) / GV_TA * GV_TA;
+    const int na_ = (n1 + GV_ROW_PAD - 1) / GV_ROW_PAD * GV_ROW_PAD;
     const int nbp_ = (nb_ + GV_BC - 1) / GV_BC * GV_BC;
-    // Trapezoid weights over all nodes (a node's weight is half the span to its neighbours).
-    std::vector<double> wm(na_, 0.0), lm(na_, 0.0), m(na_, 0.0), wqv(nbp_, 0.0), qv(nbp_, 0.0);
+    // Trapezoid weights over all nodes (a node's weight is half the span to its neighbours),
+    // and the per-node logs and reciprocals of the setup.  Padding rows keep m1 = 0 (no support).
+    std::vector<double> wm(na_, 0.0), lm(na_, 0.0), im(na_, 0.0), m(na_, 0.0);
+    std::vector<float> mf(na_, 0.0f), mlf(na_, 0.0f), imf(na_, 0.0f), l2mf(na_, 0.0f), wmf(na_, 0.0f);
+    std::vector<double> wqv(nbp_, 0.0), qv(nbp_, 0.0), lqv(nbp_, 0.0);
+    std::vector<float> qfv(nbp_, 0.0f), l2qhv(nbp_, 0.0f), l2qlv(nbp_, 0.0f), wqfv(nbp_, 0.0f);
     for (int a = 0; a < n1; ++a) {
         const double hi = a + 1 < n1 ? hm[a + 1] : hm[a], lo = a > 0 ? hm[a - 1] : hm[a];
         wm[a] = 0.5 * (hi - lo);
         m[a] = hm[a];
         lm[a] = hm[a] > 0.0 ? std::log(hm[a]) : 0.0;
+        im[a] = hm[a] > 0.0 ? 1.0 / hm[a] : 0.0;
+        mf[a] = (float)hm[a];
+        mlf[a] = (float)(hm[a] - (double)mf[a]);
+        imf[a] = (float)im[a];
+        l2mf[a] = hm[a] > 0.0 ? (float)std::log2(hm[a]) : 0.0f;
+        wmf[a] = (float)wm[a];
     }
     for (int b = 0; b < nb_; ++b) {
         const double hi = b + 1 < nq ? hq[b + 1] : hq[b], lo = b > 0 ? hq[b - 1] : hq[b];
         wqv[b] = 0.5 * (hi - lo);
         qv[b] = hq[b];
+        lqv[b] = hq[b] > 0.0 ? std::log(hq[b]) : 0.0;
+        qfv[b] = (float)hq[b];
+        const double l2 = hq[b] > 0.0 ? std::log2(hq[b]) : 0.0;
+        l2qhv[b] = (float)l2;
+        l2qlv[b] = (float)(l2 - (double)l2qhv[b]);
+        wqfv[b] = (float)wqv[b];
     }
-    const int n_rt_ = na_ / GV_TA;
-    DevBuf dm, dlm, dwa, dq, dwq, p64, p32, tmp, dbad;
+    DevBuf dm, dlm, dim, dwa, dmf, dmlf, dimf, dl2m, dwaf, dq, dlq, dwq, dqf, dl2qh, dl2ql, dwqf, p64, p32, tmp, dbad;
     auto ck = [&](cudaError_t e) { return e == cudaSuccess; };
-    const size_t packed = (size_t)n_rt_ * nbp_ * GV_TA;
-    if (!ck(dm.alloc(sizeof(double) * na_)) || !ck(dlm.alloc(sizeof(double) * na_)) ||
-        !ck(dwa.alloc(sizeof(double) * na_)) || !ck(dq.alloc(sizeof(double) * nbp_)) ||
-        !ck(dwq.alloc(sizeof(double) * nbp_)) || !ck(p64.alloc(sizeof(double) * packed)) ||
-        !ck(p32.alloc(sizeof(float) * packed)) || !ck(dbad.alloc(sizeof(int))))
+    const size_t packed = (size_t)na_ * nbp_;
+    const size_t d_na = sizeof(double) * na_, f_na = sizeof(float) * na_;
+    const size_t d_nb = sizeof(double) * nbp_, f_nb = sizeof(float) * nbp_;
+    if (!ck(dm.alloc(d_na)) || !ck(dlm.alloc(d_na)) || !ck(dim.alloc(d_na)) || !ck(dwa.alloc(d_na)) ||
+        !ck(dmf.alloc(f_na)) || !ck(dmlf.alloc(f_na)) || !ck(dimf.alloc(f_na)) || !ck(dl2m.alloc(f_na)) || !ck(dwaf.alloc(f_na)) || !ck(dq.alloc(d_nb)) ||
+        !ck(dlq.alloc(d_nb)) || !ck(dwq.alloc(d_nb)) || !ck(dqf.alloc(f_nb)) || !ck(dl2qh.alloc(f_nb)) ||
+        !ck(dl2ql.alloc(f_nb)) || !ck(dwqf.alloc(f_nb)) ||
+        !ck(p64.alloc(sizeof(double) * packed)) || !ck(p32.alloc(sizeof(float) * packed)) ||
+        !ck(dbad.alloc(sizeof(int))))
         return bad(POP_ENOMEM, "pop_load_vt_grid: device allocation failed");
+    if (!tab.p) {
+        std::vector<double2> ht(EXP_TABLE_SIZE);
+        build_exp_table(ht.data(), &kc);
+        if (!ck(tab.alloc(sizeof(double2) * EXP_TABLE_SIZE)) ||
+            !ck(cudaMemcpy(tab.p, ht.data(), sizeof(double2) * EXP_TABLE_SIZE, cudaMemcpyHostToDevice)))
+            return bad(POP_ENOMEM, "pop_load_vt_grid: exponential table");
+    }
     const double* src = pdet;
     if (!on_device) {
         if (!ck(tmp.alloc(sizeof(double) * (size_t)n1 * nq))) return bad(POP_ENOMEM, "pop_load_vt_grid: allocation");
@@ -559,16 +825,22 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
             return bad(POP_ECUDA, "pop_load_vt_grid: copying pdet failed");
         src = tmp.as<double>();
     }
-    bool okc = ck(cudaMemcpyAsync(dm.p, m.data(), sizeof(double) * na_, cudaMemcpyHostToDevice, s)) &&
-               ck(cudaMemcpyAsync(dlm.p, lm.data(), sizeof(double) * na_, cudaMemcpyHostToDevice, s)) &&
-               ck(cudaMemcpyAsync(dwa.p, wm.data(), sizeof(double) * na_, cudaMemcpyHostToDevice, s)) &&
-               ck(cudaMemcpyAsync(dq.p, qv.data(), sizeof(double) * nbp_, cudaMemcpyHostToDevice, s)) &&
-               ck(cudaMemcpyAsync(dwq.p, wqv.data(), sizeof(double) * nbp_, cudaMemcpyHostToDevice, s)) &&
+    auto up = [&](DevBuf& d, const void* h, size_t n) {
+        return ck(cudaMemcpyAsync(d.p, h, n, cudaMemcpyHostToDevice, s));
+    };
+    bool okc = up(dm, m.data(), d_na) && up(dlm, lm.data(), d_na) && up(dim, im.data(), d_na) &&
+               up(dwa, wm.data(), d_na) && up(dmf, mf.data(), f_na) &&
+               up(dmlf, mlf.data(), f_na) && up(dimf, imf.data(), f_na) && up(dl2m, l2mf.data(), f_na) &&
+               up(dwaf, wmf.data(), f_na) && up(dq, qv.data(), d_nb) && up(dlq, lqv.data(), d_nb) &&
+               up(dwq, wqv.data(), d_nb) && up(dqf, qfv.data(), f_nb) && up(dl2qh, l2qhv.data(), f_nb) &&
+               up(dl2ql, l2qlv.data(), f_nb) && up(dwqf, wqfv.data(), f_nb) &&
                ck(cudaMemsetAsync(dbad.p, 0, sizeof(int), s));
     if (!okc) return bad(POP_ECUDA, "pop_load_vt_grid: copying the nodes failed");
-    gv_pack_kernel<<<blocks_for((int64_t)packed, 256, 152 * 32), 256, 0, s>>>(src, n1, nq, nb_, nbp_, n_rt_,
-                                                                              p64.as<double>(), p32.as<float>(),
-                                                                              dbad.as<int>());
+    const int pb = blocks_for((int64_t)packed, 256, 152 * 32);
+    gv_pack_kernel<double><<<pb, 256, 0, s>>>(src, n1, nq, na_, nb_, nbp_, gv_ta<double>(), p64.as<double>(),
+                                              dbad.as<int>());
+    gv_pack_kernel<float><<<pb, 256, 0, s>>>(src, n1, nq, na_, nb_, nbp_, gv_ta<float>(), p32.as<float>(),
+                                             dbad.as<int>());
     if (!ck(cudaGetLastError())) return bad(POP_ECUDA, "pop_load_vt_grid: pack kernel launch failed");
     int hbad = 0;
     if (!ck(cudaMemcpyAsync(&hbad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost, s)) || !ck(cudaStreamSynchronize(s)))
@@ -586,9 +858,20 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
     }
     m1.swap(dm);
     lnm1.swap(dlm);
+    invm1.swap(dim);
     wa.swap(dwa);
+    m1f.swap(dmf);
+    m1lf.swap(dmlf);
+    invm1f.swap(dimf);
+    l2m1f.swap(dl2m);
+    waf.swap(dwaf);
     q.swap(dq);
+    lnq.swap(dlq);
     wq.swap(dwq);
+    qf.swap(dqf);
+    l2qh.swap(dl2qh);
+    l2ql.swap(dl2ql);
+    wqf.swap(dwqf);
     pd64.swap(p64);
     pd32.swap(p32);
     n_m1 = n1;
@@ -596,7 +879,6 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
     na = na_;
     nb = nb_;
     nbp = nbp_;
-    n_rt = n_rt_;
     k_cap = 0;  // the scratch depends on the grid shape
     slice = 0;
     return POP_OK;
@@ -607,11 +889,14 @@ cudaError_t GridVT::ensure(int64_t K)
     if (K <= k_cap && slice > 0) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(K, k_cap), 64);
     const int S = (int)std::min<int64_t>((cap + GV_TL - 1) / GV_TL * GV_TL, GV_SLICE);
-    DevBuf p, u, pt, x;
+    DevBuf p, u, pt, x, lcb, od;
     cudaError_t e;
     if ((e = p.alloc(sizeof(int32_t) * S)) != cudaSuccess) return e;
+    if ((e = od.alloc(sizeof(int32_t) * (size_t)(na / gv_ta<double>()))) != cudaSuccess) return e;
+    if ((e = lcb.alloc(sizeof(GvLam) * S)) != cudaSuccess) return e;
     if ((e = u.alloc(sizeof(double) * (size_t)S * nbp)) != cudaSuccess) return e;
-    if ((e = pt.alloc(sizeof(double) * (size_t)n_rt * S)) != cudaSuccess) return e;
+    // Row tiles: na / 32 in the FP64 form, na / 64 in the FP32 form.
+    if ((e = pt.alloc(sizeof(double) * (size_t)(na / gv_ta<double>()) * S)) != cudaSuccess) return e;
     if ((e = x.alloc(sizeof(double) * cap)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(gv_main_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)main_smem(0))) != cudaSuccess)
@@ -619,7 +904,12 @@ cudaError_t GridVT::ensure(int64_t K)
     if ((e = cudaFuncSetAttribute(gv_main_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)main_smem(1))) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(gv_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem(S))) !=
+        cudaSuccess)
+        return e;
     perm.swap(p);
+    order.swap(od);
+    lamc.swap(lcb);
     U.swap(u);
     part.swap(pt);
     xi.swap(x);
@@ -633,34 +923,41 @@ cudaError_t GridVT::enqueue(int mode, const double* lambda, int n_params, const 
 {
     if (K_cap <= 0) return cudaSuccess;
     if (K_cap > k_cap || slice <= 0) return cudaErrorInvalidValue;
-    const GvNodes g{m1.as<double>(), lnm1.as<double>(), wa.as<double>(), q.as<double>(), na, nb, nbp, n_rt};
+    const GvNodes g{m1.as<double>(), lnm1.as<double>(),  invm1.as<double>(), wa.as<double>(),
+                    m1f.as<float>(), m1lf.as<float>(),   invm1f.as<float>(), l2m1f.as<float>(),
+                    waf.as<float>(), q.as<double>(),     lnq.as<double>(),   qf.as<float>(),
+                    l2qh.as<float>(), l2ql.as<float>(),  wqf.as<float>(),    na,
+                    nb,              nbp};
+    const double2* tb = tab.as<double2>();
+    GvLam* lcp = lamc.as<GvLam>();
     const int n_sl = (int)((K_cap + slice - 1) / slice);
     cudaError_t e;
     if (timed && (e = cudaEventRecordWithFlags(ev0, s, rec)) != cudaSuccess) return e;
     for (int sl = 0; sl < n_sl; ++sl) {
         const int64_t s0 = (int64_t)sl * slice;
-        gv_sort_kernel<<<1, 1024, 0, s>>>(lambda, n_params, dK, s0, slice, perm.as<int32_t>());
-        const int64_t u_elems = (int64_t)slice * nbp;
-        const int ub = blocks_for(u_elems, 256, 152 * 16);
+        gv_sort_kernel<<<1, 1024, sort_smem(slice), s>>>(lambda, n_params, dK, s0, slice, perm.as<int32_t>());
+        gv_lamc_kernel<<<(slice + 31) / 32, 32, 0, s>>>(lambda, n_params, perm.as<int32_t>(), dK, s0, slice, lcp);
+        const int ub = blocks_for((int64_t)slice * nbp, 256, 152 * 16);
         if (mode == 0)
-            gv_u_kernel<double><<<ub, 256, 0, s>>>(g, wq.as<double>(), lambda, n_params, perm.as<int32_t>(), dK, s0,
-                                                  slice, U.as<double>());
+            gv_u_kernel<double><<<ub, 256, 0, s>>>(g, wq.as<double>(), lcp, dK, s0, slice, tb, kc, U.as<double>());
         else
-            gv_u_kernel<float><<<ub, 256, 0, s>>>(g, wq.as<double>(), lambda, n_params, perm.as<int32_t>(), dK, s0,
-                                                 slice, U.as<float>());
+            gv_u_kernel<float><<<ub, 256, 0, s>>>(g, wq.as<double>(), lcp, dK, s0, slice, tb, kc, U.as<float>());
+        const int ta = mode == 0 ? gv_ta<double>() : gv_ta<float>();
+        const int n_rt = na / ta;
+        gv_order_kernel<<<1, 1024, 0, s>>>(g, lcp, dK, s0, slice, ta, order.as<int32_t>());
         if (timed && sl == 0 && (e = cudaEventRecordWithFlags(ev1, s, rec)) != cudaSuccess) return e;
-        const dim3 grid((unsigned)n_rt, (unsigned)(slice / GV_TL));
+        const unsigned grid = (unsigned)n_rt * (unsigned)(slice / GV_TL);
         if (mode == 0)
-            gv_main_kernel<double><<<grid, GV_THREADS, main_smem(0), s>>>(
-                g, pd64.as<double>(), U.as<double>(), lambda, n_params, perm.as<int32_t>(), dK, s0, slice,
-                part.as<double>(), err.as<int>());
+            gv_main_kernel<double><<<grid, GV_THREADS, main_smem(0), s>>>(g, pd64.as<double>(), U.as<double>(), lcp,
+                                                                         order.as<int32_t>(), dK, s0, slice, tb, kc,
+                                                                         part.as<double>(), err.as<int>());
         else
-            gv_main_kernel<float><<<grid, GV_THREADS, main_smem(1), s>>>(
-                g, pd32.as<float>(), U.as<float>(), lambda, n_params, perm.as<int32_t>(), dK, s0, slice,
-                part.as<double>(), err.as<int>());
+            gv_main_kernel<float><<<grid, GV_THREADS, main_smem(1), s>>>(g, pd32.as<float>(), U.as<float>(), lcp,
+                                                                        order.as<int32_t>(), dK, s0, slice, tb, kc,
+                                                                        part.as<double>(), err.as<int>());
         if (timed && sl == 0 && (e = cudaEventRecordWithFlags(ev2, s, rec)) != cudaSuccess) return e;
-        gv_reduce_kernel<<<(slice + 255) / 256, 256, 0, s>>>(part.as<double>(), n_rt, perm.as<int32_t>(), dK, s0,
-                                                             slice, xi.as<double>());
+        gv_reduce_kernel<<<(slice + 7) / 8, 256, 0, s>>>(part.as<double>(), n_rt, perm.as<int32_t>(), dK, s0, slice,
+                                                         xi.as<double>());
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (timed && (e = cudaEventRecordWithFlags(ev3, s, rec)) != cudaSuccess) return e;

@@ -18,28 +18,34 @@
 #include <string>
 
 #include "pop_devbuf.h"
+#include "pop_math.cuh"
 
 namespace pop {
 
-constexpr int GV_TA = 64;      // m1 rows per CTA tile (and per row tile of the packed pdet)
+constexpr int GV_ROW_PAD = 64; // m1 rows are padded to a multiple of this (every row tile height divides it)
 constexpr int GV_TL = 64;      // Lambda columns per CTA tile
 constexpr int GV_BC = 32;      // q nodes per staged chunk
 constexpr int GV_SLICE = 8192; // Lambda columns per slice (bounds the U scratch)
 
 struct GridVT {
     int n_m1 = 0, n_q = 0;  // nodes as loaded
-    int na = 0;             // m1 rows padded to GV_TA
+    int na = 0;             // m1 rows padded to GV_ROW_PAD
     int nb = 0;             // q nodes with q <= 1 (the q support never reaches past 1)
     int nbp = 0;            // nb padded to GV_BC
-    int n_rt = 0;           // row tiles, na / GV_TA
-    DevBuf m1, lnm1, wa;    // FP64 [na]: nodes, ln m1, trapezoid weights (0 in the padding)
-    DevBuf q, wq;           // FP64 [nbp]
-    DevBuf pd64, pd32;      // pdet packed as [n_rt][nbp][GV_TA] in FP64 and FP32 (0 in the padding)
+    DevBuf m1, lnm1, invm1, wa;  // FP64 [na]: nodes, ln m1, 1/m1, trapezoid weights (0 in the padding)
+    DevBuf m1f, m1lf, invm1f;    // FP32 [na]: m1 as a (hi, lo) pair, 1/m1
+    DevBuf l2m1f, waf;           // FP32 [na]: log2 m1, trapezoid weights
+    DevBuf q, lnq, wq;           // FP64 [nbp]: nodes, ln q, trapezoid weights
+    DevBuf qf;                   // FP32 [nbp]: nodes (first guess of the support edge)
+    DevBuf l2qh, l2ql, wqf;      // FP32 [nbp]: log2 q as a (hi, lo) pair, trapezoid weights
+    DevBuf pd64, pd32;           // pdet packed in row tiles [na / TA][nbp][TA], TA = 32 (FP64) or 64 (FP32)
+    DevBuf tab;                  // 2^(j/2048) as (hi, lo) for the FP64 exponentials
+    ExpConsts kc{};
 
     // Scratch, sized by ensure() for batches of up to k_cap Lambda.
     int64_t k_cap = 0;
     int slice = 0;          // columns per slice, a multiple of GV_TL
-    DevBuf perm, U, part, xi, err;
+    DevBuf perm, lamc, order, U, part, xi, err;  // lamc: per-column constants; order: row tiles, heaviest first
     // Standalone evaluation (pop_xi_grid): own Lambda, K and outputs.
     int64_t k_cap_own = 0;
     DevBuf own_lambda, own_K, own_lnxi, own_flags;

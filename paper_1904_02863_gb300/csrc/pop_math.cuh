@@ -1,4 +1,4 @@
-// FP64 exponential, expm1 and reciprocal for the FP64 weight kernel.
+// FP64 exponential, expm1, log1p near 0 and reciprocal for the FP64 kernels.
 //
 // GB300 runs FP64 at 2 FMA lanes per SM per clock (1/64 of FP32), so the
 // weight kernel is bound by the number of FP64 instructions per pair; these
@@ -86,6 +86,30 @@ __device__ __forceinline__ double expm1_tab(double u, const double2* __restrict_
     const double sc = __hiloint2double((m + 1023) << 20, 0);                                     // 2^m
     const double res = fma(fma(tj.x, p, tj.y), sc, s - 1.0);
     return under ? -1.0 : (over ? __longlong_as_double(0x7ff0000000000000LL) : res);
+}
+
+// |bits(m1) - bits(mmin)| below 2^46 means m1/mmin - 1 is below ~2^-6: there
+// ln(mmin/m1) is taken as log1p((mmin - m1)/m1) by the series below, since the
+// difference of the two logs would cancel.
+constexpr long long NEAR_EDGE_BITS = 1LL << 46;
+
+// log1p(t) for |t| < 2^-5 from its Taylor series to t^12 (truncation < 1e-19
+// relative).
+__device__ __forceinline__ double log1p_near0(double t)
+{
+    double p = -1.0 / 12;
+    p = fma(p, t, 1.0 / 11);
+    p = fma(p, t, -1.0 / 10);
+    p = fma(p, t, 1.0 / 9);
+    p = fma(p, t, -1.0 / 8);
+    p = fma(p, t, 1.0 / 7);
+    p = fma(p, t, -1.0 / 6);
+    p = fma(p, t, 1.0 / 5);
+    p = fma(p, t, -1.0 / 4);
+    p = fma(p, t, 1.0 / 3);
+    p = fma(p, t, -1.0 / 2);
+    p = fma(p, t, 1.0);
+    return p * t;
 }
 
 // 1/d for positive normal d: the hardware seed (rcp.approx.ftz.f64) refined by one cubic

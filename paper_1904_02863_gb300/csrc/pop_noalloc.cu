@@ -86,25 +86,6 @@ struct Sample {
     int64_t m1b, m2b;
 };
 
-constexpr long long NEAR_EDGE_BITS = 1LL << 46;
-
-__device__ __forceinline__ double log1p_near0(double t)
-{
-    double p = -1.0 / 12;
-    p = fma(p, t, 1.0 / 11);
-    p = fma(p, t, -1.0 / 10);
-    p = fma(p, t, 1.0 / 9);
-    p = fma(p, t, -1.0 / 8);
-    p = fma(p, t, 1.0 / 7);
-    p = fma(p, t, -1.0 / 6);
-    p = fma(p, t, 1.0 / 5);
-    p = fma(p, t, -1.0 / 4);
-    p = fma(p, t, 1.0 / 3);
-    p = fma(p, t, -1.0 / 2);
-    p = fma(p, t, 1.0);
-    return p * t;
-}
-
 // Features of one raw sample; returns false for unusable input (non-finite or pi <= 0).
 __device__ __forceinline__ bool make_sample(const RawSet& r, int64_t j, int nd, Sample& x)
 {

@@ -29,27 +29,6 @@ struct F64Sample {
     int64_t m1b, m2b;  // bit patterns of m1, m2 (non-negative doubles compare as integers)
 };
 
-// |bits(m1) - bits(mmin)| below 2^46 means m1/mmin - 1 is below ~2^-6.
-constexpr long long NEAR_EDGE_BITS = 1LL << 46;
-
-// log1p(t) for |t| < 2^-5 from its Taylor series to t^12 (truncation < 1e-19
-// relative).
-__device__ __forceinline__ double log1p_near0(double t)
-{
-    double p = -1.0 / 12;
-    p = fma(p, t, 1.0 / 11);
-    p = fma(p, t, -1.0 / 10);
-    p = fma(p, t, 1.0 / 9);
-    p = fma(p, t, -1.0 / 8);
-    p = fma(p, t, 1.0 / 7);
-    p = fma(p, t, -1.0 / 6);
-    p = fma(p, t, 1.0 / 5);
-    p = fma(p, t, -1.0 / 4);
-    p = fma(p, t, 1.0 / 3);
-    p = fma(p, t, -1.0 / 2);
-    p = fma(p, t, 1.0);
-    return p * t;
-}
 
 template <bool HAS_Z>
 __device__ __forceinline__ void load_f64(const FeatF64& F, int64_t s, F64Sample& x)
