@@ -139,6 +139,21 @@ int pop_load_injections(pop_ctx* ctx, int64_t n_found, int64_t n_draw, int n_dim
 int pop_loglik(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int mode,
                double* out_lnL, double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem);
 
+/* The additive parts of ln L for K Lambda rows, for splitting a catalog over
+ * several GPUs (each loads a disjoint range of events and a disjoint share of the
+ * found injections, all with the same total n_draw):
+ *   out_events[k] = sum_i ln(S_i/n_i) over the loaded events (-inf when some S_i = 0)
+ *   out_sum_w[k]  = sum over the loaded injections of w = p(theta|Lambda)/p_draw
+ *   out_sum_w2[k] = sum of w^2
+ *   out_flags[k]  = POP_FLAG_INVALID_LAMBDA (parts -inf, 0, 0) | POP_FLAG_ZERO_EVENT  (may be NULL)
+ * Parts of disjoint sets add up to those of their union, and then, with N the
+ * total number of events, xi = sum_w / n_draw, ln L = events - N ln xi and
+ * N_eff = xi^2 / (sum_w2 / n_draw^2 - xi^2 / n_draw), as pop_loglik computes them.
+ * Modes POP_MODE_F64 and POP_MODE_F32, with the injection selection term;
+ * outputs in `mem` (asynchronous with POP_MEM_DEVICE, as pop_loglik). */
+int pop_loglik_parts(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int mode, double* out_events,
+                     double* out_sum_w, double* out_sum_w2, uint32_t* out_flags, int mem);
+
 /* ------------------------------------------------------------------ grid selection term
  * The paper evaluates VT on a regular grid with GPU acceleration, limited to a
  * low-dimensional space without spin effects (Sec. "Population acceleration").

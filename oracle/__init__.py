@@ -62,6 +62,8 @@ def _load():
         lib.pop_oracle_loglik.argtypes = [i64, p, i32, p, p, i64, i64, p, p, i64, i32, p, i32, p, p, p, p]
         lib.pop_oracle_loglik.restype = i32
         lib.pop_oracle_max_threads.restype = i32
+        lib.pop_oracle_loglik_parts.argtypes = [i64, p, i32, p, p, i64, p, p, i64, i32, p, i32, p, p, p, p]
+        lib.pop_oracle_loglik_parts.restype = i32
         lib.pop_oracle_xi_grid.argtypes = [i32, p, i32, p, p, i64, i32, p, p, p]
         lib.pop_oracle_xi_grid.restype = i32
         _lib = lib
@@ -136,6 +138,25 @@ def xi_grid(m1_nodes, q_nodes, pdet, lambdas):
     if rc != 0:
         raise ValueError("oracle rejected the grid")
     return out, fl
+
+
+def loglik_parts(catalog, injections, lambdas, nthreads=0):
+    """(sum_i ln(S_i/n_i), sum_k w_k, sum_k w_k^2, flags) for each row of ``lambdas`` over the given
+    events and found injections; parts of disjoint sets add up to those of their union."""
+    lam = np.ascontiguousarray(np.atleast_2d(lambdas), dtype=np.float64)
+    K, P = lam.shape
+    off = np.ascontiguousarray(catalog.offsets, dtype=np.int64)
+    th = np.ascontiguousarray(catalog.theta, dtype=np.float64)
+    pr = np.ascontiguousarray(catalog.prior, dtype=np.float64)
+    ith = np.ascontiguousarray(injections.theta, dtype=np.float64)
+    pd = np.ascontiguousarray(injections.p_draw, dtype=np.float64)
+    out = np.empty(K), np.empty(K), np.empty(K), np.empty(K, np.uint32)
+    rc = _load().pop_oracle_loglik_parts(len(off) - 1, _ptr(off), th.shape[1], _ptr(th), _ptr(pr), ith.shape[0],
+                                         _ptr(ith), _ptr(pd), K, P, _ptr(lam), int(nthreads),
+                                         _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(out[3]))
+    if rc != 0:
+        raise ValueError("oracle rejected the input sizes")
+    return out
 
 
 def loglik(catalog, injections, lambdas, nthreads=0):

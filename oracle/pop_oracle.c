@@ -245,6 +245,59 @@ int pop_oracle_loglik(int64_t n_events, const int64_t* offsets, int n_dims,
 }
 
 /*
+ * The additive parts of ln L for K Lambda points, over the given events and
+ * found injections: sum_i ln(S_i / n_i) (-inf when some S_i = 0), and
+ * sum_k w_k and sum_k w_k^2 over the injections (not divided by n_draw).
+ * Events and injections split into disjoint sets give parts that add up to
+ * those of the whole set; ln L then follows as in pop_oracle_loglik.
+ * Flags: invalid Lambda (parts -inf, 0, 0) and zero event only.
+ */
+int pop_oracle_loglik_parts(int64_t n_events, const int64_t* offsets, int n_dims,
+                            const double* theta, const double* prior,
+                            int64_t n_found, const double* inj_theta, const double* p_draw,
+                            int64_t K, int n_params, const double* lambda, int nthreads,
+                            double* out_events, double* out_sum_w, double* out_sum_w2, uint32_t* out_flags)
+{
+    if (n_events < 0 || (n_dims != 6 && n_dims != 7) || n_params != 11 + (n_dims == 7) || n_found < 0 || K < 0 ||
+        !out_events || !out_sum_w || !out_sum_w2 || !out_flags)
+        return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t k = 0; k < K; ++k) {
+        const double* L = lambda + k * n_params;
+        uint32_t flags = 0;
+        double sum_ln = 0.0, sw = 0.0, sw2 = 0.0;
+        if (!pop_oracle_lambda_valid(L, n_params)) {
+            flags |= OR_FLAG_INVALID_LAMBDA;
+            sum_ln = -INFINITY;
+        } else {
+            double znorm = n_dims == 7 ? pop_oracle_z_norm(L[P_KAPPA]) : 1.0;
+            for (int64_t j = 0; j < n_found; ++j) {
+                double w = p_theta_znorm(inj_theta + j * n_dims, n_dims, L, znorm) / p_draw[j];
+                sw += w;
+                sw2 += w * w;
+            }
+            for (int64_t i = 0; i < n_events; ++i) {
+                double s = 0.0;
+                int64_t n_i = offsets[i + 1] - offsets[i];
+                for (int64_t j = offsets[i]; j < offsets[i + 1]; ++j)
+                    s += p_theta_znorm(theta + j * n_dims, n_dims, L, znorm) / prior[j];
+                if (s == 0.0) flags |= OR_FLAG_ZERO_EVENT;
+                sum_ln += log(s / (double)n_i);
+            }
+            if (flags & OR_FLAG_ZERO_EVENT) sum_ln = -INFINITY;
+        }
+        out_events[k] = sum_ln;
+        out_sum_w[k] = sw;
+        out_sum_w2[k] = sw2;
+        out_flags[k] = flags;
+    }
+    return 0;
+}
+
+/*
  * Selection term on a regular grid (Sec. "Population acceleration": VT on a
  * regular grid, limited to low dimension, no spin effects).  With a detection
  * probability pdet[a * n_q + b] given at the grid nodes (m1_a, q_b), the grid

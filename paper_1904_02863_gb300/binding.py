@@ -33,7 +33,7 @@ EXPORTS = (
     "pop_xi_surrogate_train", "pop_xi_surrogate_info", "pop_xi_surrogate_infer", "pop_xi_surrogate_save",
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
-    "pop_load_vt_grid", "pop_set_xi_source", "pop_xi_grid", "pop_xi_grid_last_ms",
+    "pop_load_vt_grid", "pop_set_xi_source", "pop_xi_grid", "pop_xi_grid_last_ms", "pop_loglik_parts",
 )
 MLP_N_PARAMS = 201218
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "pop_mlp_train_step": (i32, [vp, i64, vp, vp, ctypes.c_float]),
         "pop_mlp_gemm_check": (i32, [vp, i32, i32, i32, vp, vp, vp]),
         "pop_load_vt_grid": (i32, [vp, i32, vp, i32, vp, vp, i32]),
+        "pop_loglik_parts": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp, i32]),
         "pop_set_xi_source": (i32, [vp, i32]),
         "pop_xi_grid": (i32, [vp, i64, i32, vp, i32, vp, vp, i32]),
         "pop_xi_grid_last_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
@@ -206,6 +207,17 @@ def pop_loglik(ctx, lambdas, mode=POP_MODE_F64, out=None):
                       torch.empty(K, dtype=torch.float64, device=dev), torch.empty(K, dtype=torch.int32, device=dev))
         ptrs = [ctypes.c_void_p(r.data_ptr()) for r in res]
     _check(ctx, load_library().pop_loglik(ctx, K, P, lp, int(mode), *ptrs, mem))
+    return res
+
+
+def pop_loglik_parts(ctx, lambdas, mode=POP_MODE_F64):
+    """(sum_i ln(S_i/n_i), sum w, sum w^2, flags) over the loaded events and injections (host arrays)."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    K, P = lam.shape
+    res = (np.empty(K), np.empty(K), np.empty(K), np.empty(K, np.uint32))
+    ptrs = [r.ctypes.data_as(ctypes.c_void_p) for r in res]
+    _check(ctx, load_library().pop_loglik_parts(ctx, K, P, lam.ctypes.data_as(ctypes.c_void_p), int(mode), *ptrs,
+                                                POP_MEM_HOST))
     return res
 
 

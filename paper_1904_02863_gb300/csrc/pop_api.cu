@@ -87,6 +87,7 @@ struct pop_ctx {
     int64_t k_cap = 0;
     int n_params_cap = 12;
     DevBuf d_lambda, d_c64, d_c32, d_part, d_part2, d_lnL, d_lnxi, d_neff, d_flags, d_K;
+    DevBuf d_parts;          // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2 (pop_loglik_parts)
     int32_t part_chunks = -1, part_inj = -1;
 
     Tiling tiling[2] = {{8, 256, 0}, {16, 256, 0}};
@@ -253,8 +254,9 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     const int32_t n_inj = c->n_chunks - c->n_ev_chunks;
     if (K <= c->k_cap && c->part_chunks == c->n_chunks && c->part_inj == n_inj) return POP_OK;
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(K, c->k_cap), 64);
-    DevBuf lam, c64, c32, part, part2, lnL, lnxi, neff, flags, dK;
+    DevBuf lam, c64, c32, part, part2, lnL, lnxi, neff, flags, dK, parts3;
     CK(lam.alloc(sizeof(double) * cap * 12), "cudaMalloc(lambda)");
+    CK(parts3.alloc(sizeof(double) * cap * 3), "cudaMalloc(parts)");
     CK(c64.alloc(sizeof(LamF64) * cap), "cudaMalloc(consts64)");
     CK(c32.alloc(sizeof(LamF32) * cap), "cudaMalloc(consts32)");
     CK(part.alloc(sizeof(double) * cap * c->n_chunks), "cudaMalloc(partials)");
@@ -284,6 +286,7 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     c->d_neff.swap(neff);
     c->d_flags.swap(flags);
     c->d_K.swap(dK);
+    c->d_parts.swap(parts3);
     c->k_cap = cap;
     c->part_chunks = c->n_chunks;
     c->part_inj = n_inj;
@@ -346,7 +349,8 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
                        c->d_offsets.as<int64_t>(), c->ev.n == 0 ? 0 : (int64_t)c->h_offsets.size() - 1,
                        n_items, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                        c->k_cap, c->d_lnL.as<double>(), c->d_lnxi.as<double>(), c->d_neff.as<double>(),
-                       c->d_flags.as<uint32_t>(), c->stream, sx, use_grid ? c->grid->xi.as<double>() : nullptr),
+                       c->d_flags.as<uint32_t>(), c->stream, sx, use_grid ? c->grid->xi.as<double>() : nullptr,
+                       c->d_parts.as<double>()),
        "finalise");
     CK(cudaEventRecordWithFlags(c->ev_t1, c->stream, rec), "event");
     return POP_OK;
@@ -641,31 +645,35 @@ int pop_load_injections(pop_ctx* c, int64_t n_found, int64_t n_draw, int n_dims,
     return POP_OK;
 }
 
-int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_lnL,
-               double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem)
+}  // extern "C"
+
+namespace {
+
+// Validation and one evaluation of the pipeline for K Lambda rows (results stay on the device).
+int loglik_run(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, int mem, const char* who)
 {
-    if (!c) return POP_EINVAL;
+    const std::string w(who);
     const bool use_grid = c->xi_source == POP_XI_GRID;
-    if (c->ev.n == 0) return fail(c, POP_ESTATE, "pop_loglik: load events first");
-    if (!use_grid && c->inj.n == 0) return fail(c, POP_ESTATE, "pop_loglik: load injections first");
+    if (c->ev.n == 0) return fail(c, POP_ESTATE, w + ": load events first");
+    if (!use_grid && c->inj.n == 0) return fail(c, POP_ESTATE, w + ": load injections first");
     if (use_grid && mode == POP_MODE_F32_SURROGATE)
-        return fail(c, POP_EINVAL, "pop_loglik: the surrogate mode replaces the injection selection term, not the grid");
-    if (K < 0) return fail(c, POP_EINVAL, "pop_loglik: K < 0");
+        return fail(c, POP_EINVAL, w + ": the surrogate mode replaces the injection selection term, not the grid");
+    if (K < 0) return fail(c, POP_EINVAL, w + ": K < 0");
     if (n_params != 11 + (c->ev.n_dims == 7))
-        return fail(c, POP_EINVAL, "pop_loglik: n_params must be 11 (12 with redshift samples)");
+        return fail(c, POP_EINVAL, w + ": n_params must be 11 (12 with redshift samples)");
     if (mode != POP_MODE_F64 && mode != POP_MODE_F32 && mode != POP_MODE_F32_SURROGATE)
-        return fail(c, POP_EINVAL, "pop_loglik: bad mode");
+        return fail(c, POP_EINVAL, w + ": bad mode");
     if (mode == POP_MODE_F32_SURROGATE && (!c->sur || !c->sur->trained))
-        return fail(c, POP_ESTATE, "pop_loglik: surrogate not trained (pop_xi_surrogate_train or _load)");
+        return fail(c, POP_ESTATE, w + ": surrogate not trained (pop_xi_surrogate_train or _load)");
     if (mode == POP_MODE_F32_SURROGATE && c->sur->n_params != n_params)
-        return fail(c, POP_EINVAL, "pop_loglik: the surrogate was trained for another n_params");
+        return fail(c, POP_EINVAL, w + ": the surrogate was trained for another n_params");
     const int need = mode == POP_MODE_F64 ? POP_STORE_F64 : POP_STORE_F32;
     if (!(c->ev.storage & need) || (!use_grid && !(c->inj.storage & need)))
-        return fail(c, POP_ESTATE, "pop_loglik: the loaded storage does not include this mode's precision");
-    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_loglik: bad mem");
+        return fail(c, POP_ESTATE, w + ": the loaded storage does not include this mode's precision");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, w + ": bad mem");
     if (K == 0) return POP_OK;
-    if (!lambda || !out_lnL) return fail(c, POP_EINVAL, "pop_loglik: lambda/out_lnL is NULL");
-    if (K > (1LL << 24)) return fail(c, POP_EINVAL, "pop_loglik: K too large");
+    if (!lambda) return fail(c, POP_EINVAL, w + ": lambda is NULL");
+    if (K > (1LL << 24)) return fail(c, POP_EINVAL, w + ": K too large");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     int rc = build_chunks(c);
     if (rc != POP_OK) return rc;
@@ -683,16 +691,87 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
     c->last_params = n_params;
     c->last_K = K;
     c->timed = true;
+    return POP_OK;
+}
+
+// The parts stay in [K][3] on the device; they are split into the three caller arrays here.
+__global__ void split_parts_kernel(const double* parts, const uint32_t* flags, const int64_t* dK, double* ev,
+                                   double* sw, double* sw2, uint32_t* fl)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= *dK) return;
+    ev[k] = parts[3 * k];
+    sw[k] = parts[3 * k + 1];
+    sw2[k] = parts[3 * k + 2];
+    if (fl) fl[k] = flags[k] & (POP_FLAG_INVALID_LAMBDA | POP_FLAG_ZERO_EVENT);
+}
+
+// After a synchronous (host-memory) call: the grid contraction's error word.
+int check_grid_error(pop_ctx* c, const char* who)
+{
+    if (c->xi_source != POP_XI_GRID) return POP_OK;
+    int bad = 0;
+    CK(c->grid->take_error(&bad, c->stream), "grid error word");
+    if (bad) return fail(c, POP_ETIMEOUT, std::string(who) + ": a bounded wait of the grid contraction gave up");
+    return POP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_lnL,
+               double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (K > 0 && !out_lnL) return fail(c, POP_EINVAL, "pop_loglik: out_lnL is NULL");
+    int rc = loglik_run(c, K, n_params, lambda, mode, mem, "pop_loglik");
+    if (rc != POP_OK || K == 0) return rc;
     CK(cudaMemcpyAsync(out_lnL, c->d_lnL.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnL");
     if (out_lnxi) CK(cudaMemcpyAsync(out_lnxi, c->d_lnxi.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnxi");
     if (out_neff) CK(cudaMemcpyAsync(out_neff, c->d_neff.p, sizeof(double) * K, out_kind(mem), c->stream), "copy neff");
     if (out_flags)
         CK(cudaMemcpyAsync(out_flags, c->d_flags.p, sizeof(uint32_t) * K, out_kind(mem), c->stream), "copy flags");
-    if (mem == POP_MEM_HOST) CK(cudaStreamSynchronize(c->stream), "sync");
-    if (use_grid && mem == POP_MEM_HOST) {
-        int bad = 0;
-        CK(c->grid->take_error(&bad, c->stream), "grid error word");
-        if (bad) return fail(c, POP_ETIMEOUT, "pop_loglik: a bounded wait of the grid contraction gave up");
+    if (mem == POP_MEM_HOST) {
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        return check_grid_error(c, "pop_loglik");
+    }
+    return POP_OK;
+}
+
+int pop_loglik_parts(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_events,
+                     double* out_sum_w, double* out_sum_w2, uint32_t* out_flags, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (c->xi_source != POP_XI_INJECTIONS)
+        return fail(c, POP_EINVAL, "pop_loglik_parts: needs the injection selection term");
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32)
+        return fail(c, POP_EINVAL, "pop_loglik_parts: mode must be POP_MODE_F64 or POP_MODE_F32");
+    if (K > 0 && (!out_events || !out_sum_w || !out_sum_w2))
+        return fail(c, POP_EINVAL, "pop_loglik_parts: an output is NULL");
+    int rc = loglik_run(c, K, n_params, lambda, mode, mem, "pop_loglik_parts");
+    if (rc != POP_OK || K == 0) return rc;
+    double *ev = out_events, *sw = out_sum_w, *sw2 = out_sum_w2;
+    uint32_t* fl = out_flags;
+    DevBuf tmp;
+    if (mem == POP_MEM_HOST) {  // split into device scratch, then copy out
+        CK(tmp.alloc((sizeof(double) * 3 + sizeof(uint32_t)) * K), "cudaMalloc(parts)");
+        ev = tmp.as<double>();
+        sw = ev + K;
+        sw2 = sw + K;
+        fl = reinterpret_cast<uint32_t*>(sw2 + K);
+    }
+    split_parts_kernel<<<(unsigned)((K + 255) / 256), 256, 0, c->stream>>>(
+        c->d_parts.as<double>(), c->d_flags.as<uint32_t>(), c->d_K.as<int64_t>(), ev, sw, sw2,
+        (out_flags || mem == POP_MEM_HOST) ? fl : nullptr);
+    CK(cudaGetLastError(), "split parts");
+    if (mem == POP_MEM_HOST) {
+        CK(cudaMemcpyAsync(out_events, ev, sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream), "copy events");
+        CK(cudaMemcpyAsync(out_sum_w, sw, sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream), "copy sum_w");
+        CK(cudaMemcpyAsync(out_sum_w2, sw2, sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream), "copy sum_w2");
+        if (out_flags)
+            CK(cudaMemcpyAsync(out_flags, fl, sizeof(uint32_t) * K, cudaMemcpyDeviceToHost, c->stream), "copy flags");
+        CK(cudaStreamSynchronize(c->stream), "sync");
     }
     return POP_OK;
 }

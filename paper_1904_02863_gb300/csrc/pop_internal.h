@@ -132,7 +132,8 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
                             int64_t n_draw, const LamF64* lam, const int64_t* dK, int64_t K_cap,
                             double* lnL, double* lnxi, double* neff, uint32_t* flags, cudaStream_t s,
                             SurrogateXi sx = SurrogateXi{nullptr, nullptr, nullptr},
-                            const double* grid_xi = nullptr);  // xi per Lambda from the grid (N_eff = +inf)
+                            const double* grid_xi = nullptr,  // xi per Lambda from the grid (N_eff = +inf)
+                            double* parts = nullptr);         // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2
 
 // Kernel function of a tiling (nullptr when that instantiation does not exist).
 const void* weight_f64_fn(const Tiling& t, bool has_z);

@@ -256,7 +256,7 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
                 const int32_t* __restrict__ ecb, const int64_t* __restrict__ off, int64_t n_events,
                 int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw, const LamF64* __restrict__ lam,
                 const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags,
-                SurrogateXi sx, const double* __restrict__ grid_xi)
+                SurrogateXi sx, const double* __restrict__ grid_xi, double* __restrict__ parts)
 {
     __shared__ double sh[FIN_THREADS / 32];
     const int64_t k = blockIdx.x;
@@ -267,6 +267,11 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
             lnxi[k] = 0.0;
             neff[k] = 0.0;
             flags[k] = POP_FLAG_INVALID_LAMBDA;
+            if (parts) {
+                parts[3 * k] = -INFINITY;
+                parts[3 * k + 1] = 0.0;
+                parts[3 * k + 2] = 0.0;
+            }
         }
         return;
     }
@@ -290,6 +295,11 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
     sw = block_sum<FIN_THREADS>(sw, sh);
     sw2 = block_sum<FIN_THREADS>(sw2, sh);
     if (threadIdx.x != 0) return;
+    if (parts) {  // the additive parts: event log-sum, injection sum w and sum w^2
+        parts[3 * k] = zero > 0.0 ? -INFINITY : s_ln;
+        parts[3 * k + 1] = sw;
+        parts[3 * k + 2] = sw2;
+    }
     uint32_t fl = 0;
     const double nd = (double)n_draw;
     double xi = sw / nd;
@@ -364,11 +374,12 @@ cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_c
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,
                             int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
                             const LamF64* lam, const int64_t* dK, int64_t K_cap, double* lnL, double* lnxi,
-                            double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx, const double* grid_xi)
+                            double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx, const double* grid_xi,
+                            double* parts)
 {
     if (K_cap <= 0) return cudaSuccess;
     finalise_kernel<<<(unsigned)K_cap, FIN_THREADS, 0, s>>>(part, part2, ecb, off, n_events, n_chunks, n_ev_chunks,
-                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx, grid_xi);
+                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx, grid_xi, parts);
     return cudaGetLastError();
 }
 
