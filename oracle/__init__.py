@@ -64,6 +64,8 @@ def _load():
         lib.pop_oracle_max_threads.restype = i32
         lib.pop_oracle_loglik_parts.argtypes = [i64, p, i32, p, p, i64, p, p, i64, i32, p, i32, p, p, p, p]
         lib.pop_oracle_loglik_parts.restype = i32
+        lib.pop_oracle_cbc_loglik.argtypes = [i32, i64, d, d, p, p, p, p, i64, p, i32, p]
+        lib.pop_oracle_cbc_loglik.restype = i32
         lib.pop_oracle_xi_grid.argtypes = [i32, p, i32, p, p, i64, i32, p, p, p]
         lib.pop_oracle_xi_grid.restype = i32
         _lib = lib
@@ -156,6 +158,25 @@ def loglik_parts(catalog, injections, lambdas, nthreads=0):
                                          _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(out[3]))
     if rc != 0:
         raise ValueError("oracle rejected the input sizes")
+    return out
+
+
+def cbc_loglik(f0, df, data, psd, hp, hc, thetas, nthreads=0):
+    """Single-event CBC ln L (Eq. cbclike) for each row of ``thetas`` [K, 2 + 3 n_det];
+    data [n_det, M] complex, psd [n_det, M], hp and hc [M] complex."""
+    d = np.ascontiguousarray(np.asarray(data, np.complex128)).view(np.float64)
+    S = np.ascontiguousarray(psd, dtype=np.float64)
+    a = np.ascontiguousarray(np.asarray(hp, np.complex128)).view(np.float64)
+    b = np.ascontiguousarray(np.asarray(hc, np.complex128)).view(np.float64)
+    th = np.ascontiguousarray(np.atleast_2d(thetas), dtype=np.float64)
+    n_det, M = S.shape
+    if th.shape[1] != 2 + 3 * n_det or data.shape != S.shape or len(hp) != M or len(hc) != M:
+        raise ValueError("inconsistent CBC shapes")
+    out = np.empty(th.shape[0])
+    rc = _load().pop_oracle_cbc_loglik(n_det, M, float(f0), float(df), _ptr(d), _ptr(S), _ptr(a), _ptr(b),
+                                       th.shape[0], _ptr(th), int(nthreads), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle rejected the CBC inputs")
     return out
 
 

@@ -20,6 +20,12 @@ shapes of the paper's workload.
   on [3, 100], q uniform on [3/m1, 1], uniform spins and tilts, z ~ 3 z^2/8) and
   kept when sigmoid((m1 - 20)/5) > U(0, 1).
 
+Single-event CBC workload (Sec. "Single-event Likelihood acceleration"): a
+leading-order stationary-phase chirp as the template (no waveform library is
+used), a smooth synthetic PSD in whitened units, per-detector antenna factors
+and arrival-time offsets, Gaussian noise at the PSD, scaled to a target SNR.
+Also the regular (m1, q) grid of the injection campaign for the grid VT.
+
 Everything is a numpy ``Generator(PCG64(seed))`` stream.
 """
 from __future__ import annotations
@@ -223,6 +229,79 @@ def campaign_vt_grid(n_m1=3001, n_q=801, m1_range=(3.0, 100.0), q_range=(0.03, 1
     q = np.linspace(q_range[0], q_range[1], n_q)
     pdet = np.ascontiguousarray(np.broadcast_to(campaign_pdet(m1)[:, None], (n_m1, n_q)))
     return m1, q, pdet
+
+
+# --------------------------------------------------------------------------- single-event CBC workload
+@dataclass
+class CbcData:
+    f0: float             # first bin frequency (Hz)
+    df: float             # bin spacing (Hz); the segment length is T = 1/df
+    data: np.ndarray      # complex128 [n_det, M] strain data (whitened units)
+    psd: np.ndarray       # float64 [n_det, M] one-sided noise power spectral density
+    hp: np.ndarray        # complex128 [M] plus polarisation of the template
+    hc: np.ndarray        # complex128 [M] cross polarisation
+    truth: np.ndarray     # float64 [2 + 3 n_det] the signal's (A, phi, Fp_i, Fc_i, dt_i)
+
+    @property
+    def n_det(self) -> int:
+        return self.psd.shape[0]
+
+    @property
+    def M(self) -> int:
+        return self.psd.shape[1]
+
+
+def cbc_psd(f, scale=1.0, f_knee=150.0):
+    """A smooth synthetic noise curve: steep low-frequency wall, flat bucket, rising high end."""
+    x = np.asarray(f, np.float64) / f_knee
+    return scale * (x ** -4.0 + 2.0 + 2.0 * x * x)
+
+
+def cbc_chirp(f, chirp_mass_s=5.9e-6, t_c=0.0, phi_c=0.0, cos_iota=0.6):
+    """Leading-order stationary-phase chirp (unit amplitude scale): hp = f^(-7/6) (1 + cos^2 iota)/2 e^{i Psi},
+    hc = -i cos(iota) f^(-7/6) e^{i Psi}, Psi = 2 pi f t_c - phi_c - pi/4 + (3/128) (pi Mc f)^(-5/3)."""
+    f = np.asarray(f, np.float64)
+    psi = 2.0 * np.pi * f * t_c - phi_c - np.pi / 4 + 3.0 / 128.0 * (np.pi * chirp_mass_s * f) ** (-5.0 / 3.0)
+    base = f ** (-7.0 / 6.0) * np.exp(1j * psi)
+    return base * (1.0 + cos_iota ** 2) / 2.0, -1j * cos_iota * base
+
+
+def make_cbc(M=4096, n_det=3, T=4.0, f0=20.0, snr=20.0, seed=0):
+    """Synthetic single-event data: the chirp seen by n_det detectors (own antenna factors
+    and arrival-time offsets) plus Gaussian noise at the synthetic PSD, M bins from f0 in
+    steps of 1/T, signal scaled to the given network SNR."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    df = 1.0 / T
+    f = f0 + df * np.arange(M)
+    hp, hc = cbc_chirp(f)
+    psd = np.stack([cbc_psd(f, scale=1.0 + 0.3 * i) for i in range(n_det)])
+    Fp = rng.uniform(-0.8, 0.8, n_det)
+    Fc = rng.uniform(-0.8, 0.8, n_det)
+    dt = rng.uniform(-0.02, 0.02, n_det)
+    resp = (Fp[:, None] * hp[None, :] + Fc[:, None] * hc[None, :]) * np.exp(-2j * np.pi * f[None, :] * dt[:, None])
+    rho2 = float(np.sum(4.0 * df * np.abs(resp) ** 2 / psd))
+    A = snr / np.sqrt(rho2)
+    sig = np.sqrt(T * psd / 4.0)   # each of Re, Im: E|n|^2 = T S / 2
+    noise = sig * (rng.standard_normal((n_det, M)) + 1j * rng.standard_normal((n_det, M)))
+    data = A * resp + noise
+    truth = np.concatenate([[A, 0.0], np.stack([Fp, Fc, dt], axis=1).ravel()])
+    return CbcData(f0, df, np.ascontiguousarray(data), np.ascontiguousarray(psd), hp, hc, truth)
+
+
+def make_cbc_thetas(cbc, K, seed=0):
+    """K parameter rows scattered around the truth (amplitude +-30%, phase +-0.5, antenna +-0.2, time +-1 ms)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = cbc.n_det
+    th = np.repeat(cbc.truth[None, :], K, axis=0)
+    th[:, 0] *= rng.uniform(0.7, 1.3, K)
+    th[:, 1] += rng.uniform(-0.5, 0.5, K)
+    for i in range(n):
+        th[:, 2 + 3 * i] += rng.uniform(-0.2, 0.2, K)
+        th[:, 3 + 3 * i] += rng.uniform(-0.2, 0.2, K)
+        th[:, 4 + 3 * i] += rng.uniform(-1e-3, 1e-3, K)
+    if K:
+        th[0] = cbc.truth
+    return np.ascontiguousarray(th)
 
 
 def round_to_f32(x):

@@ -1,5 +1,7 @@
 """The oracle's pins bite: each plausible mistake, planted in a copy of the oracle
-(on the CPU), makes tests/test_oracle_pins.py fail."""
+(on the CPU), makes the pins of its part fail (tests/test_oracle_pins.py for the
+population likelihood, test_gridvt_pins.py for the grid selection term,
+test_cbc_pins.py for the single-event CBC likelihood)."""
 import os
 import subprocess
 import sys
@@ -27,11 +29,28 @@ MUTANTS = {
     "event mean": ("log(s / (double)n_i)", "log(s)"),
     "prior weight": ("/ prior[j];", "* prior[j];"),
 }
+GRID_MUTANTS = {
+    "grid m1 weights": ("double wa = 0.5 * (", "double wa = ("),
+    "grid q weights": ("double wq = 0.5 * (", "double wq = 0.25 * ("),
+    "grid pdet transposed": ("pdet[(int64_t)a * n_q + b]", "pdet[(int64_t)b * n_m1 + a]"),
+}
+CBC_MUTANTS = {
+    "cbc time-shift sign": ("const double ere = cos(ang), eim = -sin(ang);",
+                            "const double ere = cos(ang), eim = sin(ang);"),
+    "cbc 2/T": ("const double two_over_T = 2.0 * df;", "const double two_over_T = df;"),
+    "cbc psd log term": ("-log(two_pi * S)", "-log(S)"),
+    "cbc complex product": ("const double vim = cre * uim + cim * ure;", "const double vim = cre * uim - cim * ure;"),
+    "cbc detector index": ("const double S = psd[(int64_t)i * M + j];", "const double S = psd[(int64_t)j * n_det + i];"),
+    "cbc cross polarisation": ("Fc * hc[2 * j]", "Fp * hc[2 * j]"),
+}
+PIN_FILES = {**{k: "test_oracle_pins.py" for k in MUTANTS}, **{k: "test_gridvt_pins.py" for k in GRID_MUTANTS},
+             **{k: "test_cbc_pins.py" for k in CBC_MUTANTS}}
+ALL = {**MUTANTS, **GRID_MUTANTS, **CBC_MUTANTS}
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+@pytest.mark.parametrize("name", sorted(ALL))
 def test_pins_catch_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new = ALL[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation site not found: {old}"
     mutant = tmp_path / "mutant.c"
@@ -41,6 +60,6 @@ def test_pins_catch_mutant(name, tmp_path):
                    check=True, capture_output=True)
     env = dict(os.environ, POP_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", PIN_FILES[name])],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant '{name}' survived the pins:\n{r.stdout[-2000:]}"
