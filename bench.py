@@ -249,6 +249,56 @@ def grid_form(B, like, lam, timed, args, world):
     return out
 
 
+# FMA-pipe operations per (bin, parameter row, detector) unit of the CBC sums kernel:
+# two complex multiply-adds (P e, Q e: 8) and the time-shift recurrence e <- e w (4).
+CBC_FMA_PER_UNIT = 12
+
+
+def cbc_form(B, like, args, world, rank):
+    """Second workload: the single-event CBC likelihood (Eq. cbclike) with per-detector
+    time shifts, M = 2^18 bins (128 s from 20 Hz), 3 detectors, K = 256 parameter rows per
+    call, FP64 and FP32; the time-shifted sums kernel gets its own roofline, and the
+    oracle (direct evaluation) is timed on 16 rows beside it."""
+    M, K, T = 2 ** 18, 256, 128.0
+    c = synth.make_cbc(M, T=T, seed=synth.seed_for(6, 0))
+    th = synth.make_cbc_thetas(c, K, seed=synth.seed_for(6, 2) + 7919 * rank)
+    B.pop_cbc_load(like.ctx, c.f0, c.df, c.data, c.psd, c.hp, c.hc)
+    units = K * c.n_det * M
+    out = {"config": {"bins": M, "detectors": c.n_det, "K": K, "segment_s": T, "f_min_hz": c.f0,
+                      "template": "leading-order stationary-phase chirp", "l2": "P, Q arrays 25 MB FP32 (L2-resident)"}}
+    peaks = {"f64": (FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6, "Top/s (FP64 pipe)", "cbc_sum_kernel<double>"),
+             "f32": (FP32_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6, "Top/s (FP32 FMA)", "cbc_sum_kernel<float>")}
+    for name, mode in (("f64", B.POP_MODE_F64), ("f32", B.POP_MODE_F32)):
+        for _ in range(args.warmup):
+            B.pop_cbc_loglik(like.ctx, th, mode)
+        sums, tots = [], []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            B.pop_cbc_loglik(like.ctx, th, mode)
+            a, b = B.pop_cbc_last_ms(like.ctx)
+            sums.append(a)
+            tots.append(b)
+        wall = time.perf_counter() - t0
+        sm, tm = statistics.median(sums), statistics.median(tots)
+        peak, unit, kern = peaks[name]
+        ach = units * CBC_FMA_PER_UNIT / (sm * 1e-3)
+        out[name] = {"value": world * K / (tm * 1e-3), "unit": "evals/s", "ms_per_call": tm, "sum_kernel_ms": sm,
+                     "e2e": {"value": world * K * args.steps / wall, "unit": "evals/s",
+                             "h2d_bytes_per_step": int(th.nbytes), "d2h_bytes_per_step": int(K * 12)},
+                     "roofline": {"bound": "alu", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12,
+                                  "unit": unit, "frac": ach / peak, "ops_per_launch": units * CBC_FMA_PER_UNIT,
+                                  "peak_basis": "lanes/SM/clk x 152 SMs x 2070 MHz", "traffic": None}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        n = 16
+        t0 = time.perf_counter()
+        oracle.cbc_loglik(c.f0, c.df, c.data, c.psd, c.hp, c.hc, th[:n], nthreads=host_cores())
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n / dt, "unit": "evals/s", "cores": min(host_cores(), n), "kind": "oracle",
+                               "sample": f"{n} parameter rows of the same data, FP64, OpenMP over rows"}
+    return out
+
+
 def run_ragged(args, B, rank, local, world):
     """Batching form: 2000 events with S_i ~ U{500..16000} in CSR (about 1.65e7 samples), redshift
     on (12 parameters), 1.8e7 injection draws, FP32 weights.  Uneven Lambda batches
@@ -450,6 +500,7 @@ def main():
                                  "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32"}}
         line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
         line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
+        line["forms"]["cbc_likelihood"] = cbc_form(B, like, args, world, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
     like.close()

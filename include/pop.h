@@ -205,6 +205,40 @@ int pop_xi_grid(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int
  * Lambda, and the whole grid term (CUDA events on the context stream). */
 int pop_xi_grid_last_ms(pop_ctx* ctx, double* contraction_ms, double* total_ms);
 
+/* ------------------------------------------------------------------ single-event CBC likelihood
+ * Paper, Sec. "Single-event Likelihood acceleration", Eq. (cbclike): for
+ * n_det detectors and M frequency bins f_j = f0 + j df (T = 1/df),
+ *
+ *   ln L(theta) = sum_i sum_j [ -ln(2 pi S_ij) - (2/T) |d_ij - h_ij(theta)|^2 / S_ij ]
+ *   h_ij = A e^{i phi} (Fp_i hp_j + Fc_i hc_j) e^{-2 pi i f_j dt_i}
+ *
+ * with the frequency-domain template given by its two polarisations hp, hc
+ * (from any waveform model), and per parameter row theta the amplitude A,
+ * phase phi and, per detector, the antenna factors Fp_i, Fc_i and the
+ * arrival-time shift dt_i (the per-detector time-shift exponential the
+ * section names as the likelihood's second largest cost). */
+
+/* Load data d[n_det][M] and templates (complex, interleaved Re, Im doubles:
+ * data[(i M + j) 2 + {0, 1}], hp[2 j + {0, 1}], hc[2 j + {0, 1}]) and the PSD
+ * psd[n_det][M] (> 0), all in `mem`, finite.  The data-only terms, the
+ * template norms and w conj(d) hp, w conj(d) hc (w = (2/T)/S) are formed once
+ * here in FP64.  Replaces earlier CBC data; synchronous. */
+int pop_cbc_load(pop_ctx* ctx, int n_det, int64_t M, double f0, double df, const double* data, const double* psd,
+                 const double* hp, const double* hc, int mem);
+
+/* ln L for K rows theta[K][n_params], n_params = 2 + 3 n_det, in the order
+ * (A, phi, Fp_1, Fc_1, dt_1, ..., Fp_n, Fc_n, dt_n).  out_lnL[K] required,
+ * out_flags[K] may be NULL (POP_FLAG_INVALID_LAMBDA for a non-finite row, whose
+ * ln L is -inf).  mode POP_MODE_F64 (FP64 throughout) or POP_MODE_F32 (FP32
+ * time shifts and bin sums, FP64 phases modulo one turn, per-block combines
+ * and the final assembly).  Outputs in `mem`; asynchronous with POP_MEM_DEVICE. */
+int pop_cbc_loglik(pop_ctx* ctx, int64_t K, int n_params, const double* theta, int mode, double* out_lnL,
+                   uint32_t* out_flags, int mem);
+
+/* Duration in milliseconds of the last pop_cbc_loglik: the time-shifted bin
+ * sums kernel, and the whole call on the device. */
+int pop_cbc_last_ms(pop_ctx* ctx, double* sum_ms, double* total_ms);
+
 /* Tiling of the persistent weight kernel for `mode` (POP_MODE_F64 or
  * POP_MODE_F32): Lambda points per work item (1, 2, 4, 8, 16 or 32), threads
  * per block (128, 256 or 512) and resident blocks per SM (0 = occupancy

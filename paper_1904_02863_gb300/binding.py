@@ -34,6 +34,7 @@ EXPORTS = (
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
     "pop_load_vt_grid", "pop_set_xi_source", "pop_xi_grid", "pop_xi_grid_last_ms", "pop_loglik_parts",
+    "pop_cbc_load", "pop_cbc_loglik", "pop_cbc_last_ms",
 )
 MLP_N_PARAMS = 201218
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -89,6 +90,9 @@ def load_library(path: str = LIB_PATH):
         "pop_mlp_gemm_check": (i32, [vp, i32, i32, i32, vp, vp, vp]),
         "pop_load_vt_grid": (i32, [vp, i32, vp, i32, vp, vp, i32]),
         "pop_loglik_parts": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp, i32]),
+        "pop_cbc_load": (i32, [vp, i32, i64, d, d, vp, vp, vp, vp, i32]),
+        "pop_cbc_loglik": (i32, [vp, i64, i32, vp, i32, vp, vp, i32]),
+        "pop_cbc_last_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
         "pop_set_xi_source": (i32, [vp, i32]),
         "pop_xi_grid": (i32, [vp, i64, i32, vp, i32, vp, vp, i32]),
         "pop_xi_grid_last_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
@@ -219,6 +223,37 @@ def pop_loglik_parts(ctx, lambdas, mode=POP_MODE_F64):
     _check(ctx, load_library().pop_loglik_parts(ctx, K, P, lam.ctypes.data_as(ctypes.c_void_p), int(mode), *ptrs,
                                                 POP_MEM_HOST))
     return res
+
+
+def pop_cbc_load(ctx, f0, df, data, psd, hp, hc):
+    """Single-event CBC data: data [n_det, M] complex, psd [n_det, M], hp and hc [M] complex (host arrays)."""
+    d = np.ascontiguousarray(np.asarray(data, np.complex128))
+    S = np.ascontiguousarray(psd, dtype=np.float64)
+    a = np.ascontiguousarray(np.asarray(hp, np.complex128))
+    b = np.ascontiguousarray(np.asarray(hc, np.complex128))
+    n_det, M = S.shape
+    if d.shape != S.shape or a.shape != (M,) or b.shape != (M,):
+        raise ValueError("pop_cbc_load: inconsistent shapes")
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(ctx, load_library().pop_cbc_load(ctx, n_det, M, float(f0), float(df), vp(d), vp(S), vp(a), vp(b),
+                                            POP_MEM_HOST))
+
+
+def pop_cbc_loglik(ctx, thetas, mode=POP_MODE_F64):
+    """ln L and flags for each row of thetas [K, 2 + 3 n_det] (host arrays; synchronous)."""
+    th = np.ascontiguousarray(np.atleast_2d(thetas), dtype=np.float64)
+    K, P = th.shape
+    out, fl = np.empty(K), np.empty(K, np.uint32)
+    _check(ctx, load_library().pop_cbc_loglik(ctx, K, P, th.ctypes.data_as(ctypes.c_void_p), int(mode),
+                                              out.ctypes.data_as(ctypes.c_void_p),
+                                              fl.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST))
+    return out, fl
+
+
+def pop_cbc_last_ms(ctx):
+    w, t = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, load_library().pop_cbc_last_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, t.value
 
 
 def pop_set_tiling(ctx, mode, lambda_tile, block_threads, blocks_per_sm=0):

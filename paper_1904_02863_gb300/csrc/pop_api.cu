@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "pop.h"
+#include "pop_cbc.h"
 #include "pop_devbuf.h"
 #include "pop_gridvt.h"
 #include "pop_internal.h"
@@ -99,6 +100,7 @@ struct pop_ctx {
     ExpConsts expc{};
     std::unique_ptr<Surrogate> sur;  // ln xi network, created on first use
     std::unique_ptr<GridVT> grid;    // grid selection term, created by pop_load_vt_grid
+    std::unique_ptr<CbcState> cbc;   // single-event CBC likelihood, created by pop_cbc_load
     int xi_source = POP_XI_INJECTIONS;
     bool timed = false;
     int64_t last_K = 0;
@@ -773,6 +775,60 @@ int pop_loglik_parts(pop_ctx* c, int64_t K, int n_params, const double* lambda, 
             CK(cudaMemcpyAsync(out_flags, fl, sizeof(uint32_t) * K, cudaMemcpyDeviceToHost, c->stream), "copy flags");
         CK(cudaStreamSynchronize(c->stream), "sync");
     }
+    return POP_OK;
+}
+
+int pop_cbc_load(pop_ctx* c, int n_det, int64_t M, double f0, double df, const double* data, const double* psd,
+                 const double* hp, const double* hc, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_cbc_load: bad mem");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    std::unique_ptr<CbcState> fresh;
+    CbcState* st = c->cbc.get();
+    if (!st) {
+        fresh.reset(new CbcState());
+        st = fresh.get();
+    }
+    const int rc = st->load(n_det, M, f0, df, data, psd, hp, hc, mem == POP_MEM_DEVICE, c->stream);
+    if (rc != POP_OK) return fail(c, rc, st->err);
+    if (fresh) c->cbc = std::move(fresh);
+    return POP_OK;
+}
+
+int pop_cbc_loglik(pop_ctx* c, int64_t K, int n_params, const double* theta, int mode, double* out_lnL,
+                   uint32_t* out_flags, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (!c->cbc) return fail(c, POP_ESTATE, "pop_cbc_loglik: load data first (pop_cbc_load)");
+    CbcState& st = *c->cbc;
+    if (n_params != 2 + 3 * st.n_det) return fail(c, POP_EINVAL, "pop_cbc_loglik: n_params must be 2 + 3 n_det");
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32) return fail(c, POP_EINVAL, "pop_cbc_loglik: bad mode");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_cbc_loglik: bad mem");
+    if (K < 0 || K > (1LL << 24)) return fail(c, POP_EINVAL, "pop_cbc_loglik: K out of range");
+    if (K == 0) return POP_OK;
+    if (!theta || !out_lnL) return fail(c, POP_EINVAL, "pop_cbc_loglik: theta/out_lnL is NULL");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int rc = st.run(K, theta, mem == POP_MEM_DEVICE, mode == POP_MODE_F64 ? 0 : 1, c->stream);
+    if (rc != POP_OK) return fail(c, rc, st.err);
+    CK(cudaMemcpyAsync(out_lnL, st.lnL.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnL");
+    if (out_flags)
+        CK(cudaMemcpyAsync(out_flags, st.flags.p, sizeof(uint32_t) * K, out_kind(mem), c->stream), "copy flags");
+    if (mem == POP_MEM_HOST) CK(cudaStreamSynchronize(c->stream), "sync");
+    return POP_OK;
+}
+
+int pop_cbc_last_ms(pop_ctx* c, double* sum_ms, double* total_ms)
+{
+    if (!c) return POP_EINVAL;
+    if (!c->cbc || !c->cbc->timed) return fail(c, POP_ESTATE, "pop_cbc_last_ms: no pop_cbc_loglik yet");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaEventSynchronize(c->cbc->ev3), "event sync");
+    float w = 0.f, t = 0.f;
+    CK(cudaEventElapsedTime(&w, c->cbc->ev1, c->cbc->ev2), "elapsed");
+    CK(cudaEventElapsedTime(&t, c->cbc->ev0, c->cbc->ev3), "elapsed");
+    if (sum_ms) *sum_ms = w;
+    if (total_ms) *total_ms = t;
     return POP_OK;
 }
 

@@ -60,7 +60,8 @@ _Z_LO = 1e-3
 
 
 def seed_for(config: int, stream: int = 0) -> int:
-    """Seed of the given workload (1..5) and sub-stream (0 events, 1 injections, 2 Lambdas)."""
+    """Seed of the given workload (1..5 population, 6 single-event CBC) and sub-stream
+    (0 events or data, 1 injections, 2 Lambdas or parameter rows)."""
     return SEED_BASE + config + 1000 * stream
 
 
