@@ -104,7 +104,7 @@ def parse():
     p.add_argument("--events", type=int, default=1000, help="events (a smaller catalog for profiling captures)")
     p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
     p.add_argument("--mode", default="both", choices=["both", "f64", "f32"])
-    p.add_argument("--workload", default="c2", choices=["c2", "c4"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc"],
                    help="c2: the metric's catalog workload (default); c4: ragged CSR + redshift, uneven batches")
     return p.parse_args()
 
@@ -299,6 +299,74 @@ def cbc_form(B, like, args, world, rank):
     return out
 
 
+def run_grid(args, B, rank, local, world):
+    """Standalone grid selection term: ln xi_grid (pop_xi_grid) for K = 1024 Lambda on the
+    3001 x 801 campaign grid, FP64 headline and FP32 form; value = Lambda evaluated / s."""
+    import torch
+    m1, q, pdet = synth.campaign_vt_grid()
+    K = 1024
+    lam = synth.make_lambdas(K, 11, seed=synth.seed_for(2, 2) + 7919 * rank)
+    ctx = B.pop_create(local, torch.cuda.current_stream(local))
+    B.pop_load_vt_grid(ctx, m1, q, pdet)
+    triples = grid_support_triples(m1, q, lam)
+    res = {}
+    with Clocks(local) as clk:
+        for name, mode in (("f64", B.POP_MODE_F64), ("f32", B.POP_MODE_F32)):
+            for _ in range(args.warmup):
+                B.pop_xi_grid(ctx, lam, mode)
+            barrier(world)
+            c_ms, t_ms = [], []
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                B.pop_xi_grid(ctx, lam, mode)
+                c, t = B.pop_xi_grid_last_ms(ctx)
+                c_ms.append(c)
+                t_ms.append(t)
+            wall = max_over_ranks(time.perf_counter() - t0, world)
+            res[name] = (max_over_ranks(statistics.median(c_ms), world), max_over_ranks(statistics.median(t_ms), world),
+                         wall)
+    B.pop_destroy(ctx)
+    c64, t64, w64 = res["f64"]
+    c32, t32, w32 = res["f32"]
+    peak64 = FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    line = {"metric": "ln xi_grid(Lambda) evals/s, 3001 x 801 (m1, q) grid", "value": world * K / (t64 * 1e-3),
+            "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "grid_vt_3001x801", "K": K, "in_support_triples": triples,
+                       "parallelism": f"replicas{world}", "l2": "grid and scratch L2-resident (29 MB)"},
+            "roofline": {"bound": "alu", "kernel": "gv_main_kernel<double>", "achieved": triples / (c64 * 1e-3) / 1e12,
+                         "peak": peak64 / 1e12, "unit": "Top/s (FP64 pipe)",
+                         "frac": triples / (c64 * 1e-3) / peak64, "traffic": None},
+            "e2e": {"value": world * K * args.steps / w64, "unit": "evals/s", "h2d_bytes_per_step": int(lam.nbytes),
+                    "d2h_bytes_per_step": int(K * 12)},
+            "forms": {"f32": {"value": world * K / (t32 * 1e-3), "unit": "evals/s", "contraction_ms": c32,
+                              "frac_of_ffma_peak": triples / (c32 * 1e-3) / (FP32_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6)}},
+            "gpu_launches": 7 * args.steps, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+
+
+def run_cbc(args, B, rank, local, world):
+    """Second workload alone: the single-event CBC likelihood form (see cbc_form)."""
+    import torch
+    like = B.Likelihood(local, torch.cuda.current_stream(local))
+    with Clocks(local) as clk:
+        f = cbc_form(B, like, args, world, rank)
+    like.close()
+    f64 = f["f64"]
+    line = {"metric": "single-event CBC ln L evals/s, 3 detectors x 2^18 bins", "value": f64["value"],
+            "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": f64["ms_per_call"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": dict(f["config"], workload="cbc_bns_2e18",
+                                                                 parallelism=f"replicas{world}"),
+            "roofline": f64["roofline"], "e2e": f64["e2e"], "forms": {"f32": f["f32"]},
+            "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
+    if "cpu_baseline" in f:
+        line["cpu_baseline"] = f["cpu_baseline"]
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+
+
 def run_ragged(args, B, rank, local, world):
     """Batching form: 2000 events with S_i ~ U{500..16000} in CSR (about 1.65e7 samples), redshift
     on (12 parameters), 1.8e7 injection draws, FP32 weights.  Uneven Lambda batches
@@ -404,6 +472,12 @@ def main():
     build.build()
     if args.workload == "c4":
         run_ragged(args, B, rank, local, world)
+        return
+    if args.workload == "grid":
+        run_grid(args, B, rank, local, world)
+        return
+    if args.workload == "cbc":
+        run_cbc(args, B, rank, local, world)
         return
 
     scale = args.events / 1000.0

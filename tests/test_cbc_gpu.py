@@ -9,10 +9,11 @@ the same kind of bound, and its exponentials (an exact phase every 8 bins, then
 the recurrence e <- e w) are within ~40 u.  FP64: |d ln L| <= (n + 200) u sum|t|.
 
 FP32 mode: the time-shifted sums SP = sum_j P_j e_j, SQ = sum_j Q_j e_j run in FP32
-(P = w conj(d) hp, Q = w conj(d) hc rounded to FP32; e_j from FP32 sincospi of the
-exact phase, within ~4 u32, then up to 7 FP32 complex products, ~3 u32 each; an
+(P = w conj(d) hp, Q = w conj(d) hc rounded to FP32; e_j from the hardware sine and
+cosine of the exact phase on [-pi, pi), within 2^-21.19 absolute plus the rounding of
+the phase to FP32, ~8 u32, then up to 7 FP32 complex products, ~3 u32 each; an
 FP32 running sum per thread of at most CB / 2048 runs of 8 bins, then 5 shuffle
-levels).  Every term P_j e_j carries at most eps = (4 + 21 + 8 + n_acc + 5 + 4) u32
+levels).  Every term P_j e_j carries at most eps = (8 + 21 + 8 + n_acc + 5 + 4) u32
 of |P_j| (n_acc = the bins a thread adds), and ln L takes 2 Re(alpha SP + beta SQ), so
 |d ln L| <= FP64 bound + 2 sum_i (|alpha_i| E_P,i + |beta_i| E_Q,i) eps,
 E_P,i = sum_j |P_ij| (E_Q likewise).
@@ -60,7 +61,7 @@ def bounds(c, th, n_acc):
     n = c.n_det * c.M
     EP = np.sum(w * np.abs(c.data) * np.abs(c.hp)[None, :], axis=1)
     EQ = np.sum(w * np.abs(c.data) * np.abs(c.hc)[None, :], axis=1)
-    eps = (4 + 21 + 8 + n_acc + 5 + 4) * U32
+    eps = (8 + 21 + 8 + n_acc + 5 + 4) * U32
     b64, b32 = [], []
     for t in th:
         h = response(c, t)
