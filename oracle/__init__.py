@@ -64,6 +64,12 @@ def _load():
         lib.pop_oracle_max_threads.restype = i32
         lib.pop_oracle_loglik_parts.argtypes = [i64, p, i32, p, p, i64, p, p, i64, i32, p, i32, p, p, p, p]
         lib.pop_oracle_loglik_parts.restype = i32
+        lib.pop_oracle_loglik_grad.argtypes = [i64, p, i32, p, p, i64, i64, p, p, i64, i32, p, i32, p, p, p]
+        lib.pop_oracle_loglik_grad.restype = i32
+        lib.pop_oracle_score.argtypes = [p, i32, p, i32, p]
+        lib.pop_oracle_score.restype = d
+        lib.pop_oracle_digamma.argtypes = [d]
+        lib.pop_oracle_digamma.restype = d
         lib.pop_oracle_cbc_loglik.argtypes = [i32, i64, d, d, p, p, p, p, i64, p, i32, p]
         lib.pop_oracle_cbc_loglik.restype = i32
         lib.pop_oracle_xi_grid.argtypes = [i32, p, i32, p, p, i64, i32, p, p, p]
@@ -159,6 +165,37 @@ def loglik_parts(catalog, injections, lambdas, nthreads=0):
     if rc != 0:
         raise ValueError("oracle rejected the input sizes")
     return out
+
+
+def score(theta, L):
+    """(p(theta | Lambda), d ln p / d Lambda) for one sample."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    a = np.ascontiguousarray(L, dtype=np.float64)
+    g = np.empty(a.size)
+    pv = _load().pop_oracle_score(_ptr(th), th.size, _ptr(a), a.size, _ptr(g))
+    return pv, g
+
+
+def digamma(x):
+    return _load().pop_oracle_digamma(float(x))
+
+
+def loglik_grad(catalog, injections, lambdas, nthreads=0):
+    """(ln L, d ln L / d Lambda [K, n_params], flags) for each row of ``lambdas``."""
+    lam = np.ascontiguousarray(np.atleast_2d(lambdas), dtype=np.float64)
+    K, P = lam.shape
+    off = np.ascontiguousarray(catalog.offsets, dtype=np.int64)
+    th = np.ascontiguousarray(catalog.theta, dtype=np.float64)
+    pr = np.ascontiguousarray(catalog.prior, dtype=np.float64)
+    ith = np.ascontiguousarray(injections.theta, dtype=np.float64)
+    pd = np.ascontiguousarray(injections.p_draw, dtype=np.float64)
+    lnL, grad, fl = np.empty(K), np.empty((K, P)), np.empty(K, np.uint32)
+    rc = _load().pop_oracle_loglik_grad(len(off) - 1, _ptr(off), th.shape[1], _ptr(th), _ptr(pr), ith.shape[0],
+                                        int(injections.n_draw), _ptr(ith), _ptr(pd), K, P, _ptr(lam), int(nthreads),
+                                        _ptr(lnL), _ptr(grad), _ptr(fl))
+    if rc != 0:
+        raise ValueError("oracle rejected the input sizes")
+    return lnL, grad, fl
 
 
 def cbc_loglik(f0, df, data, psd, hp, hc, thetas, nthreads=0):

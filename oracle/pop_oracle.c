@@ -35,9 +35,11 @@
  * Every density is evaluated directly per sample with libm (pow, exp, log,
  * erf, lgamma, expm1).  There is no blocking, fusion or reordering.
  *
- * Also here: the selection term on a regular (m1, q) grid, the additive parts
- * of ln L for split catalogs, and the single-event CBC likelihood of the
- * paper's Sec. "Single-event Likelihood acceleration" (each at its function).
+ * Also here: the gradient of ln L with respect to Lambda (from the analytic
+ * score of each density), the selection term on a regular (m1, q) grid, the
+ * additive parts of ln L for split catalogs, and the single-event CBC
+ * likelihood of the paper's Sec. "Single-event Likelihood acceleration" (each
+ * at its function).
  * It is built with -ffp-contract=off so that q*m1 rounds once, as stated.
  */
 #include <math.h>
@@ -335,6 +337,177 @@ int pop_oracle_xi_grid(int n_m1, const double* m1, int n_q, const double* q, con
         }
         out_lnxi[k] = s > 0.0 ? log(s) : -INFINITY;
         if (out_flags) out_flags[k] = s > 0.0 ? 0u : OR_FLAG_ZERO_XI;
+    }
+    return 0;
+}
+
+/* Digamma psi(x), x > 0: the recurrence psi(x) = psi(x + 1) - 1/x up to x >= 10,
+ * then the asymptotic series ln x - 1/(2x) - sum B_2k / (2k x^2k) (Abramowitz &
+ * Stegun 6.3.18) to x^-12. */
+double pop_oracle_digamma(double x)
+{
+    double r = 0.0;
+    while (x < 10.0) {
+        r -= 1.0 / x;
+        x += 1.0;
+    }
+    const double x2 = 1.0 / (x * x);
+    const double series = x2 * (1.0 / 12 - x2 * (1.0 / 120 - x2 * (1.0 / 252 - x2 * (1.0 / 240 - x2 * (1.0 / 132 - x2 * (691.0 / 32760))))));
+    return r + log(x) - 0.5 / x - series;
+}
+
+static double std_normal_pdf(double t) { return exp(-0.5 * t * t) / SQRT2PI; }
+
+/*
+ * p(theta | Lambda) and its score g[p] = d ln p(theta | Lambda) / d Lambda_p for the
+ * n_params parameters, inside the support (the support's own edges, where the
+ * density jumps, have no derivative and are left out).  Term by term:
+ *   power law  PL = x^-alpha C, C = (1-alpha) / (b^(1-alpha) - a^(1-alpha)):
+ *     d ln PL/d alpha = -ln x + d ln C/d alpha,  d ln C/d alpha = -1/(1-alpha) + (b^s ln b - a^s ln a)/(b^s - a^s)
+ *     (s = 1 - alpha; at alpha = 1, (ln a + ln b)/2); d ln C/d a = PL(a), d ln C/d b = -PL(b)
+ *     (a normalised density f = g / int_a^b g has d ln(1/int)/d a = f(a)).
+ *   truncated normal N_T = phi((x-mu)/sigma) / (sigma Z) on [a, b]:
+ *     d/d mu: (x-mu)/sigma^2 + N_T(b) - N_T(a);  d/d sigma: -1/sigma + (x-mu)^2/sigma^3 + b' N_T(b) - a' N_T(a)
+ *     (a' = (a-mu)/sigma, b' = (b-mu)/sigma); d/d a: N_T(a); d/d b: -N_T(b).
+ *   p(m1) = (1-lam) PL + lam N_T: d/d lam = (N_T - PL)/p(m1); the rest weighted by each part.
+ *   p(q|m1) = (1+beta) q^beta / (1 - rho), rho = (mmin/m1)^(1+beta):
+ *     d/d beta = 1/(1+beta) + ln q + rho ln(mmin/m1)/(1 - rho)   (beta = -1: ln q - ln(mmin/m1)/2)
+ *     d/d mmin = (1+beta) rho / (mmin (1 - rho))                 (beta = -1: 1/(mmin ln(m1/mmin)))
+ *   Beta(a; ac, bc): d/d ac = ln a - psi(ac) + psi(ac+bc), d/d bc = ln(1-a) - psi(bc) + psi(ac+bc), per spin.
+ *   tilts T = (1-xi)/4 + xi G1 G2, G = phi((c-1)/sigma_t)/(sigma_t Z_t), Z_t = erf(sqrt2/sigma_t)/2:
+ *     d/d xi = (G1 G2 - 1/4)/T;  d/d sigma_t = xi G1 G2 (-2/sigma_t + dc/sigma_t^3 + 4 phi(2/sigma_t)/(sigma_t^2 Z_t)) / T,
+ *     dc = (c1-1)^2 + (c2-1)^2.
+ *   redshift Z(z) = (1+z)^(kappa-1) z^2 / I(kappa): d/d kappa = ln(1+z) - I'(kappa)/I(kappa), I' the
+ *     same trapezoid of (1+z)^(kappa-1) ln(1+z) z^2.
+ * Returns p (0 outside the support; g is then left at 0).
+ */
+static double score_theta(const double* th, int n_dims, const double* L, double znorm, double dznorm, double* g)
+{
+    for (int p = 0; p < 12; ++p) g[p] = 0.0;
+    const double m1 = th[0], q = th[1], a1 = th[2], a2 = th[3], c1 = th[4], c2 = th[5];
+    const double alpha = L[P_ALPHA], beta = L[P_BETA], mmin = L[P_MMIN], mmax = L[P_MMAX], lam = L[P_LAM];
+    const double mu = L[P_MPP], sig = L[P_SIGPP], ac = L[P_ACHI], bc = L[P_BCHI], xit = L[P_XIT], sigt = L[P_SIGT];
+    const double p = p_theta_znorm(th, n_dims, L, znorm);
+    if (p == 0.0) return 0.0;
+    /* primary mass */
+    const double pl = powerlaw_pdf(m1, alpha, mmin, mmax);
+    const double pla = powerlaw_pdf(mmin, alpha, mmin, mmax), plb = powerlaw_pdf(mmax, alpha, mmin, mmax);
+    double dlnC_alpha;
+    if (alpha == 1.0) {
+        dlnC_alpha = 0.5 * (log(mmin) + log(mmax));
+    } else {
+        const double s = 1.0 - alpha, bs = pow(mmax, s), as = pow(mmin, s);
+        dlnC_alpha = -1.0 / s + (bs * log(mmax) - as * log(mmin)) / (bs - as);
+    }
+    const double nt = truncnorm_pdf(m1, mu, sig, mmin, mmax);
+    const double nta = truncnorm_pdf(mmin, mu, sig, mmin, mmax), ntb = truncnorm_pdf(mmax, mu, sig, mmin, mmax);
+    const double ap = (mmin - mu) / sig, bp = (mmax - mu) / sig;
+    const double pm = (1.0 - lam) * pl + lam * nt;
+    const double fpl = (1.0 - lam) * pl / pm, fnt = lam * nt / pm; /* shares of the two parts */
+    g[P_ALPHA] += fpl * (-log(m1) + dlnC_alpha);
+    g[P_LAM] += (nt - pl) / pm;
+    g[P_MPP] += fnt * ((m1 - mu) / (sig * sig) + ntb - nta);
+    g[P_SIGPP] += fnt * (-1.0 / sig + (m1 - mu) * (m1 - mu) / (sig * sig * sig) + bp * ntb - ap * nta);
+    g[P_MMIN] += fpl * pla + fnt * nta;
+    g[P_MMAX] += -fpl * plb - fnt * ntb;
+    /* mass ratio */
+    const double lr = log1p((mmin - m1) / m1); /* ln(mmin/m1) */
+    if (beta == -1.0) {
+        g[P_BETA] += log(q) - 0.5 * lr;
+        g[P_MMIN] += 1.0 / (mmin * -lr);
+    } else {
+        const double rho = exp((1.0 + beta) * lr);
+        const double one_minus = -expm1((1.0 + beta) * lr);
+        g[P_BETA] += 1.0 / (1.0 + beta) + log(q) + rho * lr / one_minus;
+        g[P_MMIN] += (1.0 + beta) * rho / (mmin * one_minus);
+    }
+    /* spin magnitudes */
+    const double psab = pop_oracle_digamma(ac + bc);
+    g[P_ACHI] += log(a1) + log(a2) - 2.0 * pop_oracle_digamma(ac) + 2.0 * psab;
+    g[P_BCHI] += log(1.0 - a1) + log(1.0 - a2) - 2.0 * pop_oracle_digamma(bc) + 2.0 * psab;
+    /* tilts */
+    const double zt = 0.5 * erf(SQRT2 / sigt);
+    const double G1 = std_normal_pdf((c1 - 1.0) / sigt) / (sigt * zt), G2 = std_normal_pdf((c2 - 1.0) / sigt) / (sigt * zt);
+    const double T = (1.0 - xit) / 4.0 + xit * G1 * G2;
+    const double dc = (c1 - 1.0) * (c1 - 1.0) + (c2 - 1.0) * (c2 - 1.0);
+    g[P_XIT] += (G1 * G2 - 0.25) / T;
+    g[P_SIGT] += xit * G1 * G2 *
+                 (-2.0 / sigt + dc / (sigt * sigt * sigt) + 4.0 * std_normal_pdf(2.0 / sigt) / (sigt * sigt * zt)) / T;
+    /* redshift */
+    if (n_dims == 7) g[P_KAPPA] += log1p(th[6]) - dznorm / znorm;
+    return p;
+}
+
+static double z_norm_dkappa(double kappa);
+
+/* p(theta | Lambda) and its score g[n_params] (0 outside the support). */
+double pop_oracle_score(const double* th, int n_dims, const double* L, int n_params, double* g)
+{
+    double gg[12];
+    const double zn = n_dims == 7 ? pop_oracle_z_norm(L[P_KAPPA]) : 1.0;
+    const double dz = n_dims == 7 ? z_norm_dkappa(L[P_KAPPA]) : 0.0;
+    const double p = score_theta(th, n_dims, L, zn, dz, gg);
+    for (int k = 0; k < n_params; ++k) g[k] = gg[k];
+    return p;
+}
+
+/* d I / d kappa for the 1024-node trapezoid I of pop_oracle_z_norm. */
+static double z_norm_dkappa(double kappa)
+{
+    const int n = 1024;
+    double h = 2.0 / (n - 1), s = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double z = 2.0 * k / (n - 1);
+        double f = pow(1.0 + z, kappa - 1.0) * log1p(z) * z * z;
+        s += (k == 0 || k == n - 1) ? 0.5 * f : f;
+    }
+    return s * h;
+}
+
+/*
+ * ln L and its gradient d ln L / d Lambda (n_params components, the C-ABI
+ * order) for K Lambda points; derived from Eq. (poplike) with the -N ln xi
+ * term (the paper does not differentiate it):
+ *   d ln L = sum_i (sum_j w_ij g_ij) / S_i - N (sum_k w_k g_k) / (sum_k w_k),
+ * g the score of p(theta|Lambda) at each sample.  Where ln L = -inf (invalid
+ * Lambda, an empty event, xi = 0) the gradient is 0.  Outputs as
+ * pop_oracle_loglik plus out_grad[K * n_params].
+ */
+int pop_oracle_loglik_grad(int64_t n_events, const int64_t* offsets, int n_dims, const double* theta,
+                           const double* prior, int64_t n_found, int64_t n_draw, const double* inj_theta,
+                           const double* p_draw, int64_t K, int n_params, const double* lambda, int nthreads,
+                           double* out_lnL, double* out_grad, uint32_t* out_flags)
+{
+    if (!out_grad) return -1;
+    int rc = pop_oracle_loglik(n_events, offsets, n_dims, theta, prior, n_found, n_draw, inj_theta, p_draw, K,
+                               n_params, lambda, nthreads, out_lnL, NULL, NULL, out_flags);
+    if (rc != 0) return rc;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t k = 0; k < K; ++k) {
+        const double* L = lambda + k * n_params;
+        double* G = out_grad + k * n_params;
+        for (int p = 0; p < n_params; ++p) G[p] = 0.0;
+        if (!isfinite(out_lnL[k])) continue;
+        const double znorm = n_dims == 7 ? pop_oracle_z_norm(L[P_KAPPA]) : 1.0;
+        const double dznorm = n_dims == 7 ? z_norm_dkappa(L[P_KAPPA]) : 0.0;
+        double g[12], sw = 0.0, swg[12] = {0};
+        for (int64_t j = 0; j < n_found; ++j) {
+            const double w = score_theta(inj_theta + j * n_dims, n_dims, L, znorm, dznorm, g) / p_draw[j];
+            sw += w;
+            for (int p = 0; p < n_params; ++p) swg[p] += w * g[p];
+        }
+        for (int p = 0; p < n_params; ++p) G[p] = -(double)n_events * swg[p] / sw;
+        for (int64_t i = 0; i < n_events; ++i) {
+            double s = 0.0, sg[12] = {0};
+            for (int64_t j = offsets[i]; j < offsets[i + 1]; ++j) {
+                const double w = score_theta(theta + j * n_dims, n_dims, L, znorm, dznorm, g) / prior[j];
+                s += w;
+                for (int p = 0; p < n_params; ++p) sg[p] += w * g[p];
+            }
+            for (int p = 0; p < n_params; ++p) G[p] += sg[p] / s;
+        }
     }
     return 0;
 }

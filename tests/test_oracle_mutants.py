@@ -1,7 +1,8 @@
 """The oracle's pins bite: each plausible mistake, planted in a copy of the oracle
 (on the CPU), makes the pins of its part fail (tests/test_oracle_pins.py for the
 population likelihood, test_gridvt_pins.py for the grid selection term,
-test_cbc_pins.py for the single-event CBC likelihood)."""
+test_cbc_pins.py for the single-event CBC likelihood, test_grad_pins.py for the
+gradient)."""
 import os
 import subprocess
 import sys
@@ -43,9 +44,16 @@ CBC_MUTANTS = {
     "cbc detector index": ("const double S = psd[(int64_t)i * M + j];", "const double S = psd[(int64_t)j * n_det + i];"),
     "cbc cross polarisation": ("Fc * hc[2 * j]", "Fp * hc[2 * j]"),
 }
+GRAD_MUTANTS = {
+    "grad power-law normalisation": ("g[P_ALPHA] += fpl * (-log(m1) + dlnC_alpha);", "g[P_ALPHA] += fpl * (-log(m1));"),
+    "grad upper edge sign": ("g[P_MMAX] += -fpl * plb - fnt * ntb;", "g[P_MMAX] += fpl * plb - fnt * ntb;"),
+    "grad spin digamma factor": ("- 2.0 * pop_oracle_digamma(ac) + 2.0 * psab;", "- pop_oracle_digamma(ac) + psab;"),
+    "grad tilt truncation": ("4.0 * std_normal_pdf(2.0 / sigt)", "2.0 * std_normal_pdf(2.0 / sigt)"),
+    "grad selection term": ("G[p] = -(double)n_events * swg[p] / sw;", "G[p] = -swg[p] / sw;"),
+}
 PIN_FILES = {**{k: "test_oracle_pins.py" for k in MUTANTS}, **{k: "test_gridvt_pins.py" for k in GRID_MUTANTS},
-             **{k: "test_cbc_pins.py" for k in CBC_MUTANTS}}
-ALL = {**MUTANTS, **GRID_MUTANTS, **CBC_MUTANTS}
+             **{k: "test_cbc_pins.py" for k in CBC_MUTANTS}, **{k: "test_grad_pins.py" for k in GRAD_MUTANTS}}
+ALL = {**MUTANTS, **GRID_MUTANTS, **CBC_MUTANTS, **GRAD_MUTANTS}
 
 
 @pytest.mark.parametrize("name", sorted(ALL))
