@@ -104,7 +104,7 @@ def parse():
     p.add_argument("--events", type=int, default=1000, help="events (a smaller catalog for profiling captures)")
     p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
     p.add_argument("--mode", default="both", choices=["both", "f64", "f32"])
-    p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc", "grad"],
                    help="c2: the metric's catalog workload (default); c4: ragged CSR + redshift, uneven batches")
     return p.parse_args()
 
@@ -249,6 +249,39 @@ def grid_form(B, like, lam, timed, args, world):
     return out
 
 
+# FP64-pipe operations per in-support (sample, Lambda) pair of the gradient kernel: the weight
+# split into its power-law and peak parts (about 67: 4 exp, 1 expm1 and 1 reciprocal with their
+# FMAs), the 11-12 score terms (about 35) and the 14 sums (14).
+FP64_OPS_PER_GRAD_PAIR = 116
+
+
+def grad_form(B, like, lam, args, world, n_pairs):
+    """ln L and its gradient with respect to Lambda (pop_loglik_grad, FP64) on the same workload
+    and K; the gradient kernel gets its own roofline (FP64 pipe)."""
+    K = len(lam)
+    for _ in range(args.warmup):
+        B.pop_loglik_grad(like.ctx, lam)
+    barrier(world)
+    ws, ts = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        B.pop_loglik_grad(like.ctx, lam)
+        w, t = B.pop_last_kernel_ms(like.ctx)
+        ws.append(w)
+        ts.append(t)
+    wall = max_over_ranks(time.perf_counter() - t0, world)
+    w, t = max_over_ranks(statistics.median(ws), world), max_over_ranks(statistics.median(ts), world)
+    peak = FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    ach = n_pairs * FP64_OPS_PER_GRAD_PAIR / (w * 1e-3)
+    return {"value": world * K / (t * 1e-3), "unit": "evals/s (ln L + gradient)", "ms_per_call": t,
+            "weight_ms": w, "dtype": "f64",
+            "e2e": {"value": world * K * args.steps / wall, "unit": "evals/s", "h2d_bytes_per_step": int(lam.nbytes),
+                    "d2h_bytes_per_step": int(K * 8 * (lam.shape[1] + 1) + 4 * K)},
+            "roofline": {"bound": "alu", "kernel": "grad_weight_kernel", "achieved": ach / 1e12, "peak": peak / 1e12,
+                         "unit": "Top/s (FP64 pipe)", "frac": ach / peak, "ops_per_in_support_pair":
+                             FP64_OPS_PER_GRAD_PAIR, "traffic": None}}
+
+
 # FMA-pipe operations per (bin, parameter row, detector) unit of the CBC sums kernel:
 # two complex multiply-adds (P e, Q e: 8) and the time-shift recurrence e <- e w (4).
 CBC_FMA_PER_UNIT = 12
@@ -367,6 +400,27 @@ def run_cbc(args, B, rank, local, world):
         print(json.dumps(line, default=_jsonable), flush=True)
 
 
+def run_grad(args, B, rank, local, world):
+    """ln L and its gradient alone, on the catalog workload (--events, --K as for the headline)."""
+    import torch
+    cat, inj, _ = synth.make_workload(WORKLOAD, scale=args.events / 1000.0)
+    lam = synth.make_lambdas(args.K, 11, seed=synth.seed_for(2, 2) + 7919 * rank)
+    like = B.Likelihood(local, torch.cuda.current_stream(local)).load(cat, inj, storage=B.POP_STORE_F64)
+    n_pairs = in_support_pairs(cat.theta, lam) + in_support_pairs(inj.theta, lam)
+    with Clocks(local) as clk:
+        f = grad_form(B, like, lam, args, world, n_pairs)
+    like.close()
+    line = {"metric": "ln L(Lambda) + gradient evals/s", "value": f["value"], "unit": f["unit"], "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms_per_call"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.events == 1000 else f"{WORKLOAD}_events{args.events}",
+                       "events": cat.n_events, "n_found": int(inj.n_found), "K": args.K,
+                       "parallelism": f"replicas{world}"},
+            "roofline": f["roofline"], "e2e": f["e2e"], "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+
+
 def run_ragged(args, B, rank, local, world):
     """Batching form: 2000 events with S_i ~ U{500..16000} in CSR (about 1.65e7 samples), redshift
     on (12 parameters), 1.8e7 injection draws, FP32 weights.  Uneven Lambda batches
@@ -479,6 +533,9 @@ def main():
     if args.workload == "cbc":
         run_cbc(args, B, rank, local, world)
         return
+    if args.workload == "grad":
+        run_grad(args, B, rank, local, world)
+        return
 
     scale = args.events / 1000.0
     cat, inj, _ = synth.make_workload(WORKLOAD, scale=scale)
@@ -575,6 +632,7 @@ def main():
         line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
         line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
         line["forms"]["cbc_likelihood"] = cbc_form(B, like, args, world, rank)
+        line["forms"]["grad_f64"] = grad_form(B, like, lam, args, world, n_ev_pairs + n_inj_pairs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
     like.close()

@@ -154,6 +154,18 @@ int pop_loglik(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int 
 int pop_loglik_parts(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, int mode, double* out_events,
                      double* out_sum_w, double* out_sum_w2, uint32_t* out_flags, int mem);
 
+/* ln L and its gradient with respect to Lambda, for gradient-based samplers (not
+ * in the paper; derived from the likelihood above):
+ *   d ln L / d Lambda_p = sum_i (sum_j w_ij g_ij,p) / S_i - N (sum_k w_k g_k,p) / (sum_k w_k),
+ * g the score d ln p(theta|Lambda) / d Lambda of the population density (its
+ * support's edges, where the density jumps, contribute nothing).  FP64, with the
+ * injection selection term; lambda[K * n_params] and the outputs out_lnL[K],
+ * out_grad[K * n_params] (row-major, the Lambda order) and out_flags[K] (may be
+ * NULL) in `mem`.  Where ln L = -inf the gradient is 0.  Synchronous for host
+ * outputs. */
+int pop_loglik_grad(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, double* out_lnL, double* out_grad,
+                    uint32_t* out_flags, int mem);
+
 /* ------------------------------------------------------------------ grid selection term
  * The paper evaluates VT on a regular grid with GPU acceleration, limited to a
  * low-dimensional space without spin effects (Sec. "Population acceleration").
@@ -257,8 +269,9 @@ int pop_autotune(pop_ctx* ctx, int mode, int64_t K, const char* cache_path);
 /* Use CUDA-graph replay for pop_loglik (1, default) or direct launches (0). */
 int pop_set_graphs(pop_ctx* ctx, int enable);
 
-/* Duration in milliseconds of the weight kernel of the last pop_loglik
- * (CUDA events around it on the context stream; waits for that call). */
+/* Duration in milliseconds of the weight kernel of the last pop_loglik or
+ * pop_loglik_grad, and of the whole call on the device (CUDA events around
+ * them on the context stream; waits for that call). */
 int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
 
 /* Diagnostic: evaluate the FP64 weight kernel's own device functions on x[n]

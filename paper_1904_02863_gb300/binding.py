@@ -34,7 +34,7 @@ EXPORTS = (
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
     "pop_load_vt_grid", "pop_set_xi_source", "pop_xi_grid", "pop_xi_grid_last_ms", "pop_loglik_parts",
-    "pop_cbc_load", "pop_cbc_loglik", "pop_cbc_last_ms",
+    "pop_cbc_load", "pop_cbc_loglik", "pop_cbc_last_ms", "pop_loglik_grad",
 )
 MLP_N_PARAMS = 201218
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "pop_load_vt_grid": (i32, [vp, i32, vp, i32, vp, vp, i32]),
         "pop_loglik_parts": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp, i32]),
         "pop_cbc_load": (i32, [vp, i32, i64, d, d, vp, vp, vp, vp, i32]),
+        "pop_loglik_grad": (i32, [vp, i64, i32, vp, vp, vp, vp, i32]),
         "pop_cbc_loglik": (i32, [vp, i64, i32, vp, i32, vp, vp, i32]),
         "pop_cbc_last_ms": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d)]),
         "pop_set_xi_source": (i32, [vp, i32]),
@@ -212,6 +213,16 @@ def pop_loglik(ctx, lambdas, mode=POP_MODE_F64, out=None):
         ptrs = [ctypes.c_void_p(r.data_ptr()) for r in res]
     _check(ctx, load_library().pop_loglik(ctx, K, P, lp, int(mode), *ptrs, mem))
     return res
+
+
+def pop_loglik_grad(ctx, lambdas):
+    """(ln L, d ln L / d Lambda [K, n_params], flags) in FP64 (host arrays; synchronous)."""
+    lam = np.ascontiguousarray(np.atleast_2d(lambdas), dtype=np.float64)
+    K, P = lam.shape
+    lnL, grad, fl = np.empty(K), np.empty((K, P)), np.empty(K, np.uint32)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(ctx, load_library().pop_loglik_grad(ctx, K, P, vp(lam), vp(lnL), vp(grad), vp(fl), POP_MEM_HOST))
+    return lnL, grad, fl
 
 
 def pop_loglik_parts(ctx, lambdas, mode=POP_MODE_F64):

@@ -89,6 +89,9 @@ struct pop_ctx {
     int n_params_cap = 12;
     DevBuf d_lambda, d_c64, d_c32, d_part, d_part2, d_lnL, d_lnxi, d_neff, d_flags, d_K;
     DevBuf d_parts;          // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2 (pop_loglik_parts)
+    DevBuf d_lamg, d_gpart, d_grad;  // gradient: per-Lambda constants, [K][n_chunks][13] sums, [K][12]
+    int64_t grad_cap = 0;
+    int32_t grad_chunks = -1;
     int32_t part_chunks = -1, part_inj = -1;
 
     Tiling tiling[2] = {{8, 256, 0}, {16, 256, 0}};
@@ -775,6 +778,68 @@ int pop_loglik_parts(pop_ctx* c, int64_t K, int n_params, const double* lambda, 
             CK(cudaMemcpyAsync(out_flags, fl, sizeof(uint32_t) * K, cudaMemcpyDeviceToHost, c->stream), "copy flags");
         CK(cudaStreamSynchronize(c->stream), "sync");
     }
+    return POP_OK;
+}
+
+int pop_loglik_grad(pop_ctx* c, int64_t K, int n_params, const double* lambda, double* out_lnL, double* out_grad,
+                    uint32_t* out_flags, int mem)
+{
+    if (!c) return POP_EINVAL;
+    if (c->xi_source != POP_XI_INJECTIONS)
+        return fail(c, POP_EINVAL, "pop_loglik_grad: needs the injection selection term");
+    if (c->ev.n == 0 || c->inj.n == 0) return fail(c, POP_ESTATE, "pop_loglik_grad: load events and injections first");
+    if (!(c->ev.storage & POP_STORE_F64) || !(c->inj.storage & POP_STORE_F64))
+        return fail(c, POP_ESTATE, "pop_loglik_grad: needs FP64 storage");
+    if (n_params != 11 + (c->ev.n_dims == 7))
+        return fail(c, POP_EINVAL, "pop_loglik_grad: n_params must be 11 (12 with redshift samples)");
+    if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_loglik_grad: bad mem");
+    if (K < 0 || K > (1LL << 24)) return fail(c, POP_EINVAL, "pop_loglik_grad: K out of range");
+    if (K == 0) return POP_OK;
+    if (!lambda || !out_lnL || !out_grad) return fail(c, POP_EINVAL, "pop_loglik_grad: NULL pointer");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    int rc = build_chunks(c);
+    if (rc != POP_OK) return rc;
+    rc = ensure_scratch(c, K);
+    if (rc != POP_OK) return rc;
+    if (K > c->grad_cap || c->grad_chunks != c->n_chunks) {
+        const int64_t cap = std::max<int64_t>(K, c->grad_cap);
+        DevBuf lg, gp, gr;
+        CK(lg.alloc(lam_grad_bytes() * cap), "cudaMalloc(grad constants)");
+        CK(gp.alloc(sizeof(double) * 13 * cap * c->n_chunks), "cudaMalloc(grad partials)");
+        CK(gr.alloc(sizeof(double) * 12 * cap), "cudaMalloc(grad)");
+        c->d_lamg.swap(lg);
+        c->d_gpart.swap(gp);
+        c->d_grad.swap(gr);
+        c->grad_cap = cap;
+        c->grad_chunks = c->n_chunks;
+    }
+    CK(cudaMemcpyAsync(c->d_lambda.p, lambda, sizeof(double) * K * n_params, in_kind(mem), c->stream), "copy lambda");
+    set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
+    CK(cudaGetLastError(), "set K");
+    CK(cudaEventRecord(c->ev_t0, c->stream), "event");
+    CK(launch_grad_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), K, n_params, c->d_lamg.p, c->stream),
+       "grad prologue");
+    WorkDesc wd{c->d_chunks.as<Chunk>(), c->n_chunks, c->n_ev_chunks, c->ev.n_dims == 7};
+    FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
+    CK(cudaEventRecord(c->ev_w0, c->stream), "event");
+    CK(launch_grad_weight(grad_grid_size(c->sm_count), e, j, wd, c->d_lamg.p, c->d_K.as<int64_t>(), n_params,
+                          c->d_gpart.as<double>(), c->d_part2.as<double>(), c->d_exptab.as<double2>(), c->expc,
+                          c->stream),
+       "grad weight");
+    CK(cudaEventRecord(c->ev_w1, c->stream), "event");
+    CK(launch_grad_finalise(c->d_gpart.as<double>(), c->d_part2.as<double>(), c->d_ecb.as<int32_t>(),
+                            c->d_offsets.as<int64_t>(), (int64_t)c->h_offsets.size() - 1, c->n_chunks, c->n_ev_chunks,
+                            c->n_draw, c->d_lamg.p, c->d_K.as<int64_t>(), K, n_params, c->d_lnL.as<double>(),
+                            c->d_lnxi.as<double>(), c->d_neff.as<double>(), c->d_flags.as<uint32_t>(),
+                            c->d_grad.as<double>(), c->stream),
+       "grad finalise");
+    CK(cudaEventRecord(c->ev_t1, c->stream), "event");
+    c->timed = true;
+    CK(cudaMemcpyAsync(out_lnL, c->d_lnL.p, sizeof(double) * K, out_kind(mem), c->stream), "copy lnL");
+    CK(cudaMemcpyAsync(out_grad, c->d_grad.p, sizeof(double) * K * n_params, out_kind(mem), c->stream), "copy grad");
+    if (out_flags)
+        CK(cudaMemcpyAsync(out_flags, c->d_flags.p, sizeof(uint32_t) * K, out_kind(mem), c->stream), "copy flags");
+    if (mem == POP_MEM_HOST) CK(cudaStreamSynchronize(c->stream), "sync");
     return POP_OK;
 }
 

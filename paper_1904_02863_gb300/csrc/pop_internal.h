@@ -135,6 +135,21 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
                             const double* grid_xi = nullptr,  // xi per Lambda from the grid (N_eff = +inf)
                             double* parts = nullptr);         // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2
 
+// Gradient of ln L (pop_grad.cu): per-Lambda constants (lam_grad_bytes() each), the
+// weight-and-derivative sums per (chunk, Lambda) ([K][n_chunks][13] doubles, plus the
+// injection sum w^2 in part2 as for ln L), and the finalise with grad[K][n_params].
+size_t lam_grad_bytes();
+cudaError_t launch_grad_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params, void* lam_g,
+                                 cudaStream_t s);
+cudaError_t launch_grad_weight(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const void* lam_g, const int64_t* dK,
+                               int n_params, double* part, double* part2, const double2* exptab, ExpConsts kc,
+                               cudaStream_t s);
+cudaError_t launch_grad_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,
+                                 int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
+                                 const void* lam_g, const int64_t* dK, int64_t K_cap, int n_params, double* lnL,
+                                 double* lnxi, double* neff, uint32_t* flags, double* grad, cudaStream_t s);
+int grad_grid_size(int sm_count);
+
 // Kernel function of a tiling (nullptr when that instantiation does not exist).
 const void* weight_f64_fn(const Tiling& t, bool has_z);
 const void* weight_f32_fn(const Tiling& t, bool has_z);
