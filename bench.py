@@ -250,9 +250,10 @@ def grid_form(B, like, lam, timed, args, world):
 
 
 # FP64-pipe operations per in-support (sample, Lambda) pair of the gradient kernel: the weight
-# split into its power-law and peak parts (about 67: 4 exp, 1 expm1 and 1 reciprocal with their
-# FMAs), the 11-12 score terms (about 35) and the 14 sums (14).
-FP64_OPS_PER_GRAD_PAIR = 116
+# split into its power-law and peak parts (4 exp, 1 expm1, 1 reciprocal and their FMAs), the
+# 11-12 score terms and the 14 sums, with the loop-invariant terms hoisted: 108, the DFMA + DADD
+# + DMUL count per in-support pair of the ncu capture in profiles/grad_weight_catalog100x4096_K16_full.md.
+FP64_OPS_PER_GRAD_PAIR = 108
 
 
 def grad_form(B, like, lam, args, world, n_pairs):
