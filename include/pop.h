@@ -251,10 +251,12 @@ int pop_cbc_loglik(pop_ctx* ctx, int64_t K, int n_params, const double* theta, i
  * sums kernel, and the whole call on the device. */
 int pop_cbc_last_ms(pop_ctx* ctx, double* sum_ms, double* total_ms);
 
-/* Tiling of the persistent weight kernel for `mode` (POP_MODE_F64 or
- * POP_MODE_F32): Lambda points per work item (1, 2, 4, 8, 16 or 32), threads
- * per block (128, 256 or 512) and resident blocks per SM (0 = occupancy
- * maximum).  Takes effect at the next pop_loglik. */
+/* Tiling of the persistent weight kernel for `mode`, with resident blocks per
+ * SM (0 = occupancy maximum).  POP_MODE_F64: Lambda points per work item (1, 2,
+ * 4, 8 or 16) and threads per block (128, 256 or 512).  POP_MODE_F32: one Lambda
+ * per thread, so lambda_tile == block_threads, 32, 64, 128 or 256; its results
+ * do not depend on the tiling.  POP_EINVAL for any other combination.  Takes
+ * effect at the next pop_loglik. */
 int pop_set_tiling(pop_ctx* ctx, int mode, int lambda_tile, int block_threads, int blocks_per_sm);
 
 /* Read back the tiling in use for `mode` (any pointer may be NULL). */

@@ -8,6 +8,7 @@
 #include <fstream>
 #include <sstream>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "pop.h"
@@ -94,10 +95,11 @@ struct pop_ctx {
     int32_t grad_chunks = -1;
     int32_t part_chunks = -1, part_inj = -1;
 
-    Tiling tiling[2] = {{8, 256, 0}, {16, 256, 0}};
+    Tiling tiling[2] = {{8, 256, 0}, {128, 128, 0}};
     bool use_graphs = true;
     Graph graph[3];  // per mode: F64, F32, F32 + surrogate
     DevBuf d_need, d_slnxi, d_slnneff;  // surrogate mode: Monte Carlo mask, ln xi, ln N_eff per Lambda
+    DevBuf d_order, d_nmc;   // FP32 kernel: lane order of the Lambda [2][K_cap], Lambda needing the injections
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts expc{};
@@ -139,16 +141,27 @@ cudaMemcpyKind out_kind(int mem) { return mem == POP_MEM_HOST ? cudaMemcpyDevice
 __global__ void set_k_kernel(int64_t* dK, int64_t K) { *dK = K; }
 
 // Load-time order of the samples: within every segment [seg[s], seg[s+1]) the
-// samples are sorted by m2 = q m1.  The lower support edge is exactly
-// m2 >= mmin, so for any Lambda the samples below it are contiguous and whole
-// warps of them skip the weight arithmetic.  Sums over a segment do not
-// depend on the order (beyond rounding).
-std::vector<int64_t> support_order(const double* theta, int64_t n, int n_dims, const std::vector<int64_t>& seg)
+// samples are sorted by (m2, m1) with m2 = fl64(q m1), compared lexicographically,
+// on the values the pack kernel stores (FP32-rounded coordinates for FP32 storage;
+// m2 = m1 = 0 for a sample outside the Lambda-independent support).  The lower
+// support edge, m1 > mmin and m2 >= mmin, is then a suffix of every segment (m2 <= m1
+// for q <= 1): the FP64 kernel's warps below it skip the arithmetic and the FP32
+// kernel finds its first index by binary search.  Sums over a segment do not depend
+// on the order (beyond rounding).
+std::vector<int64_t> support_order(const double* theta, int64_t n, int n_dims, const std::vector<int64_t>& seg,
+                                   bool round_f32)
 {
-    std::vector<double> key(n);
+    std::vector<std::pair<double, double>> key(n);
     for (int64_t j = 0; j < n; ++j) {
-        const double m2 = theta[j * n_dims + 1] * theta[j * n_dims];
-        key[j] = std::isnan(m2) ? INFINITY : m2;  // malformed rows are rejected later by the pack kernel
+        const double* th = theta + j * n_dims;
+        double v[7];
+        for (int d = 0; d < n_dims; ++d) v[d] = round_f32 ? (double)(float)th[d] : th[d];
+        const double z = n_dims == 7 ? v[6] : 1.0;
+        const bool live = v[0] > 0.0 && v[1] > 0.0 && v[1] <= 1.0 && v[2] >= 0.0 && v[2] <= 1.0 && v[3] >= 0.0 &&
+                          v[3] <= 1.0 && v[4] >= -1.0 && v[4] <= 1.0 && v[5] >= -1.0 && v[5] <= 1.0 && z >= 0.0 &&
+                          z <= 2.0 && std::isfinite(v[0]);
+        // Rows with a non-finite coordinate are rejected by the pack kernel; any key will do for them.
+        key[j] = live ? std::make_pair(v[1] * v[0], v[0]) : std::make_pair(0.0, 0.0);
     }
     std::vector<int64_t> perm(n);
     for (int64_t j = 0; j < n; ++j) perm[j] = j;
@@ -168,7 +181,7 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     out.stride = round_up(std::max<int64_t>(n, 1), ALIGN_ELEMS);
     const double* th = theta;
     const double* pr = prior;
-    DevBuf tmp_th, tmp_pr, bad, dperm;
+    DevBuf tmp_th, tmp_pr, bad, dperm, dperm32;
     {
         std::vector<double> host_th;
         const double* hth = theta;
@@ -179,11 +192,15 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
             CK(cudaStreamSynchronize(c->stream), "sync");
             hth = host_th.data();
         }
-        const std::vector<int64_t> perm = support_order(hth, n, n_dims, seg);
-        CK(dperm.alloc(sizeof(int64_t) * std::max<int64_t>(n, 1)), "cudaMalloc(order)");
-        CK(cudaMemcpyAsync(dperm.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream),
-           "copy order");
-        CK(cudaStreamSynchronize(c->stream), "sync");
+        for (int r = 0; r < 2; ++r) {
+            if (!(storage & (r == 0 ? POP_STORE_F64 : POP_STORE_F32))) continue;
+            const std::vector<int64_t> perm = support_order(hth, n, n_dims, seg, r == 1);
+            DevBuf& d = r == 0 ? dperm : dperm32;
+            CK(d.alloc(sizeof(int64_t) * std::max<int64_t>(n, 1)), "cudaMalloc(order)");
+            CK(cudaMemcpyAsync(d.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream),
+               "copy order");
+            CK(cudaStreamSynchronize(c->stream), "sync");
+        }
     }
     if (mem == POP_MEM_HOST) {
         CK(tmp_th.alloc(sizeof(double) * n * n_dims), "cudaMalloc(theta staging)");
@@ -205,7 +222,7 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     if (storage & POP_STORE_F32) {
         CK(out.f32.alloc(sizeof(float) * F_COUNT32 * out.stride), "cudaMalloc(f32 features)");
         CK(out.m2.alloc(sizeof(double) * out.stride), "cudaMalloc(m2)");
-        CK(launch_pack_f32(th, pr, dperm.as<int64_t>(), n, n_dims, out.f32.as<float>(), out.m2.as<double>(),
+        CK(launch_pack_f32(th, pr, dperm32.as<int64_t>(), n, n_dims, out.f32.as<float>(), out.m2.as<double>(),
                            out.stride,
                            bad.as<unsigned long long>(), c->stream), "pack_f32");
     }
@@ -271,11 +288,15 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     CK(neff.alloc(sizeof(double) * cap), "cudaMalloc(neff)");
     CK(flags.alloc(sizeof(uint32_t) * cap), "cudaMalloc(flags)");
     CK(dK.alloc(sizeof(int64_t)), "cudaMalloc(K)");
-    DevBuf need, slnxi, slnneff;
+    DevBuf need, slnxi, slnneff, order, nmc;
     CK(need.alloc(cap), "cudaMalloc(need)");
+    CK(order.alloc(sizeof(int32_t) * 2 * cap), "cudaMalloc(order)");
+    CK(nmc.alloc(sizeof(int32_t)), "cudaMalloc(n_mc)");
     CK(slnxi.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnxi)");
     CK(slnneff.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnneff)");
     c->d_need.swap(need);
+    c->d_order.swap(order);
+    c->d_nmc.swap(nmc);
     c->d_slnxi.swap(slnxi);
     c->d_slnneff.swap(slnneff);
     if (c->d_lambda.p)  // keep the last Lambda batch (the autotuner reuses it)
@@ -343,8 +364,11 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     } else {
         FeatF32 e{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
         FeatF32 j{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
-        CK(launch_weight_f32(c->tiling[1], grid, e, j, wd, c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(),
-                             c->d_part.as<double>(), c->d_part2.as<double>(), sx, c->stream), "weight_f32");
+        CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), sx.need_mc, c->k_cap,
+                            c->d_order.as<int32_t>(), c->d_nmc.as<int32_t>(), c->stream), "lambda order");
+        CK(launch_weight_f32(c->tiling[1], grid, e, j, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
+                             c->d_nmc.as<int32_t>(), c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(),
+                             c->d_part2.as<double>(), c->stream), "weight_f32");
     }
     CK(cudaEventRecordWithFlags(c->ev_w1, c->stream, rec), "event");
     if (use_grid)
@@ -1065,9 +1089,10 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
             return POP_OK;
         }
     }
+    // FP64: Lambda per item x threads per block.  FP32: one Lambda per thread, 32 to 256 per block.
     const int tiles64[] = {1, 2, 4, 8, 16};
-    const int tiles32[] = {2, 4, 8, 16, 32};
-    const int threads[] = {128, 256, 512};
+    const int threads64[] = {128, 256, 512};
+    const int threads32[] = {32, 64, 128, 256};
     const Tiling saved = c->tiling[mode];
     const int n_params = c->last_params;
     int rc = build_chunks(c);
@@ -1078,12 +1103,17 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
     CK(cudaGetLastError(), "set K");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
                        c->d_c32.as<LamF32>(), c->stream), "prologue");
+    if (mode == POP_MODE_F32)
+        CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), nullptr, c->k_cap, c->d_order.as<int32_t>(),
+                            c->d_nmc.as<int32_t>(), c->stream), "lambda order");
     float best_ms = 1e30f;
     Tiling best = saved;
     WorkDesc wd{c->d_chunks.as<Chunk>(), c->n_chunks, c->n_ev_chunks, c->ev.n_dims == 7};
-    for (int ti = 0; ti < 5; ++ti) {
-        for (int nt : threads) {
-            Tiling t{mode == POP_MODE_F64 ? tiles64[ti] : tiles32[ti], nt, 0};
+    const int n_cand = mode == POP_MODE_F64 ? 15 : 4;
+    for (int ci = 0; ci < n_cand; ++ci) {
+        {
+            const Tiling t = mode == POP_MODE_F64 ? Tiling{tiles64[ci / 3], threads64[ci % 3], 0}
+                                                  : Tiling{threads32[ci], threads32[ci], 0};
             c->tiling[mode] = t;
             const int grid = grid_size(c, mode);
             float ms[3];
@@ -1098,9 +1128,9 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
                 } else {
                     FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
                     FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
-                    e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(),
-                                          c->d_part.as<double>(), c->d_part2.as<double>(),
-                                          SurrogateXi{nullptr, nullptr, nullptr}, c->stream);
+                    e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
+                                          c->d_nmc.as<int32_t>(), c->k_cap, c->d_K.as<int64_t>(),
+                                          c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
                 }
                 if (e != cudaSuccess) {
                     c->tiling[mode] = saved;

@@ -122,11 +122,16 @@ struct SurrogateXi {
     const double* lnxi;
     const double* neff;
 };
-// With sx.need_mc set, injection work items whose whole Lambda tile is covered by the surrogate
-// are skipped.
+// FP32 weight kernel: one Lambda per thread, lambda_tile == block_threads Lambda per work item.
+// order[0, K) and order[K_cap, K_cap + *n_mc) are the Lambda of the event and injection items in
+// lane order (launch_lam_order); only the first *n_mc of the injection order get injection items.
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
-                              const LamF32* lam, const int64_t* dK, double* part, double* part2,
-                              SurrogateXi sx, cudaStream_t s);
+                              const LamF32* lam, const int32_t* order, const int32_t* n_mc, int64_t K_cap,
+                              const int64_t* dK, double* part, double* part2, cudaStream_t s);
+// Lane order of the FP32 weight kernel: Lambda by mmin; for the injection items the Lambda with
+// need_mc[k] != 0 first (all K when need_mc is NULL), their number in *n_mc.  order[2 K_cap].
+cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t* need_mc, int64_t K_cap,
+                             int32_t* order, int32_t* n_mc, cudaStream_t s);
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ev_chunk_begin,
                             const int64_t* offsets, int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks,
                             int64_t n_draw, const LamF64* lam, const int64_t* dK, int64_t K_cap,

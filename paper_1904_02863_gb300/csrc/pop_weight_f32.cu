@@ -1,16 +1,31 @@
-// FP32 sample-weight kernel with compensated per-thread sums.
+// FP32 sample-weight kernel: Lambda points in lanes, sample pairs in packed FP32.
 //
-// Same work decomposition as the FP64 kernel (persistent grid over
-// chunk x Lambda-tile items, features in registers, Lambda constants in shared
-// memory).  Each thread takes two samples per step, so one read of a Lambda's
-// constants serves two weights and the two dependency chains overlap.  The
-// features and constants are in base-2 log units so every exponential is one
-// ex2.approx (MUFU) and the q normalisation's reciprocal one rcp.approx.  Per
-// (thread, Lambda) the weights are summed with Kahan compensation; warps and
-// then the block combine the (sum, compensation) pairs with an error-free
-// two-sum, and one thread per Lambda widens the block result to FP64 for the
-// partial.  The per-Lambda constants come from the FP64 prologue; the
-// per-event log and the cross-event sum are FP64 in the finalise kernel.
+// A work item is one chunk (a run of one event's samples, or of injections) against
+// a tile of NT Lambda points, one per thread.  Each thread keeps its Lambda's
+// constants in registers and sums its weights over the whole chunk, so there is no
+// reduction across threads and the (Lambda, chunk) partial does not depend on which
+// lane computed it.  The block stages the chunk's features in shared memory with the
+// two samples of a pair interleaved, and all lanes read the same words (broadcast
+// loads); the pair goes through the weight in packed f32x2 FMA / ADD / MUL
+// instructions (one instruction for both samples, Blackwell's FFMA2 family), the
+// exponentials and the reciprocal per sample on MUFU (ex2.approx, rcp.approx).
+//
+// Support.  Samples are stored in increasing (q m1, m1) order per event, so the lower
+// edge (m1 > mmin and fl64(q m1) >= mmin; q m1 <= m1 because q <= 1) is a suffix of
+// the chunk: each lane finds its first index j0 by a binary search and the per-pair
+// test is j >= j0 and m1 <= mmax.  lam_order_kernel orders the Lambda across the
+// lanes by mmin, so the j0 of a warp are close and the warp starts at their minimum.
+//
+// The q normalisation 1 - 2^u (u = (1+beta) log2(mmin/m1), base-2 units) loses
+// relative accuracy as u -> 0, where the Taylor series of e^x - 1 in x = u ln2 takes
+// over (|u| < 1/8).  A lane can need it only below m2 = mmin 2^(1/(8|1+beta|)), found
+// by a second binary search; each warp runs the variant with the series up to the
+// largest such index of its lanes and the plain one after it.
+//
+// Per (thread, Lambda) the two halves of the pair accumulate separate Kahan sums
+// (packed); the thread adds the four FP32 numbers in FP64 for the partial.  The
+// per-Lambda constants come from the FP64 prologue; the per-event log and the
+// cross-event sum are FP64 in the finalise kernel.
 #include <math.h>
 
 #include "pop_internal.h"
@@ -18,6 +33,48 @@
 namespace pop {
 
 namespace {
+
+constexpr int SP = 256;  // sample pairs per staged sub-tile (512 samples)
+
+// Two FP32 values in a 64-bit register pair (first sample in the low half).
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void upk(f2 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 __device__ __forceinline__ float ex2f(float x)
 {
@@ -33,241 +90,449 @@ __device__ __forceinline__ float rcpf(float x)
     return y;
 }
 
-// 2^u - 1.  ex2(u) - 1 loses relative accuracy as u -> 0, so |u| < 1/8 uses
-// the Taylor series of e^x - 1 in x = u ln 2 to fifth order (truncation below
-// 1e-8 relative there).  The series is evaluated only in warps where some lane
-// needs it (samples within a few percent of mmin).
-__device__ __forceinline__ float exp2m1f(float u)
+__device__ __forceinline__ f2 ex2_2(f2 x)
 {
-    constexpr float c1 = 0.693147180559945f;    // ln2
-    constexpr float c2 = 0.240226506959101f;    // ln2^2 / 2
-    constexpr float c3 = 0.0555041086648216f;   // ln2^3 / 6
-    constexpr float c4 = 0.00961812910762848f;  // ln2^4 / 24
-    constexpr float c5 = 0.00133335581464284f;  // ln2^5 / 120
-    float e = ex2f(u) - 1.0f;
-    const bool small = fabsf(u) < 0.125f;
-    if (__any_sync(0xffffffffu, small)) {
-        float p = fmaf(c5, u, c4);
-        p = fmaf(p, u, c3);
-        p = fmaf(p, u, c2);
-        p = fmaf(p, u, c1);
-        p *= u;
-        e = small ? p : e;
-    }
-    return e;
+    float a, b;
+    upk(x, a, b);
+    return pk(ex2f(a), ex2f(b));
 }
 
-struct F32Sample {
-    float lm1, m1, lq, sa, sb, dc, nlpi, lz1, lm1lo;
-    int64_t m2b;
+__device__ __forceinline__ f2 bc(float a) { return pk(a, a); }
+
+// One lane's Lambda, in the packed form of the pair arithmetic.
+struct LaneConsts {
+    f2 beta, ac, bc_, km1, nalpha, cpl, nmu, nh, cg, b1, lmmin, nb1, b1lo, nht, ct, t0, neg1;
+    float thr_hi;     // largest float <= mmax
+    int beta_m1;      // beta == -1: the q normalisation is -u
+};
+
+__device__ __forceinline__ LaneConsts lane_consts(const LamF32& L)
+{
+    LaneConsts c;
+    c.beta = bc(L.beta);
+    c.ac = bc(L.ac);
+    c.bc_ = bc(L.bc);
+    c.km1 = bc(L.km1);
+    c.nalpha = bc(L.nalpha);
+    c.cpl = bc(L.cpl);
+    c.nmu = bc(-L.mu);
+    c.nh = bc(L.nh);
+    c.cg = bc(L.cg);
+    c.b1 = bc(L.b1);
+    c.lmmin = bc(L.lmmin);
+    c.nb1 = bc(L.nb1);
+    c.b1lo = bc(L.b1lmmin_lo);
+    c.nht = bc(L.nht);
+    c.ct = bc(L.ct);
+    c.t0 = bc(L.t0);
+    c.neg1 = bc(-1.0f);
+    c.thr_hi = L.thr_hi;
+    c.beta_m1 = L.beta_m1;
+    return c;
+}
+
+// Staged features of one pair: {lm1, m1}, {lq, sa}, {sb, dc}, {nlpi, lm1lo}, each
+// feature a packed (sample a, sample b) value.
+struct PairFeat {
+    f2 lm1, m1, lq, sa, sb, dc, nlpi, lm1lo, lz1;
 };
 
 template <bool HAS_Z>
-__device__ __forceinline__ void load_f32(const FeatF32& F, int64_t s, F32Sample& x)
+__device__ __forceinline__ void load_pair(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p,
+                                          PairFeat& x)
 {
-    const float* b = F.base;
-    const int64_t st = F.stride;
-    x.lm1 = __ldg(b + F_LM1 * st + s);
-    x.m1 = __ldg(b + F_M1 * st + s);
-    x.lq = __ldg(b + F_LQ * st + s);
-    x.sa = __ldg(b + F_SA * st + s);
-    x.sb = __ldg(b + F_SB * st + s);
-    x.dc = __ldg(b + F_DC * st + s);
-    x.nlpi = __ldg(b + F_NLPI * st + s);
-    x.lz1 = HAS_Z ? __ldg(b + F_LZ1 * st + s) : 0.0f;
-    x.lm1lo = __ldg(b + F32_LM1LO * st + s);
-    x.m2b = __double_as_longlong(__ldg(F.m2 + s));
+    const ulonglong2 q0 = buf[4 * p + 0], q1 = buf[4 * p + 1], q2 = buf[4 * p + 2], q3 = buf[4 * p + 3];
+    x.lm1 = q0.x;
+    x.m1 = q0.y;
+    x.lq = q1.x;
+    x.sa = q1.y;
+    x.sb = q2.x;
+    x.dc = q2.y;
+    x.nlpi = q3.x;
+    x.lm1lo = q3.y;
+    x.lz1 = HAS_Z ? zb[p] : 0ull;
 }
 
-// A sample outside every support (m1 = 0): weight 0 for any Lambda.
-__device__ __forceinline__ void dead_f32(F32Sample& x)
+// Weights of both samples of a pair (unmasked: the caller applies the support).
+//   w = (2^(-alpha lm1 + aE + cpl) + 2^(-(m1-mu)^2/(2 sig^2) + aE + cg)) (t0 + 2^(nht dc + ct)) / |1 - 2^u|
+// with aE = beta lq - log2 pi + ac sa + bc sb [+ (kappa-1) lz1] and
+// u = b1 ((lmmin - lm1) + (lmmin_lo - lm1_lo)).  SLOW adds the series for |u| < 1/8 and the
+// beta = -1 normalisation.
+template <bool SLOW, bool HAS_Z>
+__device__ __forceinline__ f2 pair_weight(const PairFeat& x, const LaneConsts& c)
 {
-    x.lm1 = x.m1 = x.lq = x.sa = x.sb = x.dc = x.nlpi = x.lz1 = x.lm1lo = 0.0f;
-    x.m2b = 0;
+    f2 aE = fma2(c.beta, x.lq, x.nlpi);
+    aE = fma2(c.ac, x.sa, aE);
+    aE = fma2(c.bc_, x.sb, aE);
+    if (HAS_Z) aE = fma2(c.km1, x.lz1, aE);
+    const f2 A = fma2(c.nalpha, x.lm1, add2(aE, c.cpl));
+    const f2 d = add2(x.m1, c.nmu);
+    const f2 B = fma2(mul2(c.nh, d), d, add2(aE, c.cg));
+    const f2 e12 = add2(ex2_2(A), ex2_2(B));
+    // The hi parts of (lmmin - lm1) cancel exactly near m1 = mmin; the lo parts carry the rest.
+    const f2 u = fma2(c.b1, sub2(c.lmmin, x.lm1), fma2(c.nb1, x.lm1lo, c.b1lo));
+    f2 den = add2(ex2_2(u), c.neg1);  // 2^u - 1
+    if (SLOW) {
+        // e^(u ln2) - 1 to fifth order in u ln2 (truncation below 1e-8 relative for |u| < 1/8).
+        const f2 c1 = bc(0.693147180559945f), c2 = bc(0.240226506959101f), c3 = bc(0.0555041086648216f),
+                 c4 = bc(0.00961812910762848f), c5 = bc(0.00133335581464284f);
+        f2 p = fma2(c5, u, c4);
+        p = fma2(p, u, c3);
+        p = fma2(p, u, c2);
+        p = fma2(p, u, c1);
+        p = mul2(p, u);
+        float ua, ub, pa, pb, da, db;
+        upk(u, ua, ub);
+        upk(p, pa, pb);
+        upk(den, da, db);
+        da = fabsf(ua) < 0.125f ? pa : da;
+        db = fabsf(ub) < 0.125f ? pb : db;
+        if (c.beta_m1) {  // normalisation ln(m1/mmin) = -u ln2 (u < 0 inside the support)
+            da = ua;
+            db = ub;
+        }
+        den = pk(da, db);
+    }
+    const f2 tt = add2(c.t0, ex2_2(fma2(c.nht, x.dc, c.ct)));
+    float da, db;
+    upk(den, da, db);
+    return mul2(mul2(e12, tt), pk(rcpf(fabsf(da)), rcpf(fabsf(db))));
 }
 
-// Support: mmin < m1 <= mmax (exact against the rounded-down float thresholds) and
-// fl64(q m1) >= mmin on the FP64 bit pattern.
-__device__ __forceinline__ bool in_support(const F32Sample& x, const LamF32& c)
+__device__ __forceinline__ void kahan2(f2& s, f2& cs, f2 w)
 {
-    return (x.m1 > c.thr_lo) & (x.m1 <= c.thr_hi) & (x.m2b >= c.mmin_bits);
-}
-
-// Weight inside the support (the caller applies in_support).
-template <bool HAS_Z>
-__device__ __forceinline__ float weight_f32(const F32Sample& x, const LamF32& c)
-{
-    float aE = fmaf(c.beta, x.lq, x.nlpi);
-    aE = fmaf(c.ac, x.sa, aE);
-    aE = fmaf(c.bc, x.sb, aE);
-    if (HAS_Z) aE = fmaf(c.km1, x.lz1, aE);
-    const float e1 = ex2f(fmaf(c.nalpha, x.lm1, aE + c.cpl));
-    const float d = x.m1 - c.mu;
-    const float e2 = ex2f(fmaf(c.nh * d, d, aE + c.cg));
-    // u = (1+beta) log2(mmin/m1): the hi parts cancel exactly near m1 = mmin and
-    // the lo parts carry the difference.
-    const float u = fmaf(c.b1, c.lmmin - x.lm1, fmaf(c.nb1, x.lm1lo, c.b1lmmin_lo));
-    const float den = c.beta_m1 ? -u : fabsf(exp2m1f(u));
-    const float tt = c.t0 + ex2f(fmaf(c.nht, x.dc, c.ct));
-    return (e1 + e2) * tt * rcpf(den);
-}
-
-__device__ __forceinline__ void kahan_add(float& s, float& c, float w)
-{
-    const float y = w - c;
-    const float t = s + y;
-    c = (t - s) - y;
+    const f2 y = sub2(w, cs);
+    const f2 t = add2(s, y);
+    cs = sub2(sub2(t, s), y);
     s = t;
 }
 
-// (s, c) += (s2, c2) for compensated pairs of value s - c (error-free two-sum of the sums).
-__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2)
+// Pairs [p0, p1) of the staged sub-tile whose first sample is chunk index jb + 2p.
+template <bool SLOW, bool INJ, bool HAS_Z>
+__device__ __forceinline__ void run_pairs(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p0, int p1,
+                                          int jb, int j0, const LaneConsts& c, f2& s, f2& cs, f2& s2, f2& cs2)
 {
-    const float S = s + s2;
-    const float bp = S - s;
-    const float e = (s - (S - bp)) + (s2 - bp);
-    c = (c + c2) - e;
-    s = S;
-}
-
-__device__ __forceinline__ void warp_combine(float& s, float& c)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-        pair_add(s, c, s2, c2);
+#pragma unroll 2
+    for (int p = p0; p < p1; ++p) {
+        PairFeat x;
+        load_pair<HAS_Z>(buf, zb, p, x);
+        const f2 w = pair_weight<SLOW, HAS_Z>(x, c);
+        const int j = jb + 2 * p;
+        float wa, wb, m1a, m1b;
+        upk(w, wa, wb);
+        upk(x.m1, m1a, m1b);
+        wa = (j >= j0 && m1a <= c.thr_hi) ? wa : 0.0f;
+        wb = (j + 1 >= j0 && m1b <= c.thr_hi) ? wb : 0.0f;
+        const f2 wm = pk(wa, wb);
+        kahan2(s, cs, wm);
+        if (INJ) kahan2(s2, cs2, mul2(wm, wm));
     }
 }
 
-template <int T, int NT, bool HAS_Z>
+// First chunk index whose (m2, m1) exceeds (mmin, mmin) lexicographically: the first
+// sample with m1 > mmin and m2 >= mmin.  len when there is none.
+__device__ __forceinline__ int lower_edge(const FeatF32& F, const Chunk& ch, double mmin)
+{
+    const double* m2 = F.m2 + ch.start;
+    const float* m1 = F.base + F_M1 * F.stride + ch.start;
+    int lo = 0, hi = ch.len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const double a = __ldg(m2 + mid);
+        if (a > mmin || (a == mmin && (double)__ldg(m1 + mid) > mmin)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// First chunk index with m2 >= t (len when there is none).
+__device__ __forceinline__ int first_m2_at_least(const FeatF32& F, const Chunk& ch, double t)
+{
+    const double* m2 = F.m2 + ch.start;
+    int lo = 0, hi = ch.len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m2 + mid) >= t) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Stage samples [2 SP st, 2 SP (st+1)) of the chunk: sample s of the sub-tile goes to pair
+// s/2, half s%2; positions past the chunk's end get a sample outside every support
+// (m1 = +inf).
+template <int NT, bool HAS_Z>
+__device__ __forceinline__ void stage(const FeatF32& F, const Chunk& ch, int st, float* __restrict__ buf,
+                                      float* __restrict__ zb)
+{
+    constexpr int rows[8] = {F_LM1, F_M1, F_LQ, F_SA, F_SB, F_DC, F_NLPI, F32_LM1LO};
+    for (int s = threadIdx.x; s < 2 * SP; s += NT) {
+        const int j = 2 * SP * st + s;
+        float* dst = buf + 16 * (s >> 1) + (s & 1);
+        if (j < ch.len) {
+            const float* src = F.base + ch.start + j;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) cp_async4(dst + 2 * f, src + rows[f] * F.stride);
+            if (HAS_Z) cp_async4(zb + s, src + F_LZ1 * F.stride);
+        } else {
+#pragma unroll
+            for (int f = 0; f < 8; ++f) dst[2 * f] = (f == 1) ? INFINITY : 0.0f;
+            if (HAS_Z) zb[s] = 0.0f;
+        }
+    }
+}
+
+template <int NT, bool HAS_Z>
 __global__ void __launch_bounds__(NT)
 weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
-                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2,
-                  const uint8_t* __restrict__ need_mc)
+                  const int32_t* __restrict__ order, const int32_t* __restrict__ n_mc, int64_t K_cap,
+                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
 {
-    constexpr int NW = NT / 32;
-    __shared__ LamF32 sl[T];
-    __shared__ float rs[NW][T], rc[NW][T], rs2[NW][T], rc2[NW][T];
+    __shared__ __align__(16) float sbuf[2][SP * 16];
+    __shared__ __align__(16) float szb[HAS_Z ? 2 : 1][HAS_Z ? 2 * SP : 2];
+    __shared__ int s_jmin;
     const int64_t K = *dK;
-    const int64_t n_tiles = (K + T - 1) / T;
-    const int64_t n_items = (int64_t)wd.n_chunks * n_tiles;
+    const int64_t K_inj = *n_mc;  // Lambda whose xi needs the injections, first in the injection order
+    const int64_t tiles_ev = (K + NT - 1) / NT;
+    const int64_t tiles_inj = (K_inj + NT - 1) / NT;
     const int n_inj_chunks = wd.n_chunks - wd.n_ev_chunks;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_ev_items = (int64_t)wd.n_ev_chunks * tiles_ev;
+    const int64_t n_items = n_ev_items + (int64_t)n_inj_chunks * tiles_inj;
+    const int lane = threadIdx.x & 31;
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int c = (int)(item / n_tiles);
-        const int64_t k0 = (item - (int64_t)c * n_tiles) * T;
-        const int tn = (int)(K - k0 < T ? K - k0 : T);
-        if (need_mc && c >= wd.n_ev_chunks) {  // injection item: needed only for Monte Carlo xi
-            bool any = false;
-            for (int l = 0; l < tn; ++l) any |= need_mc[k0 + l] != 0;
-            if (!any) continue;  // same decision on every thread of the block
+        int c;
+        int64_t tile;
+        if (item < n_ev_items) {
+            c = (int)(item / tiles_ev);
+            tile = item - (int64_t)c * tiles_ev;
+        } else {
+            const int64_t i2 = item - n_ev_items;
+            const int ci = (int)(i2 / tiles_inj);
+            tile = i2 - (int64_t)ci * tiles_inj;
+            c = wd.n_ev_chunks + ci;
         }
-        __syncthreads();
-        {
-            constexpr int W = (int)(sizeof(LamF32) / 4);
-            float* dst = reinterpret_cast<float*>(sl);
-            for (int i = threadIdx.x; i < T * W; i += NT) {
-                const int l = i / W;
-                const int64_t src = k0 + (l < tn ? l : tn - 1);
-                dst[i] = reinterpret_cast<const float*>(lam + src)[i - l * W];
-            }
-        }
-        __syncthreads();
         const Chunk ch = wd.chunks[c];
-        const FeatF32 F = ch.inj ? inj : ev;
-        float s[T], cp[T], s2[T], cp2[T];
-#pragma unroll
-        for (int l = 0; l < T; ++l) s[l] = cp[l] = s2[l] = cp2[l] = 0.0f;
-        // Every thread runs the same number of steps (slots past the end are dead
-        // samples), so all 32 lanes reach the warp vote inside exp2m1f together.
-        for (int base = 0; base < ch.len; base += 2 * NT) {
-            const int j = base + threadIdx.x;
-            F32Sample x0, x1;
-            if (j < ch.len) load_f32<HAS_Z>(F, ch.start + j, x0);
-            else dead_f32(x0);
-            if (j + NT < ch.len) load_f32<HAS_Z>(F, ch.start + j + NT, x1);
-            else dead_f32(x1);
-#pragma unroll
-            for (int l = 0; l < T; ++l) {
-                const LamF32 cl = sl[l];
-                const bool in0 = in_support(x0, cl), in1 = in_support(x1, cl);
-                // Samples are stored in increasing q m1 per event: warps wholly below the
-                // lower mass edge skip the arithmetic.
-                if (__any_sync(0xffffffffu, in0 | in1)) {
-                    // Evaluated on every lane (exp2m1f votes across the warp), then selected.
-                    float w0 = weight_f32<HAS_Z>(x0, cl);
-                    float w1 = weight_f32<HAS_Z>(x1, cl);
-                    w0 = in0 ? w0 : 0.0f;
-                    w1 = in1 ? w1 : 0.0f;
-                    kahan_add(s[l], cp[l], w0 + w1);
-                    if (ch.inj) kahan_add(s2[l], cp2[l], fmaf(w0, w0, w1 * w1));
+        const bool is_inj = ch.inj != 0;
+        const FeatF32 F = is_inj ? inj : ev;
+        const int64_t slot = tile * NT + threadIdx.x;
+        const bool active = slot < (is_inj ? K_inj : K);
+        const int k = active ? order[(is_inj ? K_cap : 0) + slot] : 0;
+        const LamF32 L = lam[k];
+        int j0 = ch.len, js = 0;
+        if (active) {
+            const double mmin = __longlong_as_double(L.mmin_bits);  // +inf for an invalid Lambda
+            j0 = lower_edge(F, ch, mmin);
+            if (j0 < ch.len) {
+                if (L.beta_m1) {
+                    js = ch.len;
+                } else {
+                    // |u| >= 1/8 (with a 2^-10 margin) from m1 >= mmin 2^(1/(8|1+beta|)) on, and m1 >= m2.
+                    const double t = mmin * exp2(0.125 / fabs((double)L.b1)) * (1.0 + 0x1p-10);
+                    js = first_m2_at_least(F, ch, t);
                 }
             }
         }
-#pragma unroll
-        for (int l = 0; l < T; ++l) {
-            warp_combine(s[l], cp[l]);
-            if (ch.inj) warp_combine(s2[l], cp2[l]);
-            if (lane == 0) {
-                rs[warp][l] = s[l];
-                rc[warp][l] = cp[l];
-                rs2[warp][l] = s2[l];
-                rc2[warp][l] = cp2[l];
+        const LaneConsts cl = lane_consts(L);
+        const int wj0 = __reduce_min_sync(0xffffffffu, j0);
+        const int wjs = __reduce_max_sync(0xffffffffu, js);
+        __syncthreads();  // the previous item is done with s_jmin
+        if (threadIdx.x == 0) s_jmin = ch.len;
+        __syncthreads();
+        if (lane == 0 && wj0 < ch.len) atomicMin(&s_jmin, wj0);
+        __syncthreads();
+        const int n_sub = (ch.len + 2 * SP - 1) / (2 * SP);
+        const int first = s_jmin < ch.len ? s_jmin / (2 * SP) : n_sub;
+        f2 s = 0ull, cs = 0ull, s2 = 0ull, cs2 = 0ull;
+        if (first < n_sub) {
+            stage<NT, HAS_Z>(F, ch, first, sbuf[0], szb[0]);
+            cp_async_commit();
+            for (int st = first; st < n_sub; ++st) {
+                const int b = (st - first) & 1;
+                if (st + 1 < n_sub) stage<NT, HAS_Z>(F, ch, st + 1, sbuf[b ^ 1], szb[HAS_Z ? (b ^ 1) : 0]);
+                cp_async_commit();
+                cp_async_wait1();
+                __syncthreads();
+                const int jb = 2 * SP * st;
+                const int p_end = min(SP, (ch.len - jb + 1) >> 1);
+                const int p_beg = min(p_end, max(0, (wj0 - jb) >> 1));
+                const int p_slow = min(p_end, max(p_beg, (wjs - jb + 1) >> 1));
+                const ulonglong2* bq = reinterpret_cast<const ulonglong2*>(sbuf[b]);
+                const f2* bz = reinterpret_cast<const f2*>(szb[HAS_Z ? b : 0]);
+                if (is_inj) {
+                    run_pairs<true, true, HAS_Z>(bq, bz, p_beg, p_slow, jb, j0, cl, s, cs, s2, cs2);
+                    run_pairs<false, true, HAS_Z>(bq, bz, p_slow, p_end, jb, j0, cl, s, cs, s2, cs2);
+                } else {
+                    run_pairs<true, false, HAS_Z>(bq, bz, p_beg, p_slow, jb, j0, cl, s, cs, s2, cs2);
+                    run_pairs<false, false, HAS_Z>(bq, bz, p_slow, p_end, jb, j0, cl, s, cs, s2, cs2);
+                }
+                __syncthreads();  // buffer b is refilled two sub-tiles on
             }
         }
-        __syncthreads();
-        if (threadIdx.x < tn) {  // one thread per Lambda, all in warp 0
-            const int l = threadIdx.x;
-            float a = rs[0][l], ac = rc[0][l], b = rs2[0][l], bc = rc2[0][l];
-            for (int w = 1; w < NW; ++w) {
-                pair_add(a, ac, rs[w][l], rc[w][l]);
-                pair_add(b, bc, rs2[w][l], rc2[w][l]);
+        if (active) {
+            float sa, sb, ca, cb;
+            upk(s, sa, sb);
+            upk(cs, ca, cb);
+            part[(int64_t)k * wd.n_chunks + c] = ((double)sa - (double)ca) + ((double)sb - (double)cb);
+            if (is_inj) {
+                upk(s2, sa, sb);
+                upk(cs2, ca, cb);
+                part2[(int64_t)k * n_inj_chunks + (c - wd.n_ev_chunks)] =
+                    ((double)sa - (double)ca) + ((double)sb - (double)cb);
             }
-            part[(k0 + l) * wd.n_chunks + c] = (double)a - (double)ac;
-            if (ch.inj) part2[(k0 + l) * n_inj_chunks + (c - wd.n_ev_chunks)] = (double)b - (double)bc;
         }
     }
-}
-
-template <int T, int NT>
-const void* pick_f32(bool has_z)
-{
-    return has_z ? (const void*)weight_f32_kernel<T, NT, true> : (const void*)weight_f32_kernel<T, NT, false>;
 }
 
 template <int NT>
-const void* pick_f32_t(int T, bool has_z)
+const void* pick_f32(bool has_z)
 {
-    switch (T) {
-        case 2: return pick_f32<2, NT>(has_z);
-        case 4: return pick_f32<4, NT>(has_z);
-        case 8: return pick_f32<8, NT>(has_z);
-        case 16: return pick_f32<16, NT>(has_z);
-        case 32: return pick_f32<32, NT>(has_z);
-        default: return nullptr;
+    return has_z ? (const void*)weight_f32_kernel<NT, true> : (const void*)weight_f32_kernel<NT, false>;
+}
+
+// ---------------------------------------------------------------- Lambda order
+constexpr int ORDER_THREADS = 1024;
+constexpr int ORDER_BINS = 1024;
+
+// Exclusive prefix sum of one value per thread over the block (ORDER_THREADS threads).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
+    __syncthreads();  // warp_tot is free
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    return (warp ? warp_tot[warp - 1] : 0) + x - v;
+}
+
+// order[0, K): the Lambda by increasing mmin (1024 equal bins over the batch's range,
+// invalid Lambda last).  order[K_cap, K_cap + K): the same with the Lambda that need the
+// Monte Carlo xi (need_mc[k] != 0) first; *n_mc = their number (K without need_mc).  The
+// order within a bin is arbitrary: it only decides which lane evaluates which Lambda.
+__global__ void __launch_bounds__(ORDER_THREADS)
+lam_order_kernel(const LamF32* __restrict__ lam, const int64_t* __restrict__ dK, const uint8_t* __restrict__ need_mc,
+                 int64_t K_cap, int32_t* __restrict__ order, int32_t* __restrict__ n_mc)
+{
+    __shared__ int h_ev[ORDER_BINS], h_inj[2 * ORDER_BINS], warp_tot[32];
+    __shared__ double s_lo[32], s_hi[32];
+    const int K = (int)*dK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double lo = INFINITY, hi = -INFINITY;
+    int cnt = 0;
+    for (int k = threadIdx.x; k < K; k += ORDER_THREADS) {
+        const double m = __longlong_as_double(lam[k].mmin_bits);
+        if (m < INFINITY) {
+            lo = fmin(lo, m);
+            hi = fmax(hi, m);
+        }
+        cnt += (need_mc == nullptr || need_mc[k]) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+        warp_tot[warp] = cnt;
+    }
+    for (int i = threadIdx.x; i < ORDER_BINS; i += ORDER_THREADS) h_ev[i] = 0;
+    for (int i = threadIdx.x; i < 2 * ORDER_BINS; i += ORDER_THREADS) h_inj[i] = 0;
+    __syncthreads();
+    lo = s_lo[0];
+    hi = s_hi[0];
+    cnt = 0;
+    for (int w = 0; w < ORDER_THREADS / 32; ++w) {
+        lo = fmin(lo, s_lo[w]);
+        hi = fmax(hi, s_hi[w]);
+        cnt += warp_tot[w];
+    }
+    const double scale = hi > lo ? ORDER_BINS / (hi - lo) : 0.0;
+    auto bin = [&](int k) {
+        const double m = __longlong_as_double(lam[k].mmin_bits);
+        if (!(m < INFINITY)) return ORDER_BINS - 1;
+        return min(ORDER_BINS - 1, (int)((m - lo) * scale));
+    };
+    for (int k = threadIdx.x; k < K; k += ORDER_THREADS) {
+        const int b = bin(k);
+        atomicAdd(&h_ev[b], 1);
+        atomicAdd(&h_inj[(need_mc == nullptr || need_mc[k]) ? b : ORDER_BINS + b], 1);
+    }
+    __syncthreads();
+    {
+        const int i = threadIdx.x;  // ORDER_THREADS == ORDER_BINS
+        const int e = block_exclusive_scan(h_ev[i], warp_tot);
+        const int a = h_inj[2 * i], b = h_inj[2 * i + 1];
+        const int f = block_exclusive_scan(a + b, warp_tot);
+        __syncthreads();
+        h_ev[i] = e;
+        h_inj[2 * i] = f;
+        h_inj[2 * i + 1] = f + a;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += ORDER_THREADS) {
+        const int b = bin(k);
+        order[atomicAdd(&h_ev[b], 1)] = k;
+        order[K_cap + atomicAdd(&h_inj[(need_mc == nullptr || need_mc[k]) ? b : ORDER_BINS + b], 1)] = k;
+    }
+    if (threadIdx.x == 0) *n_mc = cnt;
 }
 
 }  // namespace
 
 const void* weight_f32_fn(const Tiling& t, bool has_z)
 {
+    if (t.lambda_tile != t.block_threads) return nullptr;
     switch (t.block_threads) {
-        case 128: return pick_f32_t<128>(t.lambda_tile, has_z);
-        case 256: return pick_f32_t<256>(t.lambda_tile, has_z);
-        case 512: return pick_f32_t<512>(t.lambda_tile, has_z);
+        case 32: return pick_f32<32>(has_z);
+        case 64: return pick_f32<64>(has_z);
+        case 128: return pick_f32<128>(has_z);
+        case 256: return pick_f32<256>(has_z);
         default: return nullptr;
     }
 }
 
+cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t* need_mc, int64_t K_cap,
+                             int32_t* order, int32_t* n_mc, cudaStream_t s)
+{
+    static_assert(ORDER_THREADS == ORDER_BINS, "one scan element per thread");
+    lam_order_kernel<<<1, ORDER_THREADS, 0, s>>>(lam, dK, need_mc, K_cap, order, n_mc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* lam,
-                              const int64_t* dK, double* part, double* part2, SurrogateXi sx, cudaStream_t s)
+                              const int32_t* order, const int32_t* n_mc, int64_t K_cap, const int64_t* dK,
+                              double* part, double* part2, cudaStream_t s)
 {
     const void* fn = weight_f32_fn(t, wd.has_z != 0);
     if (!fn) return cudaErrorInvalidValue;
-    const uint8_t* need = sx.need_mc;
-    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2, &need};
+    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &K_cap, &dK, &part, &part2};
     return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, 0, s);
 }
 
