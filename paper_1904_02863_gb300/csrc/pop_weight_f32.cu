@@ -34,7 +34,18 @@ namespace pop {
 
 namespace {
 
-constexpr int SP = 256;  // sample pairs per staged sub-tile (512 samples)
+// Resident warps per SM the register budget is set for (65536 / (32 x this) registers per thread).
+#ifndef POP_F32_WARPS_PER_SM
+#define POP_F32_WARPS_PER_SM 24
+#endif
+
+// Sample pairs per staged sub-tile (up to 512 samples, 32 KB double-buffered) and the blocks
+// per SM of the register budget.
+template <int NT>
+struct F32Cfg {
+    static constexpr int SP = NT >= 128 ? 256 : 2 * NT;
+    static constexpr int MIN_BLOCKS = (32 * POP_F32_WARPS_PER_SM) / NT > 0 ? (32 * POP_F32_WARPS_PER_SM) / NT : 1;
+};
 
 // Two FP32 values in a 64-bit register pair (first sample in the low half).
 typedef unsigned long long f2;
@@ -207,26 +218,56 @@ __device__ __forceinline__ void kahan2(f2& s, f2& cs, f2 w)
     s = t;
 }
 
-// Pairs [p0, p1) of the staged sub-tile whose first sample is chunk index jb + 2p.
-template <bool SLOW, bool INJ, bool HAS_Z>
+// Masked weights of pair p of the staged sub-tile (first sample at chunk index j).  CHECK_J
+// applies the lower edge j >= j0; past the largest j0 of the warp only m1 <= mmax is tested
+// (a lane without in-support samples has thr_hi = -inf).
+template <bool SLOW, bool CHECK_J, bool HAS_Z>
+__device__ __forceinline__ f2 masked_pair(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p, int j,
+                                          int j0, const LaneConsts& c)
+{
+    PairFeat x;
+    load_pair<HAS_Z>(buf, zb, p, x);
+    const f2 w = pair_weight<SLOW, HAS_Z>(x, c);
+    float wa, wb, m1a, m1b;
+    upk(w, wa, wb);
+    upk(x.m1, m1a, m1b);
+    const bool ia = m1a <= c.thr_hi && (!CHECK_J || j >= j0);
+    const bool ib = m1b <= c.thr_hi && (!CHECK_J || j + 1 >= j0);
+    return pk(ia ? wa : 0.0f, ib ? wb : 0.0f);
+}
+
+// Pairs [p0, p1) of the staged sub-tile whose first sample is chunk index jb + 2p.  Two pairs
+// are added first, then the packed Kahan sums take the result (one rounding more per two
+// pairs, a third of the compensated additions).
+template <bool SLOW, bool CHECK_J, bool INJ, bool HAS_Z>
 __device__ __forceinline__ void run_pairs(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p0, int p1,
                                           int jb, int j0, const LaneConsts& c, f2& s, f2& cs, f2& s2, f2& cs2)
 {
-#pragma unroll 2
-    for (int p = p0; p < p1; ++p) {
-        PairFeat x;
-        load_pair<HAS_Z>(buf, zb, p, x);
-        const f2 w = pair_weight<SLOW, HAS_Z>(x, c);
-        const int j = jb + 2 * p;
-        float wa, wb, m1a, m1b;
-        upk(w, wa, wb);
-        upk(x.m1, m1a, m1b);
-        wa = (j >= j0 && m1a <= c.thr_hi) ? wa : 0.0f;
-        wb = (j + 1 >= j0 && m1b <= c.thr_hi) ? wb : 0.0f;
-        const f2 wm = pk(wa, wb);
-        kahan2(s, cs, wm);
-        if (INJ) kahan2(s2, cs2, mul2(wm, wm));
+    int p = p0;
+#pragma unroll 1
+    for (; p + 1 < p1; p += 2) {
+        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
+        const f2 w1 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 1, jb + 2 * p + 2, j0, c);
+        kahan2(s, cs, add2(w0, w1));
+        if (INJ) kahan2(s2, cs2, fma2(w0, w0, mul2(w1, w1)));
     }
+    if (p < p1) {
+        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
+        kahan2(s, cs, w0);
+        if (INJ) kahan2(s2, cs2, mul2(w0, w0));
+    }
+}
+
+// The three regions of a sub-tile's pairs for one warp: with the series (and the lower-edge
+// test), then without the series but with the test, then neither.
+template <bool INJ, bool HAS_Z>
+__device__ __forceinline__ void run_regions(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p_beg,
+                                            int p_slow, int p_chk, int p_end, int jb, int j0, const LaneConsts& c,
+                                            f2& s, f2& cs, f2& s2, f2& cs2)
+{
+    run_pairs<true, true, INJ, HAS_Z>(buf, zb, p_beg, p_slow, jb, j0, c, s, cs, s2, cs2);
+    run_pairs<false, true, INJ, HAS_Z>(buf, zb, p_slow, p_chk, jb, j0, c, s, cs, s2, cs2);
+    run_pairs<false, false, INJ, HAS_Z>(buf, zb, p_chk, p_end, jb, j0, c, s, cs, s2, cs2);
 }
 
 // First chunk index whose (m2, m1) exceeds (mmin, mmin) lexicographically: the first
@@ -270,19 +311,24 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 
 // Stage samples [2 SP st, 2 SP (st+1)) of the chunk: sample s of the sub-tile goes to pair
 // s/2, half s%2; positions past the chunk's end get a sample outside every support
-// (m1 = +inf).
+// (m1 = +inf).  Lane l of a warp copies feature ((l/4 + i) mod 8) of sample 32 w + l in
+// step i, so the 32 four-byte writes of a step land in 32 different banks.
 template <int NT, bool HAS_Z>
 __device__ __forceinline__ void stage(const FeatF32& F, const Chunk& ch, int st, float* __restrict__ buf,
                                       float* __restrict__ zb)
 {
-    constexpr int rows[8] = {F_LM1, F_M1, F_LQ, F_SA, F_SB, F_DC, F_NLPI, F32_LM1LO};
+    constexpr int SP = F32Cfg<NT>::SP;
+    const int lane = threadIdx.x & 31;
     for (int s = threadIdx.x; s < 2 * SP; s += NT) {
         const int j = 2 * SP * st + s;
         float* dst = buf + 16 * (s >> 1) + (s & 1);
         if (j < ch.len) {
             const float* src = F.base + ch.start + j;
 #pragma unroll
-            for (int f = 0; f < 8; ++f) cp_async4(dst + 2 * f, src + rows[f] * F.stride);
+            for (int i = 0; i < 8; ++i) {
+                const int f = ((lane >> 2) + i) & 7;  // staged slot: lm1 m1 lq sa sb dc nlpi lm1lo
+                cp_async4(dst + 2 * f, src + (f == 7 ? F32_LM1LO : f) * F.stride);
+            }
             if (HAS_Z) cp_async4(zb + s, src + F_LZ1 * F.stride);
         } else {
 #pragma unroll
@@ -293,11 +339,12 @@ __device__ __forceinline__ void stage(const FeatF32& F, const Chunk& ch, int st,
 }
 
 template <int NT, bool HAS_Z>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, F32Cfg<NT>::MIN_BLOCKS)
 weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
                   const int32_t* __restrict__ order, const int32_t* __restrict__ n_mc, int64_t K_cap,
                   const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
 {
+    constexpr int SP = F32Cfg<NT>::SP;
     __shared__ __align__(16) float sbuf[2][SP * 16];
     __shared__ __align__(16) float szb[HAS_Z ? 2 : 1][HAS_Z ? 2 * SP : 2];
     __shared__ int s_jmin;
@@ -343,8 +390,10 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
                 }
             }
         }
-        const LaneConsts cl = lane_consts(L);
+        LaneConsts cl = lane_consts(L);
+        if (j0 >= ch.len) cl.thr_hi = -INFINITY;  // no in-support sample: masked without the index test
         const int wj0 = __reduce_min_sync(0xffffffffu, j0);
+        const int wj1 = __reduce_max_sync(0xffffffffu, j0 < ch.len ? j0 : 0);
         const int wjs = __reduce_max_sync(0xffffffffu, js);
         __syncthreads();  // the previous item is done with s_jmin
         if (threadIdx.x == 0) s_jmin = ch.len;
@@ -364,18 +413,17 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
                 cp_async_wait1();
                 __syncthreads();
                 const int jb = 2 * SP * st;
+                // Region edges at even pair indices (SP is even, so even in the chunk too): the
+                // pre-summed pairs (2m, 2m+1) are the same for every warp, and so is every
+                // lane's rounding.  Zero pairs ahead of a lane's j0 leave its sums at 0.
                 const int p_end = min(SP, (ch.len - jb + 1) >> 1);
-                const int p_beg = min(p_end, max(0, (wj0 - jb) >> 1));
-                const int p_slow = min(p_end, max(p_beg, (wjs - jb + 1) >> 1));
+                const int p_beg = min(p_end, max(0, (wj0 - jb) >> 1)) & ~1;
+                const int p_slow = min(p_end, max(p_beg, (((wjs - jb + 1) >> 1) + 1) & ~1));
+                const int p_chk = min(p_end, max(p_slow, (((wj1 - jb + 1) >> 1) + 1) & ~1));
                 const ulonglong2* bq = reinterpret_cast<const ulonglong2*>(sbuf[b]);
                 const f2* bz = reinterpret_cast<const f2*>(szb[HAS_Z ? b : 0]);
-                if (is_inj) {
-                    run_pairs<true, true, HAS_Z>(bq, bz, p_beg, p_slow, jb, j0, cl, s, cs, s2, cs2);
-                    run_pairs<false, true, HAS_Z>(bq, bz, p_slow, p_end, jb, j0, cl, s, cs, s2, cs2);
-                } else {
-                    run_pairs<true, false, HAS_Z>(bq, bz, p_beg, p_slow, jb, j0, cl, s, cs, s2, cs2);
-                    run_pairs<false, false, HAS_Z>(bq, bz, p_slow, p_end, jb, j0, cl, s, cs, s2, cs2);
-                }
+                if (is_inj) run_regions<true, HAS_Z>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
+                else run_regions<false, HAS_Z>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
                 __syncthreads();  // buffer b is refilled two sub-tiles on
             }
         }
