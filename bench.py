@@ -46,6 +46,10 @@ FP64_OPS_PER_INJ_PAIR = 57
 # over 152 SMs); peak op rate = 2 * SMs * clock.
 FP64_LANES_PER_SM = 2
 FP32_LANES_PER_SM = 128
+# MUFU issue slots per SM per clock in ex2.approx units (rcp.approx takes two), and per
+# in-support pair of the FP32 weight (4 ex2 + 1 rcp).
+MUFU_SLOTS_PER_SM = 32
+MUFU_SLOTS_PER_PAIR = 6
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
@@ -67,10 +71,24 @@ def in_support_pairs(theta, lam):
     total = int((len(m2s) - np.searchsorted(m2s, mmin, side="left")).sum())
     # remove m1 > mmax (the few high-mass samples) and m1 <= mmin with m2 >= mmin (q = 1 ties)
     hi = m1 > mmax.min()
-    total -= int(((m2[hi, None] >= mmin[None, :]) & (m1[hi, None] > mmax[None, :])).sum())
     tie = m2 >= m1
-    total -= int(((m2[tie, None] >= mmin[None, :]) & (m1[tie, None] <= mmin[None, :])).sum())
+    for k0 in range(0, len(lam), 64):  # bounded temporaries on large catalogs
+        a, b = mmin[None, k0:k0 + 64], mmax[None, k0:k0 + 64]
+        total -= int(((m2[hi, None] >= a) & (m1[hi, None] > b)).sum())
+        total -= int(((m2[tie, None] >= a) & (m1[tie, None] <= a)).sum())
     return total
+
+
+def f32_roofline(pairs, weight_ms):
+    """The FP32 weight kernel against its binding unit, MUFU: per in-support pair 4 ex2.approx
+    (32 per SM per clock on GB300) and 1 rcp.approx (16 per clock, two ex2 slots), against 22
+    FP32 lane operations on the FMA pipe (128 per SM per clock): 6/32 > 22/128 clocks."""
+    peak = MUFU_SLOTS_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    achieved = MUFU_SLOTS_PER_PAIR * pairs / (weight_ms * 1e-3)
+    return {"bound": "alu", "kernel": "weight_f32_kernel", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "T MUFU slots/s", "frac": achieved / peak, "traffic": None, "weight_ms": weight_ms,
+            "in_support_pairs": pairs, "slots_per_in_support_pair": MUFU_SLOTS_PER_PAIR,
+            "peak_basis": "MUFU ex2 32/SM/clk (rcp 16: 2 slots) x 152 SMs x 2070 MHz, microbenchmark rates"}
 
 
 def grid_support_triples(m1, q, lam):
@@ -447,13 +465,16 @@ def run_ragged(args, B, rank, local, world):
     torch.cuda.synchronize()
     barrier(world)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wms = []
     with Clocks(local) as clk:
         start.record(stream)
         for k in seq:
             B.pop_loglik(like.ctx, dev[:k], B.POP_MODE_F32, out=view(k))
+            wms.append(B.pop_last_kernel_ms(like.ctx)[0])
         stop.record(stream)
         torch.cuda.synchronize()
     ms = max_over_ranks(start.elapsed_time(stop), world)
+    support = {k: in_support_pairs(cat.theta, lam[:k]) + in_support_pairs(inj.theta, lam[:k]) for k in sizes}
     t0 = time.perf_counter()
     for k in seq:
         B.pop_loglik(like.ctx, lam[:k], B.POP_MODE_F32)
@@ -467,9 +488,10 @@ def run_ragged(args, B, rank, local, world):
                        "n_draw": int(inj.n_draw), "n_found": int(inj.n_found), "K_sequence": list(sizes),
                        "tiling_f32": B.pop_get_tiling(like.ctx, B.POP_MODE_F32), "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (FP32 features 44 B/sample)"},
+            "roofline": f32_roofline(sum(support[k] for k in seq), sum(wms)),
             "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(8 * 12 * np.mean(seq)),
                     "d2h_bytes_per_step": int(28 * np.mean(seq))},
-            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+            "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
     like.close()
     if rank == 0:
         print(json.dumps(line, default=_jsonable), flush=True)
@@ -609,7 +631,7 @@ def main():
                     "ops_per_in_support_pair": FP64_OPS_PER_PAIR,
                     "peak_basis": "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz"}
     else:
-        roofline = {"bound": "alu", "kernel": "weight_f32_kernel", "weight_ms": w_h}
+        roofline = f32_roofline(n_ev_pairs + n_inj_pairs, w_h)
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_h / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -624,12 +646,14 @@ def main():
         "roofline": roofline,
         "e2e": {"value": world * K * args.steps / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(lam.nbytes), "d2h_bytes_per_step": int(K * (8 * 3 + 4))},
-        "gpu_launches": 4 * args.steps,
+        # set K, prologue, weight, finalise (+ the FP32 kernel's Lambda order)
+        "gpu_launches": (4 if head == B.POP_MODE_F64 else 5) * args.steps,
         "clocks": clocks,
     }
     if args.mode == "both":
         line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
-                                 "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32"}}
+                                 "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32",
+                                 "roofline": f32_roofline(n_ev_pairs + n_inj_pairs, w32)}}
         line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
         line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
         line["forms"]["cbc_likelihood"] = cbc_form(B, like, args, world, rank)
