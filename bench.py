@@ -211,6 +211,29 @@ def cpu_baseline(cat, inj, lam, n_rows):
             "seconds": dt}
 
 
+def ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_pairs, n_events):
+    """FP64-grade ln L with the sample weights in float-float arithmetic (POP_MODE_FF): its
+    evals/s, and its distance to the FP64 kernel's ln L in units of the FP64 parity tolerance
+    1e-12 (|sum_i ln(S_i/n_i)| + N |ln xi|) for every Lambda of the batch."""
+    import torch
+    ms, w = timed(B.POP_MODE_FF)
+    ff = [o.clone() for o in outs]
+    B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F64, out=outs)
+    torch.cuda.synchronize()
+    f64 = [o.cpu().numpy() for o in outs]
+    ffh = [o.cpu().numpy() for o in ff]
+    n = n_events
+    fin = np.isfinite(f64[0])
+    a = np.abs(np.where(fin, f64[0], 0.0) + n * f64[1])
+    tol = 1e-12 * (a + n * np.abs(f64[1])) + 1e-13
+    ratio = float(np.max(np.abs(ffh[0][fin] - f64[0][fin]) / tol[fin])) if fin.any() else 0.0
+    K = len(lam)
+    return {"value": world * K * args.steps / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / args.steps,
+            "weight_ms": w, "dtype": "float-float (2 x f32)",
+            "max_dlnL_over_f64_tol": ratio, "flags_equal": bool((ffh[3] == f64[3]).all()),
+            "in_support_pairs": n_pairs}
+
+
 def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world):
     """FP32 weights + the trained ln xi network (Monte Carlo xi only where its gate says so).
 
@@ -654,6 +677,8 @@ def main():
         line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
                                  "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32",
                                  "roofline": f32_roofline(n_ev_pairs + n_inj_pairs, w32)}}
+        line["forms"]["f64_ff"] = ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_ev_pairs + n_inj_pairs,
+                                          cat.n_events)
         line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
         line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
         line["forms"]["cbc_likelihood"] = cbc_form(B, like, args, world, rank)

@@ -68,8 +68,15 @@ enum { POP_STORE_F64 = 1, POP_STORE_F32 = 2 };
  *                 per-Lambda constants, partial combines, per-event log,
  *                 cross-event sum and xi (needs POP_STORE_F32 features).
  *   POP_MODE_F32_SURROGATE: as POP_MODE_F32, with ln xi from the trained MLP
- *                 and Monte Carlo xi only for the Lambda the gate rejects. */
-enum { POP_MODE_F64 = 0, POP_MODE_F32 = 1, POP_MODE_F32_SURROGATE = 2 };
+ *                 and Monte Carlo xi only for the Lambda the gate rejects.
+ *   POP_MODE_FF:  the FP64 result to within the FP64 mode's tolerance, with the
+ *                 sample weights in float-float arithmetic (each value an
+ *                 unevaluated sum of two FP32 numbers, ~48 significant bits,
+ *                 on the FP32 pipe) and FP64 for the exact gap m1 - mmin near
+ *                 the lower mass edge; weights below e^-87 count as 0.  Uses
+ *                 the POP_STORE_F64 features; per-Lambda constants, partials,
+ *                 logs and sums in FP64 as in POP_MODE_F64. */
+enum { POP_MODE_F64 = 0, POP_MODE_F32 = 1, POP_MODE_F32_SURROGATE = 2, POP_MODE_FF = 3 };
 
 enum { POP_MEM_HOST = 0, POP_MEM_DEVICE = 1 };
 
@@ -280,6 +287,10 @@ int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
  * and write y[n] (both in `mem`): fn 0 = exp (Tang's table-driven method,
  * 2048-entry table; 0 below x = -707, +inf above 709.7), fn 1 = expm1, fn 2 =
  * reciprocal of a positive normal x (hardware seed + one cubic Newton step).
+ * fn 3..7 evaluate the float-float functions of POP_MODE_FF on x rounded to a
+ * float-float value, returning hi + lo: 3 = exp (0 below x = -87), 4 = expm1
+ * (Taylor series below |x| = 1/16, Tang's table above), 5 = reciprocal, 6 =
+ * square, 7 = the exact square of the FP32 high part (packed FMA error term).
  * The test suite checks them against libm and CUDA's functions. */
 int pop_math_check(pop_ctx* ctx, int fn, int64_t n, const double* x, double* y, int mem);
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libpop.so")
 
 POP_OK, POP_EINVAL, POP_ENOMEM, POP_ECUDA, POP_ESTATE, POP_ETIMEOUT, POP_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 POP_STORE_F64, POP_STORE_F32 = 1, 2
-POP_MODE_F64, POP_MODE_F32, POP_MODE_F32_SURROGATE = 0, 1, 2
+POP_MODE_F64, POP_MODE_F32, POP_MODE_F32_SURROGATE, POP_MODE_FF = 0, 1, 2, 3
 POP_MEM_HOST, POP_MEM_DEVICE = 0, 1
 POP_FLAG_INVALID_LAMBDA, POP_FLAG_ZERO_EVENT, POP_FLAG_LOW_NEFF = 1, 2, 4
 POP_FLAG_SURROGATE_USED, POP_FLAG_MC_FALLBACK, POP_FLAG_ZERO_XI = 8, 16, 32
@@ -294,7 +294,8 @@ def pop_last_kernel_ms(ctx):
 
 
 def pop_math_check(ctx, fn, x):
-    """The FP64 kernel's exp (0), expm1 (1) or reciprocal (2) evaluated on the GPU."""
+    """The FP64 kernel's exp (0), expm1 (1) or reciprocal (2), or the float-float kernel's exp (3),
+    expm1 (4), reciprocal (5), square (6) and exact FP32 hi-part square (7), evaluated on the GPU."""
     xa = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(xa)
     _check(ctx, load_library().pop_math_check(ctx, int(fn), xa.size, xa.ctypes.data_as(ctypes.c_void_p),

@@ -97,12 +97,14 @@ struct pop_ctx {
 
     Tiling tiling[2] = {{8, 256, 0}, {128, 128, 0}};
     bool use_graphs = true;
-    Graph graph[3];  // per mode: F64, F32, F32 + surrogate
+    Graph graph[4];  // per mode: F64, F32, F32 + surrogate, float-float
     DevBuf d_need, d_slnxi, d_slnneff;  // surrogate mode: Monte Carlo mask, ln xi, ln N_eff per Lambda
     DevBuf d_order, d_nmc;   // FP32 kernel: lane order of the Lambda [2][K_cap], Lambda needing the injections
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts expc{};
+    DevBuf d_fftab;          // 2^(j/2048) as FP32 (hi, lo) for the float-float exponentials
+    FFConsts ffk{};
     std::unique_ptr<Surrogate> sur;  // ln xi network, created on first use
     std::unique_ptr<GridVT> grid;    // grid selection term, created by pop_load_vt_grid
     std::unique_ptr<CbcState> cbc;   // single-event CBC likelihood, created by pop_cbc_load
@@ -322,6 +324,13 @@ int ensure_scratch(pop_ctx* c, int64_t K)
 
 int grid_size(pop_ctx* c, int mode)
 {
+    if (mode == POP_MODE_FF) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, weight_ff_fn(c->ev.n_dims == 7), weight_ff_threads(), 0) !=
+            cudaSuccess)
+            occ = 1;
+        return std::max(1, occ) * c->sm_count;
+    }
     const Tiling& t = c->tiling[mode];
     const void* fn = mode == POP_MODE_F64 ? weight_f64_fn(t, c->ev.n_dims == 7) : weight_f32_fn(t, c->ev.n_dims == 7);
     int occ = 0;
@@ -337,7 +346,7 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     // Inside a capture the timing events must become external event-record
     // nodes, or the replayed graph would never record them.
     const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    const int m = mode == POP_MODE_F64 ? 0 : 1;
+    const int m = (mode == POP_MODE_F64 || mode == POP_MODE_FF) ? 0 : 1;  // FP64 or FP32 grid term and partials
     // With the grid selection term the injections are not part of the work list.
     const bool use_grid = c->xi_source == POP_XI_GRID;
     const int32_t n_items = use_grid ? c->n_ev_chunks : c->n_chunks;
@@ -356,7 +365,14 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
         sx = SurrogateXi{c->d_need.as<uint8_t>(), c->d_slnxi.as<double>(), c->d_slnneff.as<double>()};
     }
     CK(cudaEventRecordWithFlags(c->ev_w0, c->stream, rec), "event");
-    if (m == 0) {
+    if (mode == POP_MODE_FF) {
+        FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
+        CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), nullptr, c->k_cap, c->d_order.as<int32_t>(),
+                            c->d_nmc.as<int32_t>(), c->stream), "lambda order");
+        CK(launch_weight_ff(grid, e, j, wd, c->d_c64.as<LamF64>(), c->d_order.as<int32_t>(), c->d_nmc.as<int32_t>(),
+                            c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(), c->d_part2.as<double>(),
+                            c->d_fftab.as<float2>(), c->ffk, c->stream), "weight_ff");
+    } else if (m == 0) {
         FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
         CK(launch_weight_f64(c->tiling[0], grid, e, j, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                              c->d_part.as<double>(), c->d_part2.as<double>(), c->d_exptab.as<double2>(), c->expc,
@@ -387,8 +403,8 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
 
 int run_pipeline(pop_ctx* c, int mode, int n_params)
 {
-    const int m = mode == POP_MODE_F64 ? 0 : 1;
-    const int grid = grid_size(c, m);
+    const int m = mode == POP_MODE_F64 ? 0 : 1;  // tiling slot (the float-float kernel has one fixed tiling)
+    const int grid = grid_size(c, mode == POP_MODE_FF ? POP_MODE_FF : m);
     uint64_t sur_version = 0;
     if (mode == POP_MODE_F32_SURROGATE) {  // buffers first: nothing may be allocated during a capture
         const int rc = c->sur->ensure_gate(c->k_cap);
@@ -492,7 +508,7 @@ extern "C" {
 int pop_math_check(pop_ctx* c, int fn, int64_t n, const double* x, double* y, int mem)
 {
     if (!c) return POP_EINVAL;
-    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y)) || !valid_mem(mem))
+    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y)) || !valid_mem(mem))
         return fail(c, POP_EINVAL, "pop_math_check: bad arguments");
     if (n == 0) return POP_OK;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -506,7 +522,10 @@ int pop_math_check(pop_ctx* c, int fn, int64_t n, const double* x, double* y, in
         dx = bx.as<double>();
         dy = by.as<double>();
     }
-    CK(launch_math_check(fn, n, dx, dy, c->d_exptab.as<double2>(), c->expc, c->stream), "math_check");
+    if (fn <= 2)
+        CK(launch_math_check(fn, n, dx, dy, c->d_exptab.as<double2>(), c->expc, c->stream), "math_check");
+    else
+        CK(launch_ff_math_check(fn, n, dx, dy, c->d_fftab.as<float2>(), c->ffk, c->stream), "ff_math_check");
     if (mem == POP_MEM_HOST) {
         CK(cudaMemcpyAsync(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "copy y");
         CK(cudaStreamSynchronize(c->stream), "sync");
@@ -569,6 +588,11 @@ int pop_create(pop_ctx** out, int device, void* stream)
         e = c->d_exptab.alloc(sizeof(double2) * EXP_TABLE_SIZE);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d_exptab.p, tab.data(), sizeof(double2) * EXP_TABLE_SIZE, cudaMemcpyHostToDevice);
+        std::vector<float2> ftab(FF_TABLE_SIZE);
+        build_ff_table(ftab.data(), &c->ffk);
+        if (e == cudaSuccess) e = c->d_fftab.alloc(sizeof(float2) * FF_TABLE_SIZE);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_fftab.p, ftab.data(), sizeof(float2) * FF_TABLE_SIZE, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             pop_destroy(c);
             return fail(nullptr, e == cudaErrorMemoryAllocation ? POP_ENOMEM : POP_ECUDA,
@@ -690,13 +714,13 @@ int loglik_run(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
     if (K < 0) return fail(c, POP_EINVAL, w + ": K < 0");
     if (n_params != 11 + (c->ev.n_dims == 7))
         return fail(c, POP_EINVAL, w + ": n_params must be 11 (12 with redshift samples)");
-    if (mode != POP_MODE_F64 && mode != POP_MODE_F32 && mode != POP_MODE_F32_SURROGATE)
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32 && mode != POP_MODE_F32_SURROGATE && mode != POP_MODE_FF)
         return fail(c, POP_EINVAL, w + ": bad mode");
     if (mode == POP_MODE_F32_SURROGATE && (!c->sur || !c->sur->trained))
         return fail(c, POP_ESTATE, w + ": surrogate not trained (pop_xi_surrogate_train or _load)");
     if (mode == POP_MODE_F32_SURROGATE && c->sur->n_params != n_params)
         return fail(c, POP_EINVAL, w + ": the surrogate was trained for another n_params");
-    const int need = mode == POP_MODE_F64 ? POP_STORE_F64 : POP_STORE_F32;
+    const int need = (mode == POP_MODE_F64 || mode == POP_MODE_FF) ? POP_STORE_F64 : POP_STORE_F32;
     if (!(c->ev.storage & need) || (!use_grid && !(c->inj.storage & need)))
         return fail(c, POP_ESTATE, w + ": the loaded storage does not include this mode's precision");
     if (!valid_mem(mem)) return fail(c, POP_EINVAL, w + ": bad mem");
@@ -774,8 +798,8 @@ int pop_loglik_parts(pop_ctx* c, int64_t K, int n_params, const double* lambda, 
     if (!c) return POP_EINVAL;
     if (c->xi_source != POP_XI_INJECTIONS)
         return fail(c, POP_EINVAL, "pop_loglik_parts: needs the injection selection term");
-    if (mode != POP_MODE_F64 && mode != POP_MODE_F32)
-        return fail(c, POP_EINVAL, "pop_loglik_parts: mode must be POP_MODE_F64 or POP_MODE_F32");
+    if (mode != POP_MODE_F64 && mode != POP_MODE_F32 && mode != POP_MODE_FF)
+        return fail(c, POP_EINVAL, "pop_loglik_parts: mode must be POP_MODE_F64, POP_MODE_F32 or POP_MODE_FF");
     if (K > 0 && (!out_events || !out_sum_w || !out_sum_w2))
         return fail(c, POP_EINVAL, "pop_loglik_parts: an output is NULL");
     int rc = loglik_run(c, K, n_params, lambda, mode, mem, "pop_loglik_parts");

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "pop.h"
+#include "pop_ff.cuh"
 #include "pop_math.cuh"
 
 namespace pop {
@@ -128,6 +129,20 @@ struct SurrogateXi {
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
                               const LamF32* lam, const int32_t* order, const int32_t* n_mc, int64_t K_cap,
                               const int64_t* dK, double* part, double* part2, cudaStream_t s);
+// Float-float weight kernel (POP_MODE_FF): weight_ff_threads() Lambda per block, one per thread, with the
+// lane order of launch_lam_order (need_mc NULL); fftab = 2^(j/2048) as FP32 (hi, lo) pairs.
+const void* weight_ff_fn(bool has_z);
+int weight_ff_threads();
+cudaError_t launch_weight_ff(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam, const int32_t* order,
+                             const int32_t* n_mc, int64_t K_cap, const int64_t* dK, double* part, double* part2,
+                             const float2* fftab, FFConsts kc, cudaStream_t s);
+// Evaluates the float-float functions on x[n] (pairs of x packed as the kernel packs samples), each
+// result widened to hi + lo in FP64: fn 3 exp, 4 expm1 (series below |x| = 1/16), 5 reciprocal,
+// 6 square, 7 the exact square of the FP32 hi part (packed fma error term).
+cudaError_t launch_ff_math_check(int fn, int64_t n, const double* x, double* y, const float2* fftab, FFConsts kc,
+                                 cudaStream_t s);
+// Host: the FP32 (hi, lo) table of 2^(j/2048) and the reduction constants, in extended precision.
+void build_ff_table(float2* tab, FFConsts* kc);
 // Lane order of the FP32 weight kernel: Lambda by mmin; for the injection items the Lambda with
 // need_mc[k] != 0 first (all K when need_mc is NULL), their number in *n_mc.  order[2 K_cap].
 cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t* need_mc, int64_t K_cap,

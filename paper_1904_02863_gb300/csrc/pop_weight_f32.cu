@@ -28,6 +28,7 @@
 // cross-event sum are FP64 in the finalise kernel.
 #include <math.h>
 
+#include "pop_f32x2.cuh"
 #include "pop_internal.h"
 
 namespace pop {
@@ -46,69 +47,6 @@ struct F32Cfg {
     static constexpr int SP = NT >= 128 ? 256 : 2 * NT;
     static constexpr int MIN_BLOCKS = (32 * POP_F32_WARPS_PER_SM) / NT > 0 ? (32 * POP_F32_WARPS_PER_SM) / NT : 1;
 };
-
-// Two FP32 values in a 64-bit register pair (first sample in the low half).
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float a, float b)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-
-__device__ __forceinline__ void upk(f2 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-__device__ __forceinline__ float ex2f(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rcpf(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ f2 ex2_2(f2 x)
-{
-    float a, b;
-    upk(x, a, b);
-    return pk(ex2f(a), ex2f(b));
-}
-
-__device__ __forceinline__ f2 bc(float a) { return pk(a, a); }
 
 // One lane's Lambda, in the packed form of the pair arithmetic.
 struct LaneConsts {
