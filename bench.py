@@ -50,6 +50,10 @@ FP32_LANES_PER_SM = 128
 # in-support pair of the FP32 weight (4 ex2 + 1 rcp).
 MUFU_SLOTS_PER_SM = 32
 MUFU_SLOTS_PER_PAIR = 6
+# FP32 lane operations (FMA pipe) per in-support pair of the float-float weight kernel, from its
+# ncu capture (profiles/weight_ff_catalog400x4096_K1024_full.md): FMA pipe 64.6% of 53.99 M active
+# cycles x 128 lanes x 152 SMs over 1.718e9 in-support pairs.
+FF_OPS_PER_PAIR = 395
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
@@ -77,6 +81,17 @@ def in_support_pairs(theta, lam):
         total -= int(((m2[hi, None] >= a) & (m1[hi, None] > b)).sum())
         total -= int(((m2[tie, None] >= a) & (m1[tie, None] <= a)).sum())
     return total
+
+
+def ff_roofline(pairs, weight_ms):
+    """The float-float weight kernel against the FP32 FMA pipe (128 lanes per SM per clock): FF_OPS_PER_PAIR
+    FP32 lane operations per in-support pair, counted from the kernel's executed FMA-pipe instructions."""
+    peak = FP32_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6
+    achieved = FF_OPS_PER_PAIR * pairs / (weight_ms * 1e-3)
+    return {"bound": "alu", "kernel": "weight_ff_kernel", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "Top/s (FP32 FMA pipe)", "frac": achieved / peak, "traffic": None, "weight_ms": weight_ms,
+            "in_support_pairs": pairs, "ops_per_in_support_pair": FF_OPS_PER_PAIR,
+            "peak_basis": "128 FP32 lanes/SM/clk x 152 SMs x 2070 MHz"}
 
 
 def f32_roofline(pairs, weight_ms):
@@ -121,7 +136,8 @@ def parse():
     p.add_argument("--oracle-lambdas", type=int, default=32, help="Lambda rows in the CPU sample")
     p.add_argument("--events", type=int, default=1000, help="events (a smaller catalog for profiling captures)")
     p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
-    p.add_argument("--mode", default="both", choices=["both", "f64", "f32"])
+    p.add_argument("--mode", default="both", choices=["both", "f64", "f32", "ff"],
+                   help="both: the FP64 headline and every form; f64 / f32 / ff: that mode alone")
     p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc", "grad"],
                    help="c2: the metric's catalog workload (default); c4: ragged CSR + redshift, uneven batches")
     return p.parse_args()
@@ -229,7 +245,7 @@ def ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_pairs, n_events):
     ratio = float(np.max(np.abs(ffh[0][fin] - f64[0][fin]) / tol[fin])) if fin.any() else 0.0
     K = len(lam)
     return {"value": world * K * args.steps / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / args.steps,
-            "weight_ms": w, "dtype": "float-float (2 x f32)",
+            "weight_ms": w, "dtype": "float-float (2 x f32)", "roofline": ff_roofline(n_pairs, w),
             "max_dlnL_over_f64_tol": ratio, "flags_equal": bool((ffh[3] == f64[3]).all()),
             "in_support_pairs": n_pairs}
 
@@ -614,11 +630,13 @@ def main():
         ms = max_over_ranks(start.elapsed_time(stop), world)
         return ms, statistics.mean(wms)
 
-    head = B.POP_MODE_F32 if args.mode == "f32" else B.POP_MODE_F64
-    # Tiling from the autotuner (FP64 on the first 64 Lambda rows: its launches are long).
+    head = {"f32": B.POP_MODE_F32, "ff": B.POP_MODE_FF}.get(args.mode, B.POP_MODE_F64)
+    # Tiling from the autotuner (FP64 on the first 64 Lambda rows: its launches are long); the
+    # float-float kernel has one fixed tiling.
     for mode in ([head] if args.mode != "both" else [B.POP_MODE_F64, B.POP_MODE_F32]):
         B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
-        B.pop_autotune(like.ctx, mode, min(K, 64) if mode == B.POP_MODE_F64 else K)
+        if mode != B.POP_MODE_FF:
+            B.pop_autotune(like.ctx, mode, min(K, 64) if mode == B.POP_MODE_F64 else K)
     with Clocks(local) as clk:
         ms_h, w_h = timed(head)
         if args.mode == "both":
@@ -653,15 +671,18 @@ def main():
                     "in_support_pairs": n_ev_pairs + n_inj_pairs, "all_pairs": all_pairs,
                     "ops_per_in_support_pair": FP64_OPS_PER_PAIR,
                     "peak_basis": "2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz"}
-    else:
+    elif head == B.POP_MODE_F32:
         roofline = f32_roofline(n_ev_pairs + n_inj_pairs, w_h)
+    else:
+        roofline = ff_roofline(n_ev_pairs + n_inj_pairs, w_h)
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_h / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if head == B.POP_MODE_F64 else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {B.POP_MODE_F64: "f64", B.POP_MODE_F32: "f32"}.get(head, "float-float"),
+        "data": "synthetic",
         "config": {"workload": workload, "events": cat.n_events, "samples_per_event": 4096,
                    "n_draw": int(inj.n_draw), "n_found": int(inj.n_found), "K": K,
-                   "mode": "POP_MODE_F64" if head == B.POP_MODE_F64 else "POP_MODE_F32",
+                   "mode": {B.POP_MODE_F64: "POP_MODE_F64", B.POP_MODE_F32: "POP_MODE_F32"}.get(head, "POP_MODE_FF"),
                    "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (FP64 features 80 B/sample)",
                    "tiling_f64": B.pop_get_tiling(like.ctx, B.POP_MODE_F64),

@@ -99,7 +99,7 @@ struct pop_ctx {
     bool use_graphs = true;
     Graph graph[4];  // per mode: F64, F32, F32 + surrogate, float-float
     DevBuf d_need, d_slnxi, d_slnneff;  // surrogate mode: Monte Carlo mask, ln xi, ln N_eff per Lambda
-    DevBuf d_order, d_nmc;   // FP32 kernel: lane order of the Lambda [2][K_cap], Lambda needing the injections
+    DevBuf d_order, d_nmc;   // FP32 / float-float kernels: lane order [2][K_cap]; Lambda needing the injections, item queue
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts expc{};
@@ -293,7 +293,7 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     DevBuf need, slnxi, slnneff, order, nmc;
     CK(need.alloc(cap), "cudaMalloc(need)");
     CK(order.alloc(sizeof(int32_t) * 2 * cap), "cudaMalloc(order)");
-    CK(nmc.alloc(sizeof(int32_t)), "cudaMalloc(n_mc)");
+    CK(nmc.alloc(sizeof(int32_t) * 2), "cudaMalloc(n_mc)");
     CK(slnxi.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnxi)");
     CK(slnneff.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnneff)");
     c->d_need.swap(need);
@@ -1152,7 +1152,9 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
                 } else {
                     FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
                     FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
-                    e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
+                    e = cudaMemsetAsync(c->d_nmc.as<int32_t>() + 1, 0, sizeof(int32_t), c->stream);  // item queue
+                    if (e == cudaSuccess)
+                        e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
                                           c->d_nmc.as<int32_t>(), c->k_cap, c->d_K.as<int64_t>(),
                                           c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
                 }

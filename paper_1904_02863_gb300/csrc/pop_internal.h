@@ -124,17 +124,18 @@ struct SurrogateXi {
     const double* neff;
 };
 // FP32 weight kernel: one Lambda per thread, lambda_tile == block_threads Lambda per work item.
-// order[0, K) and order[K_cap, K_cap + *n_mc) are the Lambda of the event and injection items in
-// lane order (launch_lam_order); only the first *n_mc of the injection order get injection items.
+// order[0, K) and order[K_cap, K_cap + n_mc[0]) are the Lambda of the event and injection items in
+// lane order (launch_lam_order); only the first n_mc[0] of the injection order get injection items;
+// n_mc[1] is the item queue (zeroed by launch_lam_order).
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
-                              const LamF32* lam, const int32_t* order, const int32_t* n_mc, int64_t K_cap,
+                              const LamF32* lam, const int32_t* order, int32_t* n_mc, int64_t K_cap,
                               const int64_t* dK, double* part, double* part2, cudaStream_t s);
 // Float-float weight kernel (POP_MODE_FF): weight_ff_threads() Lambda per block, one per thread, with the
 // lane order of launch_lam_order (need_mc NULL); fftab = 2^(j/2048) as FP32 (hi, lo) pairs.
 const void* weight_ff_fn(bool has_z);
 int weight_ff_threads();
 cudaError_t launch_weight_ff(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam, const int32_t* order,
-                             const int32_t* n_mc, int64_t K_cap, const int64_t* dK, double* part, double* part2,
+                             int32_t* n_mc, int64_t K_cap, const int64_t* dK, double* part, double* part2,
                              const float2* fftab, FFConsts kc, cudaStream_t s);
 // Evaluates the float-float functions on x[n] (pairs of x packed as the kernel packs samples), each
 // result widened to hi + lo in FP64: fn 3 exp, 4 expm1 (series below |x| = 1/16), 5 reciprocal,
@@ -144,7 +145,8 @@ cudaError_t launch_ff_math_check(int fn, int64_t n, const double* x, double* y, 
 // Host: the FP32 (hi, lo) table of 2^(j/2048) and the reduction constants, in extended precision.
 void build_ff_table(float2* tab, FFConsts* kc);
 // Lane order of the FP32 weight kernel: Lambda by mmin; for the injection items the Lambda with
-// need_mc[k] != 0 first (all K when need_mc is NULL), their number in *n_mc.  order[2 K_cap].
+// need_mc[k] != 0 first (all K when need_mc is NULL), their number in n_mc[0]; n_mc[1] = 0 (the
+// weight kernel's item queue).  order[2 K_cap], n_mc[2].
 cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t* need_mc, int64_t K_cap,
                              int32_t* order, int32_t* n_mc, cudaStream_t s);
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ev_chunk_begin,
