@@ -99,7 +99,8 @@ struct pop_ctx {
     bool use_graphs = true;
     Graph graph[4];  // per mode: F64, F32, F32 + surrogate, float-float
     DevBuf d_need, d_slnxi, d_slnneff;  // surrogate mode: Monte Carlo mask, ln xi, ln N_eff per Lambda
-    DevBuf d_order, d_nmc;   // FP32 / float-float kernels: lane order [2][K_cap]; Lambda needing the injections, item queue
+    DevBuf d_order, d_nmc;   // FP32 / float-float kernels: lane order [2][K_cap]; Lambda needing the injections
+    DevBuf d_queue;          // the weight kernels' work-item counter
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts expc{};
@@ -290,15 +291,17 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     CK(neff.alloc(sizeof(double) * cap), "cudaMalloc(neff)");
     CK(flags.alloc(sizeof(uint32_t) * cap), "cudaMalloc(flags)");
     CK(dK.alloc(sizeof(int64_t)), "cudaMalloc(K)");
-    DevBuf need, slnxi, slnneff, order, nmc;
+    DevBuf need, slnxi, slnneff, order, nmc, queue;
     CK(need.alloc(cap), "cudaMalloc(need)");
     CK(order.alloc(sizeof(int32_t) * 2 * cap), "cudaMalloc(order)");
-    CK(nmc.alloc(sizeof(int32_t) * 2), "cudaMalloc(n_mc)");
+    CK(nmc.alloc(sizeof(int32_t)), "cudaMalloc(n_mc)");
+    CK(queue.alloc(sizeof(unsigned long long)), "cudaMalloc(queue)");
     CK(slnxi.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnxi)");
     CK(slnneff.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnneff)");
     c->d_need.swap(need);
     c->d_order.swap(order);
     c->d_nmc.swap(nmc);
+    c->d_queue.swap(queue);
     c->d_slnxi.swap(slnxi);
     c->d_slnneff.swap(slnneff);
     if (c->d_lambda.p)  // keep the last Lambda batch (the autotuner reuses it)
@@ -370,20 +373,20 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
         CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), nullptr, c->k_cap, c->d_order.as<int32_t>(),
                             c->d_nmc.as<int32_t>(), c->stream), "lambda order");
         CK(launch_weight_ff(grid, e, j, wd, c->d_c64.as<LamF64>(), c->d_order.as<int32_t>(), c->d_nmc.as<int32_t>(),
-                            c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(), c->d_part2.as<double>(),
+                            c->d_queue.as<unsigned long long>(), c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(), c->d_part2.as<double>(),
                             c->d_fftab.as<float2>(), c->ffk, c->stream), "weight_ff");
     } else if (m == 0) {
         FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
         CK(launch_weight_f64(c->tiling[0], grid, e, j, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                              c->d_part.as<double>(), c->d_part2.as<double>(), c->d_exptab.as<double2>(), c->expc,
-                             c->stream), "weight_f64");
+                             c->d_queue.as<unsigned long long>(), c->stream), "weight_f64");
     } else {
         FeatF32 e{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
         FeatF32 j{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
         CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), sx.need_mc, c->k_cap,
                             c->d_order.as<int32_t>(), c->d_nmc.as<int32_t>(), c->stream), "lambda order");
         CK(launch_weight_f32(c->tiling[1], grid, e, j, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
-                             c->d_nmc.as<int32_t>(), c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(),
+                             c->d_nmc.as<int32_t>(), c->d_queue.as<unsigned long long>(), c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(),
                              c->d_part2.as<double>(), c->stream), "weight_f32");
     }
     CK(cudaEventRecordWithFlags(c->ev_w1, c->stream, rec), "event");
@@ -1148,14 +1151,13 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
                     FeatF64 ev{c->ev.f64.as<double>(), c->ev.stride}, ij{c->inj.f64.as<double>(), c->inj.stride};
                     e = launch_weight_f64(t, grid, ev, ij, wd, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                                           c->d_part.as<double>(), c->d_part2.as<double>(),
-                                          c->d_exptab.as<double2>(), c->expc, c->stream);
+                                          c->d_exptab.as<double2>(), c->expc, c->d_queue.as<unsigned long long>(),
+                                          c->stream);
                 } else {
                     FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
                     FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
-                    e = cudaMemsetAsync(c->d_nmc.as<int32_t>() + 1, 0, sizeof(int32_t), c->stream);  // item queue
-                    if (e == cudaSuccess)
-                        e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
-                                          c->d_nmc.as<int32_t>(), c->k_cap, c->d_K.as<int64_t>(),
+                    e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
+                                          c->d_nmc.as<int32_t>(), c->d_queue.as<unsigned long long>(), c->k_cap, c->d_K.as<int64_t>(),
                                           c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);
                 }
                 if (e != cudaSuccess) {

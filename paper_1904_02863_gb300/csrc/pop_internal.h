@@ -108,9 +108,11 @@ cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_c
                             LamF64* c64, LamF32* c32, cudaStream_t s);
 // The FP64 weight kernel keeps the 2^(j/2048) table of its exponentials in dynamic shared memory.
 constexpr int WEIGHT_F64_DYN_SMEM = EXP_TABLE_SIZE * (int)sizeof(double2);
+// The weight kernels take their work items from *queue, which each launcher zeroes (a memset
+// on the stream) before the launch.
 cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd,
                               const LamF64* lam, const int64_t* dK, double* part, double* part2,
-                              const double2* exptab, ExpConsts kc, cudaStream_t s);
+                              const double2* exptab, ExpConsts kc, unsigned long long* queue, cudaStream_t s);
 // Evaluates the FP64 weight kernel's exp (fn 0), expm1 (fn 1) or reciprocal (fn 2) on x[n].
 cudaError_t launch_math_check(int fn, int64_t n, const double* x, double* y, const double2* exptab, ExpConsts kc,
                               cudaStream_t s);
@@ -124,19 +126,19 @@ struct SurrogateXi {
     const double* neff;
 };
 // FP32 weight kernel: one Lambda per thread, lambda_tile == block_threads Lambda per work item.
-// order[0, K) and order[K_cap, K_cap + n_mc[0]) are the Lambda of the event and injection items in
-// lane order (launch_lam_order); only the first n_mc[0] of the injection order get injection items;
-// n_mc[1] is the item queue (zeroed by launch_lam_order).
+// order[0, K) and order[K_cap, K_cap + *n_mc) are the Lambda of the event and injection items in
+// lane order (launch_lam_order); only the first *n_mc of the injection order get injection items.
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd,
-                              const LamF32* lam, const int32_t* order, int32_t* n_mc, int64_t K_cap,
-                              const int64_t* dK, double* part, double* part2, cudaStream_t s);
+                              const LamF32* lam, const int32_t* order, const int32_t* n_mc,
+                              unsigned long long* queue, int64_t K_cap, const int64_t* dK, double* part,
+                              double* part2, cudaStream_t s);
 // Float-float weight kernel (POP_MODE_FF): weight_ff_threads() Lambda per block, one per thread, with the
 // lane order of launch_lam_order (need_mc NULL); fftab = 2^(j/2048) as FP32 (hi, lo) pairs.
 const void* weight_ff_fn(bool has_z);
 int weight_ff_threads();
 cudaError_t launch_weight_ff(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam, const int32_t* order,
-                             int32_t* n_mc, int64_t K_cap, const int64_t* dK, double* part, double* part2,
-                             const float2* fftab, FFConsts kc, cudaStream_t s);
+                             const int32_t* n_mc, unsigned long long* queue, int64_t K_cap, const int64_t* dK,
+                             double* part, double* part2, const float2* fftab, FFConsts kc, cudaStream_t s);
 // Evaluates the float-float functions on x[n] (pairs of x packed as the kernel packs samples), each
 // result widened to hi + lo in FP64: fn 3 exp, 4 expm1 (series below |x| = 1/16), 5 reciprocal,
 // 6 square, 7 the exact square of the FP32 hi part (packed fma error term).
@@ -145,8 +147,7 @@ cudaError_t launch_ff_math_check(int fn, int64_t n, const double* x, double* y, 
 // Host: the FP32 (hi, lo) table of 2^(j/2048) and the reduction constants, in extended precision.
 void build_ff_table(float2* tab, FFConsts* kc);
 // Lane order of the FP32 weight kernel: Lambda by mmin; for the injection items the Lambda with
-// need_mc[k] != 0 first (all K when need_mc is NULL), their number in n_mc[0]; n_mc[1] = 0 (the
-// weight kernel's item queue).  order[2 K_cap], n_mc[2].
+// need_mc[k] != 0 first (all K when need_mc is NULL), their number in *n_mc.  order[2 K_cap].
 cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t* need_mc, int64_t K_cap,
                              int32_t* order, int32_t* n_mc, cudaStream_t s);
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ev_chunk_begin,

@@ -279,7 +279,8 @@ __device__ __forceinline__ void stage(const FeatF32& F, const Chunk& ch, int st,
 template <int NT, bool HAS_Z>
 __global__ void __launch_bounds__(NT, F32Cfg<NT>::MIN_BLOCKS)
 weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
-                  const int32_t* __restrict__ order, int32_t* __restrict__ n_mc, int64_t K_cap,
+                  const int32_t* __restrict__ order, const int32_t* __restrict__ n_mc,
+                  unsigned long long* __restrict__ queue, int64_t K_cap,
                   const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
 {
     constexpr int SP = F32Cfg<NT>::SP;
@@ -295,14 +296,14 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
     const int64_t n_items = n_ev_items + (int64_t)n_inj_chunks * tiles_inj;
     const int lane = threadIdx.x & 31;
 
-    // Items are taken from a queue (n_mc[1], reset by the Lambda order kernel): their costs differ
-    // (event and injection chunks, lower edges), and blocks that finish early take more.
-    __shared__ int s_item;
+    // Items come from a queue (zeroed before the launch): their costs differ (event and injection
+    // chunks, lower edges), and blocks that finish early take more.
+    __shared__ unsigned long long s_item;
     for (;;) {
         __syncthreads();  // every thread has read the previous item
-        if (threadIdx.x == 0) s_item = atomicAdd(n_mc + 1, 1);
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1ull);
         __syncthreads();
-        const int64_t item = s_item;
+        const int64_t item = (int64_t)s_item;
         if (item >= n_items) break;
         int c;
         int64_t tile;
@@ -426,9 +427,8 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot)
 
 // order[0, K): the Lambda by increasing mmin (1024 equal bins over the batch's range,
 // invalid Lambda last).  order[K_cap, K_cap + K): the same with the Lambda that need the
-// Monte Carlo xi (need_mc[k] != 0) first; n_mc[0] = their number (K without need_mc), and
-// n_mc[1] = 0 starts the weight kernel's item queue.  The order within a bin is arbitrary: it
-// only decides which lane evaluates which Lambda.
+// Monte Carlo xi (need_mc[k] != 0) first; *n_mc = their number (K without need_mc).  The order
+// within a bin is arbitrary: it only decides which lane evaluates which Lambda.
 __global__ void __launch_bounds__(ORDER_THREADS)
 lam_order_kernel(const LamF32* __restrict__ lam, const int64_t* __restrict__ dK, const uint8_t* __restrict__ need_mc,
                  int64_t K_cap, int32_t* __restrict__ order, int32_t* __restrict__ n_mc)
@@ -496,10 +496,7 @@ lam_order_kernel(const LamF32* __restrict__ lam, const int64_t* __restrict__ dK,
         order[atomicAdd(&h_ev[b], 1)] = k;
         order[K_cap + atomicAdd(&h_inj[(need_mc == nullptr || need_mc[k]) ? b : ORDER_BINS + b], 1)] = k;
     }
-    if (threadIdx.x == 0) {
-        n_mc[0] = cnt;
-        n_mc[1] = 0;  // the weight kernel's item queue
-    }
+    if (threadIdx.x == 0) *n_mc = cnt;
 }
 
 }  // namespace
@@ -525,12 +522,14 @@ cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t
 }
 
 cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* lam,
-                              const int32_t* order, int32_t* n_mc, int64_t K_cap, const int64_t* dK,
-                              double* part, double* part2, cudaStream_t s)
+                              const int32_t* order, const int32_t* n_mc, unsigned long long* queue, int64_t K_cap,
+                              const int64_t* dK, double* part, double* part2, cudaStream_t s)
 {
     const void* fn = weight_f32_fn(t, wd.has_z != 0);
     if (!fn) return cudaErrorInvalidValue;
-    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &K_cap, &dK, &part, &part2};
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &queue, &K_cap, &dK, &part, &part2};
     return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, 0, s);
 }
 

@@ -95,7 +95,7 @@ template <int T, int NT, bool HAS_Z>
 __global__ void __launch_bounds__(NT)
 weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict__ lam,
                   const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2,
-                  const double2* __restrict__ exptab, ExpConsts kc)
+                  const double2* __restrict__ exptab, ExpConsts kc, unsigned long long* __restrict__ queue)
 {
     extern __shared__ double2 stab[];  // EXP_TABLE_SIZE entries (dynamic shared memory)
     __shared__ LamF64 sl[T];
@@ -108,11 +108,18 @@ weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict
     const int n_inj_chunks = wd.n_chunks - wd.n_ev_chunks;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    // Items come from a queue (zeroed before the launch), in chunk-major order, so a chunk's
+    // Lambda tiles still run together; blocks that finish early take more.
+    __shared__ unsigned long long s_item;
+    for (;;) {
+        __syncthreads();  // the previous item is done with sl / red / s_item
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1ull);
+        __syncthreads();
+        const int64_t item = (int64_t)s_item;
+        if (item >= n_items) break;
         const int c = (int)(item / n_tiles);
         const int64_t k0 = (item - (int64_t)c * n_tiles) * T;
         const int tn = (int)(K - k0 < T ? K - k0 : T);
-        __syncthreads();  // the previous item is done with sl / red
         {
             constexpr int W = (int)(sizeof(LamF64) / 8);
             double* dst = reinterpret_cast<double*>(sl);
@@ -209,11 +216,13 @@ const void* weight_f64_fn(const Tiling& t, bool has_z)
 
 cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam,
                               const int64_t* dK, double* part, double* part2, const double2* exptab,
-                              ExpConsts kc, cudaStream_t s)
+                              ExpConsts kc, unsigned long long* queue, cudaStream_t s)
 {
     const void* fn = weight_f64_fn(t, wd.has_z != 0);
     if (!fn) return cudaErrorInvalidValue;
-    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2, &exptab, &kc};
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&ev, &inj, &wd, &lam, &dK, &part, &part2, &exptab, &kc, &queue};
     return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, WEIGHT_F64_DYN_SMEM, s);
 }
 

@@ -349,7 +349,8 @@ __device__ __forceinline__ double ff_total(const ff2& s)
 template <bool HAS_Z>
 __global__ void __launch_bounds__(FF_NT, FF_MIN_BLOCKS)
 weight_ff_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict__ lam,
-                 const int32_t* __restrict__ order, int32_t* __restrict__ n_mc, int64_t K_cap,
+                 const int32_t* __restrict__ order, const int32_t* __restrict__ n_mc,
+                  unsigned long long* __restrict__ queue, int64_t K_cap,
                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2,
                  const float2* __restrict__ fftab, FFConsts kc)
 {
@@ -370,14 +371,14 @@ weight_ff_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict_
     const int lane = threadIdx.x & 31;
     const FFSeries ser = ff_series_consts();
 
-    // Items are taken from a queue (n_mc[1], reset by the Lambda order kernel): their costs differ
-    // (event and injection chunks, lower edges), and blocks that finish early take more.
-    __shared__ int s_item;
+    // Items come from a queue (zeroed before the launch): their costs differ (event and injection
+    // chunks, lower edges), and blocks that finish early take more.
+    __shared__ unsigned long long s_item;
     for (;;) {
         __syncthreads();  // every thread has read the previous item
-        if (threadIdx.x == 0) s_item = atomicAdd(n_mc + 1, 1);
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1ull);
         __syncthreads();
-        const int64_t item = s_item;
+        const int64_t item = (int64_t)s_item;
         if (item >= n_items) break;
         int c;
         int64_t tile;
@@ -510,11 +511,13 @@ const void* weight_ff_fn(bool has_z)
 int weight_ff_threads() { return FF_NT; }
 
 cudaError_t launch_weight_ff(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* lam, const int32_t* order,
-                             int32_t* n_mc, int64_t K_cap, const int64_t* dK, double* part, double* part2,
-                             const float2* fftab, FFConsts kc, cudaStream_t s)
+                             const int32_t* n_mc, unsigned long long* queue, int64_t K_cap, const int64_t* dK,
+                             double* part, double* part2, const float2* fftab, FFConsts kc, cudaStream_t s)
 {
     const void* fn = weight_ff_fn(wd.has_z != 0);
-    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &K_cap, &dK, &part, &part2, &fftab, &kc};
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &queue, &K_cap, &dK, &part, &part2, &fftab, &kc};
     return cudaLaunchKernel(fn, dim3(grid), dim3(FF_NT), args, 0, s);
 }
 
