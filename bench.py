@@ -57,9 +57,9 @@ FF_OPS_PER_PAIR = 395
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
-# profiles/weight_f64_catalog400x4096_K64_full.md (174.22 MB / 2,077,126 units); a launch
+# profiles/weight_f64_catalog400x4096_K64_full.md (155.20 MB / 2,077,126 units); a launch
 # reads every chunk from DRAM once, so traffic scales with the units.
-F64_DRAM_BYTES_PER_UNIT = 174.22e6 / 2077126
+F64_DRAM_BYTES_PER_UNIT = 155.20e6 / 2077126
 
 
 def in_support_pairs(theta, lam):
