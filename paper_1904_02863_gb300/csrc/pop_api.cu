@@ -875,7 +875,7 @@ int pop_loglik_grad(pop_ctx* c, int64_t K, int n_params, const double* lambda, d
     CK(cudaEventRecord(c->ev_w0, c->stream), "event");
     CK(launch_grad_weight(grad_grid_size(c->sm_count), e, j, wd, c->d_lamg.p, c->d_K.as<int64_t>(), n_params,
                           c->d_gpart.as<double>(), c->d_part2.as<double>(), c->d_exptab.as<double2>(), c->expc,
-                          c->stream),
+                          c->d_queue.as<unsigned long long>(), c->stream),
        "grad weight");
     CK(cudaEventRecord(c->ev_w1, c->stream), "event");
     CK(launch_grad_finalise(c->d_gpart.as<double>(), c->d_part2.as<double>(), c->d_ecb.as<int32_t>(),

@@ -271,7 +271,8 @@ template <bool HAS_Z>
 __global__ void __launch_bounds__(GRAD_THREADS)
 grad_weight_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamG* __restrict__ lam,
                    const int64_t* __restrict__ dK, int n_params, double* __restrict__ part,
-                   double* __restrict__ part2, const double2* __restrict__ exptab, ExpConsts kc)
+                   double* __restrict__ part2, const double2* __restrict__ exptab, ExpConsts kc,
+                   unsigned long long* __restrict__ queue)
 {
     extern __shared__ double2 stab[];
     __shared__ double red[GRAD_THREADS / 32][NG + 1];
@@ -281,10 +282,17 @@ grad_weight_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamG* __restrict_
     const int64_t n_items = (int64_t)wd.n_chunks * K;
     const int n_inj = wd.n_chunks - wd.n_ev_chunks;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    // Items come from a queue (zeroed before the launch), chunk-major, so a chunk's Lambda run
+    // together; blocks that finish early take more.
+    __shared__ unsigned long long s_item;
+    for (;;) {
+        __syncthreads();  // the previous item is done with scl, red and s_item
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1ull);
+        __syncthreads();
+        const int64_t item = (int64_t)s_item;
+        if (item >= n_items) break;
         const int c = (int)(item / K);
         const int64_t k = item - (int64_t)c * K;
-        __syncthreads();  // the previous item is done with scl and red
         {
             constexpr int W = (int)(sizeof(LamG) / 8);
             for (int i = threadIdx.x; i < W; i += GRAD_THREADS)
@@ -435,15 +443,17 @@ cudaError_t launch_grad_prologue(const double* lambda, const int64_t* dK, int64_
 
 cudaError_t launch_grad_weight(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const void* lam_g, const int64_t* dK,
                                int n_params, double* part, double* part2, const double2* exptab, ExpConsts kc,
-                               cudaStream_t s)
+                               unsigned long long* queue, cudaStream_t s)
 {
     const LamG* lg = static_cast<const LamG*>(lam_g);
+    const cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     if (wd.has_z)
         grad_weight_kernel<true><<<grid, GRAD_THREADS, WEIGHT_F64_DYN_SMEM, s>>>(ev, inj, wd, lg, dK, n_params, part,
-                                                                               part2, exptab, kc);
+                                                                               part2, exptab, kc, queue);
     else
         grad_weight_kernel<false><<<grid, GRAD_THREADS, WEIGHT_F64_DYN_SMEM, s>>>(ev, inj, wd, lg, dK, n_params, part,
-                                                                                part2, exptab, kc);
+                                                                                part2, exptab, kc, queue);
     return cudaGetLastError();
 }
 

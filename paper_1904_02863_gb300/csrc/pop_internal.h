@@ -166,7 +166,7 @@ cudaError_t launch_grad_prologue(const double* lambda, const int64_t* dK, int64_
                                  cudaStream_t s);
 cudaError_t launch_grad_weight(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const void* lam_g, const int64_t* dK,
                                int n_params, double* part, double* part2, const double2* exptab, ExpConsts kc,
-                               cudaStream_t s);
+                               unsigned long long* queue, cudaStream_t s);
 cudaError_t launch_grad_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,
                                  int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
                                  const void* lam_g, const int64_t* dK, int64_t K_cap, int n_params, double* lnL,
