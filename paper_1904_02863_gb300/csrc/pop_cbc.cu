@@ -22,6 +22,7 @@
 
 #include "pop.h"
 #include "pop_cbc.h"
+#include "pop_f32x2.cuh"
 
 namespace pop {
 
@@ -201,6 +202,69 @@ cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __r
             ei[t] = ni;
         }
     };
+    if constexpr (sizeof(T) == 4) {
+        // FP32: rows (2p, 2p+1) in the halves of packed f32x2 registers, the bin's P and Q
+        // broadcast to both halves; the same fmas as the scalar path, one instruction per pair.
+        constexpr int TP = TK / 2;
+        f2 a2[TP][4], w2r[TP], w2i[TP], w2n[TP];
+#pragma unroll
+        for (int q = 0; q < TP; ++q) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a2[q][c] = 0ull;
+            w2r[q] = pk(wr[2 * q], wr[2 * q + 1]);
+            w2i[q] = pk(wi[2 * q], wi[2 * q + 1]);
+            w2n[q] = pk(-wi[2 * q], -wi[2 * q + 1]);
+        }
+        auto step2 = [&](const float (&v)[4], f2 (&e2r)[TP], f2 (&e2i)[TP]) {
+            const f2 b0 = bc(v[0]), b1 = bc(v[1]), n1 = bc(-v[1]), b2 = bc(v[2]), b3 = bc(v[3]), n3 = bc(-v[3]);
+#pragma unroll
+            for (int q = 0; q < TP; ++q) {
+                a2[q][0] = fma2(b0, e2r[q], fma2(n1, e2i[q], a2[q][0]));
+                a2[q][1] = fma2(b0, e2i[q], fma2(b1, e2r[q], a2[q][1]));
+                a2[q][2] = fma2(b2, e2r[q], fma2(n3, e2i[q], a2[q][2]));
+                a2[q][3] = fma2(b2, e2i[q], fma2(b3, e2r[q], a2[q][3]));
+                const f2 nr = fma2(e2r[q], w2r[q], mul2(e2i[q], w2n[q]));
+                const f2 ni = fma2(e2r[q], w2i[q], mul2(e2i[q], w2r[q]));
+                e2r[q] = nr;
+                e2i[q] = ni;
+            }
+        };
+        for (int64_t j0 = j_begin + (int64_t)threadIdx.x * RUN; j0 < j_end; j0 += (int64_t)CBC_THREADS * RUN) {
+            float er[TK], ei[TK];
+            f2 e2r[TP], e2i[TP];
+            if (j_end - j0 >= RUN) {
+                float v[RUN][4];
+#pragma unroll
+                for (int r = 0; r < RUN; ++r) load_pq<float>(base + j0 + r, v[r]);
+#pragma unroll
+                for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
+#pragma unroll
+                for (int q = 0; q < TP; ++q) {
+                    e2r[q] = pk(er[2 * q], er[2 * q + 1]);
+                    e2i[q] = pk(ei[2 * q], ei[2 * q + 1]);
+                }
+#pragma unroll
+                for (int r = 0; r < RUN; ++r) step2(v[r], e2r, e2i);
+            } else {
+#pragma unroll
+                for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
+#pragma unroll
+                for (int q = 0; q < TP; ++q) {
+                    e2r[q] = pk(er[2 * q], er[2 * q + 1]);
+                    e2i[q] = pk(ei[2 * q], ei[2 * q + 1]);
+                }
+                for (int r = 0; r < (int)(j_end - j0); ++r) {
+                    float v[4];
+                    load_pq<float>(base + j0 + r, v);
+                    step2(v, e2r, e2i);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < TP; ++q)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) upk(a2[q][c], acc[2 * q][c], acc[2 * q + 1][c]);
+    } else
     for (int64_t j0 = j_begin + (int64_t)threadIdx.x * RUN; j0 < j_end; j0 += (int64_t)CBC_THREADS * RUN) {
         T er[TK], ei[TK];
         if (j_end - j0 >= RUN) {

@@ -32,7 +32,11 @@ namespace {
 
 constexpr int FF_NT = 128;        // threads per block = Lambda per work item
 constexpr int FF_SP = 64;         // sample pairs per staged sub-tile
-constexpr int FF_MIN_BLOCKS = 3;  // register budget: 170 per thread
+// Resident blocks per SM the register budget is set for (65536 / (128 x this) per thread).
+#ifndef POP_FF_MIN_BLOCKS
+#define POP_FF_MIN_BLOCKS 4
+#endif
+constexpr int FF_MIN_BLOCKS = POP_FF_MIN_BLOCKS;
 
 // Staged pair (8-byte words): word 2f = hi parts (sample a, sample b) and word 2f + 1 = lo
 // parts of feature f = ln m1, m1, ln q, s_a, s_b, d_c, -ln pi (f = 0..6); words 14, 15 = the
