@@ -4,7 +4,9 @@
 //
 // GEMM: C[M x N] = A[M x K] . B[N x K]^T with A and B K-major BF16 in global
 // memory, M a multiple of 128 (one CTA per 128 rows = 128 TMEM lanes), N a
-// multiple of 16 up to 256 (FP32 accumulator columns), K a multiple of 64.
+// multiple of 16 up to 256 (FP32 accumulator columns), K a multiple of 64.  A CTA
+// takes 64 of the N columns when N is a multiple of 64 (all of them otherwise), so
+// the network's small batches still spread over many SMs.
 // Each 64-wide K stage is copied into shared memory in the no-swizzle
 // core-matrix layout (8 rows x 16 bytes per 128-byte core matrix; 128 bytes to
 // the next core matrix along K, 1024 bytes to the next 8-row group), one thread
@@ -43,6 +45,9 @@ constexpr int WAIT_LIMIT = 1 << 20;
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_F32 = 2 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Columns per CTA of a GEMM with N columns (both the kernel and its launcher use this).
+__host__ __device__ __forceinline__ int gemm_bn(int N) { return N % 64 == 0 ? 64 : N; }
 
 // tcgen05 shared-memory matrix descriptor: start address, leading (K) and stride
 // (8-row group) byte offsets, descriptor version 1, no swizzle.
@@ -160,6 +165,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + TC_SMEM_A + TC_SMEM_B + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_BM;
+    const int bn = gemm_bn(g.N);
+    const int n0 = blockIdx.z * bn;
     const int kbeg = blockIdx.y * g.k_split;
     const int kend = min(g.K, kbeg + g.k_split);
 
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = idesc_bf16(TC_BM, g.N);
+    const uint32_t idesc = idesc_bf16(TC_BM, bn);
     uint32_t parity = 0;
     int failed = 0;
     for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
@@ -178,9 +185,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
             const uint4 v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + kg * 8);
             *reinterpret_cast<uint4*>(sA + (r >> 3) * CM_SBO + kg * CM_LBO + (r & 7) * 16) = v;
         }
-        for (int i = tid; i < g.N * 8; i += TC_THREADS) {
+        for (int i = tid; i < bn * 8; i += TC_THREADS) {
             const int r = i >> 3, kg = i & 7;
-            const uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)r * g.ldb + k0 + kg * 8);
+            const uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)(n0 + r) * g.ldb + k0 + kg * 8);
             *reinterpret_cast<uint4*>(sB + (r >> 3) * CM_SBO + kg * CM_LBO + (r & 7) * 16) = v;
         }
         fence_proxy_async();  // make the generic-proxy stores visible to the tensor cores
@@ -202,26 +209,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
     if (!failed) {
         const int row = m0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < g.N; c0 += 16) {
+        // Each thread owns one row: 16 consecutive columns per step, stored as 16-byte vectors
+        // (the leading dimensions are multiples of 16 elements).
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+            const int col = n0 + c0;
             float v[16];
             tmem_ld16(trow + (uint32_t)c0, v);
             if (g.epi == EPI_FWD) {
+                float z[16];
+                __align__(16) bf16 hb[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float z = v[j] + g.bias[c0 + j];
-                    g.Z[(size_t)row * g.ldz + c0 + j] = z;
-                    g.H[(size_t)row * g.ldh + c0 + j] = __float2bfloat16(siluf_(z));
+                    z[j] = v[j] + g.bias[col + j];
+                    hb[j] = __float2bfloat16(siluf_(z[j]));
                 }
+                float4* zd = reinterpret_cast<float4*>(g.Z + (size_t)row * g.ldz + col);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) zd[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+                uint4* hd = reinterpret_cast<uint4*>(g.H + (size_t)row * g.ldh + col);
+                hd[0] = reinterpret_cast<const uint4*>(hb)[0];
+                hd[1] = reinterpret_cast<const uint4*>(hb)[1];
             } else if (g.epi == EPI_BWD) {
+                const float4* zs = reinterpret_cast<const float4*>(g.Z + (size_t)row * g.ldz + col);
+                __align__(16) bf16 hb[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float z = g.Z[(size_t)row * g.ldz + c0 + j];
-                    g.H[(size_t)row * g.ldh + c0 + j] = __float2bfloat16(v[j] * dsiluf_(z));
+                for (int q = 0; q < 4; ++q) {
+                    const float4 z = zs[q];
+                    hb[4 * q] = __float2bfloat16(v[4 * q] * dsiluf_(z.x));
+                    hb[4 * q + 1] = __float2bfloat16(v[4 * q + 1] * dsiluf_(z.y));
+                    hb[4 * q + 2] = __float2bfloat16(v[4 * q + 2] * dsiluf_(z.z));
+                    hb[4 * q + 3] = __float2bfloat16(v[4 * q + 3] * dsiluf_(z.w));
                 }
+                uint4* hd = reinterpret_cast<uint4*>(g.H + (size_t)row * g.ldh + col);
+                hd[0] = reinterpret_cast<const uint4*>(hb)[0];
+                hd[1] = reinterpret_cast<const uint4*>(hb)[1];
             } else {
-                float* C = g.C + blockIdx.y * g.c_split_stride;
+                float4* cd = reinterpret_cast<float4*>(g.C + blockIdx.y * g.c_split_stride + (size_t)row * g.ldc + col);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) C[(size_t)row * g.ldc + c0 + j] = v[j];
+                for (int q = 0; q < 4; ++q) cd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         }
     } else {
@@ -243,7 +268,9 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t s)
     if (g.M % TC_BM || g.N % 16 || g.N > 256 || g.N < 16 || g.K % TC_BK || g.k_split % TC_BK || g.k_split <= 0 ||
         (int64_t)g.k_split * k_splits < g.K || (int64_t)g.k_split * (k_splits - 1) >= g.K)
         return cudaErrorInvalidValue;
-    gemm_tc_kernel<<<dim3(g.M / TC_BM, k_splits), TC_THREADS, TC_SMEM_LAUNCH, s>>>(g);
+    if (g.ldb % 8 || (g.epi == EPI_F32 ? g.ldc : g.ldz) % 16 || (g.epi != EPI_F32 && g.ldh % 16))
+        return cudaErrorInvalidValue;  // the 16-byte loads and stores need these strides
+    gemm_tc_kernel<<<dim3(g.M / TC_BM, k_splits, g.N / gemm_bn(g.N)), TC_THREADS, TC_SMEM_LAUNCH, s>>>(g);
     return cudaGetLastError();
 }
 
