@@ -138,8 +138,9 @@ def parse():
     p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
     p.add_argument("--mode", default="both", choices=["both", "f64", "f32", "ff"],
                    help="both: the FP64 headline and every form; f64 / f32 / ff: that mode alone")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc", "grad"],
-                   help="c2: the metric's catalog workload (default); c4: ragged CSR + redshift, uneven batches")
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc", "grad", "sampler"],
+                   help="c2: the metric's catalog workload (default); c4: ragged CSR + redshift, uneven batches; "
+                        "sampler: the stretch-move ensemble sampler driving FP32 ln L on the c2 catalog")
     return p.parse_args()
 
 
@@ -458,6 +459,45 @@ def run_cbc(args, B, rank, local, world):
         print(json.dumps(line, default=_jsonable), flush=True)
 
 
+def run_sampler(args, B, rank, local, world):
+    """The ensemble sampler over Lambda on the catalog workload: 2048 walkers, each half-step one
+    batch of 1024 proposals through pop_loglik (FP32 weights), from Python with host arrays.
+    One step = one sweep of both halves; value = proposals evaluated per second, host time
+    around the whole loop (proposal arithmetic, copies and the GPU pipeline)."""
+    import torch
+    from paper_1904_02863_gb300 import sampler
+    cat, inj, _ = synth.make_workload(WORKLOAD, scale=args.events / 1000.0)
+    like = B.Likelihood(local, torch.cuda.current_stream(local)).load(cat, inj, storage=B.POP_STORE_F32)
+    box = synth.LAMBDA_BOX[:11]
+    log_prob = sampler.population_log_posterior(like, box[:, 0], box[:, 1], mode=B.POP_MODE_F32)
+    W = 2048
+    p0 = synth.make_lambdas(W, 11, seed=synth.seed_for(2, 2) + 7919 * rank)
+    chain, _, _ = sampler.stretch_sample(log_prob, p0, max(args.warmup, 1), seed=11 + rank)
+    p0 = chain[-1]
+    torch.cuda.synchronize()
+    barrier(world)
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        chain, lps, acc = sampler.stretch_sample(log_prob, p0, args.steps, seed=12 + rank)
+        torch.cuda.synchronize()
+        wall = max_over_ranks(time.perf_counter() - t0, world)
+    evals = world * args.steps * W
+    line = {"metric": "ensemble-sampler proposals evaluated/s (stretch move, 2048 walkers, FP32 ln L, 1000 x 4096 catalog)",
+            "value": evals / wall, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sampler_c2", "walkers": W, "batch_per_half_step": W // 2,
+                       "events": cat.n_events, "n_found": int(inj.n_found), "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (FP32 features 44 B/sample)"},
+            "acceptance": float(acc.mean()),
+            "e2e": {"value": evals / wall, "unit": "proposals/s", "h2d_bytes_per_step": 2 * (W // 2) * 11 * 8,
+                    "d2h_bytes_per_step": 2 * (W // 2) * 28},
+            "gpu_launches": 2 * 5 * args.steps, "clocks": clk.summary()}
+    like.close()
+    if rank == 0:
+        print(json.dumps(line, default=_jsonable), flush=True)
+
+
 def run_grad(args, B, rank, local, world):
     """ln L and its gradient alone, on the catalog workload (--events, --K as for the headline)."""
     import torch
@@ -597,6 +637,9 @@ def main():
         return
     if args.workload == "grad":
         run_grad(args, B, rank, local, world)
+        return
+    if args.workload == "sampler":
+        run_sampler(args, B, rank, local, world)
         return
 
     scale = args.events / 1000.0
