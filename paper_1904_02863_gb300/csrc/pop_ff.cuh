@@ -86,6 +86,38 @@ __device__ __forceinline__ ff2 ff_fma(ff2 x, ff2 c, ff2 y, f2 z) { return ff_add
 
 __device__ __forceinline__ ff2 ff_neg(ff2 x) { return ff2{sub2(0ull, x.hi), sub2(0ull, x.lo)}; }
 
+// A compensated sum of products and float-float terms (Ogita, Rump and Oishi's Dot2, SIAM J.
+// Sci. Comput. 26 (2005) 1955-1988, with float-float inputs): s is the running FP32 sum of the
+// terms' leading parts, kept by two-sums; c collects every rounding error and every lower-order
+// part, in FP32.  ff() renormalises once at the end.  Error: a few 2^-48 of the sum of the
+// terms' magnitudes, as a chain of float-float additions, with fewer operations.
+struct FFAcc {
+    f2 s, c;
+};
+
+__device__ __forceinline__ FFAcc acc_of(ff2 x) { return FFAcc{x.hi, x.lo}; }
+
+// a + x
+__device__ __forceinline__ FFAcc acc_add(FFAcc a, ff2 x)
+{
+    const ff2 t = two_sum2(a.s, x.hi);
+    return FFAcc{t.hi, add2(a.c, add2(t.lo, x.lo))};
+}
+
+// a + x y: the product's leading part fl(x.hi y.hi) enters the two-sum, its exact error and the
+// cross terms x.hi y.lo + x.lo y.hi go to c.
+__device__ __forceinline__ FFAcc acc_add_prod(FFAcc a, ff2 x, ff2 y, f2 z)
+{
+    const f2 p = prod2(x.hi, y.hi, z);
+    f2 e = fma2(x.hi, y.hi, sub2(0ull, p));
+    e = fma2(x.hi, y.lo, e);
+    e = fma2(x.lo, y.hi, e);
+    const ff2 t = two_sum2(a.s, p);
+    return FFAcc{t.hi, add2(a.c, add2(t.lo, e))};
+}
+
+__device__ __forceinline__ ff2 acc_ff(FFAcc a) { return fast_two_sum2(a.s, a.c); }
+
 // 1/x for normal x of either sign: the hardware seed y0 and one Newton step in float-float,
 // y = y0 + y0 (1 - x y0) (relative error about the square of the seed's, 2e-14, plus rounding).
 __device__ __forceinline__ ff2 ff_rcp(ff2 x, f2 z)

@@ -108,15 +108,16 @@ struct FFArgs {
 template <bool HAS_Z>
 __device__ __forceinline__ FFArgs ff_args(const FFPair& x, const FFLane& c, f2 z)
 {
-    ff2 aE = ff_fma(x.lq, c.beta, x.nlpi, z);
-    aE = ff_fma(x.sa, c.ac, aE, z);
-    aE = ff_fma(x.sb, c.bc_, aE, z);
-    if (HAS_Z) aE = ff_fma(x.lz1, c.km1, aE, z);
+    // aE as one compensated sum, shared by A and B, each then closed with its own terms.
+    FFAcc aE = acc_add_prod(acc_of(x.nlpi), x.lq, c.beta, z);
+    aE = acc_add_prod(aE, x.sa, c.ac, z);
+    aE = acc_add_prod(aE, x.sb, c.bc_, z);
+    if (HAS_Z) aE = acc_add_prod(aE, x.lz1, c.km1, z);
     FFArgs a;
-    a.A = ff_fma(x.lm1, c.nalpha, ff_add(aE, c.cpl), z);
+    a.A = acc_ff(acc_add_prod(acc_add(aE, c.cpl), x.lm1, c.nalpha, z));
     const ff2 d = ff_add(x.m1, c.nmu);
-    a.B = ff_add(ff_mul(ff_mul(d, c.nh, z), d, z), ff_add(aE, c.cg));
-    a.T = ff_fma(x.dc, c.nht, c.ct, z);
+    a.B = acc_ff(acc_add_prod(acc_add(aE, c.cg), ff_mul(d, c.nh, z), d, z));
+    a.T = acc_ff(acc_add_prod(acc_of(c.ct), x.dc, c.nht, z));
     return a;
 }
 
