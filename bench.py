@@ -51,9 +51,9 @@ FP32_LANES_PER_SM = 128
 MUFU_SLOTS_PER_SM = 32
 MUFU_SLOTS_PER_PAIR = 6
 # FP32 lane operations (FMA pipe) per in-support pair of the float-float weight kernel, from its
-# ncu capture (profiles/weight_ff_catalog400x4096_K1024_full.md): FMA pipe 64.6% of 53.99 M active
+# ncu capture (profiles/weight_ff_catalog400x4096_K1024_full.md): FMA pipe 70.35% of 45.39 M active
 # cycles x 128 lanes x 152 SMs over 1.718e9 in-support pairs.
-FF_OPS_PER_PAIR = 395
+FF_OPS_PER_PAIR = 362
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
