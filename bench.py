@@ -38,10 +38,10 @@ METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
 WORKLOAD = "c2_f64_catalog"
 
 # Algorithmic FP64-pipe operations per (sample, Lambda) pair of the weight
-# kernel: 15 add/mul/fma + 3 exp (9 each) + 1 expm1 (10) + 1 reciprocal (4);
+# kernel: 14 add/mul/fma + 3 exp (8 each) + 1 expm1 (9) + 1 reciprocal (4);
 # +1 fma for the squared weight on injection pairs.
-FP64_OPS_PER_PAIR = 56
-FP64_OPS_PER_INJ_PAIR = 57
+FP64_OPS_PER_PAIR = 51
+FP64_OPS_PER_INJ_PAIR = 52
 # GB300: 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2070 MHz
 # over 152 SMs); peak op rate = 2 * SMs * clock.
 FP64_LANES_PER_SM = 2
@@ -309,9 +309,10 @@ def grid_form(B, like, lam, timed, args, world):
 
 # FP64-pipe operations per in-support (sample, Lambda) pair of the gradient kernel: the weight
 # split into its power-law and peak parts (4 exp, 1 expm1, 1 reciprocal and their FMAs), the
-# 11-12 score terms and the 14 sums, with the loop-invariant terms hoisted: 108, the DFMA + DADD
-# + DMUL count per in-support pair of the ncu capture in profiles/grad_weight_catalog100x4096_K16_full.md.
-FP64_OPS_PER_GRAD_PAIR = 108
+# 11-12 score terms and the 14 sums, with the loop-invariant terms hoisted: the DFMA + DADD + DMUL
+# count per in-support pair of the ncu capture in profiles/grad_weight_catalog100x4096_K16_full.md
+# (108), less one fma for each of the 5 exponentials since their reduction takes one constant.
+FP64_OPS_PER_GRAD_PAIR = 103
 
 
 def grad_form(B, like, lam, args, world, n_pairs):

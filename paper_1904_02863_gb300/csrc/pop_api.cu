@@ -453,8 +453,8 @@ bool tiling_ok(int mode, const Tiling& t)
 
 namespace pop {
 
-// Tang's table: T_j = 2^(j/2048) = hi + lo, and ln2/2048 = l_hi + l_lo with l_hi
-// holding 31 significant bits, all from long double (extended or quad) arithmetic.
+// Tang's table: T_j = 2^(j/2048) = hi + lo, and the reduction constants 2048/ln2
+// and ln2/2048, all from long double (extended or quad) arithmetic.
 void build_exp_table(double2* tab, ExpConsts* kc)
 {
     for (int j = 0; j < EXP_TABLE_SIZE; ++j) {
@@ -463,15 +463,8 @@ void build_exp_table(double2* tab, ExpConsts* kc)
         tab[j] = make_double2(hi, (double)(v - (long double)hi));
     }
     const long double ln2 = logl(2.0L);
-    const long double L = ln2 / EXP_TABLE_SIZE;
-    double l_hi = (double)L;
-    uint64_t bits;
-    memcpy(&bits, &l_hi, sizeof bits);
-    bits &= ~((1ull << 22) - 1);  // keep 31 significant bits: kd * l_hi is exact for |kd| < 2^21
-    memcpy(&l_hi, &bits, sizeof bits);
     kc->inv_l = (double)(EXP_TABLE_SIZE / ln2);
-    kc->l_hi = l_hi;
-    kc->l_lo = (double)(L - (long double)l_hi);
+    kc->l = (double)(ln2 / EXP_TABLE_SIZE);
 }
 
 }  // namespace pop

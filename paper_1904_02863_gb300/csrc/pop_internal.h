@@ -43,6 +43,8 @@ struct alignas(16) LamF64 {
     double b1;           // 1 + beta
     double mmin;         // mmin (for (mmin - m1)/m1 near the lower mass edge)
     double lmmin;        // ln mmin
+    double kq;           // 1 + beta, or 1 when beta == -1
+    double kqlmmin;      // kq ln mmin: u = kq ln(mmin/m1) = fma(-kq, ln m1, kqlmmin)
     double nht;          // -1 / (2 sigma_t^2)
     double ct;           // ln(xi_t C_t^2)
     double t0;           // (1 - xi_t) / 4

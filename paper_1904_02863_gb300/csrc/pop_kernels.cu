@@ -198,6 +198,8 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     c.b1 = b1;
     c.mmin = mmin;
     c.lmmin = lmmin;
+    c.kq = beta_m1 ? 1.0 : b1;
+    c.kqlmmin = c.kq * lmmin;
     c.nht = -0.5 / (sigt * sigt);
     c.ct = log(xit) + 2.0 * ln_ct;
     c.t0 = 0.25 * (1.0 - xit);

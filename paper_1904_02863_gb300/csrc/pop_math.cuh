@@ -11,9 +11,17 @@
 // exp(x) = 2^m 2^(j/2048) e^r; 2^(j/2048) comes from a 2048-entry table held as
 // hi + lo doubles (built on the host in extended precision), e^r - 1 from its
 // Taylor series to r^3 for exp (truncation r^4/24 < 4e-17 of a result near 1)
-// and to r^4 for expm1 (whose result can be as small as r).  The reduction constant
-// ln2/2048 is split in a hi part with trailing zero bits (so kd * L_HI is exact
-// for |kd| < 2^21) and a lo part.
+// and to r^4 for expm1 (whose result can be as small as r).
+//
+// The reduction r = x - kd l takes one fma with l = fl(ln2/2048), not Tang's
+// two-part constant.  l carries the relative error of fl(ln 2), 3.35e-17, so r
+// is off by at most |kd| l 3.35e-17 ~ |x| 3.35e-17: the result gains |x| 3.35e-17
+// relative error (0.31 |x| ulp) over the two-part form.  An argument that comes
+// out of a rounded FP64 operation already carries up to |x| 1.1e-16, so the
+// second fma of the two-part form buys accuracy below that floor, at the cost of
+// one of the weight's 56 FP64 operations per exponential.  For expm1 the added
+// error is also relative to the result: for |kd| >= 1 the result is at least
+// about kd l / 2 in magnitude, and for kd = 0, r = u exactly.
 //
 // exp(x) for x < -707 (results below ~1e-307) is returned as 0, and above 709.7 as +inf.
 #pragma once
@@ -30,8 +38,7 @@ constexpr double EXP_SHIFTER = 6755399441055744.0;  // 1.5 * 2^52: adding it rou
 // Reduction constants (computed once on the host from long double ln 2).
 struct ExpConsts {
     double inv_l;   // 2048 / ln 2
-    double l_hi;    // ln 2 / 2048 rounded to 31 significant bits
-    double l_lo;    // ln 2 / 2048 - l_hi
+    double l;       // ln 2 / 2048, rounded to nearest
 };
 
 // Arguments whose result (and 2^m scaling) stays a normal double.
@@ -51,8 +58,7 @@ __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ 
     const double t = fma(xs, k.inv_l, EXP_SHIFTER);
     const int n = __double2loint(t);
     const double kd = t - EXP_SHIFTER;
-    double r = fma(kd, -k.l_hi, xs);
-    r = fma(kd, -k.l_lo, r);
+    const double r = fma(kd, -k.l, xs);
     const double p = fma(fma(r, 1.0 / 6.0, 0.5), r * r, r);  // e^r - 1
     // 2^(j/2048) e^r in [0.99, 2.01): the correctly rounded T_hi alone keeps the result
     // within about one ulp (the lo part matters only for expm1's cancellation).
@@ -75,8 +81,7 @@ __device__ __forceinline__ double expm1_tab(double u, const double2* __restrict_
     const double t = fma(us, k.inv_l, EXP_SHIFTER);
     const int n = __double2loint(t);
     const double kd = t - EXP_SHIFTER;
-    double r = fma(kd, -k.l_hi, us);
-    r = fma(kd, -k.l_lo, r);
+    const double r = fma(kd, -k.l, us);
     // To r^4 here: near the first table steps the result is as small as ~1.7e-4, so the
     // truncation must be small relative to r, not to 1 (r^5/120 / r < 1e-17).
     const double p = fma(fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5), r * r, r);

@@ -60,12 +60,14 @@ __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c
     const double e1 = exp_tab(fma(c.nalpha, x.lm1, aE + c.cpl), tab, kc);
     const double d = x.m1 - c.mu;
     const double e2 = exp_tab(fma(c.nh * d, d, aE + c.cg), tab, kc);
-    // ln(mmin/m1) for the q normalisation.  Within ~3% of the lower edge the
-    // log difference would cancel, so it is log1p((mmin - m1)/m1) by its series
-    // (mmin - m1 is exact there); the test runs on bit patterns (integer pipe).
-    double lr = c.lmmin - x.lm1;
-    if (llabs(x.m1b - c.mmin_bits) < NEAR_EDGE_BITS) lr = log1p_near0(x.invm1 * (c.mmin - x.m1));
-    const double den = c.beta_m1 ? -lr : fabs(expm1_tab(c.b1 * lr, tab, kc));
+    // u = kq ln(mmin/m1) for the q normalisation, one fma with kq ln mmin folded into a
+    // per-Lambda constant (kq = 1 + beta, or 1 for beta = -1, whose normalisation is
+    // ln(m1/mmin) = -u).  Within ~3% of the lower edge the log difference would cancel,
+    // so ln(mmin/m1) is log1p((mmin - m1)/m1) by its series (mmin - m1 is exact there);
+    // the test runs on bit patterns (integer pipe).
+    double u = fma(-c.kq, x.lm1, c.kqlmmin);
+    if (llabs(x.m1b - c.mmin_bits) < NEAR_EDGE_BITS) u = c.kq * log1p_near0(x.invm1 * (c.mmin - x.m1));
+    const double den = c.beta_m1 ? -u : fabs(expm1_tab(u, tab, kc));
     const double tt = c.t0 + exp_tab(fma(c.nht, x.dc, c.ct), tab, kc);
     return (e1 + e2) * tt * rcp_pos(den);
 }
