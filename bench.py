@@ -57,9 +57,9 @@ FF_OPS_PER_PAIR = 362
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
-# profiles/weight_f64_catalog400x4096_K64_full.md (155.20 MB / 2,077,126 units); a launch
+# profiles/weight_f64_catalog400x4096_K64_full.md (155.62 MB / 2,077,126 units); a launch
 # reads every chunk from DRAM once, so traffic scales with the units.
-F64_DRAM_BYTES_PER_UNIT = 155.20e6 / 2077126
+F64_DRAM_BYTES_PER_UNIT = 155.62e6 / 2077126
 
 
 def in_support_pairs(theta, lam):
@@ -309,10 +309,9 @@ def grid_form(B, like, lam, timed, args, world):
 
 # FP64-pipe operations per in-support (sample, Lambda) pair of the gradient kernel: the weight
 # split into its power-law and peak parts (4 exp, 1 expm1, 1 reciprocal and their FMAs), the
-# 11-12 score terms and the 14 sums, with the loop-invariant terms hoisted: the DFMA + DADD + DMUL
-# count per in-support pair of the ncu capture in profiles/grad_weight_catalog100x4096_K16_full.md
-# (108), less one fma for each of the 5 exponentials since their reduction takes one constant.
-FP64_OPS_PER_GRAD_PAIR = 103
+# 11-12 score terms and the 14 sums, with the loop-invariant terms hoisted: 105, the DFMA + DADD
+# + DMUL count per in-support pair of the ncu capture in profiles/grad_weight_catalog100x4096_K16_full.md.
+FP64_OPS_PER_GRAD_PAIR = 105
 
 
 def grad_form(B, like, lam, args, world, n_pairs):
