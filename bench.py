@@ -38,10 +38,10 @@ METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
 WORKLOAD = "c2_f64_catalog"
 
 # Algorithmic FP64-pipe operations per (sample, Lambda) pair of the weight
-# kernel: 14 add/mul/fma + 3 exp (8 each) + 1 expm1 (9) + 1 reciprocal (4);
+# kernel: 16 add/mul/fma + 3 exp (7 each) + 1 expm1 (10) + 1 reciprocal (3);
 # +1 fma for the squared weight on injection pairs.
-FP64_OPS_PER_PAIR = 51
-FP64_OPS_PER_INJ_PAIR = 52
+FP64_OPS_PER_PAIR = 50
+FP64_OPS_PER_INJ_PAIR = 51
 # GB300: 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2070 MHz
 # over 152 SMs); peak op rate = 2 * SMs * clock.
 FP64_LANES_PER_SM = 2

@@ -19,7 +19,7 @@
 // relative error (0.31 |x| ulp) over the two-part form.  An argument that comes
 // out of a rounded FP64 operation already carries up to |x| 1.1e-16, so the
 // second fma of the two-part form buys accuracy below that floor, at the cost of
-// one of the weight's 56 FP64 operations per exponential.  For expm1 the added
+// one FP64 operation per exponential (the weight has four).  For expm1 the added
 // error is also relative to the result: for |kd| >= 1 the result is at least
 // about kd l / 2 in magnitude, and for kd = 0, r = u exactly.
 //
