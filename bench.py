@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 from paper_1904_02863_gb300 import replicas, synth  # noqa: E402
 
 METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
-WORKLOAD = "c2_f64_catalog"
+WORKLOAD = "f64_catalog_1000x4096_inj1e7"
 
 # Algorithmic FP64-pipe operations per (sample, Lambda) pair of the weight
 # kernel: 16 add/mul/fma + 3 exp (7 each) + 1 expm1 (10) + 1 reciprocal (3);
@@ -138,9 +138,10 @@ def parse():
     p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
     p.add_argument("--mode", default="both", choices=["both", "f64", "f32", "ff"],
                    help="both: the FP64 headline and every form; f64 / f32 / ff: that mode alone")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4", "grid", "cbc", "grad", "sampler"],
-                   help="c2: the metric's catalog workload (default); c4: ragged CSR + redshift, uneven batches; "
-                        "sampler: the stretch-move ensemble sampler driving FP32 ln L on the c2 catalog")
+    p.add_argument("--workload", default="catalog", choices=["catalog", "ragged", "grid", "cbc", "grad", "sampler"],
+                   help="catalog: 1000 events x 4096 samples + 1e7 injection draws (default); "
+                        "ragged: 2000 ragged CSR events + redshift, uneven batches; "
+                        "sampler: the stretch-move ensemble sampler driving FP32 ln L on the catalog")
     return p.parse_args()
 
 
@@ -486,7 +487,7 @@ def run_sampler(args, B, rank, local, world):
             "value": evals / wall, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "sampler_c2", "walkers": W, "batch_per_half_step": W // 2,
+            "config": {"workload": "sampler_catalog_1000x4096", "walkers": W, "batch_per_half_step": W // 2,
                        "events": cat.n_events, "n_found": int(inj.n_found), "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (FP32 features 44 B/sample)"},
             "acceptance": float(acc.mean()),
@@ -525,7 +526,7 @@ def run_ragged(args, B, rank, local, world):
     (64, 200, 1000, 4096 in turn) replay one graph captured at 4096 with K read on the device;
     the tiling comes from the autotuner.  One step = one batch; value = Lambda evaluated / s."""
     import torch
-    cat, inj, _ = synth.make_workload("c4_ragged_z")
+    cat, inj, _ = synth.make_workload("f32_ragged2000_s500to16000_z")
     sizes = (64, 200, 1000, 4096)
     lam = synth.make_lambdas(max(sizes), 12, seed=synth.seed_for(4, 2) + 7919 * rank)
     stream = torch.cuda.Stream()
@@ -563,7 +564,7 @@ def run_ragged(args, B, rank, local, world):
             "value": evals / (ms * 1e-3), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "c4_ragged_z", "events": cat.n_events, "samples": int(cat.offsets[-1]),
+            "config": {"workload": "f32_ragged2000_s500to16000_z", "events": cat.n_events, "samples": int(cat.offsets[-1]),
                        "n_draw": int(inj.n_draw), "n_found": int(inj.n_found), "K_sequence": list(sizes),
                        "tiling_f32": B.pop_get_tiling(like.ctx, B.POP_MODE_F32), "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (FP32 features 44 B/sample)"},
@@ -626,7 +627,7 @@ def main():
     from paper_1904_02863_gb300 import binding as B
     from paper_1904_02863_gb300 import build
     build.build()
-    if args.workload == "c4":
+    if args.workload == "ragged":
         run_ragged(args, B, rank, local, world)
         return
     if args.workload == "grid":

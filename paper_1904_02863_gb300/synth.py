@@ -59,10 +59,14 @@ _CLIP_MLO, _CLIP_MHI = 5.0, 80.0
 _Z_LO = 1e-3
 
 
-def seed_for(config: int, stream: int = 0) -> int:
-    """Seed of the given workload (1..5 population, 6 single-event CBC) and sub-stream
-    (0 events or data, 1 injections, 2 Lambdas or parameter rows)."""
-    return SEED_BASE + config + 1000 * stream
+def seed_for(workload: int, stream: int = 0) -> int:
+    """Seed of a numbered workload and sub-stream.
+
+    Workloads: 1 FP64 10 x 1000, 2 FP64 catalog 1000 x 4096, 3 FP32 10 x 1000,
+    4 ragged 2000 events with redshift, 5 surrogate with redshift, 6 single-event CBC.
+    Sub-streams: 0 events or data, 1 injections, 2 Lambdas or parameter rows,
+    3 ragged sample counts."""
+    return SEED_BASE + workload + 1000 * stream
 
 
 @dataclass
@@ -312,13 +316,13 @@ def round_to_f32(x):
 
 # --------------------------------------------------------------------------- workload presets
 WORKLOADS = {
-    # name: (n_events, sizes, n_dims, n_draw, K, storage)
-    "c1_f64_small": dict(config=1, n_events=10, sizes=1000, n_dims=6, n_draw=10**5, K=100, storage="f64"),
-    "c2_f64_catalog": dict(config=2, n_events=1000, sizes=4096, n_dims=6, n_draw=10**7, K=1024, storage="f64"),
-    "c3_f32_small": dict(config=3, n_events=10, sizes=1000, n_dims=6, n_draw=10**5, K=1024, storage="f32"),
-    "c4_ragged_z": dict(config=4, n_events=2000, sizes=(500, 16000), n_dims=7, n_draw=18 * 10**6,
+    # name: seed_id (the seed_for workload number), n_events, sizes, n_dims, n_draw, K, storage
+    "f64_10x1000_inj1e5": dict(seed_id=1, n_events=10, sizes=1000, n_dims=6, n_draw=10**5, K=100, storage="f64"),
+    "f64_catalog_1000x4096_inj1e7": dict(seed_id=2, n_events=1000, sizes=4096, n_dims=6, n_draw=10**7, K=1024, storage="f64"),
+    "f32_10x1000_inj1e5": dict(seed_id=3, n_events=10, sizes=1000, n_dims=6, n_draw=10**5, K=1024, storage="f32"),
+    "f32_ragged2000_s500to16000_z": dict(seed_id=4, n_events=2000, sizes=(500, 16000), n_dims=7, n_draw=18 * 10**6,
                         K=(64, 200, 1000, 4096), storage="f32"),
-    "c5_surrogate": dict(config=5, n_events=10, sizes=1000, n_dims=7, n_draw=10**5, K=1024, storage="f32"),
+    "f32_z_10x1000_inj1e5_surrogate": dict(seed_id=5, n_events=10, sizes=1000, n_dims=7, n_draw=10**5, K=1024, storage="f32"),
 }
 
 
@@ -328,7 +332,7 @@ def make_workload(name, scale=1.0):
     ``scale`` < 1 shrinks the event count and the draw count (parity cases).
     """
     w = WORKLOADS[name]
-    cfg = w["config"]
+    cfg = w["seed_id"]
     n_events = max(1, int(round(w["n_events"] * scale)))
     sizes = w["sizes"]
     if isinstance(sizes, tuple):

@@ -30,7 +30,7 @@ def B():
 @pytest.fixture(scope="module")
 def small(B):
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c1_f64_small")
+    cat, inj, lam = synth.make_workload("f64_10x1000_inj1e5")
     like = B.Likelihood(0).load(cat, inj)
     yield like, cat, inj, lam
     like.close()
@@ -148,7 +148,7 @@ def test_ff_catalog_scale(B, oracle):
     """The benchmark's workload (1000 events x 4096 samples, 1e7 draws, K = 1024): every row
     against the FP64 kernel's within the FP64 bar, sampled rows against the oracle."""
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c2_f64_catalog")
+    cat, inj, lam = synth.make_workload("f64_catalog_1000x4096_inj1e7")
     like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F64)
     ff = like(lam, B.POP_MODE_FF)
     f64 = like(lam, B.POP_MODE_F64)

@@ -68,7 +68,7 @@ def tiny():
 @pytest.fixture(scope="module")
 def small(B):
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c1_f64_small")
+    cat, inj, lam = synth.make_workload("f64_10x1000_inj1e5")
     like = B.Likelihood(0).load(cat, inj)
     yield like, cat, inj, lam
     like.close()
@@ -236,7 +236,7 @@ def test_uneven_batches_reuse_scratch(B, ragged, oracle):
 
 def test_f32_small_catalog(B, oracle):
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c3_f32_small")
+    cat, inj, lam = synth.make_workload("f32_10x1000_inj1e5")
     like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F32)
     lnL = like(lam, B.POP_MODE_F32)[0]
     c32, i32 = rounded(cat, inj)
@@ -320,7 +320,7 @@ def test_ragged_redshift_scale_sampled(B, oracle):
     redshift on, 1.97e6 injections, FP32; uneven batches replay one graph (K read on the device).
     The oracle (on the FP32-rounded inputs) checks sampled rows of every batch."""
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c4_ragged_z")
+    cat, inj, lam = synth.make_workload("f32_ragged2000_s500to16000_z")
     like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F32)
     c32, i32 = rounded(cat, inj)
     picks = []
@@ -338,7 +338,7 @@ def test_catalog_scale_sampled(B, oracle):
     """The benchmark's workload (1000 events x 4096 samples, 1e7 draws, K = 1024) in
     its launch configuration; the oracle checks a sample of the Lambda rows."""
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c2_f64_catalog")
+    cat, inj, lam = synth.make_workload("f64_catalog_1000x4096_inj1e7")
     like = B.Likelihood(0).load(cat, inj)
     got = like(lam, B.POP_MODE_F64)
     got32 = like(lam, B.POP_MODE_F32)[0]

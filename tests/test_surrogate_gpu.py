@@ -110,9 +110,9 @@ def test_adam_step_matches_oracle(B, ctx):
 
 @pytest.fixture(scope="module")
 def trained(B):
-    """C5-shaped problem: 10 events x 1000 samples with redshift, 1e5 injection draws."""
+    """Surrogate problem: 10 events x 1000 samples with redshift, 1e5 injection draws."""
     from paper_1904_02863_gb300 import synth
-    cat, inj, lam = synth.make_workload("c5_surrogate")
+    cat, inj, lam = synth.make_workload("f32_z_10x1000_inj1e5_surrogate")
     like = B.Likelihood(0).load(cat, inj)
     box = synth.LAMBDA_BOX[:12]
     rmse = B.pop_xi_surrogate_train(like.ctx, 40000, box[:, 0], box[:, 1], epochs=30, seed=7)
