@@ -216,17 +216,61 @@ barrier = replicas.barrier
 max_over_ranks = replicas.max_over_ranks
 
 
-def cpu_baseline(cat, inj, lam, n_rows):
+def cpu_baseline(cat, inj, lam, n_rows, gpu_f64=None):
+    """The oracle timed on the first ``n_rows`` Lambda of the batch.  Given the FP64 kernel's
+    outputs for the batch, also reports their distance to the oracle on those rows, in units of
+    the FP64 tolerance 1e-12 (|sum_i ln(S_i/n_i)| + N |ln xi|)."""
     import oracle
     cores = host_cores()
     sub = lam[:n_rows]
     t0 = time.perf_counter()
-    oracle.loglik(cat, inj, sub, nthreads=cores)
+    ref = oracle.loglik(cat, inj, sub, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": n_rows / dt, "unit": "evals/s", "cores": min(cores, n_rows), "kind": "oracle",
-            "sample": f"{n_rows} Lambda rows of the same workload (full 1000x4096 catalog and "
-                      f"{inj.n_found} found injections per row), FP64, OpenMP over Lambda",
-            "seconds": dt}
+    out = {"value": n_rows / dt, "unit": "evals/s", "cores": min(cores, n_rows), "kind": "oracle",
+           "sample": f"{n_rows} Lambda rows of the same workload (full 1000x4096 catalog and "
+                     f"{inj.n_found} found injections per row), FP64, OpenMP over Lambda",
+           "seconds": dt}
+    if gpu_f64 is not None:
+        n = cat.n_events
+        g = [np.asarray(x)[:n_rows] for x in gpu_f64]
+        fin = np.isfinite(ref[0]) & np.isfinite(g[0])
+        tol = 1e-12 * (np.abs(np.where(fin, ref[0], 0.0) + n * ref[1]) + n * np.abs(ref[1])) + 1e-13
+        ratio = float(np.max(np.abs(g[0][fin] - ref[0][fin]) / tol[fin])) if fin.any() else 0.0
+        out["parity_f64_kernel"] = {
+            "rows": int(n_rows), "max_abs_dlnL": float(np.max(np.abs(g[0][fin] - ref[0][fin]))) if fin.any() else 0.0,
+            "max_over_f64_tol": ratio,
+            "flags_equal": bool((g[3].view(np.uint32) == ref[3].view(np.uint32)).all()),
+            "finite_rows_agree": bool((np.isfinite(ref[0]) == np.isfinite(g[0])).all())}
+    return out
+
+
+def precision_vs(res, ref):
+    """|Delta ln L| and the relative Delta xi of the outputs ``res`` against ``ref`` over every
+    Lambda of the batch (rows where both ln L are finite)."""
+    a, b = res[0], ref[0]
+    both = np.isfinite(a) & np.isfinite(b)
+    d = np.abs(a[both] - b[both])
+    dxi = np.abs(np.expm1(res[1][both] - ref[1][both]))
+    return {"rows": int(a.size), "finite_rows_agree": bool((np.isfinite(a) == np.isfinite(b)).all()),
+            "abs_dlnL": {"mean": float(d.mean()) if d.size else 0.0, "max": float(d.max()) if d.size else 0.0},
+            "rel_dxi_max": float(dxi.max()) if dxi.size else 0.0}
+
+
+def f64_on_rounded_inputs(B, cat, inj, dev_lam, device, stream):
+    """The FP64 kernel's outputs on the catalog and injections rounded to float32 (what the FP32
+    layout stores): against these, an FP32 form's difference is its arithmetic error alone."""
+    import torch
+    cat32 = synth.Catalog(cat.offsets, synth.round_to_f32(cat.theta), synth.round_to_f32(cat.prior))
+    inj32 = synth.Injections(synth.round_to_f32(inj.theta), synth.round_to_f32(inj.p_draw), inj.n_draw)
+    like = B.Likelihood(device, stream).load(cat32, inj32)
+    K = dev_lam.shape[0]
+    outs = [torch.empty(K, dtype=torch.float64, device="cuda") for _ in range(3)] + \
+           [torch.empty(K, dtype=torch.int32, device="cuda")]
+    B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F64, out=outs)
+    torch.cuda.synchronize()
+    res = [o.cpu().numpy().copy() for o in outs]
+    like.close()
+    return res
 
 
 def ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_pairs, n_events):
@@ -252,7 +296,7 @@ def ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_pairs, n_events):
             "in_support_pairs": n_pairs}
 
 
-def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world):
+def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world, ref64=None, ref64_rounded=None):
     """FP32 weights + the trained ln xi network (Monte Carlo xi only where its gate says so).
 
     Training (2e5 Lambda from the prior box, 10% held out, targets from this
@@ -276,7 +320,20 @@ def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world):
             "weight_ms": w, "dtype": "f32+bf16 network", "train_seconds": train_s,
             "heldout_rmse_lnxi": info["heldout_rmse"], "heldout_mc_noise": info["mc_noise"],
             "trusted": info["trusted"], "surrogate_used_frac": float(used.mean()),
-            "abs_dlnL_vs_f32_mc": {"mean": float(d[fin].mean()), "max": float(d[fin].max())}}
+            "abs_dlnL_vs_f32_mc": {"mean": float(d[fin].mean()), "max": float(d[fin].max())},
+            **precision_fields([o.cpu().numpy() for o in sur], ref64, ref64_rounded)}
+
+
+def precision_fields(res, ref64, ref64_rounded):
+    """The form's distance to the FP64 kernel (which matches the oracle to 1e-12): on the original
+    inputs (arithmetic and float32 storage) and on the float32-rounded inputs (arithmetic alone,
+    the quantity the 0.05-nat FP32 bar applies to)."""
+    out = {}
+    if ref64 is not None:
+        out["vs_f64"] = precision_vs(res, ref64)
+    if ref64_rounded is not None:
+        out["vs_f64_rounded_inputs"] = precision_vs(res, ref64_rounded)
+    return out
 
 
 def grid_form(B, like, lam, timed, args, world):
@@ -697,6 +754,14 @@ def main():
         B.pop_loglik(like.ctx, h_lam, head, out=h_out)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
 
+    def run_once(mode):
+        B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+        torch.cuda.synchronize()
+        return [o.cpu().numpy().copy() for o in outs]
+
+    # Untimed reference outputs for the precision report.
+    ref64 = run_once(B.POP_MODE_F64) if (head == B.POP_MODE_F64 or args.mode == "both") else None
+
     n_ev_pairs = in_support_pairs(cat.theta, lam)
     n_inj_pairs = in_support_pairs(inj.theta, lam)
     all_pairs = (int(cat.offsets[-1]) + int(inj.n_found)) * K
@@ -739,17 +804,21 @@ def main():
         "clocks": clocks,
     }
     if args.mode == "both":
+        ref64_r = f64_on_rounded_inputs(B, cat, inj, dev_lam, local, stream)
         line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
                                  "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32",
-                                 "roofline": f32_roofline(n_ev_pairs + n_inj_pairs, w32)}}
+                                 "roofline": f32_roofline(n_ev_pairs + n_inj_pairs, w32),
+                                 **precision_fields(run_once(B.POP_MODE_F32), ref64, ref64_r)}}
         line["forms"]["f64_ff"] = ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_ev_pairs + n_inj_pairs,
                                           cat.n_events)
-        line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world)
+        line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world,
+                                                             ref64, ref64_r)
         line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
         line["forms"]["cbc_likelihood"] = cbc_form(B, like, args, world, rank)
         line["forms"]["grad_f64"] = grad_form(B, like, lam, args, world, n_ev_pairs + n_inj_pairs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas)
+        line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas,
+                                             ref64 if head == B.POP_MODE_F64 else None)
     like.close()
     if rank == 0:
         print(json.dumps(line, default=_jsonable), flush=True)

@@ -1,0 +1,100 @@
+"""GPU parity on the degenerate shapes of the recycled likelihood (Eq. poplike, with the
+Monte Carlo selection term of Sec. "Population acceleration"), in every mode.
+
+* an empty Lambda batch (K = 0), then a one-row batch, in each mode;
+* a catalog of one-sample events beside one event of many chunks;
+* a single found injection, and a campaign where every draw was found (n_found = n_draw).
+
+FP64 and float-float: the FP64 parity bar (1e-12 of |sum_i ln(S_i/n_i)| + N |ln xi|,
+flags identical); FP32: 0.05 nats against the oracle on the float32-rounded inputs.
+"""
+import numpy as np
+import pytest
+
+from test_parity_gpu import assert_f64_parity, rounded
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    from paper_1904_02863_gb300 import binding, build
+    build.build()
+    binding.load_library()
+    return binding
+
+
+def check_all_modes(B, like, cat, inj, lam, oracle):
+    ref = oracle.loglik(cat, inj, lam)
+    assert_f64_parity(like(lam, B.POP_MODE_F64), ref, cat.n_events)
+    assert_f64_parity(like(lam, B.POP_MODE_FF), ref, cat.n_events)
+    c32, i32 = rounded(cat, inj)
+    ref32 = oracle.loglik(c32, i32, lam)
+    got32 = like(lam, B.POP_MODE_F32)
+    fin = np.isfinite(ref32[0])
+    np.testing.assert_array_equal(np.isfinite(got32[0]), fin)
+    d = np.abs(got32[0][fin] - ref32[0][fin])
+    assert d.size == 0 or d.max() <= 0.05, d.max()
+
+
+def test_empty_then_one_row_batch_every_mode(B, oracle):
+    from paper_1904_02863_gb300 import synth
+    cat = synth.make_catalog(4, 1500, 6, seed=611)
+    inj = synth.make_injections(20000, 6, seed=612)
+    lam = synth.make_lambdas(1, 11, seed=613)
+    like = B.Likelihood(0).load(cat, inj)
+    for mode in (B.POP_MODE_F64, B.POP_MODE_F32, B.POP_MODE_FF):
+        out = like(lam[:0], mode)
+        assert all(o.shape == (0,) for o in out), mode
+    check_all_modes(B, like, cat, inj, lam, oracle)
+    like.close()
+
+
+def test_one_sample_events_beside_a_long_event(B, oracle):
+    """300 events of one sample each and one event of 3 chunks + a tail: per-event sums of a
+    single weight, and a segmented sum that crosses many work items."""
+    from paper_1904_02863_gb300 import synth
+    sizes = np.ones(301, np.int64)
+    sizes[150] = 3 * 4096 + 77
+    cat = synth.make_catalog(len(sizes), sizes, 6, seed=621)
+    # Spin magnitudes clipped to exactly 0 or 1 have zero Beta density when alpha_chi or
+    # beta_chi > 1; keep them inside so that one-sample events do not vanish (pi has no spin term).
+    cat.theta[:, 2:4] = np.clip(cat.theta[:, 2:4], 0.02, 0.98)
+    inj = synth.make_injections(30000, 6, seed=622)
+    lam = synth.make_lambdas(41, 11, seed=623)
+    # Most rows keep every one-sample event inside the mass support (mmin < 5 <= m2,
+    # m1 <= 80 <= mmax), so ln L stays finite; the last rows keep the box's own edges.
+    rng = np.random.Generator(np.random.PCG64(624))
+    lam[:33, 2] = rng.uniform(4.0, 4.99, 33)
+    lam[:33, 3] = rng.uniform(80.0, 90.0, 33)
+    like = B.Likelihood(0).load(cat, inj)
+    check_all_modes(B, like, cat, inj, lam, oracle)
+    assert np.isfinite(like(lam[:33], B.POP_MODE_F64)[0]).all()
+    like.close()
+
+
+def test_single_found_injection(B, oracle):
+    """xi from one injection in the bulk of every support of the Lambda box: xi = w / n_draw."""
+    from paper_1904_02863_gb300 import synth
+    cat = synth.make_catalog(5, 900, 6, seed=631)
+    inj = synth.Injections(np.array([[30.0, 0.8, 0.3, 0.6, 0.2, -0.4]]), np.array([2.5e-3]), 1000)
+    lam = synth.make_lambdas(23, 11, seed=633)
+    like = B.Likelihood(0).load(cat, inj)
+    check_all_modes(B, like, cat, inj, lam, oracle)
+    like.close()
+
+
+def test_every_draw_found(B, oracle):
+    """n_found = n_draw: the campaign's estimator without missed draws."""
+    from paper_1904_02863_gb300 import synth
+    cat = synth.make_catalog(6, 1200, 6, seed=641)
+    inj = synth.make_injections(40000, 6, seed=642)
+    inj = synth.Injections(inj.theta, inj.p_draw, inj.n_found)
+    lam = synth.make_lambdas(19, 11, seed=643)
+    like = B.Likelihood(0).load(cat, inj)
+    check_all_modes(B, like, cat, inj, lam, oracle)
+    like.close()
