@@ -38,10 +38,10 @@ METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
 WORKLOAD = "f64_catalog_1000x4096_inj1e7"
 
 # Algorithmic FP64-pipe operations per (sample, Lambda) pair of the weight
-# kernel: 16 add/mul/fma + 3 exp (7 each) + 1 expm1 (10) + 1 reciprocal (3);
+# kernel: 15 add/mul/fma + 3 exp (7 each) + 1 expm1 (10) + 1 reciprocal (3);
 # +1 fma for the squared weight on injection pairs.
-FP64_OPS_PER_PAIR = 50
-FP64_OPS_PER_INJ_PAIR = 51
+FP64_OPS_PER_PAIR = 49
+FP64_OPS_PER_INJ_PAIR = 50
 # GB300: 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2070 MHz
 # over 152 SMs); peak op rate = 2 * SMs * clock.
 FP64_LANES_PER_SM = 2
@@ -57,9 +57,9 @@ FF_OPS_PER_PAIR = 362
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
-# profiles/weight_f64_catalog400x4096_K64_full.md (155.62 MB / 2,077,126 units); a launch
+# profiles/weight_f64_catalog400x4096_K64_full.md (154.18 MB / 2,077,126 units); a launch
 # reads every chunk from DRAM once, so traffic scales with the units.
-F64_DRAM_BYTES_PER_UNIT = 155.62e6 / 2077126
+F64_DRAM_BYTES_PER_UNIT = 154.18e6 / 2077126
 
 
 def in_support_pairs(theta, lam):

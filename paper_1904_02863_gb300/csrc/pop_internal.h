@@ -48,6 +48,8 @@ struct alignas(16) LamF64 {
     double nht;          // -1 / (2 sigma_t^2)
     double ct;           // ln(xi_t C_t^2)
     double t0;           // (1 - xi_t) / 4
+    double gs;           // 1 / (sqrt2 sigpp): the Gaussian exponent is -y^2, y = fma(m1, gs, gc)
+    double gc;           // -mpp gs
     int32_t beta_m1;     // beta == -1: q normalisation is ln(m1/mmin)
     int32_t valid;
 };

@@ -203,6 +203,8 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     c.nht = -0.5 / (sigt * sigt);
     c.ct = log(xit) + 2.0 * ln_ct;
     c.t0 = 0.25 * (1.0 - xit);
+    c.gs = 1.0 / (SQRT2 * sig);
+    c.gc = -mu * c.gs;
     c.beta_m1 = beta_m1;
     c.valid = 1;
     c64[k] = c;

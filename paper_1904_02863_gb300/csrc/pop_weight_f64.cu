@@ -58,8 +58,12 @@ __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c
     aE = fma(c.bc, x.sb, aE);
     if (HAS_Z) aE = fma(c.km1, x.lz1, aE);
     const double e1 = exp_tab(fma(c.nalpha, x.lm1, aE + c.cpl), tab, kc);
-    const double d = x.m1 - c.mu;
-    const double e2 = exp_tab(fma(c.nh * d, d, aE + c.cg), tab, kc);
+    // Gaussian exponent -(m1 - mu)^2 / (2 sig^2) = -y^2 with y = (m1 - mu) / (sqrt2 sig) formed
+    // by one fma from per-Lambda constants (3 FP64 ops instead of 4).  The rounding of
+    // gc = -mu gs shifts y by at most |mu gs| 1.1e-16, so the exponent by 2|y| |mu gs| 1.1e-16
+    // absolute: of the order of the roundings of the subtract-and-square form at the same y.
+    const double y = fma(x.m1, c.gs, c.gc);
+    const double e2 = exp_tab(fma(-y, y, aE + c.cg), tab, kc);
     // u = kq ln(mmin/m1) for the q normalisation, one fma with kq ln mmin folded into a
     // per-Lambda constant (kq = 1 + beta, or 1 for beta = -1, whose normalisation is
     // ln(m1/mmin) = -u).  Within ~3% of the lower edge the log difference would cancel,
@@ -150,13 +154,13 @@ weight_f64_kernel(FeatF64 ev, FeatF64 inj, WorkDesc wd, const LamF64* __restrict
             for (int l = 0; l < T; ++l) {
                 const LamF64& cl = sl[l];
                 const bool in = in_support(x, cl);
-                double w = 0.0;
+                // Warps with no lane in the support add nothing (and spend no FP64 operation).
                 if (__any_sync(0xffffffffu, in)) {
-                    w = weight_f64<HAS_Z>(x, cl, stab, kc);
+                    double w = weight_f64<HAS_Z>(x, cl, stab, kc);
                     w = in ? w : 0.0;
+                    acc[l] += w;
+                    if (ch.inj) acc2[l] = fma(w, w, acc2[l]);
                 }
-                acc[l] += w;
-                if (ch.inj) acc2[l] = fma(w, w, acc2[l]);
             }
         }
 #pragma unroll
