@@ -235,14 +235,27 @@ def test_uneven_batches_reuse_scratch(B, ragged, oracle):
 
 
 def test_f32_small_catalog(B, oracle):
+    """FP32 storage and weights, 10 events x 1000 samples, all K = 1024 Lambda: |d ln L| and the
+    relative d xi against the oracle on the float32-rounded inputs.
+
+    xi bound: an FP32 weight is 2^x with x a sum of at most 8 base-2 terms; with every term and
+    partial sum below 64 in magnitude, each rounding moves x by at most 64 u (u = 2^-24), so
+    |dx| <= 8 * 64 u = 3.1e-5 and the weight's relative error is at most ln2 |dx| + the few ulp
+    of ex2.approx / rcp.approx, under 5e-5.  xi is a mean of positive weights (Kahan-summed), so
+    its relative error has the same bound; larger terms belong to weights too small to matter.
+    """
     from paper_1904_02863_gb300 import synth
     cat, inj, lam = synth.make_workload("f32_10x1000_inj1e5")
     like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F32)
-    lnL = like(lam, B.POP_MODE_F32)[0]
+    lnL, lnxi, _, _ = like(lam, B.POP_MODE_F32)
     c32, i32 = rounded(cat, inj)
-    ref = oracle.loglik(c32, i32, lam)[0]
+    ref, ref_xi, _, _ = oracle.loglik(c32, i32, lam)
     d = np.abs(lnL - ref)
     assert np.max(d) <= 0.05, np.max(d)
+    xf = np.isfinite(ref_xi)
+    np.testing.assert_array_equal(np.isfinite(lnxi), xf)
+    rel = np.abs(np.expm1(lnxi[xf] - ref_xi[xf]))
+    assert rel.max() <= 5e-5, rel.max()
     like.close()
 
 
