@@ -294,6 +294,24 @@ int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
  * The test suite checks them against libm and CUDA's functions. */
 int pop_math_check(pop_ctx* ctx, int fn, int64_t n, const double* x, double* y, int mem);
 
+/* Largest poll limit pop_wait_check accepts: the grid contraction's and the
+ * tensor-core GEMM's own limit, about 1 s of polls (a poll of a phase that is
+ * not complete suspends the thread about 3.8 us on GB300). */
+#define POP_WAIT_CHECK_MAX_POLLS (1 << 18)
+
+/* Diagnostic of failure detection (the paper has no counterpart).  The grid
+ * contraction's shared-memory copies complete on mbarriers, and every wait on
+ * one is bounded: after a fixed number of polls it gives up, raises an error
+ * word on the device and lets the kernel return, and the host call reports
+ * POP_ETIMEOUT instead of hanging.  This runs one such wait, with the same
+ * device function and the given poll limit (1..POP_WAIT_CHECK_MAX_POLLS), on a
+ * barrier that the waiting thread first completes itself (arrive != 0: returns
+ * POP_OK) or that nothing completes (arrive == 0: returns POP_ETIMEOUT after
+ * `polls` polls).  No GPU fault or hang is involved, and the context stays
+ * usable.  Synchronous on the context stream.  POP_EINVAL for a poll limit out
+ * of range. */
+int pop_wait_check(pop_ctx* ctx, int arrive, int polls);
+
 /* ------------------------------------------------------------------ ln xi surrogate
  * The paper announces a learned selection term that includes spin effects in
  * VT at no extra run-time cost (Sec. "Population acceleration", right after the

@@ -29,7 +29,7 @@ EXPORTS = (
     "pop_create", "pop_destroy", "pop_last_error", "pop_status_string", "pop_version",
     "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
     "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
-    "pop_loglik_f64_noalloc", "pop_math_check",
+    "pop_loglik_f64_noalloc", "pop_math_check", "pop_wait_check",
     "pop_xi_surrogate_train", "pop_xi_surrogate_info", "pop_xi_surrogate_infer", "pop_xi_surrogate_save",
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "pop_loglik_f64_noalloc": (i32, [i32, vp, i64, vp, i64, i32, vp, vp, i64, i64, vp, vp, i64, i32, vp,
                                          vp, vp, vp, vp, ctypes.c_char_p, i32]),
         "pop_math_check": (i32, [vp, i32, i64, vp, vp, i32]),
+        "pop_wait_check": (i32, [vp, i32, i32]),
         "pop_xi_surrogate_train": (i32, [vp, i64, d, ctypes.c_uint64, vp, vp, i32, i32, ctypes.POINTER(d)]),
         "pop_xi_surrogate_info": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                         ctypes.POINTER(i32)]),
@@ -291,6 +292,16 @@ def pop_last_kernel_ms(ctx):
     w, t = ctypes.c_double(), ctypes.c_double()
     _check(ctx, load_library().pop_last_kernel_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
     return w.value, t.value
+
+
+POP_WAIT_CHECK_MAX_POLLS = 1 << 18
+
+
+def pop_wait_check(ctx, arrive, polls):
+    """One bounded mbarrier wait of the grid contraction's kind on the GPU: returns None when the
+    barrier completes (arrive=True) and raises PopError(POP_ETIMEOUT) when it gives up after
+    ``polls`` polls (arrive=False)."""
+    _check(ctx, load_library().pop_wait_check(ctx, int(bool(arrive)), int(polls)))
 
 
 def pop_math_check(ctx, fn, x):

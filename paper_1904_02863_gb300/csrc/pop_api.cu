@@ -529,6 +529,22 @@ int pop_math_check(pop_ctx* c, int fn, int64_t n, const double* x, double* y, in
     return POP_OK;
 }
 
+int pop_wait_check(pop_ctx* c, int arrive, int polls)
+{
+    if (!c) return POP_EINVAL;
+    if (polls < 1 || polls > POP_WAIT_CHECK_MAX_POLLS) return fail(c, POP_EINVAL, "pop_wait_check: polls out of range");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    DevBuf err;
+    CK(err.alloc(sizeof(int)), "cudaMalloc");
+    CK(cudaMemsetAsync(err.p, 0, sizeof(int), c->stream), "memset");
+    CK(launch_wait_check(arrive != 0, polls, err.as<int>(), c->stream), "wait_check");
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy error word");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (bad) return fail(c, POP_ETIMEOUT, "pop_wait_check: the bounded wait gave up after " + std::to_string(polls) + " polls");
+    return POP_OK;
+}
+
 int pop_version(void) { return 10000; }
 
 const char* pop_status_string(int s)

@@ -39,7 +39,10 @@ namespace {
 
 constexpr int GV_THREADS = 256;
 
-constexpr int GV_WAIT_LIMIT = 1 << 22;  // mbarrier polls before a wait gives up
+// mbarrier polls before a wait gives up.  A poll of a phase that is not complete suspends the
+// thread about 3.8 us on GB300 (measured through pop_wait_check), so this is about 1 s; a
+// tile's bulk copies complete within microseconds.
+constexpr int GV_WAIT_LIMIT = 1 << 18;
 constexpr int GV_BUCKETS = 1024;        // mmin buckets of the column sort
 constexpr double GV_SQRT2 = 1.4142135623730950488;
 constexpr double GV_SQRT2PI = 2.5066282746310005024;
@@ -436,10 +439,11 @@ __device__ __forceinline__ void gv_bulk_load(uint32_t dst, const void* src, uint
                  : "memory");
 }
 
-// Waits for the phase of the given parity; false after GV_WAIT_LIMIT polls.
-__device__ __forceinline__ bool gv_wait(uint32_t bar, uint32_t parity)
+// Waits for the phase of the given parity; false after `limit` polls (GV_WAIT_LIMIT in the
+// contraction).
+__device__ __forceinline__ bool gv_wait(uint32_t bar, uint32_t parity, int limit = GV_WAIT_LIMIT)
 {
-    for (int i = 0; i < GV_WAIT_LIMIT; ++i) {
+    for (int i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -969,6 +973,29 @@ cudaError_t GridVT::out_lnxi(const double* lambda, int n_params, const int64_t* 
 {
     if (K_cap <= 0) return cudaSuccess;
     gv_out_kernel<<<(unsigned)((K_cap + 255) / 256), 256, 0, s>>>(xi.as<double>(), lambda, n_params, dK, lnxi, flags);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// One thread: an mbarrier expecting one arrival; with `arrive` the thread gives it, otherwise
+// nothing ever completes the phase and the bounded wait of the contraction runs out of polls,
+// which sets the error word exactly as a contraction tile that gives up does.
+__global__ void gv_wait_check_kernel(int arrive, int polls, int* __restrict__ err)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = gv_saddr(&bar);
+    gv_bar_init(b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+    if (!gv_wait(b, 0u, polls)) atomicExch(err, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_check(int arrive, int polls, int* err, cudaStream_t s)
+{
+    gv_wait_check_kernel<<<1, 1, 0, s>>>(arrive, polls, err);
     return cudaGetLastError();
 }
 

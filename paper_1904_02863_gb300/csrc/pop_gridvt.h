@@ -78,4 +78,9 @@ struct GridVT {
     cudaError_t take_error(int* h, cudaStream_t s);
 };
 
+// One bounded mbarrier wait of the contraction's kind (gv_wait) with the given poll limit, on a
+// barrier that the waiting thread completes first (arrive != 0) or that nothing completes;
+// sets *err to 1 when the wait gives up.
+cudaError_t launch_wait_check(int arrive, int polls, int* err, cudaStream_t s);
+
 }  // namespace pop

@@ -40,7 +40,9 @@ constexpr int TC_SMEM_B = 256 * TC_BK * 2;      // 32 KB
 constexpr int TC_SMEM_LAUNCH = 112 * 1024;
 constexpr uint32_t CM_LBO = 128;   // bytes to the next core matrix along K
 constexpr uint32_t CM_SBO = 1024;  // bytes to the next 8-row group
-constexpr int WAIT_LIMIT = 1 << 20;
+// mbarrier polls before a wait gives up: about 1 s at the ~3.8 us a poll of an incomplete phase
+// suspends on GB300; a tile's TMA loads and MMAs complete within microseconds.
+constexpr int WAIT_LIMIT = 1 << 18;
 
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_F32 = 2 };
 
