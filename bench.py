@@ -230,6 +230,12 @@ def cpu_baseline(cat, inj, lam, n_rows, gpu_f64=None):
            "sample": f"{n_rows} Lambda rows of the same workload (full 1000x4096 catalog and "
                      f"{inj.n_found} found injections per row), FP64, OpenMP over Lambda",
            "seconds": dt}
+    # The paper compares against single-threaded CPU code: the same oracle on one thread.
+    n1 = min(2, n_rows)
+    t0 = time.perf_counter()
+    oracle.loglik(cat, inj, lam[:n1], nthreads=1)
+    dt1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": n1 / dt1, "unit": "evals/s", "cores": 1, "rows": n1, "seconds": dt1}
     if gpu_f64 is not None:
         n = cat.n_events
         g = [np.asarray(x)[:n_rows] for x in gpu_f64]

@@ -16,6 +16,7 @@
 #include "pop_devbuf.h"
 #include "pop_gridvt.h"
 #include "pop_internal.h"
+#include "pop_trace.h"
 #include "pop_mlp.h"
 
 #include <memory>
@@ -657,6 +658,7 @@ int pop_validate_events(int64_t n_events, const int64_t* offsets, int n_dims, ch
 int pop_load_events(pop_ctx* c, int64_t n_events, const int64_t* offsets, int n_dims, const double* theta,
                     const double* prior, int storage, int mem)
 {
+    pop::TraceRange trace_("pop_load_events");
     if (!c) return POP_EINVAL;
     char m[200];
     if (pop_validate_events(n_events, offsets, n_dims, m, sizeof m) != POP_OK)
@@ -691,6 +693,7 @@ int pop_load_events(pop_ctx* c, int64_t n_events, const int64_t* offsets, int n_
 int pop_load_injections(pop_ctx* c, int64_t n_found, int64_t n_draw, int n_dims, const double* theta,
                         const double* p_draw, int storage, int mem)
 {
+    pop::TraceRange trace_("pop_load_injections");
     if (!c) return POP_EINVAL;
     if (c->ev.n == 0) return fail(c, POP_ESTATE, "pop_load_injections: load events first");
     if (n_found < 1 || n_draw < n_found) return fail(c, POP_EINVAL, "pop_load_injections: need n_draw >= n_found >= 1");
@@ -788,6 +791,7 @@ extern "C" {
 int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_lnL,
                double* out_lnxi, double* out_neff, uint32_t* out_flags, int mem)
 {
+    pop::TraceRange trace_("pop_loglik");
     if (!c) return POP_EINVAL;
     if (K > 0 && !out_lnL) return fail(c, POP_EINVAL, "pop_loglik: out_lnL is NULL");
     int rc = loglik_run(c, K, n_params, lambda, mode, mem, "pop_loglik");
@@ -807,6 +811,7 @@ int pop_loglik(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mo
 int pop_loglik_parts(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_events,
                      double* out_sum_w, double* out_sum_w2, uint32_t* out_flags, int mem)
 {
+    pop::TraceRange trace_("pop_loglik_parts");
     if (!c) return POP_EINVAL;
     if (c->xi_source != POP_XI_INJECTIONS)
         return fail(c, POP_EINVAL, "pop_loglik_parts: needs the injection selection term");
@@ -844,6 +849,7 @@ int pop_loglik_parts(pop_ctx* c, int64_t K, int n_params, const double* lambda, 
 int pop_loglik_grad(pop_ctx* c, int64_t K, int n_params, const double* lambda, double* out_lnL, double* out_grad,
                     uint32_t* out_flags, int mem)
 {
+    pop::TraceRange trace_("pop_loglik_grad");
     if (!c) return POP_EINVAL;
     if (c->xi_source != POP_XI_INJECTIONS)
         return fail(c, POP_EINVAL, "pop_loglik_grad: needs the injection selection term");
@@ -906,6 +912,7 @@ int pop_loglik_grad(pop_ctx* c, int64_t K, int n_params, const double* lambda, d
 int pop_cbc_load(pop_ctx* c, int n_det, int64_t M, double f0, double df, const double* data, const double* psd,
                  const double* hp, const double* hc, int mem)
 {
+    pop::TraceRange trace_("pop_cbc_load");
     if (!c) return POP_EINVAL;
     if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_cbc_load: bad mem");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -924,6 +931,7 @@ int pop_cbc_load(pop_ctx* c, int n_det, int64_t M, double f0, double df, const d
 int pop_cbc_loglik(pop_ctx* c, int64_t K, int n_params, const double* theta, int mode, double* out_lnL,
                    uint32_t* out_flags, int mem)
 {
+    pop::TraceRange trace_("pop_cbc_loglik");
     if (!c) return POP_EINVAL;
     if (!c->cbc) return fail(c, POP_ESTATE, "pop_cbc_loglik: load data first (pop_cbc_load)");
     CbcState& st = *c->cbc;
@@ -959,6 +967,7 @@ int pop_cbc_last_ms(pop_ctx* c, double* sum_ms, double* total_ms)
 
 int pop_load_vt_grid(pop_ctx* c, int n_m1, const double* m1, int n_q, const double* q, const double* pdet, int mem)
 {
+    pop::TraceRange trace_("pop_load_vt_grid");
     if (!c) return POP_EINVAL;
     if (!valid_mem(mem)) return fail(c, POP_EINVAL, "pop_load_vt_grid: bad mem");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -991,6 +1000,7 @@ int pop_set_xi_source(pop_ctx* c, int source)
 int pop_xi_grid(pop_ctx* c, int64_t K, int n_params, const double* lambda, int mode, double* out_lnxi,
                 uint32_t* out_flags, int mem)
 {
+    pop::TraceRange trace_("pop_xi_grid");
     if (!c) return POP_EINVAL;
     if (!c->grid) return fail(c, POP_ESTATE, "pop_xi_grid: load a grid first (pop_load_vt_grid)");
     if (K < 0 || K > (1LL << 24)) return fail(c, POP_EINVAL, "pop_xi_grid: K out of range");
@@ -1092,6 +1102,7 @@ int pop_last_kernel_ms(pop_ctx* c, double* weight_ms, double* total_ms)
 
 int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
 {
+    pop::TraceRange trace_("pop_autotune");
     if (!c) return POP_EINVAL;
     if (mode != POP_MODE_F64 && mode != POP_MODE_F32) return fail(c, POP_EINVAL, "pop_autotune: bad mode");
     if (c->ev.n == 0 || c->inj.n == 0) return fail(c, POP_ESTATE, "pop_autotune: load events and injections first");

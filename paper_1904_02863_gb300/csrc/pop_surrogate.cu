@@ -15,6 +15,7 @@
 #include "pop.h"
 #include "pop_devbuf.h"
 #include "pop_internal.h"
+#include "pop_trace.h"
 #include "pop_mlp.h"
 
 namespace pop {
@@ -222,6 +223,7 @@ int pop_mlp_train_step(pop_ctx* c, int64_t B, const float* x, const float* t, fl
 int pop_xi_surrogate_train(pop_ctx* c, int64_t n_pairs, double heldout_frac, uint64_t seed, const double* lambda_lo,
                            const double* lambda_hi, int n_params, int epochs, double* out_heldout_rmse)
 {
+    pop::TraceRange trace_("pop_xi_surrogate_train");
     if (!c) return POP_EINVAL;
     if (!ctx_has_storage(c, POP_STORE_F64) && !ctx_has_storage(c, POP_STORE_F32))
         return ctx_fail(c, POP_ESTATE, "pop_xi_surrogate_train: load events and injections first");
@@ -376,6 +378,7 @@ int pop_xi_surrogate_info(pop_ctx* c, double* heldout_rmse, double* mc_noise, do
 int pop_xi_surrogate_infer(pop_ctx* c, int64_t K, int n_params, const double* lambda, double* out_lnxi,
                            double* out_lnneff, uint8_t* out_fallback, int mem)
 {
+    pop::TraceRange trace_("pop_xi_surrogate_infer");
     if (!c) return POP_EINVAL;
     int st;
     Surrogate* s = ctx_surrogate(c, &st);
