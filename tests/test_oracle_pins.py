@@ -173,6 +173,31 @@ def test_mean_weight_is_one_under_a_normalised_proposal(oracle, n_dims):
         assert abs(w.mean() - 1.0) < 5 * se + 1e-3, (w.mean(), se)
 
 
+# Lambda* for the self-prior pin: every clipped sample is inside its support (mmin below the
+# clip at 5, uniform spins so that a = 0 or 1 keeps density 1).
+LAMBDA_STAR = np.array([2.3, 1.0, 4.9, 80.0, 0.1, 35.0, 4.0, 1.0, 1.0, 0.5, 0.5, 2.7])
+
+
+@pytest.mark.parametrize("n_dims", [6, 7])
+def test_weights_are_one_when_the_prior_is_the_population(oracle, n_dims):
+    """With pi(theta_ij) := p(theta_ij | Lambda*), every weight p/pi is 1, so each event mean is 1
+    and ln L(Lambda*) = -N ln xi(Lambda*) up to rounding (sum of N logs of means of ones)."""
+    cat = synth.make_catalog(7, [1, 30, 200, 5, 64, 13, 99], n_dims, seed=31 + n_dims)
+    L = LAMBDA_STAR[:11 + (n_dims == 7)]
+    prior = np.array([oracle.p_theta(t, L) for t in cat.theta])
+    assert (prior > 0).all()
+    cat = synth.Catalog(cat.offsets, cat.theta, prior)
+    inj = synth.make_injections(20000, n_dims, seed=33 + n_dims)
+    lnL, lnxi, _, flags = oracle.loglik(cat, inj, L[None, :])
+    assert flags[0] & ~np.uint32(oracle.FLAG_LOW_NEFF) == 0
+    assert abs(lnL[0] + cat.n_events * lnxi[0]) <= 1e-13 * cat.n_events * (1 + abs(lnxi[0]))
+    # and away from Lambda* the event term is no longer zero
+    L2 = L.copy()
+    L2[0] = 3.0
+    lnL2, lnxi2, _, _ = oracle.loglik(cat, inj, L2[None, :])
+    assert abs(lnL2[0] + cat.n_events * lnxi2[0]) > 1e-3
+
+
 @pytest.mark.parametrize("n_dims", [6, 7])
 def test_xi_is_one_at_the_draw_distribution(oracle, n_dims):
     inj = synth.make_injections(20000, n_dims, seed=3, detect=False)
