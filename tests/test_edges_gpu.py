@@ -98,3 +98,27 @@ def test_every_draw_found(B, oracle):
     like = B.Likelihood(0).load(cat, inj)
     check_all_modes(B, like, cat, inj, lam, oracle)
     like.close()
+
+
+@pytest.mark.parametrize("n_dims", [6, 7])
+def test_unit_weights_when_the_prior_is_the_population(B, oracle, n_dims):
+    """pi(theta) := p(theta | Lambda*) from the oracle makes every GPU weight p_GPU / p_oracle; at
+    Lambda* each is 1 up to rounding, so ln L(Lambda*) = -N ln xi(Lambda*): FP64 and float-float to
+    N * 1e-13 (per-sample agreement of the two densities), FP32 to N * 2e-5 (its per-weight
+    budget).  Lambda* has mmin below the samples' clip at 5 and uniform spins, so every sample
+    is inside the support."""
+    from paper_1904_02863_gb300 import synth
+    L = np.array([2.3, 1.0, 4.9, 80.0, 0.1, 35.0, 4.0, 1.0, 1.0, 0.5, 0.5, 2.7])[:11 + (n_dims == 7)]
+    cat = synth.make_catalog(40, np.arange(40) * 97 % 5000 + 1, n_dims, seed=661 + n_dims)
+    inj = synth.make_injections(50000, n_dims, seed=663 + n_dims)
+    N = cat.n_events
+    for mode, theta, tol in ((B.POP_MODE_F64, cat.theta, 1e-13), (B.POP_MODE_FF, cat.theta, 1e-13),
+                             (B.POP_MODE_F32, synth.round_to_f32(cat.theta), 2e-5)):
+        prior = np.array([oracle.p_theta(t, L) for t in theta])
+        assert (prior > 0).all()
+        c = synth.Catalog(cat.offsets, theta, prior)
+        like = B.Likelihood(0).load(c, inj)
+        lnL, lnxi, _, flags = like(L[None, :], mode)
+        like.close()
+        assert flags[0] & ~np.uint32(B.POP_FLAG_LOW_NEFF) == 0, (mode, flags)
+        assert abs(lnL[0] + N * lnxi[0]) <= tol * N * (1 + abs(lnxi[0])), (mode, lnL[0] + N * lnxi[0])
