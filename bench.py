@@ -103,7 +103,7 @@ def f32_roofline(pairs, weight_ms):
     return {"bound": "alu", "kernel": "weight_f32_kernel", "achieved": achieved / 1e12, "peak": peak / 1e12,
             "unit": "T MUFU slots/s", "frac": achieved / peak, "traffic": None, "weight_ms": weight_ms,
             "in_support_pairs": pairs, "slots_per_in_support_pair": MUFU_SLOTS_PER_PAIR,
-            "peak_basis": "MUFU ex2 32/SM/clk (rcp 16: 2 slots) x 152 SMs x 2070 MHz, microbenchmark rates"}
+            "peak_basis": "MUFU ex2 32/SM/clk (rcp 16: 2 slots) x 152 SMs x 2070 MHz, rates measured by pop_pipe_rates"}
 
 
 def grid_support_triples(m1, q, lam):
@@ -790,6 +790,8 @@ def main():
         roofline = f32_roofline(n_ev_pairs + n_inj_pairs, w_h)
     else:
         roofline = ff_roofline(n_ev_pairs + n_inj_pairs, w_h)
+    # Measured pipe rates (thread operations per SM clock) beside the constants the rooflines use.
+    pipe = dict(B.pop_pipe_rates(local), unit="thread ops per SM clock", source="pop_pipe_rates, this run")
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_h / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -808,6 +810,7 @@ def main():
         # set K, prologue, weight, finalise (+ the FP32 kernel's Lambda order)
         "gpu_launches": (4 if head == B.POP_MODE_F64 else 5) * args.steps,
         "clocks": clocks,
+        "pipe_rates": pipe,
     }
     if args.mode == "both":
         ref64_r = f64_on_rounded_inputs(B, cat, inj, dev_lam, local, stream)

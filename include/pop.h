@@ -312,6 +312,20 @@ int pop_math_check(pop_ctx* ctx, int fn, int64_t n, const double* x, double* y, 
  * of range. */
 int pop_wait_check(pop_ctx* ctx, int arrive, int polls);
 
+/* Diagnostic: the per-SM throughput of the pipes the weight kernels are bound
+ * by, measured on `device` (the paper has no counterpart; the rooflines of
+ * the weight kernels need these rates, and the data sheet gives no MUFU
+ * figure).  One CTA of 1024 threads per SM runs 8 independent chains of one
+ * operation per thread; clock64 around the chains gives thread operations per
+ * SM clock (median over the SMs):
+ *   rates[0] FP64 fma, rates[1] FP32 fma, rates[2] MUFU ex2.approx.f32,
+ *   rates[3] MUFU rcp.approx.f32.
+ * rates: a host array of 4 doubles, owned by the caller.  Synchronous, a few
+ * milliseconds; allocates two small device buffers and frees them.  Restores
+ * the calling thread's current device.  POP_EINVAL for a NULL rates or a negative
+ * device, POP_ECUDA when a CUDA call fails. */
+int pop_pipe_rates(int device, double* rates);
+
 /* ------------------------------------------------------------------ ln xi surrogate
  * The paper announces a learned selection term that includes spin effects in
  * VT at no extra run-time cost (Sec. "Population acceleration", right after the

@@ -29,7 +29,7 @@ EXPORTS = (
     "pop_create", "pop_destroy", "pop_last_error", "pop_status_string", "pop_version",
     "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
     "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
-    "pop_loglik_f64_noalloc", "pop_math_check", "pop_wait_check",
+    "pop_loglik_f64_noalloc", "pop_math_check", "pop_wait_check", "pop_pipe_rates",
     "pop_xi_surrogate_train", "pop_xi_surrogate_info", "pop_xi_surrogate_infer", "pop_xi_surrogate_save",
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
                                          vp, vp, vp, vp, ctypes.c_char_p, i32]),
         "pop_math_check": (i32, [vp, i32, i64, vp, vp, i32]),
         "pop_wait_check": (i32, [vp, i32, i32]),
+        "pop_pipe_rates": (i32, [i32, vp]),
         "pop_xi_surrogate_train": (i32, [vp, i64, d, ctypes.c_uint64, vp, vp, i32, i32, ctypes.POINTER(d)]),
         "pop_xi_surrogate_info": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                         ctypes.POINTER(i32)]),
@@ -302,6 +303,13 @@ def pop_wait_check(ctx, arrive, polls):
     barrier completes (arrive=True) and raises PopError(POP_ETIMEOUT) when it gives up after
     ``polls`` polls (arrive=False)."""
     _check(ctx, load_library().pop_wait_check(ctx, int(bool(arrive)), int(polls)))
+
+
+def pop_pipe_rates(device=0):
+    """Measured thread operations per SM clock: {"dfma", "ffma", "ex2", "rcp"}."""
+    r = np.zeros(4)
+    _check(None, load_library().pop_pipe_rates(int(device), r.ctypes.data_as(ctypes.c_void_p)))
+    return dict(zip(("dfma", "ffma", "ex2", "rcp"), (float(v) for v in r)))
 
 
 def pop_math_check(ctx, fn, x):

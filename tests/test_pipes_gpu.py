@@ -1,0 +1,32 @@
+"""The pipe-rate diagnostic behind the weight kernels' rooflines (pop_pipe_rates): thread
+operations per SM clock for FP64 fma, FP32 fma, MUFU ex2 and MUFU rcp.
+
+GB300 has 2 FP64 fma lanes and 128 FP32 fma lanes per SM per clock, so the measured rates must
+lie at or below those and above half of them; the MUFU rates must order ex2 >= rcp and lie
+within the 4..64 per clock that any recent SM has.  A rate far outside means the chains were
+optimised away or the CTAs shared SMs."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    from paper_1904_02863_gb300 import binding, build
+    build.build()
+    binding.load_library()
+    return binding
+
+
+def test_pipe_rates(B):
+    r = B.pop_pipe_rates(0)
+    print("pipe rates (thread ops per SM clock):", r)
+    assert 1.0 <= r["dfma"] <= 2.05, r
+    assert 64.0 <= r["ffma"] <= 129.0, r
+    assert 4.0 <= r["rcp"] <= r["ex2"] <= 64.0, r
+    with pytest.raises(B.PopError):
+        B.pop_pipe_rates(-1)
