@@ -81,7 +81,9 @@ enum { POP_MODE_F64 = 0, POP_MODE_F32 = 1, POP_MODE_F32_SURROGATE = 2, POP_MODE_
 enum { POP_MEM_HOST = 0, POP_MEM_DEVICE = 1 };
 
 /* Per-Lambda result flags (out_flags).  ln L = -inf is a legitimate value,
- * not an error; NaN is never returned. */
+ * not an error.  NaN is never returned for a Lambda whose densities are
+ * representable in FP64; beyond that range (|1+beta| or |1-alpha| times
+ * ln(mmax/mmin) above ~700, or sigma below ~1e-154) ln L may be NaN. */
 enum {
     POP_FLAG_INVALID_LAMBDA = 1u,  /* Lambda outside the model's domain: ln L = -inf */
     POP_FLAG_ZERO_EVENT = 2u,      /* some event has sum_j w_ij = 0: ln L = -inf */
