@@ -75,3 +75,22 @@ def test_cpu_baseline_parity_field_against_the_oracle(oracle):
     off[0] = off[0] + 1e-6
     bad = bench.cpu_baseline(cat, inj, lam, 4, gpu_f64=off)
     assert bad["parity_f64_kernel"]["max_over_f64_tol"] > 1.0
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference times the oracle on the host and prints one JSON line with the
+    contract's keys (a bounded sample: 2 Lambda rows of the full catalog workload)."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--oracle-lambdas", "2"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "evals/s" and d["value"] > 0
+    assert d["config"]["workload"] == bench.WORKLOAD and d["config"]["events"] == 1000
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
