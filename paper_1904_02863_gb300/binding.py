@@ -41,6 +41,7 @@ POP_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class PopError(RuntimeError):
+    """A pop_status other than POP_OK, with the library's error text; .status holds the code."""
     def __init__(self, status, message):
         super().__init__(f"{status_string(status)}: {message}")
         self.status = status
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
 
 
 def status_string(status: int) -> str:
+    """Name of a pop_status value (the number itself if the library cannot be loaded)."""
     try:
         return load_library().pop_status_string(status).decode()
     except Exception:
@@ -146,6 +148,7 @@ def _stream_ptr(stream):
 
 # ------------------------------------------------------------------ C-ABI mirrors
 def pop_version() -> int:
+    """ABI version of the loaded library (major * 10000 + minor * 100 + patch)."""
     return load_library().pop_version()
 
 
@@ -158,6 +161,8 @@ def pop_validate_events(n_events, offsets, n_dims):
 
 
 def pop_create(device: int = 0, stream=None):
+    """A context on `device` whose work runs on `stream` (a torch.cuda.Stream; None = the
+    legacy default stream).  It owns all device memory of the calls made on it."""
     ctx = ctypes.c_void_p()
     rc = load_library().pop_create(ctypes.byref(ctx), int(device), _stream_ptr(stream))
     _check(None, rc)
@@ -165,14 +170,19 @@ def pop_create(device: int = 0, stream=None):
 
 
 def pop_destroy(ctx):
+    """Frees every buffer of the context."""
     _check(ctx, load_library().pop_destroy(ctx))
 
 
 def pop_last_error(ctx) -> str:
+    """Text of the last error on the context (or of the last failed pop_create for None)."""
     return load_library().pop_last_error(ctx).decode()
 
 
 def pop_load_events(ctx, offsets, theta, prior, storage=POP_STORE_F64 | POP_STORE_F32):
+    """Copies a ragged catalog: CSR offsets [N+1] (host), theta [offsets[-1], 6 or 7] and the
+    single-event prior [offsets[-1]] (both numpy, or both CUDA tensors), and packs the features
+    in the requested storage(s).  Replaces earlier events; the caller keeps its arrays."""
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     tp, mem, k1 = _arg(theta, np.float64)
     pp, mem2, k2 = _arg(prior, np.float64)
@@ -184,6 +194,8 @@ def pop_load_events(ctx, offsets, theta, prior, storage=POP_STORE_F64 | POP_STOR
 
 
 def pop_load_injections(ctx, n_draw, theta, p_draw, storage=POP_STORE_F64 | POP_STORE_F32):
+    """Copies the found injections theta [n_found, n_dims] with their draw pdf p_draw [n_found];
+    n_draw counts found and missed draws.  Load the events first (same n_dims)."""
     tp, mem, k1 = _arg(theta, np.float64)
     pp, mem2, k2 = _arg(p_draw, np.float64)
     if mem != mem2:
@@ -264,32 +276,40 @@ def pop_cbc_loglik(ctx, thetas, mode=POP_MODE_F64):
 
 
 def pop_cbc_last_ms(ctx):
+    """(sums-kernel ms, whole-call ms) of the last pop_cbc_loglik, from CUDA events."""
     w, t = ctypes.c_double(), ctypes.c_double()
     _check(ctx, load_library().pop_cbc_last_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
     return w.value, t.value
 
 
 def pop_set_tiling(ctx, mode, lambda_tile, block_threads, blocks_per_sm=0):
+    """Fixes the weight kernel's tiling for `mode` (Lambda per work item, threads per block,
+    blocks per SM; 0 = as many as fit)."""
     _check(ctx, load_library().pop_set_tiling(ctx, int(mode), int(lambda_tile), int(block_threads), int(blocks_per_sm)))
 
 
 def pop_get_tiling(ctx, mode):
+    """(lambda_tile, block_threads, blocks_per_sm) that `mode` currently uses."""
     t, b, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(ctx, load_library().pop_get_tiling(ctx, int(mode), ctypes.byref(t), ctypes.byref(b), ctypes.byref(s)))
     return t.value, b.value, s.value
 
 
 def pop_autotune(ctx, mode, K, cache_path=None):
+    """Times the candidate tilings of `mode` on a batch of K Lambda, keeps the fastest (cached in
+    `cache_path` per device and workload when given) and returns it."""
     cp = cache_path.encode() if cache_path else None
     _check(ctx, load_library().pop_autotune(ctx, int(mode), int(K), cp))
     return pop_get_tiling(ctx, mode)
 
 
 def pop_set_graphs(ctx, enable: bool):
+    """Turns CUDA-graph replay of the evaluation pipeline on (default) or off."""
     _check(ctx, load_library().pop_set_graphs(ctx, 1 if enable else 0))
 
 
 def pop_last_kernel_ms(ctx):
+    """(weight-kernel ms, whole-pipeline ms) of the last pop_loglik, from CUDA events."""
     w, t = ctypes.c_double(), ctypes.c_double()
     _check(ctx, load_library().pop_last_kernel_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
     return w.value, t.value
@@ -336,6 +356,7 @@ def pop_load_vt_grid(ctx, m1_nodes, q_nodes, pdet):
 
 
 def pop_set_xi_source(ctx, source):
+    """Selection term of pop_loglik: POP_XI_INJECTIONS (default) or POP_XI_GRID."""
     _check(ctx, load_library().pop_set_xi_source(ctx, int(source)))
 
 
@@ -351,6 +372,7 @@ def pop_xi_grid(ctx, lambdas, mode=POP_MODE_F64):
 
 
 def pop_xi_grid_last_ms(ctx):
+    """(contraction-kernel ms, whole grid-term ms) of the last grid evaluation."""
     w, t = ctypes.c_double(), ctypes.c_double()
     _check(ctx, load_library().pop_xi_grid_last_ms(ctx, ctypes.byref(w), ctypes.byref(t)))
     return w.value, t.value
@@ -375,17 +397,20 @@ def pop_mlp_gemm_check(ctx, A, B):
 
 
 def pop_mlp_set_params(ctx, flat):
+    """Sets the network's FP32 master parameters from a flat array of MLP_N_PARAMS floats."""
     p, pp = _f32(flat, (MLP_N_PARAMS,))
     _check(ctx, load_library().pop_mlp_set_params(ctx, pp, MLP_N_PARAMS))
 
 
 def pop_mlp_get_params(ctx):
+    """The network's FP32 master parameters as a flat array of MLP_N_PARAMS floats."""
     out = np.empty(MLP_N_PARAMS, np.float32)
     _check(ctx, load_library().pop_mlp_get_params(ctx, out.ctypes.data_as(ctypes.c_void_p), MLP_N_PARAMS))
     return out
 
 
 def pop_mlp_forward(ctx, x):
+    """Network outputs [B, 2] for normalised inputs x [B, 12] (BF16 tensor cores, FP32 accumulate)."""
     xa, px = _f32(x)
     y = np.empty((xa.shape[0], 2), np.float32)
     _check(ctx, load_library().pop_mlp_forward(ctx, xa.shape[0], px, y.ctypes.data_as(ctypes.c_void_p)))
@@ -393,6 +418,7 @@ def pop_mlp_forward(ctx, x):
 
 
 def pop_mlp_gradients(ctx, x, t):
+    """(flat parameter gradients, loss) of the mean squared error against targets t [B, 2]."""
     xa, px = _f32(x)
     ta, pt = _f32(t)
     g = np.empty(MLP_N_PARAMS, np.float32)
@@ -403,12 +429,15 @@ def pop_mlp_gradients(ctx, x, t):
 
 
 def pop_mlp_train_step(ctx, x, t, lr):
+    """One Adam step (beta 0.9 / 0.999, eps 1e-8) of the network on the batch (x, t)."""
     xa, px = _f32(x)
     ta, pt = _f32(t)
     _check(ctx, load_library().pop_mlp_train_step(ctx, xa.shape[0], px, pt, float(lr)))
 
 
 def pop_xi_surrogate_train(ctx, n_pairs, lo, hi, epochs=100, heldout_frac=0.1, seed=0):
+    """Trains the ln xi network on n_pairs Lambda drawn uniformly from the box [lo, hi], with
+    targets from the loaded injections; returns the held-out error in ln xi."""
     lo_a = np.ascontiguousarray(lo, dtype=np.float64)
     hi_a = np.ascontiguousarray(hi, dtype=np.float64)
     rmse = ctypes.c_double()
@@ -420,6 +449,7 @@ def pop_xi_surrogate_train(ctx, n_pairs, lo, hi, epochs=100, heldout_frac=0.1, s
 
 
 def pop_xi_surrogate_info(ctx):
+    """Held-out error, the targets' Monte Carlo scatter, their difference and the trust gate."""
     r, n, e, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     _check(ctx, load_library().pop_xi_surrogate_info(ctx, ctypes.byref(r), ctypes.byref(n), ctypes.byref(e),
                                                      ctypes.byref(t)))
@@ -427,6 +457,7 @@ def pop_xi_surrogate_info(ctx):
 
 
 def pop_xi_surrogate_infer(ctx, lambdas):
+    """(ln xi, ln N_eff, fallback mask) from the trained network for each Lambda row."""
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
     K, P = lam.shape
     lx, ln, fb = np.empty(K), np.empty(K), np.empty(K, np.uint8)
@@ -438,10 +469,12 @@ def pop_xi_surrogate_infer(ctx, lambdas):
 
 
 def pop_xi_surrogate_save(ctx, path):
+    """Writes the trained network, its normalisation and held-out statistics to `path`."""
     _check(ctx, load_library().pop_xi_surrogate_save(ctx, str(path).encode()))
 
 
 def pop_xi_surrogate_load(ctx, path):
+    """Reads a network written by pop_xi_surrogate_save."""
     _check(ctx, load_library().pop_xi_surrogate_load(ctx, str(path).encode()))
 
 
