@@ -29,6 +29,9 @@ MUTANTS = {
     "N factor of ln xi": ("sum_ln - (double)n_events * lnxi", "sum_ln - lnxi"),
     "event mean": ("log(s / (double)n_i)", "log(s)"),
     "prior weight": ("/ prior[j];", "* prior[j];"),
+    "effective sample count": ("neff = var > 0.0 ? xi * xi / var", "neff = var > 0.0 ? 2.0 * xi * xi / var"),
+    "variance of the mean": ("- xi * xi / (double)n_draw;", "- xi * xi / (double)n_found;"),
+    "low-N_eff threshold": ("if (neff < 4.0 * (double)n_events)", "if (neff < 1.0 * (double)n_events)"),
 }
 GRID_MUTANTS = {
     "grid m1 weights": ("double wa = 0.5 * (", "double wa = ("),

@@ -284,3 +284,63 @@ def test_invalid_lambda_is_minus_inf_and_flagged(oracle, bad):
     lnL, lnxi, neff, flags = oracle.loglik(cat, inj, L)
     assert lnL[0] == -np.inf and flags[0] & oracle.FLAG_INVALID_LAMBDA
     assert not np.isnan(lnL[0])
+
+
+# --------------------------------------------------------------------------- effective sample count of xi
+# N_eff of the Monte Carlo selection term (Sec. "Population acceleration": xi is a sample mean over the
+# N_draw injections, the missed ones contributing 0) is xi^2 divided by the variance of that sample mean.
+# Three pins that do not restate the oracle's formula: a two-class worked example with exact weights, the
+# variance of the explicit zero-padded draw vector (numpy), and the scatter of xi over independent
+# injection sets. The LOW_NEFF flag (N_eff < 4 N) is pinned on both sides of its threshold.
+def _exact_weight_injections(oracle, L, weights, n_draw):
+    """Found injections inside the support whose weights p/p_draw are the given numbers."""
+    th = np.array([[20.0 + 3.0 * k, 0.7, 0.3, 0.4, 0.2, 0.6] for k in range(len(weights))])
+    p = np.array([oracle.p_theta(t, L) for t in th])
+    assert (p > 0).all()
+    return synth.Injections(th, p / np.asarray(weights, float), n_draw)
+
+
+def _small_catalog(n_events):
+    g = json.load(open(GOLDEN))
+    th = np.array(g["theta"][:1] * n_events)
+    return synth.Catalog(np.arange(n_events + 1, dtype=np.int64), th, np.full(n_events, 7.5))
+
+
+def test_neff_two_class_worked_example(oracle):
+    """Draws x = (1, 1, 2, 2, 2, 0, 0, 0, 0, 0): mean 0.8, E[x^2] = 1.4, so the variance of the mean is
+    (1.4 - 0.64) / 10 = 0.076 and N_eff = 0.64 / 0.076 = 160 / 19."""
+    L = L0
+    inj = _exact_weight_injections(oracle, L, [1.0, 1.0, 2.0, 2.0, 2.0], 10)
+    for n_events, low in ((2, False), (3, True)):  # 4N = 8 < 8.42 < 12 = 4N
+        lnL, lnxi, neff, flags = oracle.loglik(_small_catalog(n_events), inj, L[None, :])
+        assert math.exp(lnxi[0]) == pytest.approx(0.8, rel=1e-14)
+        assert neff[0] == pytest.approx(160.0 / 19.0, rel=1e-12)
+        assert bool(flags[0] & oracle.FLAG_LOW_NEFF) == low, (n_events, neff[0])
+
+
+def test_neff_is_the_variance_of_the_padded_draw_vector(oracle):
+    g = json.load(open(GOLDEN))
+    cat = synth.Catalog(np.array(g["offsets"], np.int64), np.array(g["theta"]), np.array(g["prior"]))
+    inj = synth.Injections(np.array(g["injections"]), np.array(g["p_draw"]), g["n_draw"])
+    lams = np.array(g["lambdas"])
+    _, lnxi, neff, flags = oracle.loglik(cat, inj, lams)
+    for k, L in enumerate(lams):
+        x = np.zeros(inj.n_draw)
+        x[:inj.n_found] = [_ref_density(t, L) / p for t, p in zip(inj.theta, inj.p_draw)]
+        var_of_mean = np.var(x) / inj.n_draw
+        assert neff[k] == pytest.approx(np.mean(x) ** 2 / var_of_mean, rel=1e-10)
+        assert bool(flags[k] & oracle.FLAG_LOW_NEFF) == (neff[k] < 4 * cat.n_events)
+
+
+def test_neff_predicts_the_scatter_of_xi(oracle):
+    """Over independent injection sets, Var(xi_hat) = xi^2 / N_eff (to sampling error)."""
+    L = L0[None, :]
+    cat = _small_catalog(1)
+    xis, pred = [], []
+    for r in range(300):
+        inj = synth.make_injections(3000, 6, seed=1000 + r)
+        _, lnxi, neff, _ = oracle.loglik(cat, inj, L)
+        xis.append(math.exp(lnxi[0]))
+        pred.append(math.exp(2 * lnxi[0]) / neff[0])
+    ratio = np.var(xis, ddof=1) / np.mean(pred)
+    assert 0.75 < ratio < 1.33, ratio
