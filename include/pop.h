@@ -406,16 +406,24 @@ int pop_mlp_gemm_check(pop_ctx* ctx, int M, int N, int K, const float* A, const 
  *   out_lnL, out_lnxi, out_neff (double[K]), out_flags (uint32[K])  (device, all required)
  *   msg[msg_len]     host buffer for the error text (may be NULL)
  *
+ * Every pointer but msg must be device (or managed) memory of `device`;
+ * anything else (host, pinned host, another GPU's memory) fails with
+ * POP_EINVAL before any GPU work.  The calling thread's current device is
+ * restored before the call returns.
+ *
  * The scratch needed is about K * 8 * (n_events + 2 * ceil(n_found / 4096))
  * + K * 256 bytes; a call above POP_NOALLOC_SCRATCH_BYTES fails with
- * POP_EINVAL before any GPU work (split the Lambda batch).  Malformed offsets,
- * non-finite samples and prior/p_draw <= 0 give POP_EINVAL after the kernels
- * ran (outputs then undefined).  The call is synchronous: it returns after the
- * outputs are written.  The first call on a device looks up the array's device
- * address (module load and symbol lookup), so make that first call before any
- * stream capture.  All calls share the one array and each call rewrites every
- * scratch word it reads, so nothing carries over from the previous call; calls
- * that overlap on the GPU (other threads or streams) race on it. */
+ * POP_EINVAL before any GPU work (split the Lambda batch).  Malformed offsets
+ * (offsets[0] != 0, offsets[N] != n_samples, an event with no samples or one
+ * that ends beyond n_samples), non-finite samples and prior/p_draw <= 0 give
+ * POP_EINVAL after the kernels ran (outputs then undefined; the kernels never
+ * read outside the buffers).  The call is synchronous: it copies a count of
+ * malformed inputs to the host and waits for the stream before it returns.
+ * The first call on a device looks up the array's device address (module load
+ * and symbol lookup), so make that first call before any stream capture.  All
+ * calls share the one array and each call rewrites every scratch word it
+ * reads, so nothing carries over from the previous call; calls that overlap on
+ * the GPU (other threads or streams) race on it. */
 int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events, const int64_t* offsets,
                            int64_t n_samples, int n_dims, const double* theta, const double* prior,
                            int64_t n_found, int64_t n_draw, const double* inj_theta, const double* p_draw,

@@ -478,13 +478,25 @@ def pop_xi_surrogate_load(ctx, path):
     _check(ctx, load_library().pop_xi_surrogate_load(ctx, str(path).encode()))
 
 
-def pop_loglik_f64_noalloc(offsets, theta, prior, n_draw, inj_theta, p_draw, lambdas, out, device=0, stream=None):
+def pop_loglik_f64_noalloc(offsets, theta, prior, n_draw, inj_theta, p_draw, lambdas, out, stream=None):
     """FP64 ln L with no device allocation by the library (see include/pop.h).
 
-    Every argument but ``n_draw`` is a contiguous CUDA tensor the caller owns
-    (offsets int64, the rest float64; ``out`` = (lnL, lnxi, neff, flags int32),
-    each of length K).  Synchronous; raises PopError on failure.
+    Every argument but ``n_draw`` is a contiguous CUDA tensor the caller owns,
+    all on one GPU (offsets int64, the rest float64; ``out`` = (lnL, lnxi,
+    neff, flags int32), each of length K).  The call runs on that GPU, on
+    ``stream`` (default: torch's current stream there, so that it is ordered
+    after the work that wrote the inputs).  Synchronous; raises PopError on
+    failure, ValueError when a tensor is not on the GPU of ``offsets``.
     """
+    tensors = (offsets, theta, prior, inj_theta, p_draw, lambdas) + tuple(out)
+    if not all(_is_torch(t) and t.is_cuda for t in tensors):
+        raise ValueError("pop_loglik_f64_noalloc takes CUDA tensors only")
+    device = offsets.device.index
+    if any(t.device.index != device for t in tensors):
+        raise ValueError(f"every tensor must be on cuda:{device}, the device of offsets")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device)
     ptr = lambda t, dt: _arg(t, dt)[0]
     msg = ctypes.create_string_buffer(512)
     rc = load_library().pop_loglik_f64_noalloc(

@@ -66,14 +66,39 @@ Layout layout(int64_t n_events, int64_t n_inj_chunks, int64_t K)
     return L;
 }
 
-__global__ void setup_kernel(int64_t* dK, int64_t K, unsigned long long* bad, int32_t* ecb, int64_t n_events)
+// Writes K, clears the bad-input count (or sets it to 1 when the CSR offsets do
+// not start at 0 or end at n_samples) and lays out one work chunk per event.
+__global__ void setup_kernel(int64_t* dK, int64_t K, unsigned long long* bad, int32_t* ecb, int64_t n_events,
+                             const int64_t* offsets, int64_t n_samples)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) {
         *dK = K;
-        *bad = 0ull;
+        *bad = (offsets[0] != 0 || offsets[n_events] != n_samples) ? 1ull : 0ull;
     }
     if (i <= n_events) ecb[i] = (int32_t)i;  // one work chunk per event
+}
+
+// Restores the calling thread's current device on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    DeviceGuard() { (void)cudaGetDevice(&prev); }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) (void)cudaSetDevice(prev);
+    }
+};
+
+// True when p is device or managed memory of `device` (host, pinned and
+// unregistered pointers are refused before any kernel could read them).
+bool on_device(const void* p, int device)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
 }
 
 struct RawSet {
@@ -261,8 +286,18 @@ extern "C" int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events
                  (long long)n_events, (long long)n_inj_chunks, SCRATCH_BYTES);
         return fail(POP_EINVAL, m);
     }
+    const DeviceGuard guard;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(POP_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    {
+        const void* ptrs[] = {offsets, theta, prior, inj_theta, p_draw, lambda, out_lnL, out_lnxi, out_neff, out_flags};
+        const char* names[] = {"offsets", "theta", "prior", "inj_theta", "p_draw", "lambda", "out_lnL", "out_lnxi",
+                               "out_neff", "out_flags"};
+        for (int i = 0; i < 10; ++i)
+            if (!on_device(ptrs[i], device))
+                return fail(POP_EINVAL, std::string(names[i]) + " is not device memory of device " +
+                                            std::to_string(device));
+    }
     unsigned char* base = nullptr;
     {
         // One-time set-up per device: the symbol's device address (host code
@@ -286,7 +321,8 @@ extern "C" int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events
     double* part = reinterpret_cast<double*>(base + Lo.part);
     double* part2 = reinterpret_cast<double*>(base + Lo.part2);
 
-    setup_kernel<<<(unsigned)((n_events + 1 + 255) / 256), 256, 0, s>>>(dK, K, bad, ecb, n_events);
+    setup_kernel<<<(unsigned)((n_events + 1 + 255) / 256), 256, 0, s>>>(dK, K, bad, ecb, n_events, offsets,
+                                                                         n_samples);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(POP_ECUDA, cudaGetErrorString(e));
     if ((e = launch_prologue(lambda, dK, K, n_params, c64, c32, s)) != cudaSuccess)
         return fail(POP_ECUDA, cudaGetErrorString(e));
@@ -307,6 +343,8 @@ extern "C" int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events
     if ((e = cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(POP_ECUDA, cudaGetErrorString(e));
-    if (h_bad) return fail(POP_EINVAL, "malformed offsets, non-finite samples or prior/p_draw <= 0");
+    if (h_bad)
+        return fail(POP_EINVAL, "malformed offsets (offsets[0] != 0, offsets[N] != n_samples, an empty or "
+                                "out-of-range event), non-finite samples or prior/p_draw <= 0");
     return POP_OK;
 }

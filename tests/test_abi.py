@@ -92,3 +92,18 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".h", ".cuh")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "pop_oracle" not in src, f
+
+
+def test_noalloc_wrapper_takes_cuda_tensors_of_one_device_only():
+    """The no-allocation wrapper refuses numpy arrays and CPU tensors before it reaches the library
+    (the device and stream it runs on are taken from the tensors)."""
+    import torch
+    from paper_1904_02863_gb300 import binding
+    off = torch.tensor([0, 2], dtype=torch.int64)
+    th, pr = torch.zeros(2, 6, dtype=torch.float64), torch.ones(2, dtype=torch.float64)
+    lam = torch.zeros(1, 11, dtype=torch.float64)
+    out = (torch.empty(1, dtype=torch.float64),) * 3 + (torch.empty(1, dtype=torch.int32),)
+    with pytest.raises(ValueError):
+        binding.pop_loglik_f64_noalloc(off, th, pr, 10, th, pr, lam, out)
+    with pytest.raises(ValueError):
+        binding.pop_loglik_f64_noalloc(off.numpy(), th, pr, 10, th, pr, lam, out)

@@ -171,8 +171,8 @@ def test_loglik_with_surrogate_xi(B, trained):
     np.testing.assert_array_equal(fell, fb == 1)
     assert fell[:5].all()
     info = B.pop_xi_surrogate_info(like.ctx)
-    if info["trusted"]:
-        assert used[5:].mean() > 0.9
+    assert info["trusted"], info   # the seeded training must pass the gate, else this test is vacuous
+    assert used[5:].mean() > 0.9
     fin = np.isfinite(mc[0])
     # Monte Carlo rows reproduce the FP32 form exactly; surrogate rows differ only by -N (ln xi_s - ln xi_mc)
     np.testing.assert_array_equal(su[0][fell & fin], mc[0][fell & fin])
@@ -191,7 +191,7 @@ def test_surrogate_skips_the_injection_work(B):
     inj = synth.make_injections(10**7, 6, seed=402)
     like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F32)
     box = synth.LAMBDA_BOX[:11]
-    B.pop_xi_surrogate_train(like.ctx, 8192, box[:, 0], box[:, 1], epochs=10, seed=3)
+    B.pop_xi_surrogate_train(like.ctx, 40000, box[:, 0], box[:, 1], epochs=30, seed=3)
     L = synth.make_lambdas(2048, 11, seed=403)
     times = {}
     for mode in (B.POP_MODE_F32, B.POP_MODE_F32_SURROGATE):
@@ -201,25 +201,27 @@ def test_surrogate_skips_the_injection_work(B):
             out = like(L, mode)
         times[mode] = time.perf_counter() - t0
     used = (out[3] & B.POP_FLAG_SURROGATE_USED) != 0
-    if B.pop_xi_surrogate_info(like.ctx)["trusted"]:
-        assert used.mean() > 0.9
-        assert times[B.POP_MODE_F32_SURROGATE] < 0.5 * times[B.POP_MODE_F32], times
+    info = B.pop_xi_surrogate_info(like.ctx)
+    assert info["trusted"], info
+    assert used.mean() > 0.9
+    assert times[B.POP_MODE_F32_SURROGATE] < 0.5 * times[B.POP_MODE_F32], times
     like.close()
 
 
 def test_surrogate_more_accurate_than_its_training_estimate(B, trained):
     """What the network gains: its ln xi is closer to a 10x larger injection set's than
-    the Monte Carlo estimate it was trained on (it averages the Monte Carlo scatter)."""
+    the Monte Carlo estimate it was trained on (it averages the Monte Carlo scatter).  The
+    10x-injection truth and the Monte Carlo ln xi both come from the FP64 CPU oracle."""
+    import oracle
     from paper_1904_02863_gb300 import synth
     like, cat, inj, lam, rmse = trained
     big = synth.make_injections(inj.n_draw * 10, 7, seed=synth.seed_for(5, 1) + 99)
-    truth = B.Likelihood(0).load(cat, big)
-    L = lam[:512]
-    ref = truth(L, B.POP_MODE_F64)[1]
-    mc = like(L, B.POP_MODE_F64)[1]
+    L = lam[:384]
+    ref = oracle.loglik(cat, big, L)[1]
+    mc = oracle.loglik(cat, inj, L)[1]
     lx, _, fb = B.pop_xi_surrogate_infer(like.ctx, L)
     ok = np.isfinite(ref) & np.isfinite(mc)
+    assert ok.mean() > 0.9
     err_mc = np.sqrt(np.mean((mc[ok] - ref[ok]) ** 2))
     err_sur = np.sqrt(np.mean((lx[ok] - ref[ok]) ** 2))
     assert err_sur < err_mc, (err_sur, err_mc)
-    truth.close()
