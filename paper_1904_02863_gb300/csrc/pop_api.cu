@@ -38,7 +38,7 @@ struct SampleSet {
     int64_t stride = 0;
     int n_dims = 0;
     int storage = 0;
-    DevBuf f64, f32, m2;
+    DevBuf f64, f32, m2, m1d, m1sort, m1pos;
     void swap(SampleSet& o)
     {
         std::swap(n, o.n);
@@ -48,6 +48,14 @@ struct SampleSet {
         f64.swap(o.f64);
         f32.swap(o.f32);
         m2.swap(o.m2);
+        m1d.swap(o.m1d);
+        m1sort.swap(o.m1sort);
+        m1pos.swap(o.m1pos);
+    }
+    FeatF32 feat32() const
+    {
+        return FeatF32{f32.as<float>(), m2.as<double>(), m1d.as<double>(), m1sort.as<double>(), m1pos.as<uint2>(), n,
+                       stride};
     }
 };
 
@@ -144,28 +152,29 @@ cudaMemcpyKind out_kind(int mem) { return mem == POP_MEM_HOST ? cudaMemcpyDevice
 
 __global__ void set_k_kernel(int64_t* dK, int64_t K) { *dK = K; }
 
+// Whether a sample lies inside the Lambda-independent part of the support (the
+// pack kernels' test; non-finite rows are rejected there).
+bool live_sample(const double* v, int n_dims)
+{
+    const double z = n_dims == 7 ? v[6] : 1.0;
+    return v[0] > 0.0 && v[1] > 0.0 && v[1] <= 1.0 && v[2] >= 0.0 && v[2] <= 1.0 && v[3] >= 0.0 && v[3] <= 1.0 &&
+           v[4] >= -1.0 && v[4] <= 1.0 && v[5] >= -1.0 && v[5] <= 1.0 && z >= 0.0 && z <= 2.0 && std::isfinite(v[0]);
+}
+
 // Load-time order of the samples: within every segment [seg[s], seg[s+1]) the
-// samples are sorted by (m2, m1) with m2 = fl64(q m1), compared lexicographically,
-// on the values the pack kernel stores (FP32-rounded coordinates for FP32 storage;
-// m2 = m1 = 0 for a sample outside the Lambda-independent support).  The lower
+// samples are sorted by (m2, m1) with m2 = fl64(q m1), compared lexicographically
+// (m2 = m1 = 0 for a sample outside the Lambda-independent support).  The lower
 // support edge, m1 > mmin and m2 >= mmin, is then a suffix of every segment (m2 <= m1
 // for q <= 1): the FP64 kernel's warps below it skip the arithmetic and the FP32
 // kernel finds its first index by binary search.  Sums over a segment do not depend
 // on the order (beyond rounding).
-std::vector<int64_t> support_order(const double* theta, int64_t n, int n_dims, const std::vector<int64_t>& seg,
-                                   bool round_f32)
+std::vector<int64_t> support_order(const double* theta, int64_t n, int n_dims, const std::vector<int64_t>& seg)
 {
     std::vector<std::pair<double, double>> key(n);
     for (int64_t j = 0; j < n; ++j) {
-        const double* th = theta + j * n_dims;
-        double v[7];
-        for (int d = 0; d < n_dims; ++d) v[d] = round_f32 ? (double)(float)th[d] : th[d];
-        const double z = n_dims == 7 ? v[6] : 1.0;
-        const bool live = v[0] > 0.0 && v[1] > 0.0 && v[1] <= 1.0 && v[2] >= 0.0 && v[2] <= 1.0 && v[3] >= 0.0 &&
-                          v[3] <= 1.0 && v[4] >= -1.0 && v[4] <= 1.0 && v[5] >= -1.0 && v[5] <= 1.0 && z >= 0.0 &&
-                          z <= 2.0 && std::isfinite(v[0]);
+        const double* v = theta + j * n_dims;
         // Rows with a non-finite coordinate are rejected by the pack kernel; any key will do for them.
-        key[j] = live ? std::make_pair(v[1] * v[0], v[0]) : std::make_pair(0.0, 0.0);
+        key[j] = live_sample(v, n_dims) ? std::make_pair(v[1] * v[0], v[0]) : std::make_pair(0.0, 0.0);
     }
     std::vector<int64_t> perm(n);
     for (int64_t j = 0; j < n; ++j) perm[j] = j;
@@ -185,7 +194,9 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     out.stride = round_up(std::max<int64_t>(n, 1), ALIGN_ELEMS);
     const double* th = theta;
     const double* pr = prior;
-    DevBuf tmp_th, tmp_pr, bad, dperm, dperm32;
+    DevBuf tmp_th, tmp_pr, bad, dperm;
+    std::vector<double> m1sort;  // FP32 storage: the set's m1 in increasing order, and for each
+    std::vector<uint2> m1pos;    // its (position, chunk index within the set)
     {
         std::vector<double> host_th;
         const double* hth = theta;
@@ -196,15 +207,33 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
             CK(cudaStreamSynchronize(c->stream), "sync");
             hth = host_th.data();
         }
-        for (int r = 0; r < 2; ++r) {
-            if (!(storage & (r == 0 ? POP_STORE_F64 : POP_STORE_F32))) continue;
-            const std::vector<int64_t> perm = support_order(hth, n, n_dims, seg, r == 1);
-            DevBuf& d = r == 0 ? dperm : dperm32;
-            CK(d.alloc(sizeof(int64_t) * std::max<int64_t>(n, 1)), "cudaMalloc(order)");
-            CK(cudaMemcpyAsync(d.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream),
-               "copy order");
-            CK(cudaStreamSynchronize(c->stream), "sync");
+        const std::vector<int64_t> perm = support_order(hth, n, n_dims, seg);
+        CK(dperm.alloc(sizeof(int64_t) * std::max<int64_t>(n, 1)), "cudaMalloc(order)");
+        CK(cudaMemcpyAsync(dperm.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream),
+           "copy order");
+        if (storage & POP_STORE_F32) {
+            // Chunks are the CHUNK_LEN pieces of every segment (build_chunks makes the same cut).
+            std::vector<std::pair<double, uint2>> e((size_t)n);
+            uint32_t chunk = 0;
+            for (size_t sg = 0; sg + 1 < seg.size(); ++sg)
+                for (int64_t c0 = seg[sg]; c0 < seg[sg + 1]; c0 += CHUNK_LEN, ++chunk) {
+                    const int64_t len = std::min<int64_t>(CHUNK_LEN, seg[sg + 1] - c0);
+                    for (int64_t i = c0; i < c0 + len; ++i) {
+                        const double* v = hth + perm[i] * n_dims;
+                        e[i] = {live_sample(v, n_dims) ? v[0] : 0.0, make_uint2((uint32_t)i, chunk)};
+                    }
+                }
+            std::sort(e.begin(), e.end(), [](const std::pair<double, uint2>& a, const std::pair<double, uint2>& b) {
+                return a.first < b.first || (a.first == b.first && a.second.x < b.second.x);
+            });
+            m1sort.resize((size_t)std::max<int64_t>(n, 1));
+            m1pos.resize((size_t)std::max<int64_t>(n, 1));
+            for (int64_t i = 0; i < n; ++i) {
+                m1sort[i] = e[i].first;
+                m1pos[i] = e[i].second;
+            }
         }
+        CK(cudaStreamSynchronize(c->stream), "sync");
     }
     if (mem == POP_MEM_HOST) {
         CK(tmp_th.alloc(sizeof(double) * n * n_dims), "cudaMalloc(theta staging)");
@@ -226,9 +255,15 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     if (storage & POP_STORE_F32) {
         CK(out.f32.alloc(sizeof(float) * F_COUNT32 * out.stride), "cudaMalloc(f32 features)");
         CK(out.m2.alloc(sizeof(double) * out.stride), "cudaMalloc(m2)");
-        CK(launch_pack_f32(th, pr, dperm32.as<int64_t>(), n, n_dims, out.f32.as<float>(), out.m2.as<double>(),
-                           out.stride,
-                           bad.as<unsigned long long>(), c->stream), "pack_f32");
+        CK(out.m1d.alloc(sizeof(double) * out.stride), "cudaMalloc(m1)");
+        CK(out.m1sort.alloc(sizeof(double) * m1sort.size()), "cudaMalloc(m1 order)");
+        CK(out.m1pos.alloc(sizeof(uint2) * m1pos.size()), "cudaMalloc(m1 order)");
+        CK(cudaMemcpyAsync(out.m1sort.p, m1sort.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream),
+           "copy m1 order");
+        CK(cudaMemcpyAsync(out.m1pos.p, m1pos.data(), sizeof(uint2) * n, cudaMemcpyHostToDevice, c->stream),
+           "copy m1 order");
+        CK(launch_pack_f32(th, pr, dperm.as<int64_t>(), n, n_dims, out.f32.as<float>(), out.m2.as<double>(),
+                           out.m1d.as<double>(), out.stride, bad.as<unsigned long long>(), c->stream), "pack_f32");
     }
     unsigned long long h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, bad.p, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream), "copy flag");
@@ -382,13 +417,15 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
                              c->d_part.as<double>(), c->d_part2.as<double>(), c->d_exptab.as<double2>(), c->expc,
                              c->d_queue.as<unsigned long long>(), c->stream), "weight_f64");
     } else {
-        FeatF32 e{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
-        FeatF32 j{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
+        FeatF32 e = c->ev.feat32();
+        FeatF32 j = c->inj.feat32();
         CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), sx.need_mc, c->k_cap,
                             c->d_order.as<int32_t>(), c->d_nmc.as<int32_t>(), c->stream), "lambda order");
         CK(launch_weight_f32(c->tiling[1], grid, e, j, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
                              c->d_nmc.as<int32_t>(), c->d_queue.as<unsigned long long>(), c->k_cap, c->d_K.as<int64_t>(), c->d_part.as<double>(),
                              c->d_part2.as<double>(), c->stream), "weight_f32");
+        CK(launch_upper_edge_fixup(e, j, wd, c->d_c32.as<LamF32>(), sx.need_mc, c->k_cap, c->d_K.as<int64_t>(),
+                                   c->d_part.as<double>(), c->d_part2.as<double>(), c->stream), "upper-edge fix-up");
     }
     CK(cudaEventRecordWithFlags(c->ev_w1, c->stream, rec), "event");
     if (use_grid)
@@ -1174,8 +1211,8 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
                                           c->d_exptab.as<double2>(), c->expc, c->d_queue.as<unsigned long long>(),
                                           c->stream);
                 } else {
-                    FeatF32 ev{c->ev.f32.as<float>(), c->ev.m2.as<double>(), c->ev.stride};
-                    FeatF32 ij{c->inj.f32.as<float>(), c->inj.m2.as<double>(), c->inj.stride};
+                    FeatF32 ev = c->ev.feat32();
+                    FeatF32 ij = c->inj.feat32();
                     e = launch_weight_f32(t, grid, ev, ij, wd, c->d_c32.as<LamF32>(), c->d_order.as<int32_t>(),
                                           c->d_nmc.as<int32_t>(), c->d_queue.as<unsigned long long>(), c->k_cap, c->d_K.as<int64_t>(),
                                           c->d_part.as<double>(), c->d_part2.as<double>(), c->stream);

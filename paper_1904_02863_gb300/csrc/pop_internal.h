@@ -57,8 +57,9 @@ struct alignas(16) LamF64 {
 // Per-Lambda constants of the FP32 weight (base-2 units).
 struct alignas(16) LamF32 {
     int64_t mmin_bits;   // FP64 bit pattern of mmin, for the exact m2 >= mmin test
-    float thr_lo;        // largest float <= mmin   (m1 > mmin  <=>  m1_f32 > thr_lo)
-    float thr_hi;        // largest float <= mmax   (m1 <= mmax <=>  m1_f32 <= thr_hi)
+    int64_t mmax_bits;   // FP64 bit pattern of mmax, for the exact m1 <= mmax test of the fix-up
+    float thr_hi;        // rd32(mmax): m1 <= mmax implies rd32(m1) <= thr_hi; the converse fails
+                         // only for m1 in (mmax, next float above thr_hi), which the fix-up removes
     float nalpha, cpl, mu, nh, cg, beta, ac, bc, km1;
     // q normalisation exponent u = b1 ((lmmin - lm1) + (lmmin_lo - lm1_lo)) in base 2,
     // evaluated as fma(b1, lmmin - lm1, fma(nb1, lm1_lo, b1lmmin_lo)); with
@@ -82,8 +83,12 @@ struct FeatF64 {
 };
 
 struct FeatF32 {
-    const float* base;   // [F_COUNT32][stride]
-    const double* m2;    // [stride]
+    const float* base;     // [F_COUNT32][stride]; row F_M1 holds rd32(m1) (rounded toward -inf)
+    const double* m2;      // [stride]: fl64(q m1)
+    const double* m1d;     // [stride]: m1 in FP64 (0 outside the Lambda-independent support)
+    const double* m1sort;  // [n]: m1d of the whole set in increasing order
+    const uint2* m1pos;    // [n]: (position, chunk index within the set) of each m1sort entry
+    int64_t n;
     int64_t stride;
 };
 
@@ -107,7 +112,8 @@ struct Tiling {
 cudaError_t launch_pack_f64(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
                             double* feat, int64_t stride, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_pack_f32(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
-                            float* feat, double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s);
+                            float* feat, double* m2, double* m1d, int64_t stride, unsigned long long* bad,
+                            cudaStream_t s);
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params,
                             LamF64* c64, LamF32* c32, cudaStream_t s);
 // The FP64 weight kernel keeps the 2^(j/2048) table of its exponentials in dynamic shared memory.
@@ -136,6 +142,11 @@ cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj
                               const LamF32* lam, const int32_t* order, const int32_t* n_mc,
                               unsigned long long* queue, int64_t K_cap, const int64_t* dK, double* part,
                               double* part2, cudaStream_t s);
+// After launch_weight_f32: removes from the partials the samples that the FP32 upper-edge test
+// kept although m1 > mmax (one thread per Lambda; need_mc as for the weight kernel, or NULL).
+cudaError_t launch_upper_edge_fixup(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* lam,
+                                    const uint8_t* need_mc, int64_t K_cap, const int64_t* dK, double* part,
+                                    double* part2, cudaStream_t s);
 // Float-float weight kernel (POP_MODE_FF): weight_ff_threads() Lambda per block, one per thread, with the
 // lane order of launch_lam_order (need_mc NULL); fftab = 2^(j/2048) as FP32 (hi, lo) pairs.
 const void* weight_ff_fn(bool has_z);

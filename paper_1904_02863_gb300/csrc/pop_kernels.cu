@@ -29,17 +29,12 @@ struct RawSample {
 };
 
 __device__ __forceinline__ bool read_sample(const double* theta, const double* prior, int64_t j, int nd,
-                                            bool round_f32, RawSample& s, bool& live)
+                                            RawSample& s, bool& live)
 {
     const double* th = theta + j * nd;
     s.m1 = th[0]; s.q = th[1]; s.a1 = th[2]; s.a2 = th[3]; s.c1 = th[4]; s.c2 = th[5];
     s.z = nd == 7 ? th[6] : 1.0;
     s.pi = prior[j];
-    if (round_f32) {  // FP32 storage: the raw inputs are quantised first
-        s.m1 = (double)(float)s.m1; s.q = (double)(float)s.q; s.a1 = (double)(float)s.a1;
-        s.a2 = (double)(float)s.a2; s.c1 = (double)(float)s.c1; s.c2 = (double)(float)s.c2;
-        s.z = (double)(float)s.z; s.pi = (double)(float)s.pi;
-    }
     bool ok = finite_d(s.m1) && finite_d(s.q) && finite_d(s.a1) && finite_d(s.a2) && finite_d(s.c1) &&
               finite_d(s.c2) && finite_d(s.z) && finite_d(s.pi) && s.pi > 0.0;
     live = ok && s.m1 > 0.0 && s.q > 0.0 && s.q <= 1.0 && s.a1 >= 0.0 && s.a1 <= 1.0 && s.a2 >= 0.0 &&
@@ -57,7 +52,7 @@ __global__ void pack_f64_kernel(const double* __restrict__ theta, const double* 
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         RawSample s;
         bool live;
-        if (!read_sample(theta, prior, perm ? perm[j] : j, nd, false, s, live)) atomicAdd(bad, 1ull);
+        if (!read_sample(theta, prior, perm ? perm[j] : j, nd, s, live)) atomicAdd(bad, 1ull);
         double f[F_COUNT64] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (live) {
             f[F_LM1] = log(s.m1);
@@ -79,21 +74,25 @@ __global__ void pack_f64_kernel(const double* __restrict__ theta, const double* 
     }
 }
 
+// The FP32 features are formed in FP64 from the unrounded inputs and rounded once
+// each; m1 and fl64(q m1) are also kept in FP64 for the exact support decisions.
 __global__ void pack_f32_kernel(const double* __restrict__ theta, const double* __restrict__ prior,
                                 const int64_t* __restrict__ perm, int64_t n, int nd, float* __restrict__ feat,
-                                double* __restrict__ m2, int64_t stride, unsigned long long* bad)
+                                double* __restrict__ m2, double* __restrict__ m1d, int64_t stride,
+                                unsigned long long* bad)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         RawSample s;
         bool live;
-        if (!read_sample(theta, prior, perm ? perm[j] : j, nd, true, s, live)) atomicAdd(bad, 1ull);
+        if (!read_sample(theta, prior, perm ? perm[j] : j, nd, s, live)) atomicAdd(bad, 1ull);
         float f[F_COUNT32] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        double mm = 0.0;
+        double mm = 0.0, m1 = 0.0;
         if (live) {
             const double l2m1 = log2(s.m1);
             f[F_LM1] = (float)l2m1;
             f[F32_LM1LO] = (float)(l2m1 - (double)f[F_LM1]);
-            f[F_M1] = (float)s.m1;  // exact: m1 is already a float
+            f[F_M1] = __double2float_rd(s.m1);  // toward -inf: the FP32 upper-edge test never drops a sample
+            m1 = s.m1;
             f[F_LQ] = (float)log2(s.q);
             f[F_SA] = (s.a1 > 0.0 && s.a2 > 0.0) ? (float)(log2(s.a1) + log2(s.a2)) : (float)LOG_ZERO;
             f[F_SB] = (s.a1 < 1.0 && s.a2 < 1.0) ? (float)(log2(1.0 - s.a1) + log2(1.0 - s.a2)) : (float)LOG_ZERO;
@@ -104,11 +103,12 @@ __global__ void pack_f32_kernel(const double* __restrict__ theta, const double* 
                 f[F_LZ1] = (float)(log1p(s.z) * LOG2E);
             }
             f[F_NLPI] = (float)nl;
-            mm = __dmul_rn(s.q, s.m1);  // exact: product of two floats fits in 53 bits
+            mm = __dmul_rn(s.q, s.m1);  // one rounding, as the support test is defined
         }
 #pragma unroll
         for (int r = 0; r < F_COUNT32; ++r) feat[r * stride + j] = f[r];
         m2[j] = mm;
+        m1d[j] = m1;
     }
 }
 
@@ -156,7 +156,7 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
         c.valid = 0;
         f = LamF32{};
         f.mmin_bits = c.mmin_bits;
-        f.thr_lo = INFINITY;
+        f.mmax_bits = c.mmax_bits;
         f.thr_hi = INFINITY;
         f.valid = 0;
         c64[k] = c;
@@ -213,7 +213,7 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     // is formed from base-2 logs, so 1/ln 2 joins the constant.
     const double fix = beta_m1 ? -log(LN2) : 0.0;
     f.mmin_bits = c.mmin_bits;
-    f.thr_lo = __double2float_rd(mmin);
+    f.mmax_bits = c.mmax_bits;
     f.thr_hi = __double2float_rd(mmax);
     f.nalpha = (float)c.nalpha;
     f.cpl = (float)((c.cpl + fix) * LOG2E);
@@ -358,10 +358,11 @@ cudaError_t launch_pack_f64(const double* theta, const double* prior, const int6
 }
 
 cudaError_t launch_pack_f32(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
-                            float* feat, double* m2, int64_t stride, unsigned long long* bad, cudaStream_t s)
+                            float* feat, double* m2, double* m1d, int64_t stride, unsigned long long* bad,
+                            cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    pack_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, perm, n, n_dims, feat, m2, stride, bad);
+    pack_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, perm, n, n_dims, feat, m2, m1d, stride, bad);
     return cudaGetLastError();
 }
 

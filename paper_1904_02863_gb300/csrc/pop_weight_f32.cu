@@ -12,9 +12,13 @@
 //
 // Support.  Samples are stored in increasing (q m1, m1) order per event, so the lower
 // edge (m1 > mmin and fl64(q m1) >= mmin; q m1 <= m1 because q <= 1) is a suffix of
-// the chunk: each lane finds its first index j0 by a binary search and the per-pair
-// test is j >= j0 and m1 <= mmax.  lam_order_kernel orders the Lambda across the
-// lanes by mmin, so the j0 of a warp are close and the warp starts at their minimum.
+// the chunk: each lane finds its first index j0 by a binary search in FP64 and the
+// per-pair test is j >= j0 and rd32(m1) <= thr_hi = rd32(mmax) (both rounded toward
+// -inf).  That float test keeps every sample with m1 <= mmax; it also keeps the samples
+// with m1 in (mmax, next float above thr_hi), and upper_edge_fixup_kernel takes those
+// (rarely any) back out after the main loop, so every support decision is the oracle's.
+// lam_order_kernel orders the Lambda across the lanes by mmin, so the j0 of a warp are
+// close and the warp starts at their minimum.
 //
 // The q normalisation 1 - 2^u (u = (1+beta) log2(mmin/m1), base-2 units) loses
 // relative accuracy as u -> 0, where the Taylor series of e^x - 1 in x = u ln2 takes
@@ -208,33 +212,32 @@ __device__ __forceinline__ void run_regions(const ulonglong2* __restrict__ buf, 
     run_pairs<false, false, INJ, HAS_Z>(buf, zb, p_chk, p_end, jb, j0, c, s, cs, s2, cs2);
 }
 
-// First chunk index whose (m2, m1) exceeds (mmin, mmin) lexicographically: the first
-// sample with m1 > mmin and m2 >= mmin.  len when there is none.
-__device__ __forceinline__ int lower_edge(const FeatF32& F, const Chunk& ch, double mmin)
+// The two searches of a work item's start, in lockstep so that their loads overlap (each is
+// a lower bound over the chunk; the range halves the same way for both):
+//   j0 = first chunk index whose (m2, m1) exceeds (mmin, mmin) lexicographically, i.e. the
+//        first sample with m1 > mmin and m2 >= mmin (both in FP64);
+//   js = first chunk index with m2 >= t.
+// Each lower bound keeps its base on the last position known to fail its test (len >= 1).
+__device__ __forceinline__ void item_searches(const FeatF32& F, const Chunk& ch, double mmin, double t, int& j0,
+                                              int& js)
 {
     const double* m2 = F.m2 + ch.start;
-    const float* m1 = F.base + F_M1 * F.stride + ch.start;
-    int lo = 0, hi = ch.len;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const double a = __ldg(m2 + mid);
-        if (a > mmin || (a == mmin && (double)__ldg(m1 + mid) > mmin)) hi = mid;
-        else lo = mid + 1;
+    const double* m1 = F.m1d + ch.start;
+    auto before_edge = [&](int i) {
+        const double a = __ldg(m2 + i);
+        return !(a > mmin || (a == mmin && __ldg(m1 + i) > mmin));
+    };
+    int b0 = 0, b1 = 0, n = ch.len;
+    while (n > 1) {
+        const int half = n >> 1;
+        const bool f0 = before_edge(b0 + half);
+        const bool f1 = __ldg(m2 + b1 + half) < t;
+        b0 = f0 ? b0 + half : b0;
+        b1 = f1 ? b1 + half : b1;
+        n -= half;
     }
-    return lo;
-}
-
-// First chunk index with m2 >= t (len when there is none).
-__device__ __forceinline__ int first_m2_at_least(const FeatF32& F, const Chunk& ch, double t)
-{
-    const double* m2 = F.m2 + ch.start;
-    int lo = 0, hi = ch.len;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(m2 + mid) >= t) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
+    j0 = b0 + (before_edge(b0) ? 1 : 0);
+    js = b1 + (__ldg(m2 + b1) < t ? 1 : 0);
 }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src)
@@ -326,16 +329,11 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
         int j0 = ch.len, js = 0;
         if (active) {
             const double mmin = __longlong_as_double(L.mmin_bits);  // +inf for an invalid Lambda
-            j0 = lower_edge(F, ch, mmin);
-            if (j0 < ch.len) {
-                if (L.beta_m1) {
-                    js = ch.len;
-                } else {
-                    // |u| >= 1/8 (with a 2^-10 margin) from m1 >= mmin 2^(1/(8|1+beta|)) on, and m1 >= m2.
-                    const double t = mmin * exp2(0.125 / fabs((double)L.b1)) * (1.0 + 0x1p-10);
-                    js = first_m2_at_least(F, ch, t);
-                }
-            }
+            // |u| >= 1/8 (with a 2^-10 margin) from m1 >= mmin 2^(1/(8|1+beta|)) on, and m1 >= m2.
+            const double t = L.beta_m1 ? INFINITY : mmin * exp2(0.125 / fabs((double)L.b1)) * (1.0 + 0x1p-10);
+            item_searches(F, ch, mmin, t, j0, js);
+            if (j0 >= ch.len) js = 0;
+            else if (L.beta_m1) js = ch.len;
         }
         LaneConsts cl = lane_consts(L);
         if (j0 >= ch.len) cl.thr_hi = -INFINITY;  // no in-support sample: masked without the index test
@@ -384,6 +382,80 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
                 upk(cs2, ca, cb);
                 part2[(int64_t)k * n_inj_chunks + (c - wd.n_ev_chunks)] =
                     ((double)sa - (double)ca) + ((double)sb - (double)cb);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- upper-edge fix-up
+// Features of one sample in both halves of a pair, read from the feature rows.
+template <bool HAS_Z>
+__device__ __forceinline__ void load_single(const FeatF32& F, int64_t idx, PairFeat& x)
+{
+    const float* b = F.base + idx;
+    x.lm1 = bc(__ldg(b + F_LM1 * F.stride));
+    x.m1 = bc(__ldg(b + F_M1 * F.stride));
+    x.lq = bc(__ldg(b + F_LQ * F.stride));
+    x.sa = bc(__ldg(b + F_SA * F.stride));
+    x.sb = bc(__ldg(b + F_SB * F.stride));
+    x.dc = bc(__ldg(b + F_DC * F.stride));
+    x.nlpi = bc(__ldg(b + F_NLPI * F.stride));
+    x.lm1lo = bc(__ldg(b + F32_LM1LO * F.stride));
+    x.lz1 = HAS_Z ? bc(__ldg(b + F_LZ1 * F.stride)) : 0ull;
+}
+
+// First entry of the set's m1-sorted table with m1 > x (n when there is none; n >= 1).
+__device__ __forceinline__ int64_t first_m1_above(const FeatF32& F, double x)
+{
+    int64_t b = 0, n = F.n;
+    while (n > 1) {
+        const int64_t half = n >> 1;
+        b = __ldg(F.m1sort + b + half) <= x ? b + half : b;
+        n -= half;
+    }
+    return b + (__ldg(F.m1sort + b) <= x ? 1 : 0);
+}
+
+// One Lambda per thread.  The main loop kept every sample with j >= j0 and rd32(m1) <= thr_hi;
+// the ones among them with m1 > mmax lie outside the support.  They are the entries of the
+// m1-sorted table from the first m1 > mmax on, while rd32(m1) is still thr_hi (none, in
+// practice, but one per Lambda costs nothing to check).  Each one that the lower edge keeps
+// (m2 > mmin, or m2 == mmin and m1 > mmin) has its weight taken out of its chunk's partials.
+// pair_weight<true> reproduces the main loop's weight bit for bit: the series branch changes
+// the result only where |u| < 1/8 or beta = -1, and there the main loop runs it as well; so a
+// chunk whose only kept sample is such a one comes back to exactly 0.
+template <bool HAS_Z>
+__global__ void __launch_bounds__(128)
+upper_edge_fixup_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
+                        const uint8_t* __restrict__ need_mc, const int64_t* __restrict__ dK,
+                        double* __restrict__ part, double* __restrict__ part2)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= *dK) return;
+    const LamF32 L = lam[k];
+    if (!L.valid) return;
+    const double mmin = __longlong_as_double(L.mmin_bits), mmax = __longlong_as_double(L.mmax_bits);
+    const LaneConsts c = lane_consts(L);
+    const int n_inj_chunks = wd.n_chunks - wd.n_ev_chunks;
+    const bool do_inj = n_inj_chunks > 0 && inj.n > 0 && (need_mc == nullptr || need_mc[k]);
+    for (int set = 0; set < (do_inj ? 2 : 1); ++set) {
+        const FeatF32& F = set ? inj : ev;
+        if (F.n < 1) continue;
+        for (int64_t i = first_m1_above(F, mmax); i < F.n; ++i) {
+            const double m1 = __ldg(F.m1sort + i);
+            if (__double2float_rd(m1) != L.thr_hi) break;
+            const uint2 pc = F.m1pos[i];
+            const double m2 = __ldg(F.m2 + pc.x);
+            if (!(m2 > mmin || (m2 == mmin && m1 > mmin))) continue;
+            PairFeat x;
+            load_single<HAS_Z>(F, pc.x, x);
+            float w, w_b;
+            upk(pair_weight<true, HAS_Z>(x, c), w, w_b);
+            if (set == 0) {
+                part[k * wd.n_chunks + pc.y] -= (double)w;
+            } else {
+                part[k * wd.n_chunks + wd.n_ev_chunks + pc.y] -= (double)w;
+                part2[k * n_inj_chunks + pc.y] -= (double)__fmul_rn(w, w);
             }
         }
     }
@@ -511,6 +583,16 @@ const void* weight_f32_fn(const Tiling& t, bool has_z)
         case 256: return pick_f32<256>(has_z);
         default: return nullptr;
     }
+}
+
+cudaError_t launch_upper_edge_fixup(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* lam, const uint8_t* need_mc,
+                                    int64_t K_cap, const int64_t* dK, double* part, double* part2, cudaStream_t s)
+{
+    if (K_cap <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((K_cap + 127) / 128);
+    if (wd.has_z) upper_edge_fixup_kernel<true><<<blocks, 128, 0, s>>>(ev, inj, wd, lam, need_mc, dK, part, part2);
+    else upper_edge_fixup_kernel<false><<<blocks, 128, 0, s>>>(ev, inj, wd, lam, need_mc, dK, part, part2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lam_order(const LamF32* lam, const int64_t* dK, const uint8_t* need_mc, int64_t K_cap,

@@ -6,12 +6,12 @@ Monte Carlo selection term of Sec. "Population acceleration"), in every mode.
 * a single found injection, and a campaign where every draw was found (n_found = n_draw).
 
 FP64 and float-float: the FP64 parity bar (1e-12 of |sum_i ln(S_i/n_i)| + N |ln xi|,
-flags identical); FP32: 0.05 nats against the oracle on the float32-rounded inputs.
+flags identical); FP32: 0.05 nats against the oracle, flags identical.
 """
 import numpy as np
 import pytest
 
-from test_parity_gpu import assert_f64_parity, rounded
+from test_parity_gpu import assert_f64_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -32,9 +32,9 @@ def check_all_modes(B, like, cat, inj, lam, oracle):
     ref = oracle.loglik(cat, inj, lam)
     assert_f64_parity(like(lam, B.POP_MODE_F64), ref, cat.n_events)
     assert_f64_parity(like(lam, B.POP_MODE_FF), ref, cat.n_events)
-    c32, i32 = rounded(cat, inj)
-    ref32 = oracle.loglik(c32, i32, lam)
+    ref32 = ref
     got32 = like(lam, B.POP_MODE_F32)
+    np.testing.assert_array_equal(got32[3], ref32[3])
     fin = np.isfinite(ref32[0])
     np.testing.assert_array_equal(np.isfinite(got32[0]), fin)
     d = np.abs(got32[0][fin] - ref32[0][fin])
@@ -113,7 +113,7 @@ def test_unit_weights_when_the_prior_is_the_population(B, oracle, n_dims):
     inj = synth.make_injections(50000, n_dims, seed=663 + n_dims)
     N = cat.n_events
     for mode, theta, tol in ((B.POP_MODE_F64, cat.theta, 1e-13), (B.POP_MODE_FF, cat.theta, 1e-13),
-                             (B.POP_MODE_F32, synth.round_to_f32(cat.theta), 2e-5)):
+                             (B.POP_MODE_F32, cat.theta, 2e-5)):
         prior = np.array([oracle.p_theta(t, L) for t in theta])
         assert (prior > 0).all()
         c = synth.Catalog(cat.offsets, theta, prior)
@@ -122,3 +122,55 @@ def test_unit_weights_when_the_prior_is_the_population(B, oracle, n_dims):
         like.close()
         assert flags[0] & ~np.uint32(B.POP_FLAG_LOW_NEFF) == 0, (mode, flags)
         assert abs(lnL[0] + N * lnxi[0]) <= tol * N * (1 + abs(lnxi[0])), (mode, lnL[0] + N * lnxi[0])
+
+
+def test_f32_upper_mass_edge_is_decided_in_fp64(B, oracle):
+    """FP32 mode keeps m1 <= mmax exactly as the oracle does, also where m1 and mmax round to the
+    same float or to neighbouring ones: one-sample events at m1 = mmax, its FP64 neighbours, the
+    floats below and above mmax and the midpoint between them, against mmax that is not a float,
+    is a float, and is that midpoint.  Each such event is in or out of the support (ZERO_EVENT)
+    exactly as the oracle says, and ln L stays within the FP32 budget."""
+    from paper_1904_02863_gb300 import synth
+    def up(x):
+        return float(np.nextafter(x, np.inf))
+
+    def dn(x):
+        return float(np.nextafter(x, -np.inf))
+
+    base = 70.3                                   # not a float
+    hi32 = float(np.float32(base))                # rounds up: the float above 70.3
+    assert hi32 > base
+    lo32 = float(np.nextafter(np.float32(hi32), np.float32(0)))   # the float below 70.3
+    mid = 0.5 * (lo32 + hi32)                     # where rounding to float changes
+    m1s = [base, up(base), dn(base), up(up(base)), lo32, up(lo32), dn(lo32), hi32, dn(hi32), up(hi32), mid, up(mid),
+           dn(mid), 30.0]
+    theta = np.array([[m, 0.9, 0.3, 0.4, 0.2, 0.5] for m in m1s])
+    # one event per value, then one event holding all of them
+    theta = np.concatenate([theta, theta])
+    n = len(m1s)
+    offsets = np.concatenate([np.arange(n + 1), [2 * n]]).astype(np.int64)
+    cat = synth.Catalog(offsets, theta, theta[:, 0] / 4.0)
+    inj = synth.make_injections(30000, 6, seed=671)
+    rows = []
+    for mmax in (base, lo32, hi32, mid, up(mid), dn(base)):
+        L = synth.LAMBDA0[:11].copy()
+        L[3] = mmax
+        rows.append(L)
+    lam = np.array(rows)
+    like = B.Likelihood(0).load(cat, inj, storage=B.POP_STORE_F32)
+    got = like(lam, B.POP_MODE_F32)
+    ref = oracle.loglik(cat, inj, lam)
+    like.close()
+    np.testing.assert_array_equal(got[3], ref[3])
+    assert (ref[3] & B.POP_FLAG_ZERO_EVENT).all()   # the one-sample events above mmax are empty
+    # per-event agreement: the same rows evaluated on each event alone
+    for i in range(n):
+        sub = synth.Catalog(np.array([0, 1], np.int64), theta[i:i + 1], cat.prior[i:i + 1])
+        like = B.Likelihood(0).load(sub, inj, storage=B.POP_STORE_F32)
+        g = like(lam, B.POP_MODE_F32)
+        like.close()
+        r = oracle.loglik(sub, inj, lam)
+        np.testing.assert_array_equal(g[3], r[3])
+        fin = np.isfinite(r[0])
+        np.testing.assert_array_equal(np.isfinite(g[0]), fin)
+        assert np.all(np.abs(g[0][fin] - r[0][fin]) <= 1e-3), (m1s[i], g[0] - r[0])
