@@ -56,6 +56,19 @@ MUFU_SLOTS_PER_PAIR = 6
 FF_OPS_PER_PAIR = 362
 SMS = 152
 SM_MAX_MHZ = 2070.0
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# The network's training is a seconds-long loop of GEMMs: its denominator is the sustained cuBLAS
+# BF16 rate the GB300s measured (the profiling recipe's 1.7 PFLOP/s when the file is absent).
+_PEAKS = _measured_peaks()
+BF16_PEAK_TFLOPS = float(_PEAKS.get("bf16_tflops_sustained") or 1700.0)
+BF16_PEAK_BASIS = "of measured (sustained)" if _PEAKS.get("bf16_tflops_sustained") else "of fallback (sustained)"
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
 # profiles/weight_f64_catalog400x4096_K64_full.md (154.18 MB / 2,077,126 units); a launch
 # reads every chunk from DRAM once, so traffic scales with the units.
@@ -138,10 +151,13 @@ def parse():
     p.add_argument("--K", type=int, default=1024, help="Lambda points per step")
     p.add_argument("--mode", default="both", choices=["both", "f64", "f32", "ff"],
                    help="both: the FP64 headline and every form; f64 / f32 / ff: that mode alone")
-    p.add_argument("--workload", default="catalog", choices=["catalog", "ragged", "grid", "cbc", "grad", "sampler"],
-                   help="catalog: 1000 events x 4096 samples + 1e7 injection draws (default); "
+    p.add_argument("--workload", default="catalog",
+                   choices=["catalog", "ragged", "grid", "cbc", "grad", "sampler", "learned", "scan"],
+                   help="catalog: 1000 events x 4096 samples + 1e7 injection draws (default; every form); "
                         "ragged: 2000 ragged CSR events + redshift, uneven batches; "
-                        "sampler: the stretch-move ensemble sampler driving FP32 ln L on the catalog")
+                        "sampler: the stretch-move ensemble sampler driving FP32 ln L on the catalog; "
+                        "learned: 10 x 1000 + redshift with the trained ln xi network; "
+                        "scan: evals/s and roofline over 1e4 .. 2e7 posterior samples")
     return p.parse_args()
 
 
@@ -250,46 +266,60 @@ def cpu_baseline(cat, inj, lam, n_rows, gpu_f64=None):
     return out
 
 
-def precision_vs(res, ref):
+def dlnl_stats(d):
+    """mean, 99th percentile and max of |Delta ln L| (0 for no rows)."""
+    if d.size == 0:
+        return {"rows": 0, "mean": 0.0, "p99": 0.0, "max": 0.0}
+    return {"rows": int(d.size), "mean": float(d.mean()), "p99": float(np.quantile(d, 0.99)), "max": float(d.max())}
+
+
+def precision_vs(res, ref, rows=None):
     """|Delta ln L| and the relative Delta xi of the outputs ``res`` against ``ref`` over every
-    Lambda of the batch (rows where both ln L are finite)."""
+    Lambda of the batch (rows where both ln L are finite), or over the boolean mask ``rows``."""
     a, b = res[0], ref[0]
     both = np.isfinite(a) & np.isfinite(b)
+    if rows is not None:
+        both &= rows
     d = np.abs(a[both] - b[both])
     dxi = np.abs(np.expm1(res[1][both] - ref[1][both]))
-    return {"rows": int(a.size), "finite_rows_agree": bool((np.isfinite(a) == np.isfinite(b)).all()),
-            "abs_dlnL": {"mean": float(d.mean()) if d.size else 0.0, "max": float(d.max()) if d.size else 0.0},
+    return {"finite_rows_agree": bool((np.isfinite(a) == np.isfinite(b)).all()), "abs_dlnL": dlnl_stats(d),
             "rel_dxi_max": float(dxi.max()) if dxi.size else 0.0}
 
 
-def f64_on_rounded_inputs(B, cat, inj, dev_lam, device, stream):
-    """The FP64 kernel's outputs on the catalog and injections rounded to float32 (what the FP32
-    layout stores): against these, an FP32 form's difference is its arithmetic error alone."""
+def time_mode(B, like, dev_lam, outs, mode, steps, warmup, world, stream):
+    """(ms over ``steps`` pop_loglik calls on device buffers, mean weight-kernel ms): CUDA events on
+    the context's stream, a barrier and a synchronize on both sides, max over ranks."""
     import torch
-    cat32 = synth.Catalog(cat.offsets, synth.round_to_f32(cat.theta), synth.round_to_f32(cat.prior))
-    inj32 = synth.Injections(synth.round_to_f32(inj.theta), synth.round_to_f32(inj.p_draw), inj.n_draw)
-    like = B.Likelihood(device, stream).load(cat32, inj32)
-    K = dev_lam.shape[0]
-    outs = [torch.empty(K, dtype=torch.float64, device="cuda") for _ in range(3)] + \
-           [torch.empty(K, dtype=torch.int32, device="cuda")]
-    B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F64, out=outs)
+    for _ in range(warmup):
+        B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
     torch.cuda.synchronize()
-    res = [o.cpu().numpy().copy() for o in outs]
-    like.close()
-    return res
+    barrier(world)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wms = []
+    start.record(stream)
+    for _ in range(steps):
+        B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+        wms.append(B.pop_last_kernel_ms(like.ctx)[0])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    return max_over_ranks(start.elapsed_time(stop), world), statistics.mean(wms)
 
 
-def ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_pairs, n_events):
+def host_outputs(outs):
+    r = [o.cpu().numpy().copy() for o in outs]
+    r[3] = r[3].view(np.uint32)
+    return r
+
+
+def ff_form(B, like, lam, dev_lam, outs, args, world, stream, n_pairs, n_events, f64):
     """FP64-grade ln L with the sample weights in float-float arithmetic (POP_MODE_FF): its
-    evals/s, and its distance to the FP64 kernel's ln L in units of the FP64 parity tolerance
-    1e-12 (|sum_i ln(S_i/n_i)| + N |ln xi|) for every Lambda of the batch."""
-    import torch
-    ms, w = timed(B.POP_MODE_FF)
-    ff = [o.clone() for o in outs]
-    B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F64, out=outs)
-    torch.cuda.synchronize()
-    f64 = [o.cpu().numpy() for o in outs]
-    ffh = [o.cpu().numpy() for o in ff]
+    evals/s, and its distance to the FP64 kernel's ln L (``f64``, host outputs) in units of the
+    FP64 parity tolerance 1e-12 (|sum_i ln(S_i/n_i)| + N |ln xi|) for every Lambda of the batch."""
+    ms, w = time_mode(B, like, dev_lam, outs, B.POP_MODE_FF, args.steps, args.warmup, world, stream)
+    ffh = host_outputs(outs)
     n = n_events
     fin = np.isfinite(f64[0])
     a = np.abs(np.where(fin, f64[0], 0.0) + n * f64[1])
@@ -302,47 +332,72 @@ def ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_pairs, n_events):
             "in_support_pairs": n_pairs}
 
 
-def surrogate_form(B, like, lam, dev_lam, outs, timed, args, world, ref64=None, ref64_rounded=None):
-    """FP32 weights + the trained ln xi network (Monte Carlo xi only where its gate says so).
+# Tensor-core work of one training row (forward + backward, the 12-input layer unpadded):
+# forward 2 (12*256 + 3*256^2 + 256*2), weight gradients the same, input gradients
+# 2 (3*256^2 + 256*2); Adam and the SiLU epilogues are not counted.
+MLP_FLOP_PER_ROW = 2 * (12 * 256 + 3 * 256 ** 2 + 256 * 2) * 2 + 2 * (3 * 256 ** 2 + 256 * 2)
 
-    Training (2e5 Lambda from the prior box, 10% held out, targets from this
-    workload's own injections, 60 epochs) is setup, timed separately.
-    """
-    import torch
-    box = synth.LAMBDA_BOX[:11]
+
+def train_surrogate(B, like, n_params, n_pairs, epochs, seed):
+    """Trains the ln xi network on the context's own injections; returns the training report."""
+    box = synth.LAMBDA_BOX[:n_params]
     t0 = time.perf_counter()
-    B.pop_xi_surrogate_train(like.ctx, 200000, box[:, 0], box[:, 1], epochs=60, seed=synth.seed_for(2, 5))
+    B.pop_xi_surrogate_train(like.ctx, n_pairs, box[:, 0], box[:, 1], epochs=epochs, seed=seed)
     train_s = time.perf_counter() - t0
     info = B.pop_xi_surrogate_info(like.ctx)
-    ms, w = timed(B.POP_MODE_F32_SURROGATE)
-    sur = [o.clone() for o in outs]
-    B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F32, out=outs)
-    torch.cuda.synchronize()
-    used = (sur[3].cpu().numpy().view(np.uint32) & B.POP_FLAG_SURROGATE_USED) != 0
-    d = (sur[0] - outs[0]).abs().cpu().numpy()
-    fin = np.isfinite(d)
-    K = len(lam)
-    return {"value": world * K * args.steps / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / args.steps,
-            "weight_ms": w, "dtype": "f32+bf16 network", "train_seconds": train_s,
+    st = B.pop_xi_surrogate_train_stats(like.ctx)
+    fit_tflops = st["fit_rows"] * MLP_FLOP_PER_ROW / st["fit_seconds"] / 1e12
+    return {"pairs": n_pairs, "heldout_frac": 0.1, "epochs": epochs, "seconds": train_s,
+            "target_seconds": st["target_seconds"], "fit_seconds": st["fit_seconds"],
+            "fit_tflops": fit_tflops, "fit_frac_of_bf16_peak": fit_tflops / BF16_PEAK_TFLOPS,
+            "bf16_peak_tflops": BF16_PEAK_TFLOPS, "bf16_peak_basis": BF16_PEAK_BASIS,
             "heldout_rmse_lnxi": info["heldout_rmse"], "heldout_mc_noise": info["mc_noise"],
-            "trusted": info["trusted"], "surrogate_used_frac": float(used.mean()),
-            "abs_dlnL_vs_f32_mc": {"mean": float(d[fin].mean()), "max": float(d[fin].max())},
-            **precision_fields([o.cpu().numpy() for o in sur], ref64, ref64_rounded)}
+            "trusted": info["trusted"]}
 
 
-def precision_fields(res, ref64, ref64_rounded):
-    """The form's distance to the FP64 kernel (which matches the oracle to 1e-12): on the original
-    inputs (arithmetic and float32 storage) and on the float32-rounded inputs (arithmetic alone,
-    the quantity the 0.05-nat FP32 bar applies to)."""
-    out = {}
-    if ref64 is not None:
-        out["vs_f64"] = precision_vs(res, ref64)
-    if ref64_rounded is not None:
-        out["vs_f64_rounded_inputs"] = precision_vs(res, ref64_rounded)
+def gated_form(B, like, lam, dev_lam, outs, args, world, stream, ref64, mc32, steps, budget):
+    """POP_MODE_F32_SURROGATE at one error budget: evals/s, the share of Lambda on the network,
+    and |Delta ln L| against the FP64 kernel on all rows and on the network's rows (where it is
+    at most the budget when the error bounds hold)."""
+    B.pop_xi_surrogate_set_budget(like.ctx, budget)
+    ms, w = time_mode(B, like, dev_lam, outs, B.POP_MODE_F32_SURROGATE, steps, args.warmup, world, stream)
+    sur = host_outputs(outs)
+    used = (sur[3] & B.POP_FLAG_SURROGATE_USED) != 0
+    K = len(lam)
+    return {"budget_nats": budget, "value": world * K * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "weight_ms": w, "surrogate_used_frac": float(used.mean()),
+            "vs_f64": precision_vs(sur, ref64), "vs_f64_network_rows": precision_vs(sur, ref64, used)["abs_dlnL"],
+            "vs_f32_mc_network_rows": dlnl_stats(np.abs(sur[0] - mc32[0])[used & np.isfinite(mc32[0])])}
+
+
+def surrogate_form(B, like, lam, dev_lam, outs, args, world, stream, ref64, mc32, n_params=11, steps=None,
+                   seed=None, budgets=(0.25,)):
+    """FP32 weights + the trained ln xi network, which replaces the Monte Carlo xi for the Lambda
+    whose error bound times N fits the budget (pop_xi_surrogate_error); Monte Carlo elsewhere.
+
+    Training (2e5 Lambda from the prior box, 10% held out, targets from this workload's own
+    injections, 60 epochs) is setup, reported separately with its tensor-core rate.  The
+    ungated entry (budget 1e9) shows what the gate keeps out.
+    """
+    steps = steps or args.steps
+    train = train_surrogate(B, like, n_params, 200000, 60, seed if seed is not None else synth.seed_for(2, 5))
+    err = B.pop_xi_surrogate_error(like.ctx, lam)
+    n_events = like.n_events
+    out = {"dtype": "f32+bf16 network", "training": train,
+           "n_x_err_bound_nats": {"p10": float(np.quantile(n_events * err, 0.1)),
+                                  "p50": float(np.quantile(n_events * err, 0.5)),
+                                  "p90": float(np.quantile(n_events * err, 0.9))}}
+    for b in budgets:
+        out[f"budget_{b:g}"] = gated_form(B, like, lam, dev_lam, outs, args, world, stream, ref64, mc32, steps, b)
+    out["ungated"] = gated_form(B, like, lam, dev_lam, outs, args, world, stream, ref64, mc32, steps, 1e9)
+    B.pop_xi_surrogate_set_budget(like.ctx, 0.25)
+    first = out[f"budget_{budgets[0]:g}"]
+    out["value"] = first["value"]
+    out["unit"] = "evals/s"
     return out
 
 
-def grid_form(B, like, lam, timed, args, world):
+def grid_form(B, like, lam, dev_lam, outs, args, world, stream):
     """ln L with the selection term on the dense (m1, q) campaign grid (3001 x 801
     nodes, the paper's grid VT) instead of the injections, FP64 and FP32; the
     grid's node contraction gets its own roofline (FP64 pipe, resp. FP32 FMA)."""
@@ -358,7 +413,7 @@ def grid_form(B, like, lam, timed, args, world):
              "f32": (FP32_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6, "128 FP32 FMA lanes/SM/clk x 152 SMs x 2070 MHz",
                      "Top/s (FP32 FMA)", "gv_main_kernel<float>")}
     for name, mode in (("f64", B.POP_MODE_F64), ("f32", B.POP_MODE_F32)):
-        ms, w = timed(mode)
+        ms, w = time_mode(B, like, dev_lam, outs, mode, args.steps, args.warmup, world, stream)
         cms, tms = B.pop_xi_grid_last_ms(like.ctx)
         peak, basis, unit, kern = peaks[name]
         ach = triples / (cms * 1e-3)
@@ -583,61 +638,141 @@ def run_grad(args, B, rank, local, world):
         print(json.dumps(line, default=_jsonable), flush=True)
 
 
-def run_ragged(args, B, rank, local, world):
+RAGGED = "f32_ragged2000_s500to16000_z"
+
+
+def ragged_measure(B, args, rank, local, world):
     """Batching form: 2000 events with S_i ~ U{500..16000} in CSR (about 1.65e7 samples), redshift
     on (12 parameters), 1.8e7 injection draws, FP32 weights.  Uneven Lambda batches
     (64, 200, 1000, 4096 in turn) replay one graph captured at 4096 with K read on the device;
-    the tiling comes from the autotuner.  One step = one batch; value = Lambda evaluated / s."""
+    the tiling comes from the autotuner.  One step = one batch; value = Lambda evaluated / s.
+    The oracle checks the last row of each batch size (|d ln L|, flags)."""
     import torch
-    cat, inj, _ = synth.make_workload("f32_ragged2000_s500to16000_z")
+    cat, inj, _ = synth.make_workload(RAGGED)
     sizes = (64, 200, 1000, 4096)
     lam = synth.make_lambdas(max(sizes), 12, seed=synth.seed_for(4, 2) + 7919 * rank)
     stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    like = B.Likelihood(local, stream).load(cat, inj, storage=B.POP_STORE_F32)
-    dev = torch.from_numpy(lam).cuda()
-    outs = [torch.empty(max(sizes), dtype=torch.float64, device="cuda") for _ in range(3)] + \
-           [torch.empty(max(sizes), dtype=torch.int32, device="cuda")]
-    B.pop_loglik(like.ctx, dev, B.POP_MODE_F32, out=outs)
-    B.pop_autotune(like.ctx, B.POP_MODE_F32, max(sizes))
-    seq = [sizes[s % len(sizes)] for s in range(args.steps)]
-    view = lambda k: [o[:k] for o in outs]
-    for s in range(args.warmup):
-        k = sizes[s % len(sizes)]
-        B.pop_loglik(like.ctx, dev[:k], B.POP_MODE_F32, out=view(k))
-    torch.cuda.synchronize()
-    barrier(world)
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    wms = []
-    with Clocks(local) as clk:
+    with torch.cuda.stream(stream):
+        like = B.Likelihood(local, stream).load(cat, inj, storage=B.POP_STORE_F32)
+        dev = torch.from_numpy(lam).cuda()
+        outs = [torch.empty(max(sizes), dtype=torch.float64, device="cuda") for _ in range(3)] + \
+               [torch.empty(max(sizes), dtype=torch.int32, device="cuda")]
+        B.pop_loglik(like.ctx, dev, B.POP_MODE_F32, out=outs)
+        B.pop_autotune(like.ctx, B.POP_MODE_F32, max(sizes))
+        seq = [sizes[s % len(sizes)] for s in range(max(args.steps, len(sizes)))]
+        view = lambda k: [o[:k] for o in outs]
+        last = {}
+        for k in sizes:
+            B.pop_loglik(like.ctx, dev[:k], B.POP_MODE_F32, out=view(k))
+            torch.cuda.synchronize()
+            last[k] = (float(outs[0][k - 1].item()), int(outs[3][k - 1].item()) & 0xFFFFFFFF)
+        for s in range(args.warmup):
+            k = sizes[s % len(sizes)]
+            B.pop_loglik(like.ctx, dev[:k], B.POP_MODE_F32, out=view(k))
+        torch.cuda.synchronize()
+        barrier(world)
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wms = []
         start.record(stream)
         for k in seq:
             B.pop_loglik(like.ctx, dev[:k], B.POP_MODE_F32, out=view(k))
             wms.append(B.pop_last_kernel_ms(like.ctx)[0])
         stop.record(stream)
         torch.cuda.synchronize()
-    ms = max_over_ranks(start.elapsed_time(stop), world)
-    support = {k: in_support_pairs(cat.theta, lam[:k]) + in_support_pairs(inj.theta, lam[:k]) for k in sizes}
-    t0 = time.perf_counter()
-    for k in seq:
-        B.pop_loglik(like.ctx, lam[:k], B.POP_MODE_F32)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        ms = max_over_ranks(start.elapsed_time(stop), world)
+        support = {k: in_support_pairs(cat.theta, lam[:k]) + in_support_pairs(inj.theta, lam[:k]) for k in sizes}
+        t0 = time.perf_counter()
+        for k in seq:
+            B.pop_loglik(like.ctx, lam[:k], B.POP_MODE_F32)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        tiling = B.pop_get_tiling(like.ctx, B.POP_MODE_F32)
+        like.close()
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        rows = np.array([k - 1 for k in sizes])
+        ref = oracle.loglik(cat, inj, lam[rows], nthreads=host_cores())
+        got = np.array([last[k][0] for k in sizes])
+        fl = np.array([last[k][1] for k in sizes], dtype=np.uint32)
+        fin = np.isfinite(ref[0])
+        parity = {"rows": len(rows), "max_abs_dlnL_vs_oracle": float(np.max(np.abs(got[fin] - ref[0][fin])))
+                  if fin.any() else 0.0, "flags_equal": bool((fl == ref[3]).all())}
     evals = world * sum(seq)
-    line = {"metric": "ln L(Lambda) evals/s, ragged 2000-event catalog + redshift (batching form)",
-            "value": evals / (ms * 1e-3), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "f32_ragged2000_s500to16000_z", "events": cat.n_events, "samples": int(cat.offsets[-1]),
-                       "n_draw": int(inj.n_draw), "n_found": int(inj.n_found), "K_sequence": list(sizes),
-                       "tiling_f32": B.pop_get_tiling(like.ctx, B.POP_MODE_F32), "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (FP32 features 44 B/sample)"},
+    return {"value": evals / (ms * 1e-3), "unit": "evals/s", "steps": len(seq), "ms_per_step": ms / len(seq),
+            "dtype": "f32", "config": {"workload": RAGGED, "events": cat.n_events, "samples": int(cat.offsets[-1]),
+                                       "n_draw": int(inj.n_draw), "n_found": int(inj.n_found),
+                                       "K_sequence": list(sizes), "tiling_f32": tiling,
+                                       "l2": "inputs larger than L2 (FP32 features 32 B/sample streamed)"},
             "roofline": f32_roofline(sum(support[k] for k in seq), sum(wms)),
             "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(8 * 12 * np.mean(seq)),
                     "d2h_bytes_per_step": int(28 * np.mean(seq))},
-            "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
-    like.close()
+            "parity_vs_oracle": parity, "gpu_launches": 6 * len(seq)}
+
+
+def run_ragged(args, B, rank, local, world):
+    """The batching form alone (see ragged_measure), as its own JSON line."""
+    with Clocks(local) as clk:
+        r = ragged_measure(B, args, rank, local, world)
+    line = {"metric": "ln L(Lambda) evals/s, ragged 2000-event catalog + redshift (batching form)",
+            "value": r["value"], "unit": "evals/s", "n_gpus": world, "steps": r["steps"], "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": dict(r["config"], parallelism=f"replicas{world}"),
+            "roofline": r["roofline"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": clk.summary(),
+            "parity_vs_oracle": r["parity_vs_oracle"]}
     if rank == 0:
-        print(json.dumps(line, default=_jsonable), flush=True)
+        print(json.dumps(_rounded(line), default=_jsonable), flush=True)
+
+
+LEARNED = "f32_z_10x1000_inj1e5_surrogate"
+
+
+def learned_measure(B, args, rank, local, world):
+    """The learned form at its own size: 10 events x 1000 samples with redshift (12-dimensional
+    Lambda), 1e5 injection draws, K = 1024.  The ln xi network is trained on 2e5 pairs from this
+    injection set's reweighting (10% held out, 60 epochs); ln L evals/s of the FP32 + network form
+    against the plain FP64 and FP32 Monte Carlo forms, with |Delta ln L| against FP64 on every row."""
+    import torch
+    cat, inj, lam = synth.make_workload(LEARNED)
+    lam = synth.make_lambdas(len(lam), 12, seed=synth.seed_for(5, 2) + 7919 * rank)
+    steps = max(args.steps, 200)   # a step is tens of microseconds
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        like = B.Likelihood(local, stream).load(cat, inj)
+        dev_lam = torch.from_numpy(lam).cuda()
+        outs = [torch.empty(len(lam), dtype=torch.float64, device="cuda") for _ in range(3)] + \
+               [torch.empty(len(lam), dtype=torch.int32, device="cuda")]
+        K = len(lam)
+        res = {}
+        for name, mode in (("f64", B.POP_MODE_F64), ("f32", B.POP_MODE_F32)):
+            B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+            ms, w = time_mode(B, like, dev_lam, outs, mode, steps, args.warmup, world, stream)
+            res[name] = {"value": world * K * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                         "out": host_outputs(outs)}
+        sur = surrogate_form(B, like, lam, dev_lam, outs, args, world, stream, res["f64"]["out"], res["f32"]["out"],
+                             n_params=12, steps=steps, seed=synth.seed_for(5, 5), budgets=(0.25, 1.0))
+        like.close()
+    return {"config": {"workload": LEARNED, "events": cat.n_events, "samples_per_event": 1000, "n_dims": 7,
+                       "n_draw": int(inj.n_draw), "n_found": int(inj.n_found), "K": K, "steps": steps},
+            "f64": {"value": res["f64"]["value"], "ms_per_step": res["f64"]["ms_per_step"]},
+            "f32": {"value": res["f32"]["value"], "ms_per_step": res["f32"]["ms_per_step"],
+                    "vs_f64": precision_vs(res["f32"]["out"], res["f64"]["out"])},
+            "f32_surrogate": sur}
+
+
+def run_learned(args, B, rank, local, world):
+    """The learned form alone (see learned_measure), as its own JSON line."""
+    with Clocks(local) as clk:
+        r = learned_measure(B, args, rank, local, world)
+    sur = r["f32_surrogate"]
+    line = {"metric": "ln L(Lambda) evals/s, learned selection term (FP32 + network), 10 x 1000 + redshift",
+            "value": sur["value"], "unit": "evals/s", "n_gpus": world, "steps": r["config"]["steps"],
+            "warmup": args.warmup, "ms_per_step": sur["budget_0.25"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": dict(r["config"], parallelism=f"replicas{world}", l2="inputs L2-resident (small workload)"),
+            "forms": {"f64": r["f64"], "f32": r["f32"], "f32_surrogate": sur}, "clocks": clk.summary(),
+            "gpu_launches": 12 * r["config"]["steps"]}
+    if rank == 0:
+        print(json.dumps(_rounded(line), default=_jsonable), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -679,6 +814,129 @@ def _jsonable(o):
     raise TypeError(type(o).__name__)
 
 
+def run_scan(args, B, rank, local, world):
+    """Analogue of the paper's speed-up-versus-samples figure (Sec. "Population acceleration",
+    Fig. 4): FP64 and FP32 ln L evals/s at K = 1024 over N*S = 1e4 .. 2e7 posterior samples
+    (S = min(4096, N*S) samples per event), with injections in the catalog workload's proportion
+    (2 N S draws, about 0.22 N S found), the roofline fraction of each point, and the oracle timed
+    beside it on 16 rows (up to 3e6 samples).  The saturation point is the smallest N*S whose FP64
+    fraction is within 10% of the largest."""
+    import torch
+    points = [10 ** 4, 3 * 10 ** 4, 10 ** 5, 3 * 10 ** 5, 10 ** 6, 3 * 10 ** 6, 10 ** 7, 2 * 10 ** 7]
+    K = 1024
+    lam = synth.make_lambdas(K, 11, seed=synth.seed_for(7, 2) + 7919 * rank)
+    dev_lam = torch.from_numpy(lam).cuda()
+    rows = []
+    with Clocks(local) as clk:
+        for ns in points:
+            S = min(4096, ns)
+            N = ns // S
+            cat = synth.make_catalog(N, S, 6, seed=synth.seed_for(7, 0) + ns)
+            inj = synth.make_injections(2 * ns, 6, seed=synth.seed_for(7, 1) + ns)
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                like = B.Likelihood(local, stream).load(cat, inj)
+                outs = [torch.empty(K, dtype=torch.float64, device="cuda") for _ in range(3)] + \
+                       [torch.empty(K, dtype=torch.int32, device="cuda")]
+                pairs = in_support_pairs(cat.theta, lam) + in_support_pairs(inj.theta, lam)
+                steps = int(min(200, max(args.steps, 2e9 / max(pairs, 1))))
+                pt = {"samples": ns, "events": N, "samples_per_event": S, "n_found": int(inj.n_found),
+                      "in_support_pairs": pairs, "steps": steps}
+                for name, mode in (("f64", B.POP_MODE_F64), ("f32", B.POP_MODE_F32)):
+                    B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
+                    B.pop_autotune(like.ctx, mode, 64 if mode == B.POP_MODE_F64 else K)
+                    ms, w = time_mode(B, like, dev_lam, outs, mode, steps, args.warmup, world, stream)
+                    if mode == B.POP_MODE_F64:
+                        ops = in_support_pairs(cat.theta, lam) * FP64_OPS_PER_PAIR + \
+                            in_support_pairs(inj.theta, lam) * FP64_OPS_PER_INJ_PAIR
+                        frac = ops / (w * 1e-3) / (FP64_LANES_PER_SM * SMS * SM_MAX_MHZ * 1e6)
+                    else:
+                        frac = f32_roofline(pairs, w)["frac"]
+                    pt[name] = {"value": world * K * steps / (ms * 1e-3), "ms_per_step": ms / steps, "weight_ms": w,
+                                "roofline_frac": frac}
+                like.close()
+            if rank == 0 and not args.no_cpu_baseline and ns <= 3 * 10 ** 6:
+                import oracle
+                n = 16
+                t0 = time.perf_counter()
+                oracle.loglik(cat, inj, lam[:n], nthreads=host_cores())
+                pt["oracle"] = {"value": n / (time.perf_counter() - t0), "rows": n, "cores": min(n, host_cores())}
+            rows.append(pt)
+    best = max(r["f64"]["roofline_frac"] for r in rows)
+    sat = next(r["samples"] for r in rows if r["f64"]["roofline_frac"] >= 0.9 * best)
+    best32 = max(r["f32"]["roofline_frac"] for r in rows)
+    sat32 = next(r["samples"] for r in rows if r["f32"]["roofline_frac"] >= 0.9 * best32)
+    top = rows[-1]
+    line = {"metric": "ln L(Lambda) evals/s versus posterior samples N*S (K = 1024), FP64 and FP32",
+            "value": top["f64"]["value"], "unit": "evals/s", "n_gpus": world, "steps": top["steps"],
+            "warmup": args.warmup, "ms_per_step": top["f64"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "scan_samples_1e4_to_2e7_K1024", "K": K, "parallelism": f"replicas{world}",
+                       "injections": "2 N S draws, sigmoid((m1 - 20)/5) detection"},
+            "saturation_samples_f64": sat, "saturation_samples_f32": sat32, "points": rows,
+            "clocks": clk.summary(), "gpu_launches": sum(r["steps"] * 10 for r in rows)}
+    if rank == 0:
+        print(json.dumps(_rounded(line), default=_jsonable), flush=True)
+
+
+def _rounded(o, sig=6):
+    """Floats rounded to `sig` significant digits (a shorter JSON line; the values are measurements)."""
+    if isinstance(o, dict):
+        return {k: _rounded(v, sig) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_rounded(v, sig) for v in o]
+    if isinstance(o, (float, np.floating)):
+        x = float(o)
+        return float(f"{x:.{sig}g}") if np.isfinite(x) else x
+    return o
+
+
+def summarise(line):
+    """The figures of every form in a few hundred characters, for the end of the JSON line."""
+    f = line.get("forms", {})
+    r4 = lambda x: None if x is None else float(f"{x:.4g}")
+    out = {"f64": {"evals_s": r4(line["value"]), "frac": r4(line["roofline"]["frac"]),
+                   "parity_over_tol": r4(line.get("cpu_baseline", {}).get("parity_f64_kernel", {})
+                                         .get("max_over_f64_tol"))}}
+    if "f64_ff" in f:
+        out["f64_ff"] = {"evals_s": r4(f["f64_ff"]["value"]), "frac": r4(f["f64_ff"]["roofline"]["frac"]),
+                         "max_over_tol": r4(f["f64_ff"]["max_dlnL_over_f64_tol"])}
+    if "grad_f64" in f:
+        out["grad_f64"] = {"evals_s": r4(f["grad_f64"]["value"]), "frac": r4(f["grad_f64"]["roofline"]["frac"])}
+    if "grid_selection" in f:
+        g = f["grid_selection"]
+        out["grid"] = {"f64_frac": r4(g["f64"]["roofline"]["frac"]), "f32_frac": r4(g["f32"]["roofline"]["frac"])}
+    if "cbc_likelihood" in f:
+        c = f["cbc_likelihood"]
+        out["cbc"] = {"f64_evals_s": r4(c["f64"]["value"]), "f64_frac": r4(c["f64"]["roofline"]["frac"]),
+                      "f32_evals_s": r4(c["f32"]["value"]), "f32_frac": r4(c["f32"]["roofline"]["frac"])}
+    if "ragged" in f:
+        g = f["ragged"]
+        out["ragged"] = {"evals_s": r4(g["value"]), "frac": r4(g["roofline"]["frac"]),
+                         "dlnL_vs_oracle": r4((g.get("parity_vs_oracle") or {}).get("max_abs_dlnL_vs_oracle"))}
+    if "learned" in f:
+        g = f["learned"]
+        sur = g["f32_surrogate"]
+        out["learned_c5"] = {"f64_evals_s": r4(g["f64"]["value"]), "f32_evals_s": r4(g["f32"]["value"]),
+                             "fit_tflops": r4(sur["training"]["fit_tflops"]),
+                             **{b: {"evals_s": r4(sur[b]["value"]), "used": r4(sur[b]["surrogate_used_frac"]),
+                                    "dlnL_max": r4(sur[b]["vs_f64"]["abs_dlnL"]["max"]),
+                                    "dlnL_max_net": r4(sur[b]["vs_f64_network_rows"]["max"])}
+                                for b in ("budget_0.25", "budget_1", "ungated") if b in sur}}
+    if "f32_surrogate" in f:
+        sur = f["f32_surrogate"]
+        out["f32_surrogate"] = {b: {"evals_s": r4(sur[b]["value"]), "used": r4(sur[b]["surrogate_used_frac"]),
+                                    "dlnL_max": r4(sur[b]["vs_f64"]["abs_dlnL"]["max"]),
+                                    "dlnL_max_net": r4(sur[b]["vs_f64_network_rows"]["max"])}
+                                for b in ("budget_0.25", "ungated") if b in sur}
+        out["f32_surrogate"]["fit_tflops"] = r4(sur["training"]["fit_tflops"])
+    if "f32" in f:
+        out["f32"] = {"evals_s": r4(f["f32"]["value"]), "frac": r4(f["f32"]["roofline"]["frac"]),
+                      "dlnL_max_vs_f64": r4(f["f32"]["vs_f64"]["abs_dlnL"]["max"]),
+                      "dlnL_p99_vs_f64": r4(f["f32"]["vs_f64"]["abs_dlnL"]["p99"])}
+    return out
+
+
 def main():
     args = parse()
     rank, local, world = dist_setup(args.gpus)
@@ -690,20 +948,10 @@ def main():
     from paper_1904_02863_gb300 import binding as B
     from paper_1904_02863_gb300 import build
     build.build()
-    if args.workload == "ragged":
-        run_ragged(args, B, rank, local, world)
-        return
-    if args.workload == "grid":
-        run_grid(args, B, rank, local, world)
-        return
-    if args.workload == "cbc":
-        run_cbc(args, B, rank, local, world)
-        return
-    if args.workload == "grad":
-        run_grad(args, B, rank, local, world)
-        return
-    if args.workload == "sampler":
-        run_sampler(args, B, rank, local, world)
+    standalone = {"ragged": run_ragged, "grid": run_grid, "cbc": run_cbc, "grad": run_grad, "sampler": run_sampler,
+                  "learned": run_learned, "scan": run_scan}
+    if args.workload in standalone:
+        standalone[args.workload](args, B, rank, local, world)
         return
 
     scale = args.events / 1000.0
@@ -718,25 +966,6 @@ def main():
     outs = [torch.empty(K, dtype=torch.float64, device="cuda") for _ in range(3)] + \
            [torch.empty(K, dtype=torch.int32, device="cuda")]
 
-    def timed(mode):
-        for _ in range(args.warmup):
-            B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
-        torch.cuda.synchronize()
-        barrier(world)
-        torch.cuda.synchronize()
-        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        wms = []
-        start.record(stream)
-        for _ in range(args.steps):
-            B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
-            wms.append(B.pop_last_kernel_ms(like.ctx)[0])
-        stop.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        torch.cuda.synchronize()
-        ms = max_over_ranks(start.elapsed_time(stop), world)
-        return ms, statistics.mean(wms)
-
     head = {"f32": B.POP_MODE_F32, "ff": B.POP_MODE_FF}.get(args.mode, B.POP_MODE_F64)
     # Tiling from the autotuner (FP64 on the first 64 Lambda rows: its launches are long); the
     # float-float kernel has one fixed tiling.
@@ -745,9 +974,10 @@ def main():
         if mode != B.POP_MODE_FF:
             B.pop_autotune(like.ctx, mode, min(K, 64) if mode == B.POP_MODE_F64 else K)
     with Clocks(local) as clk:
-        ms_h, w_h = timed(head)
+        ms_h, w_h = time_mode(B, like, dev_lam, outs, head, args.steps, args.warmup, world, stream)
         if args.mode == "both":
-            ms32, w32 = timed(B.POP_MODE_F32)
+            ms32, w32 = time_mode(B, like, dev_lam, outs, B.POP_MODE_F32, args.steps, args.warmup, world, stream)
+            out32 = host_outputs(outs)
 
     # End to end through the public API with pinned host buffers.
     h_lam = torch.from_numpy(lam).pin_memory()
@@ -760,13 +990,11 @@ def main():
         B.pop_loglik(like.ctx, h_lam, head, out=h_out)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
 
-    def run_once(mode):
-        B.pop_loglik(like.ctx, dev_lam, mode, out=outs)
-        torch.cuda.synchronize()
-        return [o.cpu().numpy().copy() for o in outs]
-
-    # Untimed reference outputs for the precision report.
-    ref64 = run_once(B.POP_MODE_F64) if (head == B.POP_MODE_F64 or args.mode == "both") else None
+    # Untimed FP64 outputs for the precision reports.
+    ref64 = None
+    if head == B.POP_MODE_F64 or args.mode == "both":
+        B.pop_loglik(like.ctx, dev_lam, B.POP_MODE_F64, out=outs)
+        ref64 = host_outputs(outs)
 
     n_ev_pairs = in_support_pairs(cat.theta, lam)
     n_inj_pairs = in_support_pairs(inj.theta, lam)
@@ -807,30 +1035,36 @@ def main():
         "roofline": roofline,
         "e2e": {"value": world * K * args.steps / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(lam.nbytes), "d2h_bytes_per_step": int(K * (8 * 3 + 4))},
-        # set K, prologue, weight, finalise (+ the FP32 kernel's Lambda order)
-        "gpu_launches": (4 if head == B.POP_MODE_F64 else 5) * args.steps,
+        # set K, prologue, weight, finalise (+ the FP32 kernel's Lambda order and upper-edge fix-up)
+        "gpu_launches": (4 if head == B.POP_MODE_F64 else 6) * args.steps,
         "clocks": clocks,
         "pipe_rates": pipe,
     }
-    if args.mode == "both":
-        ref64_r = f64_on_rounded_inputs(B, cat, inj, dev_lam, local, stream)
-        line["forms"] = {"f32": {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
-                                 "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32",
-                                 "roofline": f32_roofline(n_ev_pairs + n_inj_pairs, w32),
-                                 **precision_fields(run_once(B.POP_MODE_F32), ref64, ref64_r)}}
-        line["forms"]["f64_ff"] = ff_form(B, like, lam, dev_lam, outs, timed, args, world, n_ev_pairs + n_inj_pairs,
-                                          cat.n_events)
-        line["forms"]["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, timed, args, world,
-                                                             ref64, ref64_r)
-        line["forms"]["grid_selection"] = grid_form(B, like, lam, timed, args, world)
-        line["forms"]["cbc_likelihood"] = cbc_form(B, like, args, world, rank)
-        line["forms"]["grad_f64"] = grad_form(B, like, lam, args, world, n_ev_pairs + n_inj_pairs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, inj, lam, args.oracle_lambdas,
                                              ref64 if head == B.POP_MODE_F64 else None)
-    like.close()
+    if args.mode == "both":
+        # Largest first, so that the driver's record (the end of the line) keeps the compact ones.
+        forms = {}
+        forms["grid_selection"] = grid_form(B, like, lam, dev_lam, outs, args, world, stream)
+        forms["cbc_likelihood"] = cbc_form(B, like, args, world, rank)
+        forms["grad_f64"] = grad_form(B, like, lam, args, world, n_ev_pairs + n_inj_pairs)
+        forms["f64_ff"] = ff_form(B, like, lam, dev_lam, outs, args, world, stream, n_ev_pairs + n_inj_pairs,
+                                  cat.n_events, ref64)
+        forms["f32_surrogate"] = surrogate_form(B, like, lam, dev_lam, outs, args, world, stream, ref64, out32)
+        forms["f32"] = {"value": world * K * args.steps / (ms32 * 1e-3), "unit": "evals/s",
+                        "ms_per_step": ms32 / args.steps, "weight_ms": w32, "dtype": "f32",
+                        "roofline": f32_roofline(n_ev_pairs + n_inj_pairs, w32), "vs_f64": precision_vs(out32, ref64)}
+        like.close()
+        like = None
+        forms["ragged"] = ragged_measure(B, args, rank, local, world)
+        forms["learned"] = learned_measure(B, args, rank, local, world)
+        line["forms"] = forms
+        line["summary"] = summarise(line)
+    if like is not None:
+        like.close()
     if rank == 0:
-        print(json.dumps(line, default=_jsonable), flush=True)
+        print(json.dumps(_rounded(line), default=_jsonable), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -358,10 +358,36 @@ int pop_xi_surrogate_info(pop_ctx* ctx, double* heldout_rmse, double* mc_noise, 
 
 /* ln xi (and ln N_eff, may be NULL) predicted for K Lambda rows; out_fallback[k]
  * (may be NULL) = 1 when the Monte Carlo xi must be used instead: surrogate
- * not trusted, Lambda outside the training box, or predicted N_eff < 4 N.
- * All arrays in `mem`; synchronous. */
+ * not trusted, Lambda outside the training box, predicted N_eff < 4 N, or
+ * N * (the Lambda's error bound, pop_xi_surrogate_error) above the budget
+ * (pop_xi_surrogate_set_budget).  pop_loglik in POP_MODE_F32_SURROGATE takes
+ * the same decision for every Lambda.  All arrays in `mem`; synchronous. */
 int pop_xi_surrogate_infer(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, double* out_lnxi,
                            double* out_lnneff, uint8_t* out_fallback, int mem);
+
+/* The surrogate's error bound on ln xi for each of K Lambda rows (out_err[K],
+ * in `mem`; synchronous).  From the held-out pairs of the training: they are
+ * split into 16 bins of equal count by the network's predicted ln N_eff (the
+ * Monte Carlo scatter of the targets, which the network cannot learn, grows
+ * like 1/sqrt(N_eff)), and a bin's bound is 1.25 x its largest held-out
+ * |ln xi_net - ln xi-hat|.  A Lambda's ln L from the surrogate then differs
+ * from the Monte Carlo one by N x that bound at most, for all but about one in
+ * (pairs per bin) Lambda.  This is a per-Lambda reading of the paper's learned
+ * VT (Sec. "Population acceleration"), which gives no error model. */
+int pop_xi_surrogate_error(pop_ctx* ctx, int64_t K, int n_params, const double* lambda, double* out_err, int mem);
+
+/* Wall time of the last pop_xi_surrogate_train in this context: generating the
+ * targets (the Monte Carlo selection term over the pairs) and fitting (forward,
+ * backward and Adam over every mini-batch, synchronised at the end), and the
+ * rows that went through forward and backward (epochs x steps x batch).  Any
+ * pointer may be NULL; POP_ESTATE when nothing was trained here (a loaded
+ * checkpoint has no timings). */
+int pop_xi_surrogate_train_stats(pop_ctx* ctx, double* target_seconds, double* fit_seconds, int64_t* fit_rows);
+
+/* Largest N x error bound (nats of ln L) for which a Lambda uses the network;
+ * default 0.25.  Takes effect on the next call; POP_EINVAL for a negative or
+ * NaN budget.  Saved in checkpoints. */
+int pop_xi_surrogate_set_budget(pop_ctx* ctx, double nats);
 
 /* Checkpoint of the trained surrogate (weights, normalisation, held-out
  * statistics) as a versioned binary file; load restores it. */

@@ -35,6 +35,7 @@ EXPORTS = (
     "pop_mlp_train_step", "pop_mlp_gemm_check",
     "pop_load_vt_grid", "pop_set_xi_source", "pop_xi_grid", "pop_xi_grid_last_ms", "pop_loglik_parts",
     "pop_cbc_load", "pop_cbc_loglik", "pop_cbc_last_ms", "pop_loglik_grad",
+    "pop_xi_surrogate_error", "pop_xi_surrogate_set_budget", "pop_xi_surrogate_train_stats",
 )
 MLP_N_PARAMS = 201218
 POP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -83,6 +84,9 @@ def load_library(path: str = LIB_PATH):
         "pop_xi_surrogate_info": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                         ctypes.POINTER(i32)]),
         "pop_xi_surrogate_infer": (i32, [vp, i64, i32, vp, vp, vp, vp, i32]),
+        "pop_xi_surrogate_error": (i32, [vp, i64, i32, vp, vp, i32]),
+        "pop_xi_surrogate_set_budget": (i32, [vp, d]),
+        "pop_xi_surrogate_train_stats": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)]),
         "pop_xi_surrogate_save": (i32, [vp, ctypes.c_char_p]),
         "pop_xi_surrogate_load": (i32, [vp, ctypes.c_char_p]),
         "pop_mlp_set_params": (i32, [vp, vp, i64]),
@@ -468,6 +472,28 @@ def pop_xi_surrogate_infer(ctx, lambdas):
     return lx, ln, fb
 
 
+def pop_xi_surrogate_error(ctx, lambdas):
+    """The surrogate's error bound on ln xi for each Lambda row (from its held-out pairs)."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    K, P = lam.shape
+    err = np.empty(K)
+    _check(ctx, load_library().pop_xi_surrogate_error(ctx, K, P, lam.ctypes.data_as(ctypes.c_void_p),
+                                                      err.ctypes.data_as(ctypes.c_void_p), POP_MEM_HOST))
+    return err
+
+
+def pop_xi_surrogate_train_stats(ctx):
+    """Seconds spent on the targets and on the fit of the last training, and the rows fitted."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, load_library().pop_xi_surrogate_train_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+    return {"target_seconds": a.value, "fit_seconds": b.value, "fit_rows": n.value}
+
+
+def pop_xi_surrogate_set_budget(ctx, nats):
+    """Largest N x error bound (nats of ln L) for which a Lambda uses the network (default 0.25)."""
+    _check(ctx, load_library().pop_xi_surrogate_set_budget(ctx, float(nats)))
+
+
 def pop_xi_surrogate_save(ctx, path):
     """Writes the trained network, its normalisation and held-out statistics to `path`."""
     _check(ctx, load_library().pop_xi_surrogate_save(ctx, str(path).encode()))
@@ -523,6 +549,7 @@ class Likelihood:
         self.ctx = pop_create(device, stream)
 
     def load(self, catalog, injections, storage=POP_STORE_F64 | POP_STORE_F32):
+        self.n_events = catalog.n_events
         pop_load_events(self.ctx, catalog.offsets, catalog.theta, catalog.prior, storage)
         pop_load_injections(self.ctx, injections.n_draw, injections.theta, injections.p_draw, storage)
         return self

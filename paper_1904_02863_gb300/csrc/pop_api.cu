@@ -398,7 +398,7 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
         // ln xi from the network for every Lambda, and which Lambda still need the Monte Carlo xi.
         const int64_t n_events = (int64_t)c->h_offsets.size() - 1;
         const int rc = c->sur->enqueue_gate(c->d_lambda.as<double>(), c->k_cap, n_params, c->d_K.as<int64_t>(),
-                                            4.0 * (double)n_events, c->d_need.as<uint8_t>(), c->d_slnxi.as<double>(),
+                                            (double)n_events, c->d_need.as<uint8_t>(), c->d_slnxi.as<double>(),
                                             c->d_slnneff.as<double>());
         if (rc != POP_OK) return fail(c, rc, "surrogate: " + c->sur->err);
         sx = SurrogateXi{c->d_need.as<uint8_t>(), c->d_slnxi.as<double>(), c->d_slnneff.as<double>()};

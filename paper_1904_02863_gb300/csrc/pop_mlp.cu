@@ -507,12 +507,13 @@ __global__ void gather_rows_kernel(const bf16* __restrict__ xall, const float* _
 unsigned grid1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 struct GateArgs {
-    double mu0, sd0, mu1, sd1, need_neff;
+    double mu0, sd0, mu1, sd1, n_events, budget;
     int trusted;
+    ErrTable table;
 };
 
 // Per Lambda: ln xi and ln N_eff from the network, and whether the Monte Carlo xi is needed
-// (untrusted network, Lambda outside the training box, predicted N_eff < 4 N, or a timed-out wait).
+// (need_monte_carlo: the trust gate, the box, a timed-out wait, N_eff < 4 N, the error budget).
 __global__ void gate_kernel(const float* __restrict__ y, const uint8_t* __restrict__ outside,
                             const int64_t* __restrict__ dK, const int* __restrict__ err, GateArgs a,
                             uint8_t* __restrict__ need, double* __restrict__ lnxi, double* __restrict__ lnneff)
@@ -523,12 +524,13 @@ __global__ void gate_kernel(const float* __restrict__ y, const uint8_t* __restri
     const double ln = (double)y[k * 2 + 1] * a.sd1 + a.mu1;
     lnxi[k] = lx;
     lnneff[k] = ln;
-    need[k] = (uint8_t)(!a.trusted || outside[k] || *err || !(exp(ln) >= a.need_neff) || !isfinite(lx));
+    need[k] = (uint8_t)need_monte_carlo(a.trusted != 0, outside[k] != 0, *err != 0, lx, ln, a.n_events, a.budget,
+                                        a.table);
 }
 
 }  // namespace
 
-int Surrogate::enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double need_neff,
+int Surrogate::enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double n_events,
                             uint8_t* need, double* lnxi, double* lnneff)
 {
     const int64_t rp = (k_cap + TC_BM - 1) / TC_BM * TC_BM;
@@ -540,7 +542,7 @@ int Surrogate::enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const 
     if (rc != POP_OK) return rc;
     rc = forward(rp);
     if (rc != POP_OK) return rc;
-    GateArgs a{mu[0], sd[0], mu[1], sd[1], need_neff, trusted ? 1 : 0};
+    GateArgs a{mu[0], sd[0], mu[1], sd[1], n_events, budget, trusted ? 1 : 0, table};
     gate_kernel<<<grid1(k_cap, 256), 256, 0, stream>>>(y.as<float>(), outside.as<uint8_t>(), dK, err_flag.as<int>(), a,
                                                        need, lnxi, lnneff);
     const cudaError_t e = cudaGetLastError();

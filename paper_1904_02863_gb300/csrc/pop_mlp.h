@@ -28,6 +28,39 @@ constexpr int MLP_LAYERS = 5;
 constexpr int64_t MLP_N_PARAMS = (int64_t)MLP_HID * MLP_IN + MLP_HID + 3 * ((int64_t)MLP_HID * MLP_HID + MLP_HID) +
                                  (int64_t)MLP_OUT * MLP_HID + MLP_OUT;
 
+// Per-Lambda error model of the network's ln xi, from the held-out pairs: the pairs are split
+// into ERR_BINS bins of equal count by the network's own ln N_eff prediction (the Monte Carlo
+// scatter of the targets, ~1/sqrt(N_eff), is what the network cannot learn), and each bin keeps
+// ERR_MARGIN times the largest |ln xi_net - ln xi-hat| of its pairs.  A Lambda uses the network
+// only when N times its bin's error is within the budget (nats of ln L).
+constexpr int ERR_BINS = 16;
+constexpr double ERR_MARGIN = 1.25;
+constexpr double DEFAULT_BUDGET_NATS = 0.25;
+
+struct ErrTable {
+    double edge[ERR_BINS - 1];  // increasing ln N_eff bin edges
+    double err[ERR_BINS];       // error bound of ln xi per bin
+};
+
+__host__ __device__ inline double err_bound(const ErrTable& t, double ln_neff)
+{
+    int b = 0;
+    for (int i = 0; i < ERR_BINS - 1; ++i) b += ln_neff >= t.edge[i] ? 1 : 0;
+    return t.err[b];
+}
+
+// Whether the Monte Carlo xi is needed for one Lambda: untrusted network, Lambda outside the
+// training box, a timed-out wait, a non-finite prediction, predicted N_eff < 4 N, or N times the
+// error bound above the budget.  The same decision on the host (pop_xi_surrogate_infer) and on
+// the device (inside pop_loglik).
+__host__ __device__ inline bool need_monte_carlo(bool trusted, bool outside, bool timed_out, double lnxi,
+                                                 double ln_neff, double n_events, double budget, const ErrTable& t)
+{
+    const bool ok = trusted && !outside && !timed_out && isfinite(lnxi) && exp(ln_neff) >= 4.0 * n_events &&
+                    n_events * err_bound(t, ln_neff) <= budget;
+    return !ok;
+}
+
 struct Surrogate {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -41,6 +74,10 @@ struct Surrogate {
     bool trained = false;
     bool trusted = false;
     double heldout_rmse = 0, heldout_mc_noise = 0, heldout_excess = 0;
+    double target_seconds = 0, fit_seconds = 0;  // last training: target generation, fitting
+    int64_t fit_rows = 0;                      // rows through forward + backward in the last fit
+    ErrTable table{};                          // per-Lambda error model (held-out pairs)
+    double budget = DEFAULT_BUDGET_NATS;       // largest N x error bound the gate accepts
     int64_t adam_step = 0;
 
     DevBuf params, adam_m, adam_v, grads;  // FP32 [MLP_N_PARAMS]
@@ -71,7 +108,7 @@ struct Surrogate {
     DevBuf outside;
     uint64_t version = 0;  // bumped when the parameters or the normalisation change
     int ensure_gate(int64_t k_cap);
-    int enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double need_neff, uint8_t* need,
+    int enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double n_events, uint8_t* need,
                      double* lnxi, double* lnneff);
 };
 

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,7 +74,8 @@ int upload_inputs(pop_ctx* c, Surrogate* s, int64_t B, const float* x)
     return POP_OK;
 }
 
-// ln xi, ln N_eff and the fallback mask for K Lambda rows (device pointers).
+// ln xi, ln N_eff and the fallback mask for K Lambda rows (device Lambda, host outputs; any
+// output but lnxi may be NULL).
 int infer_device(pop_ctx* c, Surrogate* s, int64_t K, int P, const double* d_lambda, double* lnxi, double* lnneff,
                  uint8_t* fallback)
 {
@@ -89,15 +91,36 @@ int infer_device(pop_ctx* c, Surrogate* s, int64_t K, int P, const double* d_lam
     CKC(cudaMemcpyAsync(y.data(), s->y.p, y.size() * 4, cudaMemcpyDeviceToHost, s->stream), "copy y");
     CKC(cudaMemcpyAsync(out.data(), outside.p, K, cudaMemcpyDeviceToHost, s->stream), "copy mask");
     CKC(cudaStreamSynchronize(s->stream), "sync");
-    const double need = 4.0 * (double)ctx_n_events(c);
+    const double n_events = (double)ctx_n_events(c);
     for (int64_t k = 0; k < K; ++k) {
-        const double lx = y[k * 2] * s->sd[0] + s->mu[0];
-        const double ln = y[k * 2 + 1] * s->sd[1] + s->mu[1];
+        // the gate kernel's arithmetic: FP32 outputs widened, then scaled in FP64
+        const double lx = (double)y[k * 2] * s->sd[0] + s->mu[0];
+        const double ln = (double)y[k * 2 + 1] * s->sd[1] + s->mu[1];
         lnxi[k] = lx;
         if (lnneff) lnneff[k] = ln;
-        if (fallback) fallback[k] = (uint8_t)(!s->trusted || out[k] || !(std::exp(ln) >= need));
+        if (fallback)
+            fallback[k] = (uint8_t)need_monte_carlo(s->trusted, out[k] != 0, false, lx, ln, n_events, s->budget,
+                                                    s->table);
     }
     return POP_OK;
+}
+
+// The per-Lambda error table from the held-out pairs: bins of equal count by predicted ln N_eff,
+// each bin's bound ERR_MARGIN x its largest |ln xi_net - ln xi-hat|.
+void build_err_table(Surrogate* s, const std::vector<double>& pred_lnneff, const std::vector<double>& abs_err)
+{
+    const size_t n = abs_err.size();
+    std::vector<size_t> idx(n);
+    for (size_t i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return pred_lnneff[a] < pred_lnneff[b]; });
+    for (int b = 0; b < ERR_BINS; ++b) {
+        const size_t i0 = n * (size_t)b / ERR_BINS, i1 = n * (size_t)(b + 1) / ERR_BINS;
+        double m = 0.0;
+        for (size_t i = i0; i < i1; ++i) m = std::max(m, abs_err[idx[i]]);
+        // an empty bin (fewer pairs than bins) keeps no claim: never within a budget
+        s->table.err[b] = i1 > i0 ? ERR_MARGIN * m : INFINITY;
+        if (b > 0) s->table.edge[b - 1] = i0 < n ? pred_lnneff[idx[i0]] : INFINITY;
+    }
 }
 
 }  // namespace
@@ -241,6 +264,7 @@ int pop_xi_surrogate_train(pop_ctx* c, int64_t n_pairs, double heldout_frac, uin
     CKC(cudaSetDevice(ctx_device(c)), "cudaSetDevice");
 
     // 1. Lambda drawn uniformly from the box; targets from the Monte Carlo selection term.
+    const auto t_gen = std::chrono::steady_clock::now();
     std::mt19937_64 rng(seed);
     std::uniform_real_distribution<double> u01(0.0, 1.0);
     std::vector<double> lam((size_t)n_pairs * n_params);
@@ -257,6 +281,7 @@ int pop_xi_surrogate_train(pop_ctx* c, int64_t n_pairs, double heldout_frac, uin
                                   lnxi.data() + k0, neff.data() + k0, flags.data() + k0, POP_MEM_HOST);
         if (rc != POP_OK) return rc;
     }
+    const double target_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_gen).count();
     std::vector<int64_t> keep;
     for (int64_t k = 0; k < n_pairs; ++k)
         if (std::isfinite(lnxi[k]) && neff[k] > 0.0 && std::isfinite(neff[k]) && !(flags[k] & POP_FLAG_INVALID_LAMBDA))
@@ -308,6 +333,8 @@ int pop_xi_surrogate_train(pop_ctx* c, int64_t n_pairs, double heldout_frac, uin
     CKC(tb.alloc((size_t)TRAIN_BATCH * 2 * 4), "cudaMalloc");
 
     // 3. Adam on shuffled mini-batches, cosine learning-rate decay.
+    CKC(cudaStreamSynchronize(s->stream), "sync");
+    const auto t_fit = std::chrono::steady_clock::now();
     SUR(s->init_params(seed ^ 0x9E3779B97F4A7C15ull));
     const int64_t B = std::min<int64_t>(TRAIN_BATCH, n_train);
     const int64_t steps_per_epoch = std::max<int64_t>(1, n_train / B);
@@ -332,6 +359,9 @@ int pop_xi_surrogate_train(pop_ctx* c, int64_t n_pairs, double heldout_frac, uin
     }
     SUR(s->check_error());
     s->has_params = true;
+    s->fit_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_fit).count();
+    s->fit_rows = total * B;
+    s->target_seconds = target_seconds;
 
     // 4. Held-out error in ln xi, and the targets' own Monte Carlo scatter (Var ln xi-hat ~ 1/N_eff).
     std::vector<int64_t> hold(keep.begin() + n_train, keep.end());
@@ -341,15 +371,17 @@ int pop_xi_surrogate_train(pop_ctx* c, int64_t n_pairs, double heldout_frac, uin
     DevBuf d_hl;
     CKC(d_hl.alloc(hl.size() * 8), "cudaMalloc");
     CKC(cudaMemcpyAsync(d_hl.p, hl.data(), hl.size() * 8, cudaMemcpyHostToDevice, s->stream), "copy");
-    std::vector<double> pred(n_hold);
-    const int rc = infer_device(c, s, n_hold, n_params, d_hl.as<double>(), pred.data(), nullptr, nullptr);
+    std::vector<double> pred(n_hold), pred_ln(n_hold), abs_err(n_hold);
+    const int rc = infer_device(c, s, n_hold, n_params, d_hl.as<double>(), pred.data(), pred_ln.data(), nullptr);
     if (rc != POP_OK) return rc;
     double se = 0, noise = 0;
     for (int64_t i = 0; i < n_hold; ++i) {
         const double d = pred[i] - lnxi[hold[i]];
         se += d * d;
         noise += 1.0 / neff[hold[i]];
+        abs_err[i] = std::fabs(d);
     }
+    build_err_table(s, pred_ln, abs_err);
     s->heldout_rmse = std::sqrt(se / (double)n_hold);
     s->heldout_mc_noise = std::sqrt(noise / (double)n_hold);
     s->heldout_excess = std::sqrt(std::max(0.0, s->heldout_rmse * s->heldout_rmse -
@@ -419,7 +451,7 @@ int pop_xi_surrogate_save(pop_ctx* c, const char* path)
     SUR(s->get_params_host(p.data()));
     std::ofstream f(path, std::ios::binary);
     if (!f) return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_save: cannot open file");
-    const int32_t version = 1, np = s->n_params, trusted = s->trusted;
+    const int32_t version = 2, np = s->n_params, trusted = s->trusted;
     const int64_t n = MLP_N_PARAMS;
     f.write(CKPT_MAGIC, 8);
     f.write((const char*)&version, 4);
@@ -432,6 +464,8 @@ int pop_xi_surrogate_save(pop_ctx* c, const char* path)
     f.write((const char*)&s->heldout_mc_noise, 8);
     f.write((const char*)&s->heldout_excess, 8);
     f.write((const char*)&trusted, 4);
+    f.write((const char*)&s->table, sizeof s->table);
+    f.write((const char*)&s->budget, 8);
     f.write((const char*)&n, 8);
     f.write((const char*)p.data(), n * 4);
     if (!f) return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_save: write failed");
@@ -447,7 +481,8 @@ int pop_xi_surrogate_load(pop_ctx* c, const char* path)
     char magic[8];
     int32_t version = 0, np = 0, trusted = 0;
     int64_t n = 0;
-    double lo[MLP_IN], hi[MLP_IN], mu[2], sd[2], rmse, noise, excess;
+    double lo[MLP_IN], hi[MLP_IN], mu[2], sd[2], rmse, noise, excess, budget = DEFAULT_BUDGET_NATS;
+    ErrTable table{};
     f.read(magic, 8);
     f.read((char*)&version, 4);
     f.read((char*)&np, 4);
@@ -459,9 +494,17 @@ int pop_xi_surrogate_load(pop_ctx* c, const char* path)
     f.read((char*)&noise, 8);
     f.read((char*)&excess, 8);
     f.read((char*)&trusted, 4);
+    if (version == 2) {
+        f.read((char*)&table, sizeof table);
+        f.read((char*)&budget, 8);
+    } else {  // version 1 has no per-Lambda table: every Lambda gets no error claim
+        for (int b = 0; b < ERR_BINS; ++b) table.err[b] = INFINITY;
+        for (int b = 0; b < ERR_BINS - 1; ++b) table.edge[b] = INFINITY;
+    }
     f.read((char*)&n, 8);
-    if (!f || memcmp(magic, CKPT_MAGIC, 8) != 0 || version != 1 || n != MLP_N_PARAMS || (np != 11 && np != 12))
-        return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_load: not a surrogate checkpoint of this version");
+    if (!f || memcmp(magic, CKPT_MAGIC, 8) != 0 || (version != 1 && version != 2) || n != MLP_N_PARAMS ||
+        (np != 11 && np != 12))
+        return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_load: not a surrogate checkpoint of a known version");
     std::vector<float> p(n);
     f.read((char*)p.data(), n * 4);
     if (!f) return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_load: truncated file");
@@ -479,8 +522,66 @@ int pop_xi_surrogate_load(pop_ctx* c, const char* path)
     s->heldout_mc_noise = noise;
     s->heldout_excess = excess;
     s->trusted = trusted != 0;
+    s->table = table;
+    s->budget = budget;
     s->trained = true;
     s->version++;
+    CKC(cudaStreamSynchronize(s->stream), "sync");
+    return POP_OK;
+}
+
+int pop_xi_surrogate_train_stats(pop_ctx* c, double* target_seconds, double* fit_seconds, int64_t* fit_rows)
+{
+    if (!c) return POP_EINVAL;
+    int st;
+    Surrogate* s = ctx_surrogate(c, &st);
+    if (!s) return st;
+    if (!s->trained || s->fit_rows == 0)
+        return ctx_fail(c, POP_ESTATE, "pop_xi_surrogate_train_stats: no training in this context");
+    if (target_seconds) *target_seconds = s->target_seconds;
+    if (fit_seconds) *fit_seconds = s->fit_seconds;
+    if (fit_rows) *fit_rows = s->fit_rows;
+    return POP_OK;
+}
+
+int pop_xi_surrogate_set_budget(pop_ctx* c, double nats)
+{
+    if (!c) return POP_EINVAL;
+    if (!(nats >= 0.0)) return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_set_budget: need a budget >= 0 nats");
+    int st;
+    Surrogate* s = ctx_surrogate(c, &st);
+    if (!s) return st;
+    s->budget = nats;
+    s->version++;  // the captured gate holds the budget
+    return POP_OK;
+}
+
+int pop_xi_surrogate_error(pop_ctx* c, int64_t K, int n_params, const double* lambda, double* out_err, int mem)
+{
+    pop::TraceRange trace_("pop_xi_surrogate_error");
+    if (!c) return POP_EINVAL;
+    int st;
+    Surrogate* s = ctx_surrogate(c, &st);
+    if (!s) return st;
+    if (!s->trained) return ctx_fail(c, POP_ESTATE, "pop_xi_surrogate_error: surrogate not trained");
+    if (n_params != s->n_params) return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_error: n_params differs");
+    if (K < 0 || (K > 0 && (!lambda || !out_err)) || (mem != POP_MEM_HOST && mem != POP_MEM_DEVICE))
+        return ctx_fail(c, POP_EINVAL, "pop_xi_surrogate_error: bad arguments");
+    if (K == 0) return POP_OK;
+    CKC(cudaSetDevice(ctx_device(c)), "cudaSetDevice");
+    DevBuf dl;
+    const double* d_lambda = lambda;
+    if (mem == POP_MEM_HOST) {
+        CKC(dl.alloc((size_t)K * n_params * 8), "cudaMalloc");
+        CKC(cudaMemcpyAsync(dl.p, lambda, (size_t)K * n_params * 8, cudaMemcpyHostToDevice, s->stream), "copy");
+        d_lambda = dl.as<double>();
+    }
+    std::vector<double> lx(K), ln(K), e(K);
+    const int rc = infer_device(c, s, K, n_params, d_lambda, lx.data(), ln.data(), nullptr);
+    if (rc != POP_OK) return rc;
+    for (int64_t k = 0; k < K; ++k) e[k] = err_bound(s->table, ln[k]);
+    CKC(cudaMemcpyAsync(out_err, e.data(), K * 8, mem == POP_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice,
+                        s->stream), "copy");
     CKC(cudaStreamSynchronize(s->stream), "sync");
     return POP_OK;
 }

@@ -58,9 +58,23 @@ def test_precision_report_fields():
     a = [np.array([1.0, -np.inf, 3.0]), np.log(np.array([2.0, 1.0, 4.0]))]
     b = [np.array([1.5, -np.inf, 2.0]), np.log(np.array([2.0, 1.0, 5.0]))]
     r = bench.precision_vs(a, b)
-    assert r["rows"] == 3 and r["finite_rows_agree"]
+    assert r["abs_dlnL"]["rows"] == 2 and r["finite_rows_agree"]
     assert r["abs_dlnL"]["max"] == pytest.approx(1.0) and r["abs_dlnL"]["mean"] == pytest.approx(0.75)
     assert r["rel_dxi_max"] == pytest.approx(0.2)
+    sub = bench.precision_vs(a, b, rows=np.array([True, True, False]))
+    assert sub["abs_dlnL"]["rows"] == 1 and sub["abs_dlnL"]["max"] == pytest.approx(0.5)
+    s = bench.dlnl_stats(np.arange(101.0))
+    assert s["p99"] == pytest.approx(99.0) and s["max"] == 100.0 and bench.dlnl_stats(np.array([]))["rows"] == 0
+
+
+def test_rounding_and_summary_of_a_line():
+    line = {"value": 2529.0123456, "roofline": {"frac": 0.8412345678}, "x": [1.23456789012, np.float64(2.0)],
+            "forms": {"f32": {"value": 250812.3, "roofline": {"frac": 0.63}, "vs_f64": {"abs_dlnL": {
+                "max": 6.2e-4, "p99": 5e-4}}}}}
+    r = bench._rounded(line)
+    assert r["value"] == 2529.01 and r["x"][0] == 1.23457 and isinstance(r["x"][1], float)
+    s = bench.summarise(line)
+    assert s["f64"]["evals_s"] == 2529.0 and s["f32"]["dlnL_max_vs_f64"] == 6.2e-4
 
 
 def test_cpu_baseline_parity_field_against_the_oracle(oracle):

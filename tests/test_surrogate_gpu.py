@@ -152,7 +152,48 @@ def test_surrogate_checkpoint_round_trip(B, trained, tmp_path):
     b = B.pop_xi_surrogate_infer(ctx2, lam[:64])
     np.testing.assert_array_equal(a[0], b[0])
     assert B.pop_xi_surrogate_info(ctx2) == B.pop_xi_surrogate_info(like.ctx)
+    np.testing.assert_array_equal(B.pop_xi_surrogate_error(ctx2, lam[:64]), B.pop_xi_surrogate_error(like.ctx, lam[:64]))
     B.pop_destroy(ctx2)
+
+
+def test_per_lambda_gate_holds_the_budget(B, trained):
+    """The network is used for a Lambda only where N x its error bound fits the budget, in
+    pop_xi_surrogate_infer and in pop_loglik alike; there ln L differs from the Monte Carlo form
+    by N |d ln xi| <= the budget.  The error bounds themselves cover the network's actual
+    deviation from the Monte Carlo ln xi on all but a few of 1024 fresh Lambda."""
+    like, cat, inj, lam, rmse = trained
+    N = cat.n_events
+    L = lam[:1024]
+    err = B.pop_xi_surrogate_error(like.ctx, L)
+    assert np.isfinite(err).all() and (err > 0).all()
+    mc = like(L, B.POP_MODE_F32)
+    fin = np.isfinite(mc[0])
+    try:
+        B.pop_xi_surrogate_set_budget(like.ctx, 1e9)   # only the other conditions remain
+        _, _, fb_free = B.pop_xi_surrogate_infer(like.ctx, L)
+        su = like(L, B.POP_MODE_F32_SURROGATE)
+        used = (su[3] & B.POP_FLAG_SURROGATE_USED) != 0
+        assert used.mean() > 0.9, used.mean()
+        d = np.abs(su[0] - mc[0])
+        ok = used & fin
+        coverage = np.mean(d[ok] <= N * err[ok] + 1e-6)
+        print(f"error bound covers {coverage:.4f} of rows; N x bound quantiles "
+              f"{np.quantile(N * err, [0.1, 0.5, 0.9])}")
+        assert coverage >= 0.99, coverage
+        for budget in (1.0, 0.25, 0.05, 1e-4):
+            B.pop_xi_surrogate_set_budget(like.ctx, budget)
+            _, _, fb = B.pop_xi_surrogate_infer(like.ctx, L)
+            np.testing.assert_array_equal(fb, (fb_free | (N * err > budget)).astype(np.uint8))
+            su = like(L, B.POP_MODE_F32_SURROGATE)
+            used = (su[3] & B.POP_FLAG_SURROGATE_USED) != 0
+            np.testing.assert_array_equal(used, fb == 0)
+            np.testing.assert_array_equal(((su[3] & B.POP_FLAG_MC_FALLBACK) != 0), fb == 1)
+            d = np.abs(su[0] - mc[0])[used & fin]
+            print(f"budget {budget}: used {used.mean():.3f}, max |dlnL| {d.max() if d.size else 0:.3g}")
+            assert d.size == 0 or d.max() <= budget + 1e-6, (budget, d.max())
+        assert not used.any()   # 1e-4 nats is below every bound
+    finally:
+        B.pop_xi_surrogate_set_budget(like.ctx, 0.25)
 
 
 def test_loglik_with_surrogate_xi(B, trained):
@@ -162,6 +203,7 @@ def test_loglik_with_surrogate_xi(B, trained):
     like, cat, inj, lam, rmse = trained
     L = lam[:300].copy()
     L[:5, 0] = synth.LAMBDA_BOX[0, 1] + 0.3   # outside the training box -> Monte Carlo
+    B.pop_xi_surrogate_set_budget(like.ctx, 1e9)   # the box and the trust gate decide here
     mc = like(L, B.POP_MODE_F32)
     su = like(L, B.POP_MODE_F32_SURROGATE)
     lx, _, fb = B.pop_xi_surrogate_infer(like.ctx, L)
@@ -172,7 +214,7 @@ def test_loglik_with_surrogate_xi(B, trained):
     assert fell[:5].all()
     info = B.pop_xi_surrogate_info(like.ctx)
     assert info["trusted"], info   # the seeded training must pass the gate, else this test is vacuous
-    assert used[5:].mean() > 0.9
+    assert used[5:].mean() > 0.9, used[5:].mean()
     fin = np.isfinite(mc[0])
     # Monte Carlo rows reproduce the FP32 form exactly; surrogate rows differ only by -N (ln xi_s - ln xi_mc)
     np.testing.assert_array_equal(su[0][fell & fin], mc[0][fell & fin])
@@ -180,11 +222,13 @@ def test_loglik_with_surrogate_xi(B, trained):
     np.testing.assert_allclose(su[1][used], lx[used], rtol=1e-12)
     np.testing.assert_allclose(su[0][used & fin], mc[0][used & fin] - N * (lx[used & fin] - mc[1][used & fin]),
                                rtol=1e-9, atol=1e-6)
+    B.pop_xi_surrogate_set_budget(like.ctx, 0.25)
 
 
 def test_surrogate_skips_the_injection_work(B):
     """With many injections (1e7 draws, 1.1e6 found) the selection term dominates the cost
-    of a small catalog; the network replaces it for the Lambda it is trusted on."""
+    of a small catalog; where the network is used (here every Lambda the trust gate, the box and
+    N_eff >= 4 N admit, with no error budget) it replaces that work."""
     import time
     from paper_1904_02863_gb300 import synth
     cat = synth.make_catalog(10, 1000, 6, seed=401)
@@ -193,6 +237,9 @@ def test_surrogate_skips_the_injection_work(B):
     box = synth.LAMBDA_BOX[:11]
     B.pop_xi_surrogate_train(like.ctx, 40000, box[:, 0], box[:, 1], epochs=30, seed=3)
     L = synth.make_lambdas(2048, 11, seed=403)
+    err = B.pop_xi_surrogate_error(like.ctx, L)
+    print(f"N x error bound quantiles (10/50/90%): {np.quantile(10 * err, [0.1, 0.5, 0.9])}")
+    B.pop_xi_surrogate_set_budget(like.ctx, 1e9)   # the cost of the skipped work, not the gate
     times = {}
     for mode in (B.POP_MODE_F32, B.POP_MODE_F32_SURROGATE):
         like(L, mode)
@@ -203,7 +250,7 @@ def test_surrogate_skips_the_injection_work(B):
     used = (out[3] & B.POP_FLAG_SURROGATE_USED) != 0
     info = B.pop_xi_surrogate_info(like.ctx)
     assert info["trusted"], info
-    assert used.mean() > 0.9
+    assert used.mean() > 0.9, used.mean()
     assert times[B.POP_MODE_F32_SURROGATE] < 0.5 * times[B.POP_MODE_F32], times
     like.close()
 
