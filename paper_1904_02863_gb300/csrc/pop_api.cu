@@ -112,6 +112,7 @@ struct pop_ctx {
     DevBuf d_queue;          // the weight kernels' work-item counter
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
+    DevBuf d_ztab;           // redshift trapezoid nodes (ln(1 + z_i), w_i z_i^2)
     ExpConsts expc{};
     DevBuf d_fftab;          // 2^(j/2048) as FP32 (hi, lo) for the float-float exponentials
     FFConsts ffk{};
@@ -392,7 +393,8 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     WorkDesc wd{c->d_chunks.as<Chunk>(), n_items, c->n_ev_chunks, c->ev.n_dims == 7};
     CK(cudaEventRecordWithFlags(c->ev_t0, c->stream, rec), "event");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
-                       c->d_c32.as<LamF32>(), c->stream), "prologue");
+                       c->d_c32.as<LamF32>(), c->stream, c->d_ztab.as<double2>(),
+                       c->d_exptab.as<double2>(), c->expc), "prologue");
     SurrogateXi sx{nullptr, nullptr, nullptr};
     if (mode == POP_MODE_F32_SURROGATE) {
         // ln xi from the network for every Lambda, and which Lambda still need the Monte Carlo xi.
@@ -638,6 +640,11 @@ int pop_create(pop_ctx** out, int device, void* stream)
         e = c->d_exptab.alloc(sizeof(double2) * EXP_TABLE_SIZE);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d_exptab.p, tab.data(), sizeof(double2) * EXP_TABLE_SIZE, cudaMemcpyHostToDevice);
+        std::vector<double2> ztab(REDSHIFT_NODES);
+        build_z_table(ztab.data());
+        if (e == cudaSuccess) e = c->d_ztab.alloc(sizeof(double2) * REDSHIFT_NODES);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_ztab.p, ztab.data(), sizeof(double2) * REDSHIFT_NODES, cudaMemcpyHostToDevice);
         std::vector<float2> ftab(FF_TABLE_SIZE);
         build_ff_table(ftab.data(), &c->ffk);
         if (e == cudaSuccess) e = c->d_fftab.alloc(sizeof(float2) * FF_TABLE_SIZE);
@@ -920,7 +927,8 @@ int pop_loglik_grad(pop_ctx* c, int64_t K, int n_params, const double* lambda, d
     set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
     CK(cudaGetLastError(), "set K");
     CK(cudaEventRecord(c->ev_t0, c->stream), "event");
-    CK(launch_grad_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), K, n_params, c->d_lamg.p, c->stream),
+    CK(launch_grad_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), K, n_params, c->d_lamg.p, c->stream,
+                            c->d_ztab.as<double2>(), c->d_exptab.as<double2>(), c->expc),
        "grad prologue");
     WorkDesc wd{c->d_chunks.as<Chunk>(), c->n_chunks, c->n_ev_chunks, c->ev.n_dims == 7};
     FeatF64 e{c->ev.f64.as<double>(), c->ev.stride}, j{c->inj.f64.as<double>(), c->inj.stride};
@@ -1186,7 +1194,8 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
     set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
     CK(cudaGetLastError(), "set K");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
-                       c->d_c32.as<LamF32>(), c->stream), "prologue");
+                       c->d_c32.as<LamF32>(), c->stream, c->d_ztab.as<double2>(),
+                       c->d_exptab.as<double2>(), c->expc), "prologue");
     if (mode == POP_MODE_F32)
         CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), nullptr, c->k_cap, c->d_order.as<int32_t>(),
                             c->d_nmc.as<int32_t>(), c->stream), "lambda order");

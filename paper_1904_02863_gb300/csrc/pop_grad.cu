@@ -74,7 +74,8 @@ __device__ double std_phi(double t) { return exp(-0.5 * t * t) / G_SQRT2PI; }
 // One warp per Lambda: the redshift trapezoid and its kappa-derivative on the lanes,
 // the rest on lane 0.
 __global__ void grad_prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
-                                     LamG* __restrict__ out)
+                                     LamG* __restrict__ out, const double2* __restrict__ ztab,
+                                     const double2* __restrict__ exptab, ExpConsts kc)
 {
     const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -84,12 +85,12 @@ __global__ void grad_prologue_kernel(const double* __restrict__ lambda, const in
     double I = 0.0, dI = 0.0;
     if (has_z) {
         const double km1 = L[P_KAPPA] - 1.0;
+        // node i: (ln(1 + z_i), w_i z_i^2); one table-driven exponential per node
         for (int i = lane; i < G_Z_NODES; i += 32) {
-            const double z = 2.0 * i / (G_Z_NODES - 1);
-            const double f = z > 0.0 ? exp(km1 * log1p(z)) * z * z : 0.0;
-            const double wgt = (i == 0 || i == G_Z_NODES - 1) ? 0.5 : 1.0;
-            I += wgt * f;
-            dI += wgt * f * log1p(z);
+            const double2 t = ztab[i];
+            const double f = t.y * exp_tab(km1 * t.x, exptab, kc);
+            I += f;
+            dI = fma(f, t.x, dI);
         }
         for (int o = 16; o > 0; o >>= 1) {
             I += __shfl_xor_sync(0xffffffffu, I, o);
@@ -432,12 +433,13 @@ grad_finalise_kernel(const double* __restrict__ part, const double* __restrict__
 size_t lam_grad_bytes() { return sizeof(LamG); }
 
 cudaError_t launch_grad_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params, void* lam_g,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const double2* ztab, const double2* exptab, ExpConsts kc)
 {
     if (K_cap <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (int)((K_cap * 32 + threads - 1) / threads);
-    grad_prologue_kernel<<<blocks, threads, 0, s>>>(lambda, dK, n_params, static_cast<LamG*>(lam_g));
+    grad_prologue_kernel<<<blocks, threads, 0, s>>>(lambda, dK, n_params, static_cast<LamG*>(lam_g), ztab, exptab,
+                                                    kc);
     return cudaGetLastError();
 }
 

@@ -114,8 +114,14 @@ cudaError_t launch_pack_f64(const double* theta, const double* prior, const int6
 cudaError_t launch_pack_f32(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
                             float* feat, double* m2, double* m1d, int64_t stride, unsigned long long* bad,
                             cudaStream_t s);
+// ztab (REDSHIFT_NODES entries, build_z_table) and exptab make the redshift trapezoid one
+// table-driven exponential per node; with ztab NULL it is evaluated directly.
+constexpr int REDSHIFT_NODES = 1024;
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params,
-                            LamF64* c64, LamF32* c32, cudaStream_t s);
+                            LamF64* c64, LamF32* c32, cudaStream_t s, const double2* ztab = nullptr,
+                            const double2* exptab = nullptr, ExpConsts kc = ExpConsts{});
+// Host: node i of the redshift trapezoid on [0, 2]: (ln(1 + z_i), w_i z_i^2), w = 1/2 at the ends.
+void build_z_table(double2* tab);
 // The FP64 weight kernel keeps the 2^(j/2048) table of its exponentials in dynamic shared memory.
 constexpr int WEIGHT_F64_DYN_SMEM = EXP_TABLE_SIZE * (int)sizeof(double2);
 // The weight kernels take their work items from *queue, which each launcher zeroes (a memset
@@ -178,7 +184,7 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
 // injection sum w^2 in part2 as for ln L), and the finalise with grad[K][n_params].
 size_t lam_grad_bytes();
 cudaError_t launch_grad_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params, void* lam_g,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const double2* ztab, const double2* exptab, ExpConsts kc);
 cudaError_t launch_grad_weight(int grid, FeatF64 ev, FeatF64 inj, WorkDesc wd, const void* lam_g, const int64_t* dK,
                                int n_params, double* part, double* part2, const double2* exptab, ExpConsts kc,
                                unsigned long long* queue, cudaStream_t s);

@@ -115,9 +115,12 @@ __global__ void pack_f32_kernel(const double* __restrict__ theta, const double* 
 __device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
 
 // Per-Lambda constants.  One warp per Lambda: the lanes share the 1024-node
-// redshift trapezoid, lane 0 does the rest.
+// redshift trapezoid, lane 0 does the rest.  With ztab (node i: ln(1 + z_i) and its
+// trapezoid weight times z_i^2) each node costs one table-driven exponential; without it
+// (callers that hold no tables) the logarithm and exponential are evaluated directly.
 __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
-                                LamF64* __restrict__ c64, LamF32* __restrict__ c32)
+                                LamF64* __restrict__ c64, LamF32* __restrict__ c32, const double2* __restrict__ ztab,
+                                const double2* __restrict__ exptab, ExpConsts kc)
 {
     const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -129,10 +132,17 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     double zs = 0.0;
     if (has_z) {
         const double km1 = L[P_KAPPA] - 1.0;
-        for (int i = lane; i < Z_NODES; i += 32) {
-            double z = 2.0 * i / (Z_NODES - 1);
-            double f = exp(km1 * log1p(z)) * z * z;
-            zs += (i == 0 || i == Z_NODES - 1) ? 0.5 * f : f;
+        if (ztab) {
+            for (int i = lane; i < Z_NODES; i += 32) {
+                const double2 t = ztab[i];
+                zs = fma(t.y, exp_tab(km1 * t.x, exptab, kc), zs);
+            }
+        } else {
+            for (int i = lane; i < Z_NODES; i += 32) {
+                double z = 2.0 * i / (Z_NODES - 1);
+                double f = exp(km1 * log1p(z)) * z * z;
+                zs += (i == 0 || i == Z_NODES - 1) ? 0.5 * f : f;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
         zs *= 2.0 / (Z_NODES - 1);
@@ -367,13 +377,21 @@ cudaError_t launch_pack_f32(const double* theta, const double* prior, const int6
 }
 
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params, LamF64* c64,
-                            LamF32* c32, cudaStream_t s)
+                            LamF32* c32, cudaStream_t s, const double2* ztab, const double2* exptab, ExpConsts kc)
 {
     if (K_cap <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (int)((K_cap * 32 + threads - 1) / threads);
-    prologue_kernel<<<blocks, threads, 0, s>>>(lambda, dK, n_params, c64, c32);
+    prologue_kernel<<<blocks, threads, 0, s>>>(lambda, dK, n_params, c64, c32, ztab, exptab, kc);
     return cudaGetLastError();
+}
+
+void build_z_table(double2* tab)
+{
+    for (int i = 0; i < Z_NODES; ++i) {
+        const double z = 2.0 * i / (Z_NODES - 1);
+        tab[i] = make_double2(log1p(z), ((i == 0 || i == Z_NODES - 1) ? 0.5 : 1.0) * z * z);
+    }
 }
 
 cudaError_t launch_finalise(const double* part, const double* part2, const int32_t* ecb, const int64_t* off,

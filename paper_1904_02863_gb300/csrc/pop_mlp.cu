@@ -22,12 +22,14 @@
 
 #include "pop_internal.h"
 #include "pop_mlp.h"
+#include "pop_tc.cuh"
 
 namespace pop {
 
 namespace {
 
 using bf16 = __nv_bfloat16;
+using namespace tc;
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
@@ -40,13 +42,7 @@ constexpr int TC_SMEM_B = 256 * TC_BK * 2;      // 32 KB
 constexpr int TC_SMEM_LAUNCH = 112 * 1024;
 constexpr uint32_t CM_LBO = 128;   // bytes to the next core matrix along K
 constexpr uint32_t CM_SBO = 1024;  // bytes to the next 8-row group
-// mbarrier polls before a wait gives up: about 1 s at the ~3.8 us a poll of an incomplete phase
-// suspends on GB300; a tile's TMA loads and MMAs complete within microseconds.
-constexpr int WAIT_LIMIT = 1 << 18;
-
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_F32 = 2 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Columns per CTA of a GEMM with N columns (both the kernel and its launcher use this).
 __host__ __device__ __forceinline__ int gemm_bn(int N) { return N % 64 == 0 ? 64 : N; }
@@ -57,79 +53,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((CM_LBO >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((CM_SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 D, BF16 A and B (both K-major), M x N.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Waits for the phase with the given parity; false after WAIT_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
-{
-    for (int i = 0; i < WAIT_LIMIT; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// 32 lanes x 16 consecutive FP32 columns: thread = lane (row), v[j] = column c0 + j.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
@@ -355,61 +278,77 @@ __global__ void out_bwd_kernel(const float* __restrict__ dy, const float* __rest
     dz4[i] = __float2bfloat16(dh * dsiluf_(z4[i]));
 }
 
-// Column sums out[c] = sum_r X[r][c] in a fixed order (8 warps over rows, then warps in order).
+// Column reductions over the batch, in two passes with a fixed order: RED_SLICES row slices
+// each give a partial (8 warps over the slice's rows, then the warps in order), and a second
+// pass adds the slices in order.  512 blocks instead of 8 keep the SMs busy.
+constexpr int RED_SLICES = 64;
+constexpr int RED_COLS = 2 * MLP_HID + 2;  // widest partial row: dW4 (2 x 256) and db4 (2)
+
+// part[slice][c] = sum over the slice's rows of X[r][c].
 template <class T>
-__global__ void colsum_kernel(const T* __restrict__ x, int64_t rows, int cols, float* __restrict__ out)
+__global__ void colsum_part_kernel(const T* __restrict__ x, int64_t rows, int cols, float* __restrict__ part)
 {
-    __shared__ float part[8][32];
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int w = threadIdx.x >> 5;
+    __shared__ float sp[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const int64_t per = (rows + RED_SLICES - 1) / RED_SLICES;
+    const int64_t r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
     float s = 0.f;
     if (c < cols)
-        for (int64_t r = w; r < rows; r += 8) s += (float)x[r * cols + c];
-    part[w][threadIdx.x & 31] = s;
+        for (int64_t r = r0 + w; r < r1; r += 8) s += (float)x[r * cols + c];
+    sp[w][lane] = s;
     __syncthreads();
     if (w == 0 && c < cols) {
         float t = 0.f;
-        for (int i = 0; i < 8; ++i) t += part[i][threadIdx.x & 31];
-        out[c] = t;
+        for (int i = 0; i < 8; ++i) t += sp[i][lane];
+        part[(int64_t)blockIdx.y * RED_COLS + c] = t;
     }
 }
 
-// dW4[o][c] = sum_r dY[r][o] H4[r][c], db4[o] = sum_r dY[r][o] (fixed order).
-__global__ void out_wgrad_kernel(const float* __restrict__ dy, const bf16* __restrict__ h4, int64_t rows,
-                                 float* __restrict__ dw4, float* __restrict__ db4)
+// part[slice][o * 256 + c] = sum over the slice of dY[r][o] H4[r][c]; part[slice][512 + o] = sum dY[r][o].
+__global__ void out_wgrad_part_kernel(const float* __restrict__ dy, const bf16* __restrict__ h4, int64_t rows,
+                                      float* __restrict__ part)
 {
-    __shared__ float part[2][8][32];
-    __shared__ float bpart[2][8][32];
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int w = threadIdx.x >> 5;
+    __shared__ float sp[4][8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const int64_t per = (rows + RED_SLICES - 1) / RED_SLICES;
+    const int64_t r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
     float s0 = 0.f, s1 = 0.f, b0 = 0.f, b1 = 0.f;
-    for (int64_t r = w; r < rows; r += 8) {
+    for (int64_t r = r0 + w; r < r1; r += 8) {
         const float h = __bfloat162float(h4[r * MLP_HID + c]);
         s0 = fmaf(dy[r * 2], h, s0);
         s1 = fmaf(dy[r * 2 + 1], h, s1);
         b0 += dy[r * 2];
         b1 += dy[r * 2 + 1];
     }
-    part[0][w][threadIdx.x & 31] = s0;
-    part[1][w][threadIdx.x & 31] = s1;
-    bpart[0][w][threadIdx.x & 31] = b0;
-    bpart[1][w][threadIdx.x & 31] = b1;
+    sp[0][w][lane] = s0;
+    sp[1][w][lane] = s1;
+    sp[2][w][lane] = b0;
+    sp[3][w][lane] = b1;
     __syncthreads();
     if (w == 0) {
-        float t0 = 0.f, t1 = 0.f, u0 = 0.f, u1 = 0.f;
-        for (int i = 0; i < 8; ++i) {
-            t0 += part[0][i][threadIdx.x & 31];
-            t1 += part[1][i][threadIdx.x & 31];
-            u0 += bpart[0][i][threadIdx.x & 31];
-            u1 += bpart[1][i][threadIdx.x & 31];
-        }
-        dw4[c] = t0;
-        dw4[MLP_HID + c] = t1;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            db4[0] = u0;
-            db4[1] = u1;
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = 0; i < 8; ++i)
+            for (int q = 0; q < 4; ++q) t[q] += sp[q][i][lane];
+        float* pr = part + (int64_t)blockIdx.y * RED_COLS;
+        pr[c] = t[0];
+        pr[MLP_HID + c] = t[1];
+        if (blockIdx.x == 0 && lane == 0) {
+            pr[2 * MLP_HID] = t[2];
+            pr[2 * MLP_HID + 1] = t[3];
         }
     }
+}
+
+// out[c] = sum over the slices, in order, of part[slice][c], for c < cols.
+__global__ void slices_sum_kernel(const float* __restrict__ part, int cols, float* __restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float t = 0.f;
+    for (int s = 0; s < RED_SLICES; ++s) t += part[(int64_t)s * RED_COLS + c];
+    out[c] = t;
 }
 
 // out[C x R] = in[R x C]^T (BF16), 32 x 32 tiles.
@@ -455,17 +394,6 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float*
     p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
-// Layer offsets in the flat parameter vector.
-__host__ __device__ constexpr int64_t off_w(int l)
-{
-    return l == 0 ? 0
-                  : (int64_t)MLP_HID * MLP_IN + MLP_HID + (int64_t)(l - 1) * ((int64_t)MLP_HID * MLP_HID + MLP_HID);
-}
-__host__ __device__ constexpr int64_t off_b(int l)
-{
-    return off_w(l) + (l == 0 ? (int64_t)MLP_HID * MLP_IN : (l == 4 ? (int64_t)MLP_OUT * MLP_HID : (int64_t)MLP_HID * MLP_HID));
-}
-
 // BF16 GEMM copies of the FP32 master weights: w0p [256 x 64] (zero-padded), w[l] [256 x 256],
 // wt[l] = w[l]^T, w4f = BF16-rounded W4 as FP32.
 __global__ void refresh_kernel(const float* __restrict__ p, bf16* __restrict__ w0p, bf16* __restrict__ w1,
@@ -506,28 +434,6 @@ __global__ void gather_rows_kernel(const bf16* __restrict__ xall, const float* _
 
 unsigned grid1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-struct GateArgs {
-    double mu0, sd0, mu1, sd1, n_events, budget;
-    int trusted;
-    ErrTable table;
-};
-
-// Per Lambda: ln xi and ln N_eff from the network, and whether the Monte Carlo xi is needed
-// (need_monte_carlo: the trust gate, the box, a timed-out wait, N_eff < 4 N, the error budget).
-__global__ void gate_kernel(const float* __restrict__ y, const uint8_t* __restrict__ outside,
-                            const int64_t* __restrict__ dK, const int* __restrict__ err, GateArgs a,
-                            uint8_t* __restrict__ need, double* __restrict__ lnxi, double* __restrict__ lnneff)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= *dK) return;
-    const double lx = (double)y[k * 2] * a.sd0 + a.mu0;
-    const double ln = (double)y[k * 2 + 1] * a.sd1 + a.mu1;
-    lnxi[k] = lx;
-    lnneff[k] = ln;
-    need[k] = (uint8_t)need_monte_carlo(a.trusted != 0, outside[k] != 0, *err != 0, lx, ln, a.n_events, a.budget,
-                                        a.table);
-}
-
 }  // namespace
 
 int Surrogate::enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double n_events,
@@ -538,19 +444,9 @@ int Surrogate::enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const 
         err = "surrogate buffers not sized for the batch";
         return POP_ESTATE;
     }
-    int rc = normalise(d_lambda, k_cap, P, outside.as<uint8_t>());
-    if (rc != POP_OK) return rc;
-    rc = forward(rp);
-    if (rc != POP_OK) return rc;
-    GateArgs a{mu[0], sd[0], mu[1], sd[1], n_events, budget, trusted ? 1 : 0, table};
-    gate_kernel<<<grid1(k_cap, 256), 256, 0, stream>>>(y.as<float>(), outside.as<uint8_t>(), dK, err_flag.as<int>(), a,
-                                                       need, lnxi, lnneff);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        err = cudaGetErrorString(e);
-        return POP_ECUDA;
-    }
-    return POP_OK;
+    // normalise -> network -> gate in one launch (pop_mlp_fused.cu)
+    return fused_forward(d_lambda, P, nullptr, k_cap, dK, nullptr, outside.as<uint8_t>(), n_events, need, lnxi,
+                         lnneff);
 }
 
 int Surrogate::ensure_gate(int64_t k_cap)
@@ -595,7 +491,8 @@ int Surrogate::init(int dev, cudaStream_t s)
     SK(err_flag.alloc(sizeof(int)));
     SK(cudaMemsetAsync(err_flag.p, 0, sizeof(int), stream));
     SK(dw0.alloc(sizeof(float) * MLP_HID * MLP_IN_PAD));
-    return POP_OK;
+    SK(red.alloc(sizeof(float) * RED_SLICES * RED_COLS));
+    return prepare_fused();
 }
 
 int Surrogate::ensure_rows(int64_t rows)
@@ -699,7 +596,10 @@ int Surrogate::backward(int64_t rows, int64_t rows_pad, const float* t)
     float* dyp = dy.as<float>();
     float* row_loss = dyp + rows_pad * 2;
     loss_grad_kernel<<<grid1(rows_pad, 256), 256, 0, stream>>>(y.as<float>(), t, rows, rows_pad, dyp, row_loss);
-    out_wgrad_kernel<<<MLP_HID / 32, 256, 0, stream>>>(dyp, h[3].as<bf16>(), rows_pad, gr + off_w(4), gr + off_b(4));
+    out_wgrad_part_kernel<<<dim3(MLP_HID / 32, RED_SLICES), 256, 0, stream>>>(dyp, h[3].as<bf16>(), rows_pad,
+                                                                             red.as<float>());
+    // off_w(4) .. off_b(4) + 2 is one contiguous run: dW4 (2 x 256) then db4 (2)
+    slices_sum_kernel<<<grid1(RED_COLS, 256), 256, 0, stream>>>(red.as<float>(), RED_COLS, gr + off_w(4));
     out_bwd_kernel<<<grid1(rows_pad * MLP_HID, 256), 256, 0, stream>>>(dyp, w4f.as<float>(), z[3].as<float>(),
                                                                         dz[0].as<bf16>(), rows_pad);
     SK(cudaGetLastError());
@@ -739,7 +639,9 @@ int Surrogate::backward(int64_t rows, int64_t rows_pad, const float* t)
         if (l == 0)  // keep the 12 real input columns of the padded input layer
             splitk_reduce_kernel<<<grid1((int64_t)MLP_HID * MLP_IN, 256), 256, 0, stream>>>(
                 dw0.as<float>(), 1, 0, MLP_HID, MLP_IN_PAD, MLP_IN, gr + off_w(0));
-        colsum_kernel<bf16><<<MLP_HID / 32, 256, 0, stream>>>(dzc, rows_pad, MLP_HID, gr + off_b(l));
+        colsum_part_kernel<bf16><<<dim3(MLP_HID / 32, RED_SLICES), 256, 0, stream>>>(dzc, rows_pad, MLP_HID,
+                                                                                   red.as<float>());
+        slices_sum_kernel<<<grid1(MLP_HID, 256), 256, 0, stream>>>(red.as<float>(), MLP_HID, gr + off_b(l));
         SK(cudaGetLastError());
         if (l > 0) {  // dZ_l = (dZ_{l+1} W_l) * SiLU'(Z_l)
             GemmArgs b{};

@@ -8,6 +8,7 @@
 // and Adam.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,6 +28,18 @@ constexpr int MLP_LAYERS = 5;
 // Flat FP32 parameter vector: W0 [256x12], b0, W1 [256x256], b1, W2, b2, W3, b3, W4 [2x256], b4.
 constexpr int64_t MLP_N_PARAMS = (int64_t)MLP_HID * MLP_IN + MLP_HID + 3 * ((int64_t)MLP_HID * MLP_HID + MLP_HID) +
                                  (int64_t)MLP_OUT * MLP_HID + MLP_OUT;
+
+// Layer offsets in the flat parameter vector.
+__host__ __device__ constexpr int64_t off_w(int l)
+{
+    return l == 0 ? 0
+                  : (int64_t)MLP_HID * MLP_IN + MLP_HID + (int64_t)(l - 1) * ((int64_t)MLP_HID * MLP_HID + MLP_HID);
+}
+__host__ __device__ constexpr int64_t off_b(int l)
+{
+    return off_w(l) +
+           (l == 0 ? (int64_t)MLP_HID * MLP_IN : (l == 4 ? (int64_t)MLP_OUT * MLP_HID : (int64_t)MLP_HID * MLP_HID));
+}
 
 // Per-Lambda error model of the network's ln xi, from the held-out pairs: the pairs are split
 // into ERR_BINS bins of equal count by the network's own ln N_eff prediction (the Monte Carlo
@@ -84,7 +97,9 @@ struct Surrogate {
     DevBuf w0p, w[3], wt[3], w4f;          // BF16 GEMM copies (w0p [256x64]); w4f FP32 of the BF16-rounded W4
     DevBuf err_flag;                       // int: a bounded tcgen05 wait gave up
     int64_t cap = 0;                       // rows of the activation buffers
-    DevBuf x0, z[4], h[4], y, dy, dz[2], dzt, ht, parts, dw0;
+    DevBuf x0, z[4], h[4], y, dy, dz[2], dzt, ht, parts, dw0, red;
+    CUtensorMap wmap[4];                   // TMA maps of w0p, w[0..2]: 256 x 64 BF16 tiles, 128-byte swizzle
+    bool wmaps_ok = false;
 
     int init(int dev, cudaStream_t s);
     int ensure_rows(int64_t rows);
@@ -110,6 +125,14 @@ struct Surrogate {
     int ensure_gate(int64_t k_cap);
     int enqueue_gate(const double* d_lambda, int64_t k_cap, int P, const int64_t* dK, double n_events, uint8_t* need,
                      double* lnxi, double* lnneff);
+
+    // The inference forward in one launch (pop_mlp_fused.cu): rows [0, K) (K = *dK when dK is not
+    // NULL, else K_cap) from Lambda rows (normalised in the kernel, outside[] set) or, when x0 is not
+    // NULL, from normalised BF16 inputs [rows x 64]; y[rows x 2] when y is not NULL; with need
+    // not NULL, also the gate's need / lnxi / lnneff.  No host synchronisation.
+    int fused_forward(const double* d_lambda, int P, const __nv_bfloat16* x0, int64_t K_cap, const int64_t* dK,
+                      float* y, uint8_t* outside, double n_events, uint8_t* need, double* lnxi, double* lnneff);
+    int prepare_fused();  // tensor maps of the weight copies and the kernel's shared-memory size (init)
 };
 
 // Diagnostic: C[M x N] = A[M x K] B[N x K]^T on the tensor cores (FP32 out).

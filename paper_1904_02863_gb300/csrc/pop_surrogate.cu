@@ -83,8 +83,8 @@ int infer_device(pop_ctx* c, Surrogate* s, int64_t K, int P, const double* d_lam
     SUR(s->ensure_rows(rp));
     DevBuf outside;
     CKC(outside.alloc(std::max<int64_t>(K, 1)), "cudaMalloc");
-    SUR(s->normalise(d_lambda, K, P, outside.as<uint8_t>()));
-    SUR(s->forward(rp));
+    SUR(s->fused_forward(d_lambda, P, nullptr, K, nullptr, s->y.as<float>(), outside.as<uint8_t>(), 0.0, nullptr,
+                         nullptr, nullptr));
     SUR(s->check_error());
     std::vector<float> y((size_t)rp * 2);
     std::vector<uint8_t> out(K);
@@ -190,7 +190,8 @@ int pop_mlp_forward(pop_ctx* c, int64_t B, const float* x, float* y)
     CKC(cudaSetDevice(ctx_device(c)), "cudaSetDevice");
     int rc = upload_inputs(c, s, B, x);
     if (rc != POP_OK) return rc;
-    SUR(s->forward(pad128(B)));
+    SUR(s->fused_forward(nullptr, 0, s->x0.as<__nv_bfloat16>(), B, nullptr, s->y.as<float>(), nullptr, 0.0, nullptr,
+                         nullptr, nullptr));
     SUR(s->check_error());
     CKC(cudaMemcpyAsync(y, s->y.p, (size_t)B * 2 * 4, cudaMemcpyDeviceToHost, s->stream), "copy y");
     CKC(cudaStreamSynchronize(s->stream), "sync");
