@@ -1,24 +1,29 @@
-// Surrogate network kernels: tcgen05 BF16 GEMM with TMEM accumulators and
-// fused epilogues, plus the small CUDA-core kernels of the input/output layers,
-// the reductions, transposes and Adam.
+// Surrogate network kernels: the tcgen05 BF16 GEMM of training with TMEM
+// accumulators and fused epilogues, plus the small CUDA-core kernels of the
+// input/output layers, the reductions, transposes and Adam.  (The inference
+// forward is one fused kernel, pop_mlp_fused.cu.)
 //
 // GEMM: C[M x N] = A[M x K] . B[N x K]^T with A and B K-major BF16 in global
 // memory, M a multiple of 128 (one CTA per 128 rows = 128 TMEM lanes), N a
 // multiple of 16 up to 256 (FP32 accumulator columns), K a multiple of 64.  A CTA
 // takes 64 of the N columns when N is a multiple of 64 (all of them otherwise), so
-// the network's small batches still spread over many SMs.
-// Each 64-wide K stage is copied into shared memory in the no-swizzle
-// core-matrix layout (8 rows x 16 bytes per 128-byte core matrix; 128 bytes to
-// the next core matrix along K, 1024 bytes to the next 8-row group), one thread
-// issues four tcgen05.mma (K = 16 each) and commits them to an mbarrier that
-// all threads wait on (with an iteration limit: on time-out the CTA sets the
-// error flag, waits once more and frees its TMEM).  The epilogue reads the
-// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = its 32 rows).
+// the network's small batches still spread over many SMs.  Its 64-wide K tiles
+// of A (128 rows) and B come by 2-D TMA loads (128-byte swizzle) into a ring of up
+// to four stages, all issued ahead, so that the copies of later tiles run under
+// the MMAs of earlier ones; one thread issues the four K = 16 tcgen05.mma of a
+// tile and commits them to the stage's mbarrier, and refills the stage of the
+// tile before once its MMAs are done.  Every wait has a time limit: on time-out
+// the CTA sets the error flag, waits once more for what it issued and frees its
+// TMEM.  The epilogue reads the accumulator with tcgen05.ld (warp w owns lanes
+// 32w..32w+31 = its 32 rows).
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <random>
+#include <tuple>
+#include <map>
 
 #include "pop_internal.h"
 #include "pop_mlp.h"
@@ -34,26 +39,26 @@ using namespace tc;
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
 constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_TMEM_COLS = 256;
-constexpr int TC_SMEM_A = TC_BM * TC_BK * 2;    // 16 KB
-constexpr int TC_SMEM_B = 256 * TC_BK * 2;      // 32 KB
-// Requested dynamic shared memory: at most two CTAs per SM, so their
-// 2 x 256 TMEM columns always fit in the SM's 512.
-constexpr int TC_SMEM_LAUNCH = 112 * 1024;
-constexpr uint32_t CM_LBO = 128;   // bytes to the next core matrix along K
-constexpr uint32_t CM_SBO = 1024;  // bytes to the next 8-row group
+constexpr int TC_STAGES = 4;                      // ring depth (K tiles in flight)
+constexpr uint32_t TC_A_TILE = TC_BM * TC_BK * 2;  // 16 KB
+// Dynamic shared memory: 1 KB to align the base, 1 KB of barriers, then the ring.
+constexpr int TC_SMEM_MAX = 2048 + TC_STAGES * (TC_A_TILE + 256 * TC_BK * 2);
+
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_F32 = 2 };
 
 // Columns per CTA of a GEMM with N columns (both the kernel and its launcher use this).
 __host__ __device__ __forceinline__ int gemm_bn(int N) { return N % 64 == 0 ? 64 : N; }
 
-// tcgen05 shared-memory matrix descriptor: start address, leading (K) and stride
-// (8-row group) byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+// TMEM columns of a CTA with bn accumulator columns (a power of two, at least 32).
+__host__ __device__ __forceinline__ uint32_t gemm_tmem_cols(int bn)
 {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((CM_LBO >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((CM_SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+    uint32_t c = 32;
+    while ((int)c < bn) c <<= 1;
+    return c;
 }
+
+// Bytes of one ring stage: an A tile and a B tile of bn rows (a multiple of 1024).
+__host__ __device__ __forceinline__ uint32_t gemm_stage_bytes(int bn) { return TC_A_TILE + (uint32_t)bn * TC_BK * 2; }
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float siluf_(float z) { return z * sigmoidf_(z); }
@@ -81,55 +86,87 @@ struct GemmArgs {
     int* err;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
+__global__ void __launch_bounds__(TC_THREADS)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+               const __grid_constant__ GemmArgs g)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + TC_SMEM_A;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + TC_SMEM_A + TC_SMEM_B);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + TC_SMEM_A + TC_SMEM_B + 8);
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gb = smem_raw + (base - raw);
+    const uint32_t bar_full = base;                 // TC_STAGES barriers: tile landed
+    const uint32_t bar_done = base + 8 * TC_STAGES; // TC_STAGES barriers: its MMAs finished
+    const uint32_t bar_fin = base + 16 * TC_STAGES; // every MMA issued so far finished
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gb + 16 * TC_STAGES + 8);
+    const uint32_t ring = base + 1024;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_BM;
     const int bn = gemm_bn(g.N);
     const int n0 = blockIdx.z * bn;
     const int kbeg = blockIdx.y * g.k_split;
     const int kend = min(g.K, kbeg + g.k_split);
+    const int nk = (kend - kbeg) / TC_BK;
+    const int S = min(TC_STAGES, nk);
+    const uint32_t sbytes = gemm_stage_bytes(bn);
+    const uint32_t ncols = gemm_tmem_cols(bn);
 
-    if (warp == 0) tmem_alloc(smem_u32(tslot), TC_TMEM_COLS);
-    if (tid == 0) mbar_init(smem_u32(mbar), 1);
+    if (warp == 0) tmem_alloc(smem_u32(tslot), ncols);
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_done + 8 * s, 1);
+        }
+        mbar_init(bar_fin, 1);
+        for (int t = 0; t < S; ++t) {  // one arrival per stage, expecting both tiles' bytes
+            const uint32_t st = ring + t * sbytes;
+            mbar_expect_tx(bar_full + 8 * t, sbytes);
+            tma_copy_2d(st, &map_a, kbeg + t * TC_BK, m0, bar_full + 8 * t);
+            tma_copy_2d(st + TC_A_TILE, &map_b, kbeg + t * TC_BK, n0, bar_full + 8 * t);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = idesc_bf16(TC_BM, bn);
-    uint32_t parity = 0;
-    int failed = 0;
-    for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
-        for (int i = tid; i < TC_BM * 8; i += TC_THREADS) {
-            const int r = i >> 3, kg = i & 7;
-            const uint4 v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + kg * 8);
-            *reinterpret_cast<uint4*>(sA + (r >> 3) * CM_SBO + kg * CM_LBO + (r & 7) * 16) = v;
-        }
-        for (int i = tid; i < bn * 8; i += TC_THREADS) {
-            const int r = i >> 3, kg = i & 7;
-            const uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)(n0 + r) * g.ldb + k0 + kg * 8);
-            *reinterpret_cast<uint4*>(sB + (r >> 3) * CM_SBO + kg * CM_LBO + (r & 7) * 16) = v;
-        }
-        fence_proxy_async();  // make the generic-proxy stores visible to the tensor cores
-        __syncthreads();
-        if (tid == 0) {
+    int bad = 0, t = 0, issued = S;
+    uint32_t full_ph = 0, done_ph = 0;
+    if (tid == 0) {
+        for (; t < nk; ++t) {
+            const int s = t % S;
+            if (!mbar_wait(bar_full + 8 * s, (full_ph >> s) & 1u)) {
+                bad = 1;
+                break;
+            }
+            full_ph ^= 1u << s;
             tc_fence_after();
+            const uint32_t st = ring + s * sbytes;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk)
-                mma_bf16(tmem, sdesc(smem_u32(sA) + kk * 2 * CM_LBO), sdesc(smem_u32(sB) + kk * 2 * CM_LBO), idesc,
-                         (k0 > kbeg || kk > 0) ? 1u : 0u);
-            mma_commit(smem_u32(mbar));
+                mma_bf16(tmem, sdesc_sw128(st + kk * 32), sdesc_sw128(st + TC_A_TILE + kk * 32), idesc,
+                         (t > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(bar_done + 8 * s);
+            // The stage of the tile before takes the tile S after it once its MMAs are done.
+            if (t >= 1 && t - 1 + S < nk) {
+                const int sp = (t - 1) % S;
+                if (!mbar_wait(bar_done + 8 * sp, (done_ph >> sp) & 1u)) {
+                    ++t;
+                    bad = 1;
+                    break;
+                }
+                done_ph ^= 1u << sp;
+                const uint32_t sq = ring + sp * sbytes;
+                const int k0 = kbeg + (t - 1 + S) * TC_BK;
+                mbar_expect_tx(bar_full + 8 * sp, sbytes);
+                tma_copy_2d(sq, &map_a, k0, m0, bar_full + 8 * sp);
+                tma_copy_2d(sq + TC_A_TILE, &map_b, k0, n0, bar_full + 8 * sp);
+                ++issued;
+            }
         }
-        const bool ok = mbar_wait(smem_u32(mbar), parity);
-        failed = __syncthreads_or(!ok);
-        if (failed) break;
-        parity ^= 1u;
+        mma_commit(bar_fin);
     }
+    int failed = __syncthreads_or(bad);
+    if (!failed) failed = __syncthreads_or(!mbar_wait(bar_fin, 0));
     tc_fence_after();
     if (!failed) {
         const int row = m0 + warp * 32 + lane;
@@ -174,18 +211,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(GemmArgs g)
                 for (int q = 0; q < 4; ++q) cd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         }
-    } else {
-        if (tid == 0) atomicExch(g.err, 1);
-        mbar_wait(smem_u32(mbar), parity);  // let the MMAs in flight finish before TMEM is freed
+    } else if (tid == 0) {
+        atomicExch(g.err, 1);
+        // Let the MMAs and copies in flight finish before the TMEM and the shared memory go.
+        mma_commit(bar_fin);
+        mbar_wait(bar_fin, 0);
+        for (int u = t; u < issued; ++u) {
+            const int s = u % S;
+            mbar_wait(bar_full + 8 * s, (full_ph >> s) & 1u);
+            full_ph ^= 1u << s;
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+    if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
 cudaError_t set_gemm_attributes()
 {
-    return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_LAUNCH);
+    return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_MAX);
+}
+
+// The TMA maps of the GEMM operands, made once per (buffer, rows, width, box rows): a map is a
+// function of those alone, so a cached one stays valid when a buffer is freed and another takes
+// its address.
+const CUtensorMap* operand_map(const void* ptr, int rows, int cols, int box_rows)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, int>, CUtensorMap> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(ptr, rows, cols, box_rows);
+    auto it = cache.find(key);
+    if (it != cache.end()) return &it->second;
+    if (cache.size() > 512) cache.clear();
+    CUtensorMap m;
+    if (!make_tile_map(&m, ptr, rows, cols, box_rows)) return nullptr;
+    return &cache.emplace(key, m).first->second;
 }
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t s)
@@ -193,9 +254,16 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t s)
     if (g.M % TC_BM || g.N % 16 || g.N > 256 || g.N < 16 || g.K % TC_BK || g.k_split % TC_BK || g.k_split <= 0 ||
         (int64_t)g.k_split * k_splits < g.K || (int64_t)g.k_split * (k_splits - 1) >= g.K)
         return cudaErrorInvalidValue;
-    if (g.ldb % 8 || (g.epi == EPI_F32 ? g.ldc : g.ldz) % 16 || (g.epi != EPI_F32 && g.ldh % 16))
-        return cudaErrorInvalidValue;  // the 16-byte loads and stores need these strides
-    gemm_tc_kernel<<<dim3(g.M / TC_BM, k_splits, g.N / gemm_bn(g.N)), TC_THREADS, TC_SMEM_LAUNCH, s>>>(g);
+    if (g.lda % 8 || g.ldb % 8 || (g.epi == EPI_F32 ? g.ldc : g.ldz) % 16 || (g.epi != EPI_F32 && g.ldh % 16))
+        return cudaErrorInvalidValue;  // TMA row strides and the epilogue's 16-byte stores need these
+    const int bn = gemm_bn(g.N);
+    // A: M rows x lda (the K tiles' x coordinates stay below K <= lda); B: N rows x ldb.
+    const CUtensorMap* ma = operand_map(g.A, g.M, g.lda, TC_BM);
+    const CUtensorMap* mb = operand_map(g.B, g.N, g.ldb, bn);
+    if (!ma || !mb) return cudaErrorInvalidValue;
+    const int nk = std::min(g.k_split, g.K) / TC_BK;
+    const int smem = 2048 + std::min(TC_STAGES, std::max(nk, 1)) * (int)gemm_stage_bytes(bn);
+    gemm_tc_kernel<<<dim3(g.M / TC_BM, k_splits, g.N / bn), TC_THREADS, smem, s>>>(*ma, *mb, g);
     return cudaGetLastError();
 }
 

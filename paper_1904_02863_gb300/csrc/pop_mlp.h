@@ -135,6 +135,10 @@ struct Surrogate {
     int prepare_fused();  // tensor maps of the weight copies and the kernel's shared-memory size (init)
 };
 
+// TMA map of a row-major [rows x cols] BF16 matrix read in box_rows x 64-column tiles with the
+// 128-byte swizzle (false when the driver refuses it).  cols x 2 bytes must be a multiple of 16.
+bool make_tile_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows);
+
 // Diagnostic: C[M x N] = A[M x K] B[N x K]^T on the tensor cores (FP32 out).
 cudaError_t mlp_gemm_check(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N, int K,
                            int* err, cudaStream_t s);

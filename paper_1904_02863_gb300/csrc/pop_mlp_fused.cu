@@ -305,22 +305,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// Map of a row-major [rows x cols] BF16 matrix read in 256-row x 64-column tiles with the
-// 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols)
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols) { return make_tile_map(m, ptr, rows, cols, MLP_HID); }
+
+}  // namespace
+
+bool make_tile_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (!enc) return false;
+    if (!enc || box_rows < 1 || box_rows > 256) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)MLP_HID};
+    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 int Surrogate::prepare_fused()
 {

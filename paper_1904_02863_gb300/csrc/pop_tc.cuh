@@ -58,9 +58,9 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Waits for the phase with the given parity; false after WAIT_CYCLES.  The polls are
-// mbarrier.test_wait, which never suspends the thread: a suspending try_wait returned
-// microseconds after the phase completed, which cost the network's kernels most of their time.
+// Waits for the phase with the given parity; false after WAIT_CYCLES of the SM clock.  The
+// polls are mbarrier.test_wait, which does not suspend the thread, so the limit is a time
+// whatever a poll costs.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 {
     const long long t0 = clock64();
@@ -91,17 +91,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// 2-D tiled TMA load of the box at (x, y) of `map` into shared memory at dst, completing
-// `bytes` on the mbarrier (arrive + expect_tx by the same thread).  x times the element size
-// must be a multiple of 16 bytes.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
-                                            uint32_t bytes)
+// The thread's arrival on the mbarrier, announcing `bytes` of copies that will complete on it.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load of the box at (x, y) of `map` into shared memory at dst; its bytes
+// complete on the mbarrier, whose expected count the caller has raised (mbar_expect_tx).
+// x times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_copy_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar)
+{
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
         : "memory");
+}
+
+// One tile: arrive + expect its `bytes`, then the copy.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
+                                            uint32_t bytes)
+{
+    mbar_expect_tx(mbar, bytes);
+    tma_copy_2d(dst, map, x, y, mbar);
 }
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle layout that a
