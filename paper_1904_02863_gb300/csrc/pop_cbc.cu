@@ -29,20 +29,26 @@ namespace pop {
 namespace {
 
 constexpr int CBC_THREADS = 256;
-constexpr int RUN = 8;                 // bins per exact-phase anchor
 constexpr int PREP_THREADS = 256;
 constexpr int PREP_BLOCKS_MAX = 152 * 8;
 constexpr double TWO_PI = 6.283185307179586476925;
 
 template <class T>
 struct CbcCfg;
+// TK rows per work item; RUN bins per exact-phase anchor (the recurrence e <- e w between
+// anchors adds about 3 roundings per product: RUN - 1 products).
+// SUB bins' loads a thread issues together (their registers: SUB x 4 values).
 template <>
 struct CbcCfg<double> {
-    static constexpr int TK = 4;  // rows per work item
+    static constexpr int TK = 4;
+    static constexpr int RUN = 32;
+    static constexpr int SUB = 4;
 };
 template <>
 struct CbcCfg<float> {
     static constexpr int TK = 8;
+    static constexpr int RUN = 16;
+    static constexpr int SUB = 8;
 };
 
 // Per (row, detector) constants.
@@ -134,17 +140,17 @@ struct Vec4T<double> {
     using type = PQ64;
 };
 
-template <class T>
-__device__ __forceinline__ void load_pq(const typename Vec4T<T>::type* p, T (&v)[4])
+__device__ __forceinline__ void load_pq(const PQ64* p, double (&v)[4])
 {
-    if constexpr (sizeof(T) == 4) {
-        const float4 x = __ldg(p);
-        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    } else {
-        const double2* q = reinterpret_cast<const double2*>(p);
-        const double2 x = __ldg(q), y = __ldg(q + 1);
-        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-    }
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 x = __ldg(q), y = __ldg(q + 1);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
+__device__ __forceinline__ void load_pq(const float4* p, float (&v)[4])
+{
+    const float4 x = __ldg(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
 }
 
 // Partial sums SP, SQ (as Re, Im, Re, Im) of one work item for TK rows.
@@ -188,6 +194,8 @@ cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __r
     const int64_t j_begin = (int64_t)chunk * CB;
     const int64_t j_end = min(M, j_begin + CB);
     const typename Vec4T<T>::type* base = pq + (int64_t)det * M;
+    constexpr int RUN_T = CbcCfg<T>::RUN;
+    constexpr int SUB = CbcCfg<T>::SUB;
     // (P e, Q e) accumulated for every row; then e <- e w.
     auto step = [&](const T (&v)[4], T (&er)[TK], T (&ei)[TK]) {
 #pragma unroll
@@ -202,6 +210,8 @@ cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __r
             ei[t] = ni;
         }
     };
+    // A thread takes runs of RUN_T consecutive bins: one exact anchor per run, then the
+    // recurrence, the bins in batches of SUB whose loads go out together.
     if constexpr (sizeof(T) == 4) {
         // FP32: rows (2p, 2p+1) in the halves of packed f32x2 registers, the bin's P and Q
         // broadcast to both halves; the same fmas as the scalar path, one instruction per pair.
@@ -229,13 +239,11 @@ cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __r
                 e2i[q] = ni;
             }
         };
-        for (int64_t j0 = j_begin + (int64_t)threadIdx.x * RUN; j0 < j_end; j0 += (int64_t)CBC_THREADS * RUN) {
-            float er[TK], ei[TK];
+        for (int64_t j0 = j_begin + (int64_t)threadIdx.x * RUN_T; j0 < j_end; j0 += (int64_t)CBC_THREADS * RUN_T) {
+            const int64_t jr = min(j_end, j0 + RUN_T);
             f2 e2r[TP], e2i[TP];
-            if (j_end - j0 >= RUN) {
-                float v[RUN][4];
-#pragma unroll
-                for (int r = 0; r < RUN; ++r) load_pq<float>(base + j0 + r, v[r]);
+            {
+                float er[TK], ei[TK];
 #pragma unroll
                 for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
 #pragma unroll
@@ -243,20 +251,20 @@ cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __r
                     e2r[q] = pk(er[2 * q], er[2 * q + 1]);
                     e2i[q] = pk(ei[2 * q], ei[2 * q + 1]);
                 }
+            }
+            for (int64_t js = j0; js < jr; js += SUB) {
+                if (jr - js >= SUB) {
+                    float v[SUB][4];
 #pragma unroll
-                for (int r = 0; r < RUN; ++r) step2(v[r], e2r, e2i);
-            } else {
+                    for (int r = 0; r < SUB; ++r) load_pq(base + js + r, v[r]);
 #pragma unroll
-                for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
-#pragma unroll
-                for (int q = 0; q < TP; ++q) {
-                    e2r[q] = pk(er[2 * q], er[2 * q + 1]);
-                    e2i[q] = pk(ei[2 * q], ei[2 * q + 1]);
-                }
-                for (int r = 0; r < (int)(j_end - j0); ++r) {
-                    float v[4];
-                    load_pq<float>(base + j0 + r, v);
-                    step2(v, e2r, e2i);
+                    for (int r = 0; r < SUB; ++r) step2(v[r], e2r, e2i);
+                } else {
+                    for (int r = 0; r < (int)(jr - js); ++r) {
+                        float v[4];
+                        load_pq(base + js + r, v);
+                        step2(v, e2r, e2i);
+                    }
                 }
             }
         }
@@ -265,24 +273,24 @@ cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __r
 #pragma unroll
             for (int c = 0; c < 4; ++c) upk(a2[q][c], acc[2 * q][c], acc[2 * q + 1][c]);
     } else
-    for (int64_t j0 = j_begin + (int64_t)threadIdx.x * RUN; j0 < j_end; j0 += (int64_t)CBC_THREADS * RUN) {
+    for (int64_t j0 = j_begin + (int64_t)threadIdx.x * RUN_T; j0 < j_end; j0 += (int64_t)CBC_THREADS * RUN_T) {
+        const int64_t jr = min(j_end, j0 + RUN_T);
         T er[TK], ei[TK];
-        if (j_end - j0 >= RUN) {
-            // Whole run: the loads go out first, the anchors' arithmetic covers their latency.
-            T v[RUN][4];
 #pragma unroll
-            for (int r = 0; r < RUN; ++r) load_pq<T>(base + j0 + r, v[r]);
+        for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
+        for (int64_t js = j0; js < jr; js += SUB) {
+            if (jr - js >= SUB) {
+                T v[SUB][4];
 #pragma unroll
-            for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
+                for (int r = 0; r < SUB; ++r) load_pq(base + js + r, v[r]);
 #pragma unroll
-            for (int r = 0; r < RUN; ++r) step(v[r], er, ei);
-        } else {
-#pragma unroll
-            for (int t = 0; t < TK; ++t) anchor(sa[t] + (unsigned long long)j0 * sb[t], er[t], ei[t]);
-            for (int r = 0; r < (int)(j_end - j0); ++r) {
-                T v[4];
-                load_pq<T>(base + j0 + r, v);
-                step(v, er, ei);
+                for (int r = 0; r < SUB; ++r) step(v[r], er, ei);
+            } else {
+                for (int r = 0; r < (int)(jr - js); ++r) {
+                    T v[4];
+                    load_pq(base + js + r, v);
+                    step(v, er, ei);
+                }
             }
         }
     }
@@ -475,11 +483,30 @@ int CbcState::run(int64_t K, const double* theta_in, bool theta_on_device, int m
 {
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
     const int TK = mode == 0 ? CbcCfg<double>::TK : CbcCfg<float>::TK;
+    const int RUN = mode == 0 ? CbcCfg<double>::RUN : CbcCfg<float>::RUN;
     const int n_tiles = (int)((K + TK - 1) / TK);
-    // Chunks of the bins: enough work items for ~8 blocks per SM, at least one run per thread.
-    const int64_t target_items = 152 * 8;
-    int64_t CB = round_up(std::max<int64_t>(1, (int64_t)n_det * n_tiles * M / target_items), (int64_t)RUN * CBC_THREADS);
-    CB = std::min<int64_t>(CB, round_up(M, (int64_t)RUN));
+    // Chunks of the bins (multiples of the run).  The items are alike, so a launch lasts
+    // ceil(items / resident blocks) item times: the chunk count is the one whose waves times a
+    // thread's bins (plus a per-item cost for the block sum, as bins) is least.
+    int occ = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, mode == 0 ? (const void*)cbc_sum_kernel<double> : (const void*)cbc_sum_kernel<float>, CBC_THREADS, 0);
+    const int64_t slots = (int64_t)std::max(occ, 1) * std::max(sms, 1);
+    const int64_t per_chunk = (int64_t)n_det * n_tiles;
+    constexpr int64_t ITEM_COST_BINS = 8;
+    int64_t CB = round_up(M, (int64_t)RUN), best = INT64_MAX;
+    for (int64_t n = 1; n <= 4 * slots / std::max<int64_t>(per_chunk, 1) + 16; ++n) {
+        const int64_t cb = round_up((M + n - 1) / n, (int64_t)RUN);
+        const int64_t nc = (M + cb - 1) / cb;
+        const int64_t waves = (per_chunk * nc + slots - 1) / slots;
+        const int64_t cost = waves * (round_up(cb, (int64_t)RUN * CBC_THREADS) / CBC_THREADS + ITEM_COST_BINS);
+        if (cost < best) {
+            best = cost;
+            CB = cb;
+        }
+    }
     const int n_chunks = (int)((M + CB - 1) / CB);
     const int64_t n_items = (int64_t)n_det * n_tiles * n_chunks;
     const int P = 2 + 3 * n_det;
