@@ -3,22 +3,23 @@
 // reduction (paper, Sec. "Population acceleration": VT on a regular grid with
 // GPU acceleration, low-dimensional, no spin effects).
 //
-// Work layout.  The contraction sum_a W_a sum_{b >= b0} pdet[a, b] U_b runs as
-// tiles of 64 m1 rows x 64 Lambda columns, one CTA each, every thread holding
-// a 4 x 4 block of (row, column) accumulators.  Chunks of 32 q nodes of the
-// packed pdet tile and of U are staged in shared memory by cp.async.bulk
-// copies that complete on an mbarrier (two stages).  Each thread computes W_a
-// and b0 of its own 16 pairs, so nothing per (row, Lambda) pair is stored:
-// in FP64 with the table-driven exp/expm1 of the FP64 weight kernel (its
-// 2^(j/2048) table sits in the stage buffers until the first copy), in FP32
-// with CUDA's exp2f/log1pf/expm1f for the FP32 form; the support decisions
-// are FP64 in both.
+// Work layout.  The contraction sum_a W_a sum_{b >= b0} pdet[a, b] U_b runs over
+// tiles of m1 rows x Lambda columns whose chunks of 32 q nodes (packed pdet and U)
+// are staged in shared memory by cp.async.bulk copies that complete on mbarriers.
+// FP64: tiles of 32 rows x 64 columns, one CTA each, 2 x 4 (row, column)
+// accumulators per thread; each thread computes W_a and b0 of its own pairs with
+// the table-driven exp/expm1 of the FP64 weight kernel (its 2^(j/2048) table sits
+// in the stage buffers until the first copy).  FP32: a setup kernel computes W_a
+// (CUDA's exp2f/log1pf/expm1f) and b0 of every pair at full occupancy, then
+// persistent CTAs contract tiles of 128 rows x 128 columns in 4 parts of the q
+// range with 8 x 8 accumulators per thread (see the FP32 section).  The support
+// decisions are FP64 in both forms.
 // Lambda columns are placed in ascending mmin order (a counting sort per slice)
-// so that the 4 columns of a thread have nearly the same lower q edges: chunks
-// at or past every edge of the thread run unmasked, chunks below all of them
-// are skipped, and only the chunks between use a per-pair mask.  The result of
-// a column does not depend on where the sort puts it: the sum over b of a pair
-// runs in node order, and the sum over rows in a fixed order.
+// so that the columns of a thread or warp have nearly the same lower q edges:
+// chunks at or past every edge run unmasked, chunks below all of them are
+// skipped, and only the chunks between use a per-pair mask.  The result of a
+// column does not depend on where the sort puts it: the sum over b of a pair runs
+// in node order, and the sum over rows in a fixed order.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -30,6 +31,7 @@
 #include <vector>
 
 #include "pop.h"
+#include "pop_f32x2.cuh"
 #include "pop_gridvt.h"
 #include "pop_internal.h"
 
@@ -64,6 +66,9 @@ struct GvNodes {
     const float* l2q_h;   // [nbp] log2 q as an FP32 (hi, lo) pair
     const float* l2q_l;
     const float* wqf;     // [nbp]
+    const int* qbk;       // [nqb + 1] first node of each of nqb equal-width bins over [qf[0], qf[nb - 1]]
+    float qb0, qbinv;     // qf[0] and 1 / bin width (0 with one bin)
+    int nqb;
     int na, nb, nbp;
 };
 
@@ -142,15 +147,21 @@ __device__ void gv_consts(const double* L, int P, GvLam& c)
 // the FP64 test (which rounds once, 2^-53), and one below thr (1 - 2^-18)
 // fails it.  When both neighbours of j are that clear, j is exact; otherwise
 // (a node within ~2^-18 of the edge) the FP64 test itself moves j.
+// The FP32 search starts from the bin of thr: a binary search over the bin's nodes, then a
+// walk to the first node >= thr (the bin index is a rounded float, so the bin can miss by a node).
 __device__ __forceinline__ int gv_edge(const GvNodes& g, double m1, double mmin, float thr)
 {
-    int lo = 0, hi = g.nb;
+    const float x = (thr - g.qb0) * g.qbinv;
+    const int k = !(x > 0.0f) ? 0 : (x >= (float)g.nqb ? g.nqb - 1 : (int)x);
+    int lo = __ldg(g.qbk + k), hi = __ldg(g.qbk + k + 1);
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (g.qf[mid] >= thr) hi = mid;
         else lo = mid + 1;
     }
     int j = lo;
+    while (j > 0 && g.qf[j - 1] >= thr) --j;
+    while (j < g.nb && g.qf[j] < thr) ++j;
     const bool clear_above = j == g.nb || g.qf[j] >= thr * (1.0f + 0x1p-18f);
     const bool clear_below = j == 0 || g.qf[j - 1] < thr * (1.0f - 0x1p-18f);
     if (clear_above && clear_below) return j;
@@ -189,28 +200,51 @@ __device__ __forceinline__ void gv_pair64(const GvNodes& g, const GvLam& c, int 
     b0 = gv_edge(g, m1, c.mmin, __fdividef(c.mmin_f, g.m1f[a]));
 }
 
+// Per-row and per-column constants of the FP32 form, packed for 16-byte loads.
+struct alignas(16) GvRow32 {
+    double m1;
+    float m1f, m1lf, l2m1f, invm1f, waf, pad;  // m1 as an FP32 (hi, lo) pair, log2 m1, 1/m1, trapezoid weight
+};
+struct alignas(16) GvCol32 {
+    long long mmin_bits, mmax_bits;  // -1 in both for a column without a valid Lambda
+    float nalpha_f, l2cpl_f, mu_h, mu_l, nh2_f, l2cg_f, mmin_f, mmin_l, b1_f;
+    int beta_m1, pad[2];
+};
+static_assert(sizeof(GvRow32) == 32 && sizeof(GvCol32) == 64, "two and four 16-byte words");
+
+template <class T>
+__device__ __forceinline__ T gv_ld16(const T* p)
+{
+    T v;
+    const int4* s = reinterpret_cast<const int4*>(p);
+    int4* d = reinterpret_cast<int4*>(&v);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(T) / 16); ++w) d[w] = __ldg(s + w);
+    return v;
+}
+
 // The same pair in the FP32 form: base-2 exponentials and log1p/expm1 in FP32
 // (CUDA exp2f, log1pf, expm1f).  m1 - mpp and mmin - m1 come from (hi, lo) FP32
 // pairs; within ~2^-6 of the lower mass edge mmin - m1 is taken in FP64, where
 // it is exact.
-__device__ __forceinline__ void gv_pair32(const GvNodes& g, const GvLam& c, int a, float& W, int& b0)
+__device__ __forceinline__ void gv_pair32(const GvNodes& g, const GvCol32& c, const GvRow32& r, int a, float& W,
+                                          int& b0)
 {
     W = 0.0f;
     b0 = g.nb;
-    const double m1 = g.m1[a];
-    const long long mb = __double_as_longlong(m1);
-    if (!gv_in_mass(mb, c)) return;
-    const float m1h = g.m1f[a], m1l = g.m1lf[a];
-    const float e1 = exp2f(fmaf(c.nalpha_f, g.l2m1f[a], c.l2cpl_f));
-    const float d = (m1h - c.mu_h) + (m1l - c.mu_l);
+    const long long mb = __double_as_longlong(r.m1);
+    if (!(mb > c.mmin_bits && mb <= c.mmax_bits)) return;
+    const float e1 = exp2f(fmaf(c.nalpha_f, r.l2m1f, c.l2cpl_f));
+    const float d = (r.m1f - c.mu_h) + (r.m1lf - c.mu_l);
     const float e2 = exp2f(fmaf(c.nh2_f * d, d, c.l2cg_f));
+    const double mmin = __longlong_as_double(c.mmin_bits);
     float t;
-    if (llabs(mb - c.mmin_bits) < NEAR_EDGE_BITS) t = (float)(g.invm1[a] * (c.mmin - m1));
-    else t = ((c.mmin_f - m1h) + (c.mmin_l - m1l)) * g.invm1f[a];
+    if (llabs(mb - c.mmin_bits) < NEAR_EDGE_BITS) t = (float)(g.invm1[a] * (mmin - r.m1));
+    else t = ((c.mmin_f - r.m1f) + (c.mmin_l - r.m1lf)) * r.invm1f;
     const float lr = log1pf(t);
     const float den = c.beta_m1 ? -lr : fabsf(expm1f(c.b1_f * lr));
-    W = g.waf[a] * (e1 + e2) * __frcp_rn(den);
-    b0 = gv_edge(g, m1, c.mmin, __fdividef(c.mmin_f, m1h));
+    W = r.waf * (e1 + e2) * __frcp_rn(den);
+    b0 = gv_edge(g, r.m1, mmin, __fdividef(c.mmin_f, r.m1f));
 }
 
 __device__ __forceinline__ int slice_count(const int64_t* dK, int64_t slice0, int S)
@@ -318,10 +352,11 @@ gv_sort_kernel(const double* __restrict__ lambda, int P, const int64_t* __restri
 
 // Per-column constants of the slice (live = 0 for padding columns).
 __global__ void gv_lamc_kernel(const double* __restrict__ lambda, int P, const int32_t* __restrict__ perm,
-                               const int64_t* __restrict__ dK, int64_t slice0, int S, GvLam* __restrict__ lamc)
+                               const int64_t* __restrict__ dK, int64_t slice0, int S, GvLam* __restrict__ lamc,
+                               GvCol32* __restrict__ lamc32)
 {
     const int n = slice_count(dK, slice0, S);
-    const int npad = (n + GV_TL - 1) / GV_TL * GV_TL;
+    const int npad = (n + 127) / 128 * 128;  // whole tiles of both contractions (64 and 128 columns)
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= npad) return;
     const int k = r < n ? perm[r] : -1;
@@ -330,6 +365,22 @@ __global__ void gv_lamc_kernel(const double* __restrict__ lambda, int P, const i
     c.beta = 0.0;
     if (k >= 0) gv_consts(lambda + (int64_t)k * P, P, c);
     lamc[r] = c;
+    GvCol32 c32{};
+    c32.mmin_bits = c.live ? c.mmin_bits : -1;
+    c32.mmax_bits = c.live ? c.mmax_bits : -1;
+    if (c.live) {
+        c32.nalpha_f = c.nalpha_f;
+        c32.l2cpl_f = c.l2cpl_f;
+        c32.mu_h = c.mu_h;
+        c32.mu_l = c.mu_l;
+        c32.nh2_f = c.nh2_f;
+        c32.l2cg_f = c.l2cg_f;
+        c32.mmin_f = c.mmin_f;
+        c32.mmin_l = c.mmin_l;
+        c32.b1_f = c.b1_f;
+        c32.beta_m1 = c.beta_m1;
+    }
+    lamc32[r] = c32;
 }
 
 // ---------------------------------------------------------------- tile order
@@ -394,11 +445,10 @@ gv_order_kernel(GvNodes g, const GvLam* __restrict__ lamc, const int64_t* __rest
 
 // ---------------------------------------------------------------- U_b per column
 // U[lt][b][c] = wq_b q_b^beta for column r = lt * 64 + c (0 for padding
-// columns, invalid Lambda and nodes past nb).
-template <class T>
+// columns, invalid Lambda and nodes past nb), FP64.
 __global__ void gv_u_kernel(GvNodes g, const double* __restrict__ wq, const GvLam* __restrict__ lamc,
                             const int64_t* __restrict__ dK, int64_t slice0, int S, const double2* __restrict__ tab,
-                            ExpConsts kc, T* __restrict__ U)
+                            ExpConsts kc, double* __restrict__ U)
 {
     const int n = slice_count(dK, slice0, S);
     const int64_t total = (int64_t)((n + GV_TL - 1) / GV_TL) * g.nbp * GV_TL;
@@ -409,11 +459,8 @@ __global__ void gv_u_kernel(GvNodes g, const double* __restrict__ wq, const GvLa
         const int lt = (int)(rest / g.nbp);
         const GvLam& L = lamc[lt * GV_TL + c];
         double u = 0.0;
-        if (L.live && b < g.nb && g.q[b] > 0.0) {
-            if constexpr (sizeof(T) == 8) u = wq[b] * exp_tab(L.beta * g.lnq[b], tab, kc);
-            else u = (double)(g.wqf[b] * exp2f(fmaf(L.beta_h, g.l2q_h[b], fmaf(L.beta_h, g.l2q_l[b], L.beta_l * g.l2q_h[b]))));
-        }
-        U[t] = (T)u;
+        if (L.live && b < g.nb && g.q[b] > 0.0) u = wq[b] * exp_tab(L.beta * g.lnq[b], tab, kc);
+        U[t] = u;
     }
 }
 
@@ -479,42 +526,25 @@ __device__ __forceinline__ void gv_load(const T* src, T (&v)[N])
     }
 }
 
-// ---------------------------------------------------------------- contraction
-// Tile shapes.  RA m1 rows x 4 Lambda columns per thread; a warp is 8 x 4 threads
-// (8 RA rows x 16 consecutive columns); a CTA is 2 x 4 warps (TA = 16 RA rows x 64
-// columns).  FP64 is bound by its two-lane pipe, so small 2 x 4 thread tiles
-// (more CTAs, a shorter wave tail) cost nothing; FP32 keeps 4 x 4 tiles for
-// operand reuse and keeps more chunks in flight, two per barrier step.
-template <class T>
-struct GvCfg;
-template <>
-struct GvCfg<double> {
-    static constexpr int RA = 2, STAGES = 2, CPB = 1, MIN_BLOCKS = 3;
-};
-template <>
-struct GvCfg<float> {
-    static constexpr int RA = 4, STAGES = 4, CPB = 2, MIN_BLOCKS = 2;
-};
-template <class T>
-constexpr int gv_ta() { return 16 * GvCfg<T>::RA; }
-template <class T>
-constexpr size_t gv_dyn_smem() { return (size_t)GvCfg<T>::STAGES * GV_BC * (gv_ta<T>() + GV_TL) * sizeof(T); }
+// ---------------------------------------------------------------- FP64 contraction
+// Tile shapes.  2 m1 rows x 4 Lambda columns per thread; a warp is 8 x 4 threads
+// (16 rows x 16 consecutive columns); a CTA is 2 x 4 warps (32 rows x 64 columns).
+// The FP64 pipe (two lanes per SM and clock) binds, so small thread tiles (more CTAs,
+// a shorter wave tail) cost nothing.
+constexpr int G64_RA = 2, G64_TA = 16 * G64_RA, G64_STAGES = 2;
+__host__ __device__ constexpr size_t g64_smem() { return (size_t)G64_STAGES * GV_BC * (G64_TA + GV_TL) * sizeof(double); }
 
-// part[rt][r] = sum over the TA rows of row tile rt of W_a sum_{b >= b0} pdet[a, b] U_b
-// for every column r of Lambda tile blockIdx.y.  T = double: FP64 throughout.
-// T = float: FP32 pdet and U, FP32 sums per 32-node chunk added into an FP32
-// running sum, FP32 row factor, FP64 row combine.
-template <class T>
-__global__ void __launch_bounds__(GV_THREADS, GvCfg<T>::MIN_BLOCKS)
-gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, const GvLam* __restrict__ lamc,
+// part[rt][r] = sum over the 32 rows of row tile rt of W_a sum_{b >= b0} pdet[a, b] U_b
+// for every column r of the CTA's Lambda tile, FP64 throughout.
+__global__ void __launch_bounds__(GV_THREADS, 3)
+gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restrict__ U, const GvLam* __restrict__ lamc,
                const int32_t* __restrict__ rt_order, const int64_t* __restrict__ dK, int64_t slice0, int S,
                const double2* __restrict__ tab_g, ExpConsts kc, double* __restrict__ part, int* __restrict__ err)
 {
-    constexpr int RA = GvCfg<T>::RA, STAGES = GvCfg<T>::STAGES, CPB = GvCfg<T>::CPB;
-    constexpr int TA = gv_ta<T>();
+    using T = double;
+    constexpr int RA = G64_RA, STAGES = G64_STAGES, TA = G64_TA;
     constexpr int PD_ELEMS = GV_BC * TA, U_ELEMS = GV_BC * GV_TL;  // one chunk of each operand
     constexpr uint32_t PD_BYTES = PD_ELEMS * sizeof(T), U_BYTES = U_ELEMS * sizeof(T);
-    static_assert(STAGES % CPB == 0 && STAGES >= 2 * CPB, "whole steps in flight");
     extern __shared__ __align__(128) unsigned char gv_dyn[];
     T* sp = reinterpret_cast<T*>(gv_dyn);  // [STAGES][BC][TA] pdet
     T* su = sp + STAGES * PD_ELEMS;        // [STAGES][BC][64] U
@@ -537,13 +567,10 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
         for (int st = 0; st < STAGES; ++st) gv_bar_init(gv_saddr(&bar[st]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // FP64 form: the exponential table lives in the stage buffers until the first copy.
+    // The exponential table lives in the stage buffers until the first copy.
     const double2* tab = reinterpret_cast<const double2*>(gv_dyn);
-    if constexpr (sizeof(T) == 8) {
-        static_assert(gv_dyn_smem<T>() >= EXP_TABLE_SIZE * sizeof(double2), "the table fits the stages");
-        double2* st = reinterpret_cast<double2*>(gv_dyn);
-        for (int i = tid; i < EXP_TABLE_SIZE; i += GV_THREADS) st[i] = tab_g[i];
-    }
+    static_assert(g64_smem() >= EXP_TABLE_SIZE * sizeof(double2), "the table fits the stages");
+    for (int i = tid; i < EXP_TABLE_SIZE; i += GV_THREADS) reinterpret_cast<double2*>(gv_dyn)[i] = tab_g[i];
     __syncthreads();
 
     T W[RA][4];
@@ -554,8 +581,7 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int a = rt * TA + ty * RA + i;
-            if constexpr (sizeof(T) == 8) gv_pair64(g, lc[tx * 4 + j], a, tab, kc, W[i][j], b0[i][j]);
-            else gv_pair32(g, lc[tx * 4 + j], a, W[i][j], b0[i][j]);
+            gv_pair64(g, lc[tx * 4 + j], a, tab, kc, W[i][j], b0[i][j]);
             if (b0[i][j] < g.nb) {
                 tmin = min(tmin, b0[i][j]);
                 tmax = max(tmax, b0[i][j]);
@@ -585,19 +611,12 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
         for (int c = c0; c < nch && c < c0 + STAGES; ++c) issue(c);
 
     T acc[RA][4];
-    float run[RA][4];  // FP32 form: running sum of the chunk sums
 #pragma unroll
     for (int i = 0; i < RA; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            acc[i][j] = T(0);
-            run[i][j] = 0.0f;
-        }
-    for (int s = c0; s < nch; s += CPB) {
-        const int e = min(s + CPB, nch);
-        bool ok = true;
-        for (int c = s; c < e; ++c)
-            ok &= gv_wait(gv_saddr(&bar[(c - c0) % STAGES]), (uint32_t)(((c - c0) / STAGES) & 1));
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int s = c0; s < nch; ++s) {
+        const bool ok = gv_wait(gv_saddr(&bar[(s - c0) % STAGES]), (uint32_t)(((s - c0) / STAGES) & 1));
         if (__syncthreads_or(!ok)) {
             // Give up: flag it, let the copies already issued land (bounded), leave NaN.
             if (tid == 0) {
@@ -609,10 +628,9 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
             if (tid < GV_TL) out[tid] = NAN;
             return;
         }
-        for (int c = s; c < e; ++c) {
-            const int cb = c * GV_BC;
-            if (cb + GV_BC <= tmin) continue;  // below every support edge of this thread
-            const int st = (c - c0) % STAGES;
+        const int cb = s * GV_BC;
+        if (cb + GV_BC > tmin) {  // else below every support edge of this thread
+            const int st = (s - c0) % STAGES;
             const T* ps = sp + st * PD_ELEMS + ty * RA;
             const T* us = su + st * U_ELEMS + tx * 4;
             const int bend = min(GV_BC, g.nb - cb);  // the last chunk stops at the last q node
@@ -640,19 +658,9 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
                         for (int j = 0; j < 4; ++j) acc[i][j] = fma(p[i], b >= b0[i][j] ? u[j] : T(0), acc[i][j]);
                 }
             }
-            if constexpr (sizeof(T) == 4) {
-#pragma unroll
-                for (int i = 0; i < RA; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        run[i][j] += acc[i][j];
-                        acc[i][j] = 0.0f;
-                    }
-            }
         }
-        __syncthreads();  // the step's stages are free again
-        if (tid == 0)
-            for (int c = s + STAGES; c < nch && c < s + STAGES + CPB; ++c) issue(c);
+        __syncthreads();  // the stage is free again
+        if (tid == 0 && s + STAGES < nch) issue(s + STAGES);
     }
 
     // Fixed-order combine: rows of the thread (i = 0..RA-1), then the 16 row groups.
@@ -660,12 +668,7 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
     for (int j = 0; j < 4; ++j) {
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < RA; ++i) {
-            double v;
-            if constexpr (sizeof(T) == 4) v = (double)(W[i][j] * run[i][j]);
-            else v = W[i][j] * acc[i][j];
-            t += b0[i][j] < g.nb ? v : 0.0;
-        }
+        for (int i = 0; i < RA; ++i) t += b0[i][j] < g.nb ? W[i][j] * acc[i][j] : 0.0;
         red[ty][tx * 4 + j] = t;
     }
     __syncthreads();
@@ -673,6 +676,318 @@ gv_main_kernel(GvNodes g, const T* __restrict__ pd, const T* __restrict__ U, con
         double sum = 0.0;
         for (int y = 0; y < 16; ++y) sum += red[y][tid];
         out[tid] = sum;
+    }
+}
+
+// ---------------------------------------------------------------- FP32 contraction
+// A setup kernel computes W_a and b0 of every (row, column) pair at full occupancy (FP32 W
+// as gv_pair32 defines it), in the order the contraction reads them.  The contraction's
+// persistent CTAs (one per SM) take items from a queue: a tile of 128 m1 rows x 128 Lambda
+// columns and one of 4 fixed parts of the q range, the top parts (the heaviest) first.
+// A thread holds 8 rows x 8 columns as 32 packed (row, row + 1) accumulator pairs: per q
+// node, two 16-byte shared loads of its 8 pdet values, two of its 8 U values and 32
+// f32x2 FMAs, so that the shared-memory path (16-byte loads at 4 SM cycles per warp) and
+// the FMA pipe are about equally busy.  The rows and columns of a staged chunk are stored
+// in the order the threads read them (g32_perm).  A warp covers 32 rows x 64 columns and
+// decides per 8-node sub-block, from the lowest and highest support edge of its pairs,
+// whether the sub-block is below every edge (skipped), past every edge (no mask) or in
+// between (per-pair masks built from the edges kept in shared memory).  Every pair's sum
+// still runs over its own in-support nodes in node order, 32-node chunk sums added into a
+// running sum per q part, so the result does not depend on the tiling.
+constexpr int G32_T = 128;      // m1 rows and Lambda columns of a tile
+constexpr int G32_STAGES = 4;   // staged chunks in flight
+constexpr int G32_CPB = 2;      // chunks per barrier step
+constexpr int G32_SUB = 8;      // q nodes per masking decision
+constexpr int G32_QP = 4;       // parts of the q range (items per tile)
+constexpr int G32_CHUNK = GV_BC * G32_T;  // floats of one pdet or U chunk
+constexpr int G32_PAIRS = G32_T * G32_T;  // pairs of a tile, 64 per thread
+__host__ __device__ constexpr size_t g32_stage_bytes() { return (size_t)G32_STAGES * 2 * G32_CHUNK * sizeof(float); }
+__host__ __device__ constexpr size_t g32_smem() { return g32_stage_bytes() + (size_t)G32_PAIRS * sizeof(int); }
+static_assert(g32_stage_bytes() >= 16 * G32_T * sizeof(double), "the row combine fits the stages");
+
+// Thread t of a contraction CTA: rows 8 ty .. 8 ty + 7, columns 8 tx .. 8 tx + 7 of its tile.
+__host__ __device__ inline int g32_ty(int t) { return 4 * ((t >> 5) >> 1) + ((t & 31) >> 3); }
+__host__ __device__ inline int g32_tx(int t) { return 8 * ((t >> 5) & 1) + (t & 7); }
+// Row (or column) of a tile stored at position pos of a staged node: pos = 64 h + 4 t + e holds
+// row 8 t + 4 h + e, so thread t's 8 rows are two 16-byte words and a warp's words are contiguous.
+__host__ __device__ inline int g32_perm(int pos) { return ((pos >> 2) & 15) * 8 + (pos >> 6) * 4 + (pos & 3); }
+
+// One 8-node sub-block.  ps / us: this thread's words in the stage's pdet / U chunk at the
+// sub-block's first node; mk (MASK): bit n of byte k is set when node n is in the support of
+// pair k = 8 i + j (row i, column j of the thread).
+template <bool MASK>
+__device__ __forceinline__ void g32_block(const float* ps, const float* us, const uint32_t (&mk)[16], f2 (&acc)[4][8])
+{
+#pragma unroll
+    for (int bb = 0; bb < G32_SUB; ++bb) {
+        const ulonglong2 pa = *reinterpret_cast<const ulonglong2*>(ps + bb * G32_T);
+        const ulonglong2 pb = *reinterpret_cast<const ulonglong2*>(ps + bb * G32_T + 64);
+        const float4 ua = *reinterpret_cast<const float4*>(us + bb * G32_T);
+        const float4 ub = *reinterpret_cast<const float4*>(us + bb * G32_T + 64);
+        const f2 p[4] = {pa.x, pa.y, pb.x, pb.y};
+        const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if constexpr (!MASK) {
+                const f2 uj = bc(u[j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i][j] = fma2(p[i], uj, acc[i][j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k0 = 16 * i + j, k1 = k0 + 8;
+                    const bool in0 = (mk[k0 >> 2] >> (8 * (k0 & 3) + bb)) & 1u;
+                    const bool in1 = (mk[k1 >> 2] >> (8 * (k1 & 3) + bb)) & 1u;
+                    acc[i][j] = fma2(p[i], pk(in0 ? u[j] : 0.0f, in1 ? u[j] : 0.0f), acc[i][j]);
+                }
+            }
+        }
+    }
+}
+
+// W (wg) and b0 (b0g) of pair k = 8 i + j of thread t of tile (rt, lt) at
+// ((rt * n_lt + lt) * 64 + k) * 256 + t: row 8 ty(t) + i, column 8 tx(t) + j; W = 0 for a pair
+// without support (b0 = nb).  wmm[(rt * n_lt + lt) * 8 + w] = (lowest, highest) support edge
+// over the pairs of warp w of the contraction (unsigned 0xffffffff and -1 when it has none; the
+// array is 0xff bytes at the launch).  A warp-wide read of the contraction is one contiguous line.
+__global__ void gv_setup32_kernel(GvNodes g, const GvRow32* __restrict__ rows, const GvCol32* __restrict__ cols,
+                                  const int64_t* __restrict__ dK, int64_t slice0, int S, float* __restrict__ wg,
+                                  int* __restrict__ b0g, int2* __restrict__ wmm)
+{
+    const int n = slice_count(dK, slice0, S);
+    const int n_lt = (n + G32_T - 1) / G32_T;
+    const int total = (g.na / G32_T) * n_lt * G32_PAIRS;  // a multiple of 32: warps stay whole
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int t = e & (GV_THREADS - 1), k = (e >> 8) & 63, item = e >> 14;
+        const int rt = item / n_lt, lt = item - rt * n_lt;
+        float W;
+        int b0;
+        const int a = rt * G32_T + g32_ty(t) * 8 + (k >> 3);
+        gv_pair32(g, gv_ld16(cols + lt * G32_T + g32_tx(t) * 8 + (k & 7)), gv_ld16(rows + a), a, W, b0);
+        const bool in = b0 < g.nb;
+        wg[e] = in ? W : 0.0f;
+        b0g[e] = b0;
+        const unsigned lo = __reduce_min_sync(0xffffffffu, in ? (unsigned)b0 : 0xffffffffu);
+        const int hi = __reduce_max_sync(0xffffffffu, in ? b0 : -1);
+        if ((t & 31) == 0 && lo != 0xffffffffu) {
+            int2* m = wmm + item * 8 + (t >> 5);
+            atomicMin(reinterpret_cast<unsigned*>(&m->x), lo);
+            atomicMax(&m->y, hi);
+        }
+    }
+}
+static_assert(GV_THREADS == 256 && G32_PAIRS == 64 * GV_THREADS, "setup index layout");
+
+// Exact product and float-float accumulation (Knuth's TwoSum, an FMA for the product's error).
+__device__ __forceinline__ void g32_ff_add(float& sh, float& sl, float w, float r)
+{
+    const float p = w * r;
+    const float pe = fmaf(w, r, -p);
+    const float s = sh + p;
+    const float bp = s - sh;
+    sl += ((sh - (s - bp)) + (p - bp)) + pe;
+    sh = s;
+}
+
+// part[rt * 4 + qp][r] = sum over the 128 rows of row tile rt of W_a times the FP32 sum of
+// pdet[a, b] U_b over the nodes b >= b0 of q part qp (32-node chunk sums added into an FP32
+// running sum), FP32 row factor, the products and their sum over rows in float-float (exact
+// products, FP32 pairs carrying the rounding errors), rounded to FP64.  *queue is zero at the
+// launch.
+__global__ void __launch_bounds__(GV_THREADS, 1)
+gv_main32_kernel(GvNodes g, const float* __restrict__ pd, const float* __restrict__ U, const float* __restrict__ wg,
+                 const int* __restrict__ b0g, const int2* __restrict__ wmm, const int32_t* __restrict__ rt_order,
+                 const int64_t* __restrict__ dK, int64_t slice0, int S, unsigned* __restrict__ queue,
+                 double* __restrict__ part, int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char gv_dyn[];
+    float* sp = reinterpret_cast<float*>(gv_dyn);   // [STAGES][pdet chunk, U chunk]
+    int* b0s = reinterpret_cast<int*>(gv_dyn + g32_stage_bytes());  // [64][256] support edges of the item
+    float2* red = reinterpret_cast<float2*>(gv_dyn);  // [16][128], over the stages once an item's chunks are done
+    __shared__ __align__(8) uint64_t bar[G32_STAGES];
+    __shared__ __align__(8) uint64_t ebar;  // the item's support edges
+    __shared__ int s_tmin;
+    __shared__ unsigned s_item;
+
+    const int n = slice_count(dK, slice0, S);
+    const int n_lt = (n + G32_T - 1) / G32_T;
+    const unsigned per_part = (unsigned)(g.na / G32_T) * (unsigned)n_lt;
+    const unsigned n_items = per_part * G32_QP;
+    const int nch = g.nbp / GV_BC;
+    const int tid = threadIdx.x, ty = g32_ty(tid), tx = g32_tx(tid);
+    if (tid == 0) {
+        for (int st = 0; st < G32_STAGES; ++st) gv_bar_init(gv_saddr(&bar[st]));
+        gv_bar_init(gv_saddr(&ebar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    unsigned seq = 0;    // chunks this CTA has staged so far: chunk number seq goes to stage seq % STAGES
+    unsigned n_ecp = 0;  // support-edge copies this CTA has issued
+    bool dead = false;   // a wait gave up: the CTA only marks its remaining items
+    for (;;) {
+        // This thread's reads of the stages, the edges and the row combine (generic proxy) are
+        // ordered before the next bulk copies (async proxy) into the same bytes.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();  // the previous item is done with the stages, b0s, red and s_item
+        if (tid == 0) {
+            s_item = atomicAdd(queue, 1u);
+            s_tmin = INT_MAX;
+        }
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item >= n_items) break;
+        const int qp = G32_QP - 1 - (int)(item / per_part);
+        const unsigned rem = item % per_part;
+        const int rt = rt_order[rem / n_lt], lt = (int)(rem % n_lt);
+        double* out = part + ((int64_t)rt * G32_QP + qp) * S + lt * G32_T;
+        if (dead) {
+            if (tid < G32_T) out[tid] = NAN;
+            continue;
+        }
+        const int tile = rt * n_lt + lt;
+        const int2 mm = wmm[tile * 8 + (tid >> 5)];
+        const int wmin = mm.x < 0 ? INT_MAX : mm.x, wmax = mm.y;  // 0xffffffff: no support in the warp
+        if ((tid & 31) == 0) atomicMin(&s_tmin, wmin);
+        __syncthreads();
+        const int cq0 = qp * nch / G32_QP, cq1 = (qp + 1) * nch / G32_QP;
+        const int c_lo = max(cq0, s_tmin / GV_BC);  // s_tmin = INT_MAX: no pair of the tile has support
+        if (c_lo >= cq1) {
+            if (tid < G32_T) out[tid] = 0.0;
+            continue;
+        }
+        const float* pd_tile = pd + (int64_t)rt * g.nbp * G32_T;
+        const float* u_tile = U + (int64_t)lt * g.nbp * G32_T;
+        auto issue = [&](int c) {
+            const int st = (int)((seq + (unsigned)(c - c_lo)) % G32_STAGES);
+            const uint32_t b = gv_saddr(&bar[st]);
+            gv_expect_tx(b, 2 * G32_CHUNK * sizeof(float));
+            gv_bulk_load(gv_saddr(sp + st * 2 * G32_CHUNK), pd_tile + (int64_t)c * G32_CHUNK, G32_CHUNK * sizeof(float), b);
+            gv_bulk_load(gv_saddr(sp + st * 2 * G32_CHUNK + G32_CHUNK), u_tile + (int64_t)c * G32_CHUNK,
+                         G32_CHUNK * sizeof(float), b);
+        };
+        auto wait = [&](int c) {
+            const unsigned q = seq + (unsigned)(c - c_lo);
+            return gv_wait(gv_saddr(&bar[q % G32_STAGES]), (q / G32_STAGES) & 1u);
+        };
+        if (tid == 0) {
+            gv_expect_tx(gv_saddr(&ebar), G32_PAIRS * sizeof(int));
+            gv_bulk_load(gv_saddr(b0s), b0g + (int64_t)tile * G32_PAIRS, G32_PAIRS * sizeof(int), gv_saddr(&ebar));
+            for (int c = c_lo; c < cq1 && c < c_lo + G32_STAGES; ++c) issue(c);
+        }
+        const uint32_t eparity = n_ecp & 1u;
+        ++n_ecp;
+
+        f2 acc[4][8], run[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = run[i][j] = 0ull;
+        bool ok = gv_wait(gv_saddr(&ebar), eparity);
+        for (int s = c_lo; s < cq1; s += G32_CPB) {
+            const int e = min(s + G32_CPB, cq1);
+            for (int c = s; c < e; ++c) ok &= wait(c);
+            if (__syncthreads_or(!ok)) {
+                // Give up: flag it and let the copies already issued land (bounded).
+                if (tid == 0) {
+                    atomicExch(err, 1);
+                    gv_wait(gv_saddr(&ebar), eparity);
+                    for (int d = s; d < cq1 && d < s + G32_STAGES; ++d) wait(d);
+                }
+                ok = false;
+                break;
+            }
+            for (int c = s; c < e; ++c) {
+                const int cb = c * GV_BC;
+                if (cb + GV_BC <= wmin) continue;  // below every support edge of the warp
+                const int st = (int)((seq + (unsigned)(c - c_lo)) % G32_STAGES);
+                const float* ps = sp + st * 2 * G32_CHUNK + ty * 4;
+                const float* us = sp + st * 2 * G32_CHUNK + G32_CHUNK + tx * 4;
+#pragma unroll 1
+                for (int sb = 0; sb < GV_BC; sb += G32_SUB) {
+                    const int b = cb + sb;
+                    if (b + G32_SUB <= wmin || b >= g.nb) continue;
+                    uint32_t mk[16];
+                    if (b >= wmax) {
+                        g32_block<false>(ps + sb * G32_T, us + sb * G32_T, mk, acc);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) {
+                            uint32_t m = 0;
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const int d = b0s[(4 * r + h) * GV_THREADS + tid] - b;  // first in-support node
+                                const uint32_t byte = d <= 0 ? 0xffu : (d >= G32_SUB ? 0u : (0xffu << d) & 0xffu);
+                                m |= byte << (8 * h);
+                            }
+                            mk[r] = m;
+                        }
+                        g32_block<true>(ps + sb * G32_T, us + sb * G32_T, mk, acc);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        run[i][j] = add2(run[i][j], acc[i][j]);
+                        acc[i][j] = 0ull;
+                    }
+            }
+            __syncthreads();  // the step's stages are free again
+            if (tid == 0)
+                for (int c = s + G32_STAGES; c < cq1 && c < s + G32_STAGES + G32_CPB; ++c) issue(c);
+        }
+        seq += (unsigned)(cq1 - c_lo);
+        if (!ok) {
+            dead = true;
+            if (tid < G32_T) out[tid] = NAN;
+            continue;
+        }
+        // Fixed-order combine (W = 0 without support): rows of the thread (i = 0..7), then the
+        // 16 row groups, in float-float.
+        const float* wt = wg + (int64_t)tile * G32_PAIRS + tid;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float r0, r1;
+                upk(run[i][j], r0, r1);
+                g32_ff_add(sh, sl, wt[(16 * i + j) * GV_THREADS], r0);
+                g32_ff_add(sh, sl, wt[(16 * i + 8 + j) * GV_THREADS], r1);
+            }
+            red[ty * G32_T + tx * 8 + j] = make_float2(sh, sl);
+        }
+        __syncthreads();
+        if (tid < G32_T) {
+            float sh = 0.0f, sl = 0.0f;
+            for (int y = 0; y < 16; ++y) {
+                const float2 v = red[y * G32_T + tid];
+                const float s = sh + v.x;
+                const float bp = s - sh;
+                sl += ((sh - (s - bp)) + (v.x - bp)) + v.y;
+                sh = s;
+            }
+            out[tid] = (double)sh + (double)sl;
+        }
+    }
+}
+
+// U of the FP32 contraction: U[lt][b][pos] = wq_b q_b^beta for column lt * 128 + g32_perm(pos)
+// (0 for padding columns, invalid Lambda and nodes past nb).
+__global__ void gv_u32_kernel(GvNodes g, const GvLam* __restrict__ lamc, const int64_t* __restrict__ dK,
+                              int64_t slice0, int S, float* __restrict__ U)
+{
+    const int n = slice_count(dK, slice0, S);
+    const int64_t total = (int64_t)((n + G32_T - 1) / G32_T) * g.nbp * G32_T;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int pos = (int)(t % G32_T);
+        const int64_t rest = t / G32_T;
+        const int b = (int)(rest % g.nbp);
+        const int lt = (int)(rest / g.nbp);
+        const GvLam& L = lamc[lt * G32_T + g32_perm(pos)];
+        float u = 0.0f;
+        if (L.live && b < g.nb && g.q[b] > 0.0)
+            u = g.wqf[b] * exp2f(fmaf(L.beta_h, g.l2q_h[b], fmaf(L.beta_h, g.l2q_l[b], L.beta_l * g.l2q_h[b])));
+        U[t] = u;
     }
 }
 
@@ -706,8 +1021,9 @@ __global__ void gv_out_kernel(const double* __restrict__ xi, const double* __res
     flags[k] = x > 0.0 ? 0u : (uint32_t)POP_FLAG_ZERO_XI;
 }
 
-// pdet [n_m1][n_q] -> [na / TA][nbp][TA] in T (zeros in the padding); *bad = 1
-// when a used entry is not finite or negative.
+// pdet [n_m1][n_q] -> [na / TA][nbp][TA] in T (zeros in the padding), position c of a node
+// holding row c (FP64 tiles of 32) or row g32_perm(c) (FP32 tiles of 128); *bad = 1 when a
+// used entry is not finite or negative.
 template <class T>
 __global__ void gv_pack_kernel(const double* __restrict__ pdet, int n_m1, int n_q, int na, int nb, int nbp, int TA,
                                T* __restrict__ out, int* __restrict__ bad)
@@ -717,7 +1033,7 @@ __global__ void gv_pack_kernel(const double* __restrict__ pdet, int n_m1, int n_
         const int c = (int)(t % TA);
         const int64_t rest = t / TA;
         const int b = (int)(rest % nbp);
-        const int a = (int)(rest / nbp) * TA + c;
+        const int a = (int)(rest / nbp) * TA + (sizeof(T) == 4 ? g32_perm(c) : c);
         double v = 0.0;
         if (a < n_m1 && b < nb) {
             v = pdet[(int64_t)a * n_q + b];
@@ -736,7 +1052,6 @@ int blocks_for(int64_t n, int threads, int cap)
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
-size_t main_smem(int mode) { return mode == 0 ? gv_dyn_smem<double>() : gv_dyn_smem<float>(); }
 
 size_t sort_smem(int S) { return sizeof(int) * (GV_BUCKETS + 4) + (sizeof(int32_t) + sizeof(float)) * (size_t)S; }
 
@@ -803,7 +1118,23 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
         l2qlv[b] = (float)(l2 - (double)l2qhv[b]);
         wqfv[b] = (float)wqv[b];
     }
-    DevBuf dm, dlm, dim, dwa, dmf, dmlf, dimf, dl2m, dwaf, dq, dlq, dwq, dqf, dl2qh, dl2ql, dwqf, p64, p32, tmp, dbad;
+    std::vector<GvRow32> r32(na_);
+    for (int a = 0; a < na_; ++a) r32[a] = GvRow32{m[a], mf[a], mlf[a], l2mf[a], imf[a], wmf[a], 0.0f};
+    // Bins of the support-edge search: up to 1024 of equal width over the FP32 nodes.
+    int nqb_ = 1;
+    float qb0_ = qfv[0], qbinv_ = 0.0f;
+    if (nb_ >= 2 && qfv[nb_ - 1] > qfv[0]) {
+        nqb_ = std::min(1024, nb_);
+        qbinv_ = (float)(nqb_ / ((double)qfv[nb_ - 1] - (double)qfv[0]));
+    }
+    std::vector<int> qbkv(nqb_ + 1, nb_);
+    for (int k = 0, j = 0; k < nqb_; ++k) {
+        const double edge = (double)qfv[0] + (double)k / (double)qbinv_;
+        while (j < nb_ && (double)qfv[j] < edge) ++j;
+        qbkv[k] = k == 0 ? 0 : j;
+    }
+    DevBuf dm, dlm, dim, dwa, dmf, dmlf, dimf, dl2m, dwaf, dq, dlq, dwq, dqf, dl2qh, dl2ql, dwqf, dqbk, dr32, p64, p32,
+        tmp, dbad;
     auto ck = [&](cudaError_t e) { return e == cudaSuccess; };
     const size_t packed = (size_t)na_ * nbp_;
     const size_t d_na = sizeof(double) * na_, f_na = sizeof(float) * na_;
@@ -811,7 +1142,8 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
     if (!ck(dm.alloc(d_na)) || !ck(dlm.alloc(d_na)) || !ck(dim.alloc(d_na)) || !ck(dwa.alloc(d_na)) ||
         !ck(dmf.alloc(f_na)) || !ck(dmlf.alloc(f_na)) || !ck(dimf.alloc(f_na)) || !ck(dl2m.alloc(f_na)) || !ck(dwaf.alloc(f_na)) || !ck(dq.alloc(d_nb)) ||
         !ck(dlq.alloc(d_nb)) || !ck(dwq.alloc(d_nb)) || !ck(dqf.alloc(f_nb)) || !ck(dl2qh.alloc(f_nb)) ||
-        !ck(dl2ql.alloc(f_nb)) || !ck(dwqf.alloc(f_nb)) ||
+        !ck(dl2ql.alloc(f_nb)) || !ck(dwqf.alloc(f_nb)) || !ck(dqbk.alloc(sizeof(int) * (nqb_ + 1))) ||
+        !ck(dr32.alloc(sizeof(GvRow32) * na_)) ||
         !ck(p64.alloc(sizeof(double) * packed)) || !ck(p32.alloc(sizeof(float) * packed)) ||
         !ck(dbad.alloc(sizeof(int))))
         return bad(POP_ENOMEM, "pop_load_vt_grid: device allocation failed");
@@ -838,12 +1170,13 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
                up(dwaf, wmf.data(), f_na) && up(dq, qv.data(), d_nb) && up(dlq, lqv.data(), d_nb) &&
                up(dwq, wqv.data(), d_nb) && up(dqf, qfv.data(), f_nb) && up(dl2qh, l2qhv.data(), f_nb) &&
                up(dl2ql, l2qlv.data(), f_nb) && up(dwqf, wqfv.data(), f_nb) &&
+               up(dqbk, qbkv.data(), sizeof(int) * (nqb_ + 1)) && up(dr32, r32.data(), sizeof(GvRow32) * na_) &&
                ck(cudaMemsetAsync(dbad.p, 0, sizeof(int), s));
     if (!okc) return bad(POP_ECUDA, "pop_load_vt_grid: copying the nodes failed");
     const int pb = blocks_for((int64_t)packed, 256, 152 * 32);
-    gv_pack_kernel<double><<<pb, 256, 0, s>>>(src, n1, nq, na_, nb_, nbp_, gv_ta<double>(), p64.as<double>(),
+    gv_pack_kernel<double><<<pb, 256, 0, s>>>(src, n1, nq, na_, nb_, nbp_, G64_TA, p64.as<double>(),
                                               dbad.as<int>());
-    gv_pack_kernel<float><<<pb, 256, 0, s>>>(src, n1, nq, na_, nb_, nbp_, gv_ta<float>(), p32.as<float>(),
+    gv_pack_kernel<float><<<pb, 256, 0, s>>>(src, n1, nq, na_, nb_, nbp_, G32_T, p32.as<float>(),
                                              dbad.as<int>());
     if (!ck(cudaGetLastError())) return bad(POP_ECUDA, "pop_load_vt_grid: pack kernel launch failed");
     int hbad = 0;
@@ -876,6 +1209,11 @@ int GridVT::load(int n1, const double* m1_nodes, int nq, const double* q_nodes, 
     l2qh.swap(dl2qh);
     l2ql.swap(dl2ql);
     wqf.swap(dwqf);
+    qbk.swap(dqbk);
+    rows32.swap(dr32);
+    nqb = nqb_;
+    qb0 = qb0_;
+    qbinv = qbinv_;
     pd64.swap(p64);
     pd32.swap(p32);
     n_m1 = n1;
@@ -892,28 +1230,51 @@ cudaError_t GridVT::ensure(int64_t K)
 {
     if (K <= k_cap && slice > 0) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(K, k_cap), 64);
-    const int S = (int)std::min<int64_t>((cap + GV_TL - 1) / GV_TL * GV_TL, GV_SLICE);
-    DevBuf p, u, pt, x, lcb, od;
+    // Columns per slice, a multiple of 128: up to GV_SLICE, fewer on tall grids (the FP32 pair
+    // buffers, 8 na S bytes, up to 1 GiB).
+    const int64_t s_mem = std::max<int64_t>(G32_T, ((int64_t)1 << 30) / (8 * (int64_t)na) / G32_T * G32_T);
+    const int S = (int)std::min<int64_t>(std::min<int64_t>((cap + G32_T - 1) / G32_T * G32_T, GV_SLICE), s_mem);
+    DevBuf p, u, pt, x, lcb, lcb32, od, qu, w, b, mm;
     cudaError_t e;
+    const int n_sl = (int)((cap + S - 1) / S);
     if ((e = p.alloc(sizeof(int32_t) * S)) != cudaSuccess) return e;
-    if ((e = od.alloc(sizeof(int32_t) * (size_t)(na / gv_ta<double>()))) != cudaSuccess) return e;
+    if ((e = od.alloc(sizeof(int32_t) * (size_t)(na / G64_TA))) != cudaSuccess) return e;
     if ((e = lcb.alloc(sizeof(GvLam) * S)) != cudaSuccess) return e;
+    if ((e = lcb32.alloc(sizeof(GvCol32) * S)) != cudaSuccess) return e;
     if ((e = u.alloc(sizeof(double) * (size_t)S * nbp)) != cudaSuccess) return e;
-    // Row tiles: na / 32 in the FP64 form, na / 64 in the FP32 form.
-    if ((e = pt.alloc(sizeof(double) * (size_t)(na / gv_ta<double>()) * S)) != cudaSuccess) return e;
+    // Partial sums: na / 32 row tiles in the FP64 form, na / 128 row tiles x 4 q parts in the FP32 form.
+    static_assert(G32_QP * G64_TA <= G32_T, "the FP32 partial sums fit the FP64 rows");
+    if ((e = pt.alloc(sizeof(double) * (size_t)(na / G64_TA) * S)) != cudaSuccess) return e;
     if ((e = x.alloc(sizeof(double) * cap)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(gv_main_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)main_smem(0))) != cudaSuccess)
+    if ((e = qu.alloc(sizeof(unsigned) * n_sl)) != cudaSuccess) return e;
+    // FP32 row factors and support edges of every (row, column) pair of a slice.
+    if ((e = w.alloc(sizeof(float) * (size_t)na * S)) != cudaSuccess) return e;
+    if ((e = b.alloc(sizeof(int) * (size_t)na * S)) != cudaSuccess) return e;
+    if ((e = mm.alloc(sizeof(int2) * 8 * (size_t)(na / G32_T) * (S / G32_T))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(gv_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g64_smem())) !=
+        cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(gv_main_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)main_smem(1))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(gv_main32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g32_smem())) !=
+        cudaSuccess)
         return e;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gv_main32_kernel, GV_THREADS, g32_smem())) !=
+            cudaSuccess)
+        return e;
+    g32_ctas = std::max(1, n_sm * per_sm);
     if ((e = cudaFuncSetAttribute(gv_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem(S))) !=
         cudaSuccess)
         return e;
     perm.swap(p);
     order.swap(od);
+    queue.swap(qu);
+    wg.swap(w);
+    b0g.swap(b);
+    wmm.swap(mm);
     lamc.swap(lcb);
+    lamc32.swap(lcb32);
     U.swap(u);
     part.swap(pt);
     xi.swap(x);
@@ -927,41 +1288,51 @@ cudaError_t GridVT::enqueue(int mode, const double* lambda, int n_params, const 
 {
     if (K_cap <= 0) return cudaSuccess;
     if (K_cap > k_cap || slice <= 0) return cudaErrorInvalidValue;
-    const GvNodes g{m1.as<double>(), lnm1.as<double>(),  invm1.as<double>(), wa.as<double>(),
-                    m1f.as<float>(), m1lf.as<float>(),   invm1f.as<float>(), l2m1f.as<float>(),
-                    waf.as<float>(), q.as<double>(),     lnq.as<double>(),   qf.as<float>(),
-                    l2qh.as<float>(), l2ql.as<float>(),  wqf.as<float>(),    na,
-                    nb,              nbp};
+    const GvNodes g{m1.as<double>(), lnm1.as<double>(), invm1.as<double>(), wa.as<double>(), m1f.as<float>(),
+                    m1lf.as<float>(), invm1f.as<float>(), l2m1f.as<float>(), waf.as<float>(), q.as<double>(),
+                    lnq.as<double>(), qf.as<float>(), l2qh.as<float>(), l2ql.as<float>(), wqf.as<float>(),
+                    qbk.as<int>(), qb0, qbinv, nqb, na, nb, nbp};
     const double2* tb = tab.as<double2>();
     GvLam* lcp = lamc.as<GvLam>();
     const int n_sl = (int)((K_cap + slice - 1) / slice);
     cudaError_t e;
     if (timed && (e = cudaEventRecordWithFlags(ev0, s, rec)) != cudaSuccess) return e;
+    if (mode != 0 && (e = cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * n_sl, s)) != cudaSuccess) return e;
     for (int sl = 0; sl < n_sl; ++sl) {
         const int64_t s0 = (int64_t)sl * slice;
         gv_sort_kernel<<<1, 1024, sort_smem(slice), s>>>(lambda, n_params, dK, s0, slice, perm.as<int32_t>());
-        gv_lamc_kernel<<<(slice + 31) / 32, 32, 0, s>>>(lambda, n_params, perm.as<int32_t>(), dK, s0, slice, lcp);
+        gv_lamc_kernel<<<(slice + 31) / 32, 32, 0, s>>>(lambda, n_params, perm.as<int32_t>(), dK, s0, slice, lcp,
+                                                        lamc32.as<GvCol32>());
         const int ub = blocks_for((int64_t)slice * nbp, 256, 152 * 16);
         if (mode == 0)
-            gv_u_kernel<double><<<ub, 256, 0, s>>>(g, wq.as<double>(), lcp, dK, s0, slice, tb, kc, U.as<double>());
+            gv_u_kernel<<<ub, 256, 0, s>>>(g, wq.as<double>(), lcp, dK, s0, slice, tb, kc, U.as<double>());
         else
-            gv_u_kernel<float><<<ub, 256, 0, s>>>(g, wq.as<double>(), lcp, dK, s0, slice, tb, kc, U.as<float>());
-        const int ta = mode == 0 ? gv_ta<double>() : gv_ta<float>();
+            gv_u32_kernel<<<ub, 256, 0, s>>>(g, lcp, dK, s0, slice, U.as<float>());
+        const int ta = mode == 0 ? G64_TA : G32_T;
         const int n_rt = na / ta;
         gv_order_kernel<<<1, 1024, 0, s>>>(g, lcp, dK, s0, slice, ta, order.as<int32_t>());
         if (timed && sl == 0 && (e = cudaEventRecordWithFlags(ev1, s, rec)) != cudaSuccess) return e;
-        const unsigned grid = (unsigned)n_rt * (unsigned)(slice / GV_TL);
-        if (mode == 0)
-            gv_main_kernel<double><<<grid, GV_THREADS, main_smem(0), s>>>(g, pd64.as<double>(), U.as<double>(), lcp,
-                                                                         order.as<int32_t>(), dK, s0, slice, tb, kc,
-                                                                         part.as<double>(), err.as<int>());
-        else
-            gv_main_kernel<float><<<grid, GV_THREADS, main_smem(1), s>>>(g, pd32.as<float>(), U.as<float>(), lcp,
-                                                                        order.as<int32_t>(), dK, s0, slice, tb, kc,
-                                                                        part.as<double>(), err.as<int>());
+        if (mode == 0) {
+            const unsigned grid = (unsigned)n_rt * (unsigned)(slice / GV_TL);
+            gv_main_kernel<<<grid, GV_THREADS, g64_smem(), s>>>(g, pd64.as<double>(), U.as<double>(), lcp,
+                                                               order.as<int32_t>(), dK, s0, slice, tb, kc,
+                                                               part.as<double>(), err.as<int>());
+        } else {
+            if ((e = cudaMemsetAsync(wmm.p, 0xff, sizeof(int2) * 8 * (size_t)n_rt * (slice / G32_T), s)) !=
+                cudaSuccess)
+                return e;
+            gv_setup32_kernel<<<blocks_for((int64_t)na * slice, 256, 152 * 32), 256, 0, s>>>(
+                g, rows32.as<GvRow32>(), lamc32.as<GvCol32>(), dK, s0, slice, wg.as<float>(), b0g.as<int>(),
+                wmm.as<int2>());
+            const unsigned items = (unsigned)n_rt * (unsigned)(slice / G32_T) * G32_QP;
+            gv_main32_kernel<<<std::min<unsigned>(items, (unsigned)g32_ctas), GV_THREADS, g32_smem(), s>>>(
+                g, pd32.as<float>(), U.as<float>(), wg.as<float>(), b0g.as<int>(), wmm.as<int2>(), order.as<int32_t>(),
+                dK, s0, slice,
+                queue.as<unsigned>() + sl, part.as<double>(), err.as<int>());
+        }
         if (timed && sl == 0 && (e = cudaEventRecordWithFlags(ev2, s, rec)) != cudaSuccess) return e;
-        gv_reduce_kernel<<<(slice + 7) / 8, 256, 0, s>>>(part.as<double>(), n_rt, perm.as<int32_t>(), dK, s0, slice,
-                                                         xi.as<double>());
+        gv_reduce_kernel<<<(slice + 7) / 8, 256, 0, s>>>(part.as<double>(), mode == 0 ? n_rt : n_rt * G32_QP,
+                                                         perm.as<int32_t>(), dK, s0, slice, xi.as<double>());
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (timed && (e = cudaEventRecordWithFlags(ev3, s, rec)) != cudaSuccess) return e;

@@ -22,7 +22,7 @@
 
 namespace pop {
 
-constexpr int GV_ROW_PAD = 64; // m1 rows are padded to a multiple of this (every row tile height divides it)
+constexpr int GV_ROW_PAD = 128; // m1 rows are padded to a multiple of this (every row tile height divides it)
 constexpr int GV_TL = 64;      // Lambda columns per CTA tile
 constexpr int GV_BC = 32;      // q nodes per staged chunk
 constexpr int GV_SLICE = 8192; // Lambda columns per slice (bounds the U scratch)
@@ -38,7 +38,11 @@ struct GridVT {
     DevBuf q, lnq, wq;           // FP64 [nbp]: nodes, ln q, trapezoid weights
     DevBuf qf;                   // FP32 [nbp]: nodes (first guess of the support edge)
     DevBuf l2qh, l2ql, wqf;      // FP32 [nbp]: log2 q as a (hi, lo) pair, trapezoid weights
-    DevBuf pd64, pd32;           // pdet packed in row tiles [na / TA][nbp][TA], TA = 32 (FP64) or 64 (FP32)
+    DevBuf qbk;                  // [nqb + 1] first q node of each bin of the support-edge search
+    DevBuf rows32;               // [na] FP32 form's per-row constants, packed
+    float qb0 = 0.0f, qbinv = 0.0f;
+    int nqb = 1;
+    DevBuf pd64, pd32;           // pdet packed in row tiles [na / TA][nbp][TA], TA = 32 (FP64) or 128 (FP32)
     DevBuf tab;                  // 2^(j/2048) as (hi, lo) for the FP64 exponentials
     ExpConsts kc{};
 
@@ -46,6 +50,10 @@ struct GridVT {
     int64_t k_cap = 0;
     int slice = 0;          // columns per slice, a multiple of GV_TL
     DevBuf perm, lamc, order, U, part, xi, err;  // lamc: per-column constants; order: row tiles, heaviest first
+    DevBuf lamc32;                               // per-column constants of the FP32 form, packed
+    DevBuf queue;                                // FP32 contraction: one item counter per slice
+    DevBuf wg, b0g, wmm;                         // FP32 contraction: W and b0 of every pair of a slice, edge ranges
+    int g32_ctas = 0;                            // resident CTAs of the FP32 contraction (persistent grid)
     // Standalone evaluation (pop_xi_grid): own Lambda, K and outputs.
     int64_t k_cap_own = 0;
     DevBuf own_lambda, own_K, own_lnxi, own_flags;
