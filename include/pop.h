@@ -328,6 +328,15 @@ int pop_wait_check(pop_ctx* ctx, int arrive, int polls);
  * device, POP_ECUDA when a CUDA call fails. */
 int pop_pipe_rates(int device, double* rates);
 
+/* pop_pipe_rates with more rates: rates[0..n_rates) of, in order, the four above,
+ *   rates[4] FP32 lanes of packed fma.rn.f32x2 per SM clock,
+ *   rates[5] warp-wide 16-byte shared loads (ld.shared.v4, 32 distinct addresses) per SM clock,
+ *   rates[6] the same with 4 distinct addresses (8 lanes on each word).
+ * n_rates is clamped to 7; rates: a host array of n_rates doubles, owned by the caller.
+ * Synchronous; POP_EINVAL for a NULL rates, a negative device or n_rates < 1, POP_ECUDA when
+ * a CUDA call fails; restores the calling thread's current device. */
+int pop_pipe_rates_n(int device, double* rates, int n_rates);
+
 /* ------------------------------------------------------------------ ln xi surrogate
  * The paper announces a learned selection term that includes spin effects in
  * VT at no extra run-time cost (Sec. "Population acceleration", right after the

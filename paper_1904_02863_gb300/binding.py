@@ -29,7 +29,7 @@ EXPORTS = (
     "pop_create", "pop_destroy", "pop_last_error", "pop_status_string", "pop_version",
     "pop_validate_events", "pop_load_events", "pop_load_injections", "pop_loglik",
     "pop_set_tiling", "pop_get_tiling", "pop_autotune", "pop_set_graphs", "pop_last_kernel_ms",
-    "pop_loglik_f64_noalloc", "pop_math_check", "pop_wait_check", "pop_pipe_rates",
+    "pop_loglik_f64_noalloc", "pop_math_check", "pop_wait_check", "pop_pipe_rates", "pop_pipe_rates_n",
     "pop_xi_surrogate_train", "pop_xi_surrogate_info", "pop_xi_surrogate_infer", "pop_xi_surrogate_save",
     "pop_xi_surrogate_load", "pop_mlp_set_params", "pop_mlp_get_params", "pop_mlp_forward", "pop_mlp_gradients",
     "pop_mlp_train_step", "pop_mlp_gemm_check",
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "pop_math_check": (i32, [vp, i32, i64, vp, vp, i32]),
         "pop_wait_check": (i32, [vp, i32, i32]),
         "pop_pipe_rates": (i32, [i32, vp]),
+        "pop_pipe_rates_n": (i32, [i32, vp, i32]),
         "pop_xi_surrogate_train": (i32, [vp, i64, d, ctypes.c_uint64, vp, vp, i32, i32, ctypes.POINTER(d)]),
         "pop_xi_surrogate_info": (i32, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                         ctypes.POINTER(i32)]),
@@ -329,11 +330,16 @@ def pop_wait_check(ctx, arrive, polls):
     _check(ctx, load_library().pop_wait_check(ctx, int(bool(arrive)), int(polls)))
 
 
+PIPE_RATE_NAMES = ("dfma", "ffma", "ex2", "rcp", "ffma2_lanes", "lds128_32addr", "lds128_4addr")
+
+
 def pop_pipe_rates(device=0):
-    """Measured thread operations per SM clock: {"dfma", "ffma", "ex2", "rcp"}."""
-    r = np.zeros(4)
-    _check(None, load_library().pop_pipe_rates(int(device), r.ctypes.data_as(ctypes.c_void_p)))
-    return dict(zip(("dfma", "ffma", "ex2", "rcp"), (float(v) for v in r)))
+    """Measured rates per SM clock: thread operations for "dfma", "ffma", "ex2", "rcp"; FP32 lanes
+    of packed fma.rn.f32x2 ("ffma2_lanes"); warp-wide 16-byte shared loads with 32 and 4 distinct
+    addresses ("lds128_32addr", "lds128_4addr")."""
+    r = np.zeros(len(PIPE_RATE_NAMES))
+    _check(None, load_library().pop_pipe_rates_n(int(device), r.ctypes.data_as(ctypes.c_void_p), r.size))
+    return dict(zip(PIPE_RATE_NAMES, (float(v) for v in r)))
 
 
 def pop_math_check(ctx, fn, x):

@@ -1,10 +1,13 @@
-"""The pipe-rate diagnostic behind the weight kernels' rooflines (pop_pipe_rates): thread
-operations per SM clock for FP64 fma, FP32 fma, MUFU ex2 and MUFU rcp.
+"""The pipe-rate diagnostic behind the kernels' rooflines (pop_pipe_rates): thread operations
+per SM clock for FP64 fma, FP32 fma, MUFU ex2 and MUFU rcp, FP32 lanes of the packed fma, and
+warp-wide 16-byte shared loads per SM clock.
 
 GB300 has 2 FP64 fma lanes and 128 FP32 fma lanes per SM per clock, so the measured rates must
 lie at or below those and above half of them; the MUFU rates must order ex2 >= rcp and lie
-within the 4..64 per clock that any recent SM has.  A rate far outside means the chains were
-optimised away or the CTAs shared SMs."""
+within the 4..64 per clock that any recent SM has.  A 16-byte load of a whole warp moves 512
+bytes, so at 128 bytes per clock it takes at least 4 clocks when the 32 addresses differ, and
+sharing addresses cannot make it slower.  A rate far outside means the chains were optimised
+away or the CTAs shared SMs."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -28,5 +31,8 @@ def test_pipe_rates(B):
     assert 1.0 <= r["dfma"] <= 2.05, r
     assert 64.0 <= r["ffma"] <= 129.0, r
     assert 4.0 <= r["rcp"] <= r["ex2"] <= 64.0, r
+    assert 64.0 <= r["ffma2_lanes"] <= 129.0, r
+    assert 0.1 <= r["lds128_32addr"] <= 0.26, r
+    assert r["lds128_32addr"] * 0.95 <= r["lds128_4addr"] <= 1.01, r
     with pytest.raises(B.PopError):
         B.pop_pipe_rates(-1)
