@@ -27,7 +27,16 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int CHUNK_LEN = 4096;  // samples per work chunk (events are split at this length)
+// Samples per work chunk (events are split at this length): 4096, halved down to 256 while a
+// set would have fewer than about one chunk per SM, so that small sets still fill the GPU.
+constexpr int CHUNK_LEN_MAX = 4096, CHUNK_LEN_MIN = 256, CHUNK_TARGET = 152;
+
+int chunk_len_for(int64_t n)
+{
+    int len = CHUNK_LEN_MAX;
+    while (len > CHUNK_LEN_MIN && n / len < CHUNK_TARGET) len >>= 1;
+    return len;
+}
 constexpr int64_t ALIGN_ELEMS = 64;
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -38,10 +47,12 @@ struct SampleSet {
     int64_t stride = 0;
     int n_dims = 0;
     int storage = 0;
+    int chunk_len = CHUNK_LEN_MAX;  // samples per work chunk of this set
     DevBuf f64, f32, m2, m1d, m1sort, m1pos;
     void swap(SampleSet& o)
     {
         std::swap(n, o.n);
+        std::swap(chunk_len, o.chunk_len);
         std::swap(stride, o.stride);
         std::swap(n_dims, o.n_dims);
         std::swap(storage, o.storage);
@@ -192,6 +203,8 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
     out.n = n;
     out.n_dims = n_dims;
     out.storage = storage;
+    out.chunk_len = chunk_len_for(n);
+    const int64_t cl = out.chunk_len;
     out.stride = round_up(std::max<int64_t>(n, 1), ALIGN_ELEMS);
     const double* th = theta;
     const double* pr = prior;
@@ -213,12 +226,12 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
         CK(cudaMemcpyAsync(dperm.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream),
            "copy order");
         if (storage & POP_STORE_F32) {
-            // Chunks are the CHUNK_LEN pieces of every segment (build_chunks makes the same cut).
+            // Chunks are the chunk_len pieces of every segment (build_chunks makes the same cut).
             std::vector<std::pair<double, uint2>> e((size_t)n);
             uint32_t chunk = 0;
             for (size_t sg = 0; sg + 1 < seg.size(); ++sg)
-                for (int64_t c0 = seg[sg]; c0 < seg[sg + 1]; c0 += CHUNK_LEN, ++chunk) {
-                    const int64_t len = std::min<int64_t>(CHUNK_LEN, seg[sg + 1] - c0);
+                for (int64_t c0 = seg[sg]; c0 < seg[sg + 1]; c0 += cl, ++chunk) {
+                    const int64_t len = std::min<int64_t>(cl, seg[sg + 1] - c0);
                     for (int64_t i = c0; i < c0 + len; ++i) {
                         const double* v = hth + perm[i] * n_dims;
                         e[i] = {live_sample(v, n_dims) ? v[0] : 0.0, make_uint2((uint32_t)i, chunk)};
@@ -286,13 +299,13 @@ int build_chunks(pop_ctx* c)
     const int64_t N = (int64_t)c->h_offsets.size() - 1;
     for (int64_t i = 0; i < N; ++i) {
         ecb[i] = (int32_t)ch.size();
-        for (int64_t s = c->h_offsets[i]; s < c->h_offsets[i + 1]; s += CHUNK_LEN)
-            ch.push_back(Chunk{s, (int32_t)std::min<int64_t>(CHUNK_LEN, c->h_offsets[i + 1] - s), 0});
+        for (int64_t s = c->h_offsets[i]; s < c->h_offsets[i + 1]; s += c->ev.chunk_len)
+            ch.push_back(Chunk{s, (int32_t)std::min<int64_t>(c->ev.chunk_len, c->h_offsets[i + 1] - s), 0});
     }
     ecb[N] = (int32_t)ch.size();
     const int32_t n_ev = (int32_t)ch.size();
-    for (int64_t s = 0; s < c->inj.n; s += CHUNK_LEN)
-        ch.push_back(Chunk{s, (int32_t)std::min<int64_t>(CHUNK_LEN, c->inj.n - s), 1});
+    for (int64_t s = 0; s < c->inj.n; s += c->inj.chunk_len)
+        ch.push_back(Chunk{s, (int32_t)std::min<int64_t>(c->inj.chunk_len, c->inj.n - s), 1});
     if (ch.size() > (size_t)INT32_MAX / 2) return fail(c, POP_EINVAL, "too many work chunks");
     DevBuf dch, decb;
     CK(dch.alloc(sizeof(Chunk) * ch.size()), "cudaMalloc(chunks)");
