@@ -14,7 +14,9 @@ wq 2^(beta log2 q) with an FP32 exponent |arg| < 20 (~14) and exp2f (2 ulp)
 and two roundings (24 in all); the FP32 row factor W (exponents |arg| < 30
 rounded three times, ~62, exp2f, log1pf, expm1f, the reciprocal and four
 products, 81 in all); the FP32 sum of a 32-node chunk (31) and the FP32
-running sum over the chunks (n_chunks).
+running sum over the chunks (n_chunks; the kernel runs one per quarter of the q
+range, which only shortens it).  Its row combine (exact products, float-float
+sums) is as accurate as the FP64 one.
 """
 import numpy as np
 import pytest
