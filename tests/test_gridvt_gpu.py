@@ -127,7 +127,8 @@ def test_grid_column_order_does_not_change_results(B, ctx):
 
 
 def test_grid_two_slices_and_uneven_batches(B, ctx, oracle):
-    """K above one 8192-column slice, then smaller batches reusing the scratch."""
+    """K above one 8192-column slice, then smaller batches reusing the scratch (FP32: partial
+    128-column tiles, several q parts of a 33-node axis, the per-slice work queues)."""
     from paper_1904_02863_gb300 import synth
     m1 = np.linspace(3.0, 100.0, 70)
     q = np.linspace(0.05, 1.0, 33)
@@ -136,8 +137,11 @@ def test_grid_two_slices_and_uneven_batches(B, ctx, oracle):
     lam = synth.make_lambdas(8192 + 77, 12, seed=703)
     ref = oracle.xi_grid(m1, q, pdet, lam)
     check(B.pop_xi_grid(ctx, lam, B.POP_MODE_F64), ref, f64_tol(m1.size * q.size, 33))
-    for K in (1, 63, 65, 1000):
-        check(B.pop_xi_grid(ctx, lam[:K], B.POP_MODE_F64), (ref[0][:K], ref[1][:K]), f64_tol(m1.size * q.size, 33))
+    check(B.pop_xi_grid(ctx, lam, B.POP_MODE_F32), ref, f32_tol(m1.size * q.size, 33))
+    for K in (1, 63, 65, 127, 129, 1000):
+        sub = (ref[0][:K], ref[1][:K])
+        check(B.pop_xi_grid(ctx, lam[:K], B.POP_MODE_F64), sub, f64_tol(m1.size * q.size, 33))
+        check(B.pop_xi_grid(ctx, lam[:K], B.POP_MODE_F32), sub, f32_tol(m1.size * q.size, 33))
 
 
 def test_grid_from_device_tensors(B, ctx, oracle):

@@ -36,3 +36,16 @@ def test_pipe_rates(B):
     assert r["lds128_32addr"] * 0.95 <= r["lds128_4addr"] <= 1.01, r
     with pytest.raises(B.PopError):
         B.pop_pipe_rates(-1)
+
+
+def test_pipe_rates_n_writes_only_what_is_asked(B):
+    import ctypes
+    import numpy as np
+    lib = B.load_library()
+    r = np.full(9, -7.0)
+    assert lib.pop_pipe_rates_n(0, r.ctypes.data_as(ctypes.c_void_p), 2) == B.POP_OK
+    assert 1.0 <= r[0] <= 2.05 and 64.0 <= r[1] <= 129.0 and (r[2:] == -7.0).all(), r
+    assert lib.pop_pipe_rates_n(0, r.ctypes.data_as(ctypes.c_void_p), 9) == B.POP_OK   # clamped to 7
+    assert (r[7:] == -7.0).all() and 0.1 <= r[5] <= 0.26, r
+    assert lib.pop_pipe_rates_n(0, r.ctypes.data_as(ctypes.c_void_p), 0) == B.POP_EINVAL
+    assert lib.pop_pipe_rates_n(0, None, 3) == B.POP_EINVAL
