@@ -110,6 +110,7 @@ struct pop_ctx {
     int n_params_cap = 12;
     DevBuf d_lambda, d_c64, d_c32, d_part, d_part2, d_lnL, d_lnxi, d_neff, d_flags, d_K;
     DevBuf d_parts;          // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2 (pop_loglik_parts)
+    DevBuf d_zint;           // [K]: the redshift normalisation of each Lambda (prologue)
     DevBuf d_lamg, d_gpart, d_grad;  // gradient: per-Lambda constants, [K][n_chunks][13] sums, [K][12]
     int64_t grad_cap = 0;
     int32_t grad_chunks = -1;
@@ -348,6 +349,9 @@ int ensure_scratch(pop_ctx* c, int64_t K)
     CK(queue.alloc(sizeof(unsigned long long)), "cudaMalloc(queue)");
     CK(slnxi.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnxi)");
     CK(slnneff.alloc(sizeof(double) * cap), "cudaMalloc(surrogate lnneff)");
+    DevBuf zint;
+    CK(zint.alloc(sizeof(double) * cap), "cudaMalloc(redshift normalisation)");
+    c->d_zint.swap(zint);
     c->d_need.swap(need);
     c->d_order.swap(order);
     c->d_nmc.swap(nmc);
@@ -406,7 +410,7 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
     WorkDesc wd{c->d_chunks.as<Chunk>(), n_items, c->n_ev_chunks, c->ev.n_dims == 7};
     CK(cudaEventRecordWithFlags(c->ev_t0, c->stream, rec), "event");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
-                       c->d_c32.as<LamF32>(), c->stream, c->d_ztab.as<double2>(),
+                       c->d_c32.as<LamF32>(), c->d_zint.as<double>(), c->stream, c->d_ztab.as<double2>(),
                        c->d_exptab.as<double2>(), c->expc), "prologue");
     SurrogateXi sx{nullptr, nullptr, nullptr};
     if (mode == POP_MODE_F32_SURROGATE) {
@@ -1207,7 +1211,7 @@ int pop_autotune(pop_ctx* c, int mode, int64_t K, const char* cache_path)
     set_k_kernel<<<1, 1, 0, c->stream>>>(c->d_K.as<int64_t>(), K);
     CK(cudaGetLastError(), "set K");
     CK(launch_prologue(c->d_lambda.as<double>(), c->d_K.as<int64_t>(), c->k_cap, n_params, c->d_c64.as<LamF64>(),
-                       c->d_c32.as<LamF32>(), c->stream, c->d_ztab.as<double2>(),
+                       c->d_c32.as<LamF32>(), c->d_zint.as<double>(), c->stream, c->d_ztab.as<double2>(),
                        c->d_exptab.as<double2>(), c->expc), "prologue");
     if (mode == POP_MODE_F32)
         CK(launch_lam_order(c->d_c32.as<LamF32>(), c->d_K.as<int64_t>(), nullptr, c->k_cap, c->d_order.as<int32_t>(),

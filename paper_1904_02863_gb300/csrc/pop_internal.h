@@ -117,8 +117,10 @@ cudaError_t launch_pack_f32(const double* theta, const double* prior, const int6
 // ztab (REDSHIFT_NODES entries, build_z_table) and exptab make the redshift trapezoid one
 // table-driven exponential per node; with ztab NULL it is evaluated directly.
 constexpr int REDSHIFT_NODES = 1024;
+// zint: device scratch of K_cap doubles for the redshift normalisation (used, and required,
+// when n_params == 12).
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params,
-                            LamF64* c64, LamF32* c32, cudaStream_t s, const double2* ztab = nullptr,
+                            LamF64* c64, LamF32* c32, double* zint, cudaStream_t s, const double2* ztab = nullptr,
                             const double2* exptab = nullptr, ExpConsts kc = ExpConsts{});
 // Host: node i of the redshift trapezoid on [0, 2]: (ln(1 + z_i), w_i z_i^2), w = 1/2 at the ends.
 void build_z_table(double2* tab);

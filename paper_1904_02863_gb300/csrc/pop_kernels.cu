@@ -114,40 +114,46 @@ __global__ void pack_f32_kernel(const double* __restrict__ theta, const double* 
 
 __device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
 
-// Per-Lambda constants.  One warp per Lambda: the lanes share the 1024-node
-// redshift trapezoid, lane 0 does the rest.  With ztab (node i: ln(1 + z_i) and its
-// trapezoid weight times z_i^2) each node costs one table-driven exponential; without it
-// (callers that hold no tables) the logarithm and exponential are evaluated directly.
-__global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
-                                LamF64* __restrict__ c64, LamF32* __restrict__ c32, const double2* __restrict__ ztab,
-                                const double2* __restrict__ exptab, ExpConsts kc)
+// Redshift normalisation per Lambda, I(kappa) = trapezoid of (1+z)^(kappa-1) z^2 on
+// z_k = 2k/1023: one warp per Lambda, the lanes share the 1024 nodes.  With ztab (node i:
+// ln(1 + z_i) and its trapezoid weight times z_i^2) each node costs one table-driven
+// exponential; without it (callers that hold no tables) the logarithm and exponential are
+// evaluated directly.
+__global__ void zint_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
+                            const double2* __restrict__ ztab, const double2* __restrict__ exptab, ExpConsts kc,
+                            double* __restrict__ zint)
 {
     const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= *dK) return;
+    const double km1 = lambda[k * n_params + P_KAPPA] - 1.0;
+    double zs = 0.0;
+    if (ztab) {
+        for (int i = lane; i < Z_NODES; i += 32) {
+            const double2 t = ztab[i];
+            zs = fma(t.y, exp_tab(km1 * t.x, exptab, kc), zs);
+        }
+    } else {
+        for (int i = lane; i < Z_NODES; i += 32) {
+            double z = 2.0 * i / (Z_NODES - 1);
+            double f = exp(km1 * log1p(z)) * z * z;
+            zs += (i == 0 || i == Z_NODES - 1) ? 0.5 * f : f;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
+    if (lane == 0) zint[k] = zs * (2.0 / (Z_NODES - 1));
+}
+
+// Per-Lambda constants, one thread per Lambda (the special functions of a warp's 32 Lambda
+// share each FP64 instruction); zint from zint_kernel when the model has redshift.
+__global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
+                                LamF64* __restrict__ c64, LamF32* __restrict__ c32, const double* __restrict__ zint)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= *dK) return;
     const double* L = lambda + k * n_params;
     const bool has_z = n_params == 12;
-
-    // I(kappa) = trapezoid of (1+z)^(kappa-1) z^2 on z_k = 2k/1023.
-    double zs = 0.0;
-    if (has_z) {
-        const double km1 = L[P_KAPPA] - 1.0;
-        if (ztab) {
-            for (int i = lane; i < Z_NODES; i += 32) {
-                const double2 t = ztab[i];
-                zs = fma(t.y, exp_tab(km1 * t.x, exptab, kc), zs);
-            }
-        } else {
-            for (int i = lane; i < Z_NODES; i += 32) {
-                double z = 2.0 * i / (Z_NODES - 1);
-                double f = exp(km1 * log1p(z)) * z * z;
-                zs += (i == 0 || i == Z_NODES - 1) ? 0.5 * f : f;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
-        zs *= 2.0 / (Z_NODES - 1);
-    }
-    if (lane != 0) return;
+    const double zs = has_z ? zint[k] : 0.0;
 
     bool valid = true;
     for (int p = 0; p < n_params; ++p) valid = valid && finite_d(L[p]);
@@ -377,12 +383,16 @@ cudaError_t launch_pack_f32(const double* theta, const double* prior, const int6
 }
 
 cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_cap, int n_params, LamF64* c64,
-                            LamF32* c32, cudaStream_t s, const double2* ztab, const double2* exptab, ExpConsts kc)
+                            LamF32* c32, double* zint, cudaStream_t s, const double2* ztab, const double2* exptab,
+                            ExpConsts kc)
 {
     if (K_cap <= 0) return cudaSuccess;
-    const int threads = 256;
-    const int blocks = (int)((K_cap * 32 + threads - 1) / threads);
-    prologue_kernel<<<blocks, threads, 0, s>>>(lambda, dK, n_params, c64, c32, ztab, exptab, kc);
+    if (n_params == 12) {
+        if (!zint) return cudaErrorInvalidValue;
+        zint_kernel<<<(unsigned)((K_cap * 32 + 255) / 256), 256, 0, s>>>(lambda, dK, n_params, ztab, exptab, kc, zint);
+    }
+    // Blocks of one warp, so that a small batch still spreads over many SMs.
+    prologue_kernel<<<(unsigned)((K_cap + 31) / 32), 32, 0, s>>>(lambda, dK, n_params, c64, c32, zint);
     return cudaGetLastError();
 }
 

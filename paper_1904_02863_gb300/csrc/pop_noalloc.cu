@@ -49,7 +49,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the scratch sections for a problem size.
 struct Layout {
-    size_t k, bad, c64, c32, ecb, part, part2, total;
+    size_t k, bad, c64, c32, zint, ecb, part, part2, total;
 };
 
 Layout layout(int64_t n_events, int64_t n_inj_chunks, int64_t K)
@@ -59,7 +59,8 @@ Layout layout(int64_t n_events, int64_t n_inj_chunks, int64_t K)
     L.bad = 8;
     L.c64 = 256;
     L.c32 = align256(L.c64 + sizeof(LamF64) * (size_t)K);
-    L.ecb = align256(L.c32 + sizeof(LamF32) * (size_t)K);
+    L.zint = align256(L.c32 + sizeof(LamF32) * (size_t)K);
+    L.ecb = align256(L.zint + sizeof(double) * (size_t)K);
     L.part = align256(L.ecb + sizeof(int32_t) * (size_t)(n_events + 1));
     L.part2 = align256(L.part + sizeof(double) * (size_t)K * (size_t)(n_events + n_inj_chunks));
     L.total = L.part2 + sizeof(double) * (size_t)K * (size_t)n_inj_chunks;
@@ -317,6 +318,7 @@ extern "C" int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events
     unsigned long long* bad = reinterpret_cast<unsigned long long*>(base + Lo.bad);
     LamF64* c64 = reinterpret_cast<LamF64*>(base + Lo.c64);
     LamF32* c32 = reinterpret_cast<LamF32*>(base + Lo.c32);
+    double* zint = reinterpret_cast<double*>(base + Lo.zint);
     int32_t* ecb = reinterpret_cast<int32_t*>(base + Lo.ecb);
     double* part = reinterpret_cast<double*>(base + Lo.part);
     double* part2 = reinterpret_cast<double*>(base + Lo.part2);
@@ -324,7 +326,7 @@ extern "C" int pop_loglik_f64_noalloc(int device, void* stream, int64_t n_events
     setup_kernel<<<(unsigned)((n_events + 1 + 255) / 256), 256, 0, s>>>(dK, K, bad, ecb, n_events, offsets,
                                                                          n_samples);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(POP_ECUDA, cudaGetErrorString(e));
-    if ((e = launch_prologue(lambda, dK, K, n_params, c64, c32, s)) != cudaSuccess)
+    if ((e = launch_prologue(lambda, dK, K, n_params, c64, c32, zint, s)) != cudaSuccess)
         return fail(POP_ECUDA, cudaGetErrorString(e));
     RawDesc a{{theta, prior}, {inj_theta, p_draw}, offsets, n_events, n_samples, n_found, (int32_t)n_inj_chunks,
               n_dims};
