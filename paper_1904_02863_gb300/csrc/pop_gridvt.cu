@@ -686,8 +686,9 @@ gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restric
 // columns and one of 4 fixed parts of the q range, the top parts (the heaviest) first.
 // A thread holds 8 rows x 8 columns as 32 packed (row, row + 1) accumulator pairs: per q
 // node, two 16-byte shared loads of its 8 pdet values, two of its 8 U values and 32
-// f32x2 FMAs, so that the shared-memory path (16-byte loads at 4 SM cycles per warp) and
-// the FMA pipe are about equally busy.  The rows and columns of a staged chunk are stored
+// f32x2 FMAs, so that the SM's one shared-memory path (a warp's 16-byte load takes 2.5 to
+// 4 SM cycles) stays below the FMA pipe's rate (4 x 4 tiles would cap the FMA pipe at
+// two thirds of it).  The rows and columns of a staged chunk are stored
 // in the order the threads read them (g32_perm).  A warp covers 32 rows x 64 columns and
 // decides per 8-node sub-block, from the lowest and highest support edge of its pairs,
 // whether the sub-block is below every edge (skipped), past every edge (no mask) or in
