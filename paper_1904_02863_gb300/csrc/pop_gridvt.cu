@@ -6,14 +6,13 @@
 // Work layout.  The contraction sum_a W_a sum_{b >= b0} pdet[a, b] U_b runs over
 // tiles of m1 rows x Lambda columns whose chunks of 32 q nodes (packed pdet and U)
 // are staged in shared memory by cp.async.bulk copies that complete on mbarriers.
-// FP64: tiles of 32 rows x 64 columns, one CTA each, 2 x 4 (row, column)
-// accumulators per thread; each thread computes W_a and b0 of its own pairs with
-// the table-driven exp/expm1 of the FP64 weight kernel (its 2^(j/2048) table sits
-// in the stage buffers until the first copy).  FP32: a setup kernel computes W_a
-// (CUDA's exp2f/log1pf/expm1f) and b0 of every pair at full occupancy, then
-// persistent CTAs contract tiles of 128 rows x 128 columns in 4 parts of the q
-// range with 8 x 8 accumulators per thread (see the FP32 section).  The support
-// decisions are FP64 in both forms.
+// In both forms a setup kernel first computes W_a and b0 of every (row, column) pair
+// at full occupancy: FP64 with the table-driven exp/expm1 of the FP64 weight kernel,
+// FP32 with CUDA's exp2f/log1pf/expm1f; the support decisions are FP64 in both.
+// FP64: tiles of 32 rows x 64 columns in 4 parts of the q range, one CTA each, 2 x 4
+// (row, column) accumulators per thread.  FP32: persistent CTAs contract tiles of 128
+// rows x 128 columns in 4 parts of the q range with 8 x 8 accumulators per thread (see
+// the FP32 section).
 // Lambda columns are placed in ascending mmin order (a counting sort per slice)
 // so that the columns of a thread or warp have nearly the same lower q edges:
 // chunks at or past every edge run unmasked, chunks below all of them are
@@ -529,17 +528,50 @@ __device__ __forceinline__ void gv_load(const T* src, T (&v)[N])
 // ---------------------------------------------------------------- FP64 contraction
 // Tile shapes.  2 m1 rows x 4 Lambda columns per thread; a warp is 8 x 4 threads
 // (16 rows x 16 consecutive columns); a CTA is 2 x 4 warps (32 rows x 64 columns).
-// The FP64 pipe (two lanes per SM and clock) binds, so small thread tiles (more CTAs,
-// a shorter wave tail) cost nothing.
-constexpr int G64_RA = 2, G64_TA = 16 * G64_RA, G64_STAGES = 2;
+// The FP64 pipe (two lanes per SM and clock) binds, so small thread tiles cost nothing.
+// A setup kernel computes W_a and b0 of every pair once; the contraction's items are a
+// tile and one of 4 fixed parts of the q range (the top parts, the heaviest, first), which
+// makes the last wave of CTAs short.
+constexpr int G64_RA = 2, G64_TA = 16 * G64_RA, G64_STAGES = 2, G64_QP = 4;
+constexpr int G64_PAIRS = G64_TA * GV_TL;  // pairs of a tile, 8 per thread
 __host__ __device__ constexpr size_t g64_smem() { return (size_t)G64_STAGES * GV_BC * (G64_TA + GV_TL) * sizeof(double); }
 
-// part[rt][r] = sum over the 32 rows of row tile rt of W_a sum_{b >= b0} pdet[a, b] U_b
-// for every column r of the CTA's Lambda tile, FP64 throughout.
+// Thread t of an FP64 contraction CTA: rows 2 ty .. 2 ty + 1, columns 4 tx .. 4 tx + 3.
+__host__ __device__ inline int g64_ty(int t) { return 8 * ((t >> 5) >> 2) + ((t & 31) >> 2); }
+__host__ __device__ inline int g64_tx(int t) { return 4 * ((t >> 5) & 3) + (t & 3); }
+
+// W (w64) and b0 (b0g) of pair k = 4 i + j of thread t of tile (rt, lt) at
+// ((rt * n_lt + lt) * 8 + k) * 256 + t: row 2 ty(t) + i, column 4 tx(t) + j; W = 0 for a pair
+// without support.  The exponential table is staged in shared memory once per block.
+__global__ void __launch_bounds__(GV_THREADS)
+gv_setup64_kernel(GvNodes g, const GvLam* __restrict__ lamc, const int64_t* __restrict__ dK, int64_t slice0, int S,
+                  const double2* __restrict__ tab_g, ExpConsts kc, double* __restrict__ w64, int* __restrict__ b0g)
+{
+    __shared__ double2 tab[EXP_TABLE_SIZE];
+    for (int i = threadIdx.x; i < EXP_TABLE_SIZE; i += GV_THREADS) tab[i] = tab_g[i];
+    __syncthreads();
+    const int n = slice_count(dK, slice0, S);
+    const int n_lt = (n + GV_TL - 1) / GV_TL;
+    const int total = (g.na / G64_TA) * n_lt * G64_PAIRS;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int t = e & (GV_THREADS - 1), k = (e >> 8) & 7, item = e >> 11;
+        const int rt = item / n_lt, lt = item - rt * n_lt;
+        double W;
+        int b0;
+        gv_pair64(g, lamc[lt * GV_TL + g64_tx(t) * 4 + (k & 3)], rt * G64_TA + g64_ty(t) * G64_RA + (k >> 2), tab, kc,
+                  W, b0);
+        w64[e] = b0 < g.nb ? W : 0.0;
+        b0g[e] = b0;
+    }
+}
+static_assert(G64_PAIRS == 8 * GV_THREADS, "setup index layout");
+
+// part[rt * 4 + qp][r] = sum over the 32 rows of row tile rt of W_a sum_{b >= b0} pdet[a, b] U_b
+// over the nodes b of q part qp, for every column r of the CTA's Lambda tile, FP64 throughout.
 __global__ void __launch_bounds__(GV_THREADS, 3)
-gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restrict__ U, const GvLam* __restrict__ lamc,
-               const int32_t* __restrict__ rt_order, const int64_t* __restrict__ dK, int64_t slice0, int S,
-               const double2* __restrict__ tab_g, ExpConsts kc, double* __restrict__ part, int* __restrict__ err)
+gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restrict__ U, const double* __restrict__ w64,
+               const int* __restrict__ b0g, const int32_t* __restrict__ rt_order, const int64_t* __restrict__ dK,
+               int64_t slice0, int S, double* __restrict__ part, int* __restrict__ err)
 {
     using T = double;
     constexpr int RA = G64_RA, STAGES = G64_STAGES, TA = G64_TA;
@@ -549,30 +581,26 @@ gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restric
     T* sp = reinterpret_cast<T*>(gv_dyn);  // [STAGES][BC][TA] pdet
     T* su = sp + STAGES * PD_ELEMS;        // [STAGES][BC][64] U
     __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ GvLam lc[GV_TL];
     __shared__ int s_tmin;
     __shared__ double red[16][GV_TL];
 
     const int n = slice_count(dK, slice0, S);
-    // Linear block index -> (row tile in launch order, Lambda tile).
-    const int n_lt = S / GV_TL;
-    const int rt = rt_order[blockIdx.x / n_lt], lt = blockIdx.x % n_lt;
-    if (lt * GV_TL >= n) return;
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int ty = 8 * (w >> 2) + (lane >> 2);  // 0..15
-    const int tx = 4 * (w & 3) + (lane & 3);    // 0..15
-    if (tid < GV_TL) lc[tid] = lamc[lt * GV_TL + tid];
+    const int n_lt = (n + GV_TL - 1) / GV_TL;
+    const unsigned per_part = (unsigned)(g.na / TA) * (unsigned)n_lt;
+    // Linear block index -> (q part, heaviest parts first; row tile in launch order; Lambda tile).
+    if (blockIdx.x >= per_part * G64_QP) return;
+    const int qp = G64_QP - 1 - (int)(blockIdx.x / per_part);
+    const unsigned rem = blockIdx.x % per_part;
+    const int rt = rt_order[rem / n_lt], lt = (int)(rem % n_lt);
+    const int tid = threadIdx.x, ty = g64_ty(tid), tx = g64_tx(tid);
     if (tid == 0) {
         s_tmin = INT_MAX;
         for (int st = 0; st < STAGES; ++st) gv_bar_init(gv_saddr(&bar[st]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // The exponential table lives in the stage buffers until the first copy.
-    const double2* tab = reinterpret_cast<const double2*>(gv_dyn);
-    static_assert(g64_smem() >= EXP_TABLE_SIZE * sizeof(double2), "the table fits the stages");
-    for (int i = tid; i < EXP_TABLE_SIZE; i += GV_THREADS) reinterpret_cast<double2*>(gv_dyn)[i] = tab_g[i];
     __syncthreads();
 
+    const int64_t pbase = (int64_t)(rt * n_lt + lt) * G64_PAIRS + tid;
     T W[RA][4];
     int b0[RA][4];
     int tmin = INT_MAX, tmax = -1;
@@ -580,24 +608,23 @@ gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restric
     for (int i = 0; i < RA; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int a = rt * TA + ty * RA + i;
-            gv_pair64(g, lc[tx * 4 + j], a, tab, kc, W[i][j], b0[i][j]);
+            W[i][j] = w64[pbase + (4 * i + j) * GV_THREADS];
+            b0[i][j] = b0g[pbase + (4 * i + j) * GV_THREADS];
             if (b0[i][j] < g.nb) {
                 tmin = min(tmin, b0[i][j]);
                 tmax = max(tmax, b0[i][j]);
             }
         }
     if (tmin != INT_MAX) atomicMin(&s_tmin, tmin);
-    // The table reads (generic proxy) are ordered before the bulk copies (async proxy) into the same bytes.
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    double* out = part + (int64_t)rt * S + lt * GV_TL;
-    if (s_tmin >= g.nb) {  // no pair of the tile has support
+    double* out = part + ((int64_t)rt * G64_QP + qp) * S + lt * GV_TL;
+    const int nch = g.nbp / GV_BC;
+    const int cq0 = qp * nch / G64_QP, cq1 = (qp + 1) * nch / G64_QP;
+    const int c0 = max(cq0, s_tmin / GV_BC);  // s_tmin = INT_MAX: no pair of the tile has support
+    if (c0 >= cq1) {
         if (tid < GV_TL) out[tid] = 0.0;
         return;
     }
-    const int nch = g.nbp / GV_BC;
-    const int c0 = s_tmin / GV_BC;
     const T* pd_tile = pd + (int64_t)rt * g.nbp * TA;
     const T* u_tile = U + (int64_t)lt * g.nbp * GV_TL;
     auto issue = [&](int c) {
@@ -608,20 +635,20 @@ gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restric
         gv_bulk_load(gv_saddr(su + st * U_ELEMS), u_tile + (int64_t)c * U_ELEMS, U_BYTES, b);
     };
     if (tid == 0)
-        for (int c = c0; c < nch && c < c0 + STAGES; ++c) issue(c);
+        for (int c = c0; c < cq1 && c < c0 + STAGES; ++c) issue(c);
 
     T acc[RA][4];
 #pragma unroll
     for (int i = 0; i < RA; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int s = c0; s < nch; ++s) {
+    for (int s = c0; s < cq1; ++s) {
         const bool ok = gv_wait(gv_saddr(&bar[(s - c0) % STAGES]), (uint32_t)(((s - c0) / STAGES) & 1));
         if (__syncthreads_or(!ok)) {
             // Give up: flag it, let the copies already issued land (bounded), leave NaN.
             if (tid == 0) {
                 atomicExch(err, 1);
-                for (int d = s; d < nch && d < s + STAGES; ++d)
+                for (int d = s; d < cq1 && d < s + STAGES; ++d)
                     gv_wait(gv_saddr(&bar[(d - c0) % STAGES]), (uint32_t)(((d - c0) / STAGES) & 1));
             }
             __syncthreads();
@@ -660,15 +687,15 @@ gv_main_kernel(GvNodes g, const double* __restrict__ pd, const double* __restric
             }
         }
         __syncthreads();  // the stage is free again
-        if (tid == 0 && s + STAGES < nch) issue(s + STAGES);
+        if (tid == 0 && s + STAGES < cq1) issue(s + STAGES);
     }
 
-    // Fixed-order combine: rows of the thread (i = 0..RA-1), then the 16 row groups.
+    // Fixed-order combine (W = 0 without support): rows of the thread, then the 16 row groups.
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < RA; ++i) t += b0[i][j] < g.nb ? W[i][j] * acc[i][j] : 0.0;
+        for (int i = 0; i < RA; ++i) t += W[i][j] * acc[i][j];
         red[ty][tx * 4 + j] = t;
     }
     __syncthreads();
@@ -1231,9 +1258,9 @@ cudaError_t GridVT::ensure(int64_t K)
 {
     if (K <= k_cap && slice > 0) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(std::max<int64_t>(K, k_cap), 64);
-    // Columns per slice, a multiple of 128: up to GV_SLICE, fewer on tall grids (the FP32 pair
-    // buffers, 8 na S bytes, up to 1 GiB).
-    const int64_t s_mem = std::max<int64_t>(G32_T, ((int64_t)1 << 30) / (8 * (int64_t)na) / G32_T * G32_T);
+    // Columns per slice, a multiple of 128: up to GV_SLICE, fewer on tall grids (the pair buffers,
+    // 12 na S bytes, up to 1.5 GiB).
+    const int64_t s_mem = std::max<int64_t>(G32_T, ((int64_t)3 << 29) / (12 * (int64_t)na) / G32_T * G32_T);
     const int S = (int)std::min<int64_t>(std::min<int64_t>((cap + G32_T - 1) / G32_T * G32_T, GV_SLICE), s_mem);
     DevBuf p, u, pt, x, lcb, lcb32, od, qu, w, b, mm;
     cudaError_t e;
@@ -1243,13 +1270,14 @@ cudaError_t GridVT::ensure(int64_t K)
     if ((e = lcb.alloc(sizeof(GvLam) * S)) != cudaSuccess) return e;
     if ((e = lcb32.alloc(sizeof(GvCol32) * S)) != cudaSuccess) return e;
     if ((e = u.alloc(sizeof(double) * (size_t)S * nbp)) != cudaSuccess) return e;
-    // Partial sums: na / 32 row tiles in the FP64 form, na / 128 row tiles x 4 q parts in the FP32 form.
-    static_assert(G32_QP * G64_TA <= G32_T, "the FP32 partial sums fit the FP64 rows");
-    if ((e = pt.alloc(sizeof(double) * (size_t)(na / G64_TA) * S)) != cudaSuccess) return e;
+    // Partial sums: na / 32 row tiles x 4 q parts in the FP64 form, na / 128 row tiles x 4 q parts
+    // in the FP32 form.
+    static_assert(G32_QP * G64_TA <= G32_T * G64_QP, "the FP32 partial sums fit the FP64 rows");
+    if ((e = pt.alloc(sizeof(double) * (size_t)(na / G64_TA) * G64_QP * S)) != cudaSuccess) return e;
     if ((e = x.alloc(sizeof(double) * cap)) != cudaSuccess) return e;
     if ((e = qu.alloc(sizeof(unsigned) * n_sl)) != cudaSuccess) return e;
-    // FP32 row factors and support edges of every (row, column) pair of a slice.
-    if ((e = w.alloc(sizeof(float) * (size_t)na * S)) != cudaSuccess) return e;
+    // Row factors (FP64, or FP32 in the same bytes) and support edges of every pair of a slice.
+    if ((e = w.alloc(sizeof(double) * (size_t)na * S)) != cudaSuccess) return e;
     if ((e = b.alloc(sizeof(int) * (size_t)na * S)) != cudaSuccess) return e;
     if ((e = mm.alloc(sizeof(int2) * 8 * (size_t)(na / G32_T) * (S / G32_T))) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(gv_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g64_smem())) !=
@@ -1314,9 +1342,11 @@ cudaError_t GridVT::enqueue(int mode, const double* lambda, int n_params, const 
         gv_order_kernel<<<1, 1024, 0, s>>>(g, lcp, dK, s0, slice, ta, order.as<int32_t>());
         if (timed && sl == 0 && (e = cudaEventRecordWithFlags(ev1, s, rec)) != cudaSuccess) return e;
         if (mode == 0) {
-            const unsigned grid = (unsigned)n_rt * (unsigned)(slice / GV_TL);
-            gv_main_kernel<<<grid, GV_THREADS, g64_smem(), s>>>(g, pd64.as<double>(), U.as<double>(), lcp,
-                                                               order.as<int32_t>(), dK, s0, slice, tb, kc,
+            gv_setup64_kernel<<<blocks_for((int64_t)na * slice, GV_THREADS, 152 * 8), GV_THREADS, 0, s>>>(
+                g, lcp, dK, s0, slice, tb, kc, wg.as<double>(), b0g.as<int>());
+            const unsigned grid = (unsigned)n_rt * (unsigned)(slice / GV_TL) * G64_QP;
+            gv_main_kernel<<<grid, GV_THREADS, g64_smem(), s>>>(g, pd64.as<double>(), U.as<double>(), wg.as<double>(),
+                                                               b0g.as<int>(), order.as<int32_t>(), dK, s0, slice,
                                                                part.as<double>(), err.as<int>());
         } else {
             if ((e = cudaMemsetAsync(wmm.p, 0xff, sizeof(int2) * 8 * (size_t)n_rt * (slice / G32_T), s)) !=
@@ -1332,7 +1362,7 @@ cudaError_t GridVT::enqueue(int mode, const double* lambda, int n_params, const 
                 queue.as<unsigned>() + sl, part.as<double>(), err.as<int>());
         }
         if (timed && sl == 0 && (e = cudaEventRecordWithFlags(ev2, s, rec)) != cudaSuccess) return e;
-        gv_reduce_kernel<<<(slice + 7) / 8, 256, 0, s>>>(part.as<double>(), mode == 0 ? n_rt : n_rt * G32_QP,
+        gv_reduce_kernel<<<(slice + 7) / 8, 256, 0, s>>>(part.as<double>(), mode == 0 ? n_rt * G64_QP : n_rt * G32_QP,
                                                          perm.as<int32_t>(), dK, s0, slice, xi.as<double>());
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
