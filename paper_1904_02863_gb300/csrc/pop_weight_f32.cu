@@ -178,14 +178,24 @@ __device__ __forceinline__ f2 masked_pair(const ulonglong2* __restrict__ buf, co
     return pk(ia ? wa : 0.0f, ib ? wb : 0.0f);
 }
 
-// Pairs [p0, p1) of the staged sub-tile whose first sample is chunk index jb + 2p.  Two pairs
-// are added first, then the packed Kahan sums take the result (one rounding more per two
-// pairs, a third of the compensated additions).
+// Pairs [p0, p1) of the staged sub-tile whose first sample is chunk index jb + 2p.  Four pairs
+// are added first (two roundings more per four pairs), then the packed Kahan sums take the
+// result: a fifth of the compensated additions.  p0 is a multiple of 4, so the groups are the
+// same for every lane whatever its warp.
 template <bool SLOW, bool CHECK_J, bool INJ, bool HAS_Z>
 __device__ __forceinline__ void run_pairs(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p0, int p1,
                                           int jb, int j0, const LaneConsts& c, f2& s, f2& cs, f2& s2, f2& cs2)
 {
     int p = p0;
+#pragma unroll 1
+    for (; p + 3 < p1; p += 4) {
+        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
+        const f2 w1 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 1, jb + 2 * p + 2, j0, c);
+        const f2 w2 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 2, jb + 2 * p + 4, j0, c);
+        const f2 w3 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 3, jb + 2 * p + 6, j0, c);
+        kahan2(s, cs, add2(add2(w0, w1), add2(w2, w3)));
+        if (INJ) kahan2(s2, cs2, fma2(w0, w0, fma2(w1, w1, fma2(w2, w2, mul2(w3, w3)))));
+    }
 #pragma unroll 1
     for (; p + 1 < p1; p += 2) {
         const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
@@ -358,13 +368,14 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
                 cp_async_wait1();
                 __syncthreads();
                 const int jb = 2 * SP * st;
-                // Region edges at even pair indices (SP is even, so even in the chunk too): the
-                // pre-summed pairs (2m, 2m+1) are the same for every warp, and so is every
-                // lane's rounding.  Zero pairs ahead of a lane's j0 leave its sums at 0.
+                // Region edges at pair indices that are multiples of 4 (SP is one, so they are in
+                // the chunk too): the pre-summed groups of 4 pairs are the same for every warp,
+                // and so is every lane's rounding.  Zero pairs ahead of a lane's j0 leave its sums
+                // at 0.  Only p_end, the same for every warp, may fall between.
                 const int p_end = min(SP, (ch.len - jb + 1) >> 1);
-                const int p_beg = min(p_end, max(0, (wj0 - jb) >> 1)) & ~1;
-                const int p_slow = min(p_end, max(p_beg, (((wjs - jb + 1) >> 1) + 1) & ~1));
-                const int p_chk = min(p_end, max(p_slow, (((wj1 - jb + 1) >> 1) + 1) & ~1));
+                const int p_beg = min(p_end, max(0, (wj0 - jb) >> 1)) & ~3;
+                const int p_slow = min(p_end, max(p_beg, ((((wjs - jb + 1) >> 1) + 1) + 3) & ~3));
+                const int p_chk = min(p_end, max(p_slow, ((((wj1 - jb + 1) >> 1) + 1) + 3) & ~3));
                 const ulonglong2* bq = reinterpret_cast<const ulonglong2*>(sbuf[b]);
                 const f2* bz = reinterpret_cast<const f2*>(szb[HAS_Z ? b : 0]);
                 if (is_inj) run_regions<true, HAS_Z>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
