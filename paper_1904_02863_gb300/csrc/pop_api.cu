@@ -48,7 +48,7 @@ struct SampleSet {
     int n_dims = 0;
     int storage = 0;
     int chunk_len = CHUNK_LEN_MAX;  // samples per work chunk of this set
-    DevBuf f64, f32, m2, m1d, m1sort, m1pos;
+    DevBuf f64, f32, m2, m1d, m1sort, m1pos, m1max;
     void swap(SampleSet& o)
     {
         std::swap(n, o.n);
@@ -62,11 +62,12 @@ struct SampleSet {
         m1d.swap(o.m1d);
         m1sort.swap(o.m1sort);
         m1pos.swap(o.m1pos);
+        m1max.swap(o.m1max);
     }
     FeatF32 feat32() const
     {
-        return FeatF32{f32.as<float>(), m2.as<double>(), m1d.as<double>(), m1sort.as<double>(), m1pos.as<uint2>(), n,
-                       stride};
+        return FeatF32{f32.as<float>(), m2.as<double>(), m1d.as<double>(), m1sort.as<double>(), m1pos.as<uint2>(),
+                       m1max.as<float>(), n, stride};
     }
 };
 
@@ -279,6 +280,8 @@ int pack_samples(pop_ctx* c, int64_t n, int n_dims, const double* theta, const d
            "copy m1 order");
         CK(launch_pack_f32(th, pr, dperm.as<int64_t>(), n, n_dims, out.f32.as<float>(), out.m2.as<double>(),
                            out.m1d.as<double>(), out.stride, bad.as<unsigned long long>(), c->stream), "pack_f32");
+        CK(out.m1max.alloc(sizeof(float) * (size_t)((n + M1MAX_BLOCK - 1) / M1MAX_BLOCK + 1)), "cudaMalloc(m1 maxima)");
+        CK(launch_m1_blockmax(out.f32.as<float>(), out.stride, n, out.m1max.as<float>(), c->stream), "m1 maxima");
     }
     unsigned long long h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, bad.p, sizeof(h_bad), cudaMemcpyDeviceToHost, c->stream), "copy flag");

@@ -82,12 +82,15 @@ struct FeatF64 {
     int64_t stride;
 };
 
+constexpr int M1MAX_BLOCK = 64;  // samples per block of FeatF32::m1max
+
 struct FeatF32 {
     const float* base;     // [F_COUNT32][stride]; row F_M1 holds rd32(m1) (rounded toward -inf)
     const double* m2;      // [stride]: fl64(q m1)
     const double* m1d;     // [stride]: m1 in FP64 (0 outside the Lambda-independent support)
     const double* m1sort;  // [n]: m1d of the whole set in increasing order
     const uint2* m1pos;    // [n]: (position, chunk index within the set) of each m1sort entry
+    const float* m1max;    // [ceil(n / M1MAX_BLOCK)]: the largest rd32(m1) of each block of samples
     int64_t n;
     int64_t stride;
 };
@@ -114,6 +117,9 @@ cudaError_t launch_pack_f64(const double* theta, const double* prior, const int6
 cudaError_t launch_pack_f32(const double* theta, const double* prior, const int64_t* perm, int64_t n, int n_dims,
                             float* feat, double* m2, double* m1d, int64_t stride, unsigned long long* bad,
                             cudaStream_t s);
+// m1max[b] = the largest rd32(m1) (feature row F_M1 of the packed FP32 features) over samples
+// [M1MAX_BLOCK b, M1MAX_BLOCK (b + 1)) of the n.
+cudaError_t launch_m1_blockmax(const float* feat, int64_t stride, int64_t n, float* m1max, cudaStream_t s);
 // ztab (REDSHIFT_NODES entries, build_z_table) and exptab make the redshift trapezoid one
 // table-driven exponential per node; with ztab NULL it is evaluated directly.
 constexpr int REDSHIFT_NODES = 1024;

@@ -356,6 +356,23 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
     flags[k] = fl;
 }
 
+// One warp per block of M1MAX_BLOCK samples.  The values are clamped at 0 from below (an upper
+// bound is all the caller needs), so their float bits order like the values.
+__global__ void m1_blockmax_kernel(const float* __restrict__ m1, int64_t n, float* __restrict__ m1max)
+{
+    static_assert(M1MAX_BLOCK == 64, "two samples per lane");
+    const int64_t nb = (n + M1MAX_BLOCK - 1) / M1MAX_BLOCK;
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; b < nb;
+         b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t j = b * M1MAX_BLOCK + lane;
+        float v = j < n ? fmaxf(m1[j], 0.0f) : 0.0f;
+        if (j + 32 < n) v = fmaxf(v, m1[j + 32]);
+        const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+        if (lane == 0) m1max[b] = __uint_as_float(mx);
+    }
+}
+
 int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -370,6 +387,14 @@ cudaError_t launch_pack_f64(const double* theta, const double* prior, const int6
 {
     if (n <= 0) return cudaSuccess;
     pack_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(theta, prior, perm, n, n_dims, feat, stride, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m1_blockmax(const float* feat, int64_t stride, int64_t n, float* m1max, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = (n + M1MAX_BLOCK - 1) / M1MAX_BLOCK;
+    m1_blockmax_kernel<<<grid_for(nb * 32, 256), 256, 0, s>>>(feat + F_M1 * stride, n, m1max);
     return cudaGetLastError();
 }
 

@@ -55,11 +55,12 @@ struct F32Cfg {
 // One lane's Lambda, in the packed form of the pair arithmetic.
 struct LaneConsts {
     f2 beta, ac, bc_, km1, nalpha, cpl, nmu, nh, cg, b1, lmmin, nb1, b1lo, nht, ct, t0, neg1;
+    f2 zero;          // 0 that the compiler cannot see (see pair_weight)
     float thr_hi;     // largest float <= mmax
     int beta_m1;      // beta == -1: the q normalisation is -u
 };
 
-__device__ __forceinline__ LaneConsts lane_consts(const LamF32& L)
+__device__ __forceinline__ LaneConsts lane_consts(const LamF32& L, float zero = 0.0f)
 {
     LaneConsts c;
     c.beta = bc(L.beta);
@@ -79,6 +80,7 @@ __device__ __forceinline__ LaneConsts lane_consts(const LamF32& L)
     c.ct = bc(L.ct);
     c.t0 = bc(L.t0);
     c.neg1 = bc(-1.0f);
+    c.zero = bc(zero);
     c.thr_hi = L.thr_hi;
     c.beta_m1 = L.beta_m1;
     return c;
@@ -149,7 +151,11 @@ __device__ __forceinline__ f2 pair_weight(const PairFeat& x, const LaneConsts& c
     const f2 tt = add2(c.t0, ex2_2(fma2(c.nht, x.dc, c.ct)));
     float da, db;
     upk(den, da, db);
-    return mul2(mul2(e12, tt), pk(rcpf(fabsf(da)), rcpf(fabsf(db))));
+    // The last product as an fma with a zero addend that the compiler cannot see, so that it is
+    // rounded on its own even where an add follows it directly (the compiler otherwise contracts
+    // a packed multiply into a following packed add, and the sums would depend on which path
+    // the caller took).
+    return fma2(mul2(e12, tt), pk(rcpf(fabsf(da)), rcpf(fabsf(db))), c.zero);
 }
 
 __device__ __forceinline__ void kahan2(f2& s, f2& cs, f2 w)
@@ -162,8 +168,9 @@ __device__ __forceinline__ void kahan2(f2& s, f2& cs, f2 w)
 
 // Masked weights of pair p of the staged sub-tile (first sample at chunk index j).  CHECK_J
 // applies the lower edge j >= j0; past the largest j0 of the warp only m1 <= mmax is tested
-// (a lane without in-support samples has thr_hi = -inf).
-template <bool SLOW, bool CHECK_J, bool HAS_Z>
+// (a lane without in-support samples has thr_hi = -inf).  CHECK_HI = false drops that test
+// where the caller knows that every staged m1 passes it for every lane with support.
+template <bool SLOW, bool CHECK_J, bool HAS_Z, bool CHECK_HI>
 __device__ __forceinline__ f2 masked_pair(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p, int j,
                                           int j0, const LaneConsts& c)
 {
@@ -173,8 +180,8 @@ __device__ __forceinline__ f2 masked_pair(const ulonglong2* __restrict__ buf, co
     float wa, wb, m1a, m1b;
     upk(w, wa, wb);
     upk(x.m1, m1a, m1b);
-    const bool ia = m1a <= c.thr_hi && (!CHECK_J || j >= j0);
-    const bool ib = m1b <= c.thr_hi && (!CHECK_J || j + 1 >= j0);
+    const bool ia = (!CHECK_HI || m1a <= c.thr_hi) && (!CHECK_J || j >= j0);
+    const bool ib = (!CHECK_HI || m1b <= c.thr_hi) && (!CHECK_J || j + 1 >= j0);
     return pk(ia ? wa : 0.0f, ib ? wb : 0.0f);
 }
 
@@ -182,29 +189,29 @@ __device__ __forceinline__ f2 masked_pair(const ulonglong2* __restrict__ buf, co
 // are added first (two roundings more per four pairs), then the packed Kahan sums take the
 // result: a fifth of the compensated additions.  p0 is a multiple of 4, so the groups are the
 // same for every lane whatever its warp.
-template <bool SLOW, bool CHECK_J, bool INJ, bool HAS_Z>
+template <bool SLOW, bool CHECK_J, bool INJ, bool HAS_Z, bool CHECK_HI>
 __device__ __forceinline__ void run_pairs(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p0, int p1,
                                           int jb, int j0, const LaneConsts& c, f2& s, f2& cs, f2& s2, f2& cs2)
 {
     int p = p0;
 #pragma unroll 1
     for (; p + 3 < p1; p += 4) {
-        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
-        const f2 w1 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 1, jb + 2 * p + 2, j0, c);
-        const f2 w2 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 2, jb + 2 * p + 4, j0, c);
-        const f2 w3 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 3, jb + 2 * p + 6, j0, c);
+        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p, jb + 2 * p, j0, c);
+        const f2 w1 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p + 1, jb + 2 * p + 2, j0, c);
+        const f2 w2 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p + 2, jb + 2 * p + 4, j0, c);
+        const f2 w3 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p + 3, jb + 2 * p + 6, j0, c);
         kahan2(s, cs, add2(add2(w0, w1), add2(w2, w3)));
         if (INJ) kahan2(s2, cs2, fma2(w0, w0, fma2(w1, w1, fma2(w2, w2, mul2(w3, w3)))));
     }
 #pragma unroll 1
     for (; p + 1 < p1; p += 2) {
-        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
-        const f2 w1 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p + 1, jb + 2 * p + 2, j0, c);
+        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p, jb + 2 * p, j0, c);
+        const f2 w1 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p + 1, jb + 2 * p + 2, j0, c);
         kahan2(s, cs, add2(w0, w1));
         if (INJ) kahan2(s2, cs2, fma2(w0, w0, mul2(w1, w1)));
     }
     if (p < p1) {
-        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z>(buf, zb, p, jb + 2 * p, j0, c);
+        const f2 w0 = masked_pair<SLOW, CHECK_J, HAS_Z, CHECK_HI>(buf, zb, p, jb + 2 * p, j0, c);
         kahan2(s, cs, w0);
         if (INJ) kahan2(s2, cs2, mul2(w0, w0));
     }
@@ -212,14 +219,14 @@ __device__ __forceinline__ void run_pairs(const ulonglong2* __restrict__ buf, co
 
 // The three regions of a sub-tile's pairs for one warp: with the series (and the lower-edge
 // test), then without the series but with the test, then neither.
-template <bool INJ, bool HAS_Z>
+template <bool INJ, bool HAS_Z, bool CHECK_HI>
 __device__ __forceinline__ void run_regions(const ulonglong2* __restrict__ buf, const f2* __restrict__ zb, int p_beg,
                                             int p_slow, int p_chk, int p_end, int jb, int j0, const LaneConsts& c,
                                             f2& s, f2& cs, f2& s2, f2& cs2)
 {
-    run_pairs<true, true, INJ, HAS_Z>(buf, zb, p_beg, p_slow, jb, j0, c, s, cs, s2, cs2);
-    run_pairs<false, true, INJ, HAS_Z>(buf, zb, p_slow, p_chk, jb, j0, c, s, cs, s2, cs2);
-    run_pairs<false, false, INJ, HAS_Z>(buf, zb, p_chk, p_end, jb, j0, c, s, cs, s2, cs2);
+    run_pairs<true, true, INJ, HAS_Z, CHECK_HI>(buf, zb, p_beg, p_slow, jb, j0, c, s, cs, s2, cs2);
+    run_pairs<false, true, INJ, HAS_Z, CHECK_HI>(buf, zb, p_slow, p_chk, jb, j0, c, s, cs, s2, cs2);
+    run_pairs<false, false, INJ, HAS_Z, CHECK_HI>(buf, zb, p_chk, p_end, jb, j0, c, s, cs, s2, cs2);
 }
 
 // The two searches of a work item's start, in lockstep so that their loads overlap (each is
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(NT, F32Cfg<NT>::MIN_BLOCKS)
 weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict__ lam,
                   const int32_t* __restrict__ order, const int32_t* __restrict__ n_mc,
                   unsigned long long* __restrict__ queue, int64_t K_cap,
-                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2)
+                  const int64_t* __restrict__ dK, double* __restrict__ part, double* __restrict__ part2, float zero)
 {
     constexpr int SP = F32Cfg<NT>::SP;
     __shared__ __align__(16) float sbuf[2][SP * 16];
@@ -345,7 +352,11 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
             if (j0 >= ch.len) js = 0;
             else if (L.beta_m1) js = ch.len;
         }
-        LaneConsts cl = lane_consts(L);
+        LaneConsts cl = lane_consts(L, zero);
+        // The smallest upper edge over the warp's lanes with in-support samples (positive floats
+        // order like their bits; +inf when there is none).
+        const float wthr =
+            __uint_as_float(__reduce_min_sync(0xffffffffu, j0 < ch.len ? __float_as_uint(cl.thr_hi) : 0x7f800000u));
         if (j0 >= ch.len) cl.thr_hi = -INFINITY;  // no in-support sample: masked without the index test
         const int wj0 = __reduce_min_sync(0xffffffffu, j0);
         const int wj1 = __reduce_max_sync(0xffffffffu, j0 < ch.len ? j0 : 0);
@@ -378,11 +389,31 @@ weight_f32_kernel(FeatF32 ev, FeatF32 inj, WorkDesc wd, const LamF32* __restrict
                 const int p_chk = min(p_end, max(p_slow, ((((wj1 - jb + 1) >> 1) + 1) + 3) & ~3));
                 const ulonglong2* bq = reinterpret_cast<const ulonglong2*>(sbuf[b]);
                 const f2* bz = reinterpret_cast<const f2*>(szb[HAS_Z ? b : 0]);
-                if (is_inj) run_regions<true, HAS_Z>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
-                else run_regions<false, HAS_Z>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
+                // A sub-tile without padding whose samples all lie at or below the warp's smallest
+                // upper edge (from the per-block maxima of rd32(m1)) skips the upper-edge test.
+                bool check_hi = true;
+                if (jb + 2 * SP <= ch.len) {
+                    const int64_t b0 = (ch.start + jb) / M1MAX_BLOCK, b1 = (ch.start + jb + 2 * SP - 1) / M1MAX_BLOCK;
+                    static_assert(2 * SP / M1MAX_BLOCK + 1 <= 32, "a lane per block");
+                    const unsigned mx = __reduce_max_sync(
+                        0xffffffffu, b0 + lane <= b1 ? __float_as_uint(__ldg(F.m1max + b0 + lane)) : 0u);
+                    check_hi = !(__uint_as_float(mx) <= wthr);
+                }
+                if (check_hi) {
+                    if (is_inj)
+                        run_regions<true, HAS_Z, true>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
+                    else
+                        run_regions<false, HAS_Z, true>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
+                } else {
+                    if (is_inj)
+                        run_regions<true, HAS_Z, false>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
+                    else
+                        run_regions<false, HAS_Z, false>(bq, bz, p_beg, p_slow, p_chk, p_end, jb, j0, cl, s, cs, s2, cs2);
+                }
                 __syncthreads();  // buffer b is refilled two sub-tiles on
             }
         }
+        if (j0 >= ch.len) s = cs = s2 = cs2 = 0ull;  // no in-support sample (the unchecked sub-tiles added to it)
         if (active) {
             float sa, sb, ca, cb;
             upk(s, sa, sb);
@@ -622,7 +653,8 @@ cudaError_t launch_weight_f32(const Tiling& t, int grid, FeatF32 ev, FeatF32 inj
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &queue, &K_cap, &dK, &part, &part2};
+    float zero = 0.0f;  // passed at run time (pair_weight)
+    void* args[] = {&ev, &inj, &wd, &lam, &order, &n_mc, &queue, &K_cap, &dK, &part, &part2, &zero};
     return cudaLaunchKernel(fn, dim3(grid), dim3(t.block_threads), args, 0, s);
 }
 
