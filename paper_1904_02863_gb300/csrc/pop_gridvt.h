@@ -48,11 +48,12 @@ struct GridVT {
 
     // Scratch, sized by ensure() for batches of up to k_cap Lambda.
     int64_t k_cap = 0;
-    int slice = 0;          // columns per slice, a multiple of GV_TL
+    int slice = 0;          // columns per slice, a multiple of 128
     DevBuf perm, lamc, order, U, part, xi, err;  // lamc: per-column constants; order: row tiles, heaviest first
     DevBuf lamc32;                               // per-column constants of the FP32 form, packed
     DevBuf queue;                                // FP32 contraction: one item counter per slice
-    DevBuf wg, b0g, wmm;                         // FP32 contraction: W and b0 of every pair of a slice, edge ranges
+    DevBuf wg, b0g;                              // W (FP64, or FP32 in the same bytes) and b0 of every pair of a slice
+    DevBuf wmm;                                  // FP32 contraction: each warp's lowest and highest support edge
     int g32_ctas = 0;                            // resident CTAs of the FP32 contraction (persistent grid)
     // Standalone evaluation (pop_xi_grid): own Lambda, K and outputs.
     int64_t k_cap_own = 0;
@@ -73,10 +74,12 @@ struct GridVT {
     // enqueue below may run inside a stream capture).
     cudaError_t ensure(int64_t K);
     // xi_grid for the K (read from dK) Lambda rows of lambda[K_cap][n_params]
-    // into xi[k] (FP64): sort by mmin, U, masked contraction, fixed-order
-    // reduction, per slice.  mode: 0 = FP64 contraction, 1 = FP32 contraction
-    // (FP64 W, b0 and combine).  Events ev0..ev3 bracket the whole and the
-    // contraction of the first slice when `timed`.
+    // into xi[k] (FP64): sort by mmin, U, the pairs' W and b0, masked
+    // contraction, fixed-order reduction, per slice.  mode: 0 = FP64
+    // throughout, 1 = FP32 W, pdet, U and node sums (FP64 support edges, an
+    // exact-product float-float row combine, FP64 reduction).  Events ev0..ev3
+    // bracket the whole and the contraction (setup included) of the first slice
+    // when `timed`.
     cudaError_t enqueue(int mode, const double* lambda, int n_params, const int64_t* dK, int64_t K_cap, bool timed,
                         unsigned record_flags, cudaStream_t s);
     // pop_xi_grid: ln xi and flags (1 = invalid Lambda, 32 = xi = 0).
