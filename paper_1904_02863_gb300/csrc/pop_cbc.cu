@@ -38,17 +38,22 @@ struct CbcCfg;
 // TK rows per work item; RUN bins per exact-phase anchor (the recurrence e <- e w between
 // anchors adds about 3 roundings per product: RUN - 1 products).
 // SUB bins' loads a thread issues together (their registers: SUB x 4 values).
+// MIN_BLOCKS: resident blocks per SM that the register budget allows.  FP64: 3 (80 registers;
+// a few values spill to L1 outside the bins' loop, and the extra warps keep the FP64 pipe busier:
+// 0.85 of its peak against 0.83 with 2).  FP32: 2.
 template <>
 struct CbcCfg<double> {
     static constexpr int TK = 4;
     static constexpr int RUN = 32;
     static constexpr int SUB = 4;
+    static constexpr int MIN_BLOCKS = 3;
 };
 template <>
 struct CbcCfg<float> {
     static constexpr int TK = 8;
     static constexpr int RUN = 16;
     static constexpr int SUB = 8;
+    static constexpr int MIN_BLOCKS = 2;
 };
 
 // Per (row, detector) constants.
@@ -155,7 +160,7 @@ __device__ __forceinline__ void load_pq(const float4* p, float (&v)[4])
 
 // Partial sums SP, SQ (as Re, Im, Re, Im) of one work item for TK rows.
 template <class T>
-__global__ void __launch_bounds__(CBC_THREADS, 2)
+__global__ void __launch_bounds__(CBC_THREADS, CbcCfg<T>::MIN_BLOCKS)
 cbc_sum_kernel(const typename Vec4T<T>::type* __restrict__ pq, const CbcRow* __restrict__ rows, int n_det, int64_t M,
                int n_tiles, int n_chunks, int64_t CB, const int64_t* __restrict__ dK, double* __restrict__ part)
 {
