@@ -523,7 +523,7 @@ void build_exp_table(double2* tab, ExpConsts* kc)
         tab[j] = make_double2(hi, (double)(v - (long double)hi));
     }
     const long double ln2 = logl(2.0L);
-    kc->inv_l = (double)(EXP_TABLE_SIZE / ln2);
+    kc->inv_l = (float)(EXP_TABLE_SIZE / ln2);
     kc->l = (double)(ln2 / EXP_TABLE_SIZE);
 }
 

@@ -13,6 +13,17 @@
 // Taylor series to r^3 for exp (truncation r^4/24 < 4e-17 of a result near 1)
 // and to r^4 for expm1 (whose result can be as small as r).
 //
+// The index k = m 2048 + j, the integer nearest to x 2048/ln2, is found off the FP64
+// pipe: an FP32 image of x (its top 24 significant bits, assembled from the bit
+// pattern by integer operations), one FP32 fma with the 1.5 2^23 rounding shift, and
+// kd = (double)k assembled from k's bits.  The FP32 rounding leaves k within one of
+// the nearest integer: |x 2048/ln2 - k| <= 0.5 + |x| 5.3e-4 (the image's truncation,
+// 2^-23, and fl32(2048/ln2), 2^-24, relative), so |r| <= 0.51 ln2/2048 for |x| <= 20
+// and 0.88 ln2/2048 at the ends of the range.  The exp series' truncation r^4/24 stays
+// below 5e-17 relative for |x| <= 20 (3.4e-17 with exact rounding) and 3.3e-16 at
+// |x| = 709; expm1's, r^4/120 relative to the result, below 7e-17.  Only the
+// reduction's fma and the series remain on the FP64 pipe.
+//
 // The reduction r = x - kd l takes one fma with l = fl(ln2/2048), not Tang's
 // two-part constant.  l carries the relative error of fl(ln 2), 3.35e-17, so r
 // is off by at most |kd| l 3.35e-17 ~ |x| 3.35e-17: the result gains |x| 3.35e-17
@@ -33,11 +44,9 @@ namespace pop {
 constexpr int EXP_TABLE_BITS = 11;
 constexpr int EXP_TABLE_SIZE = 1 << EXP_TABLE_BITS;   // 2048 entries of (hi, lo)
 
-constexpr double EXP_SHIFTER = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
-
 // Reduction constants (computed once on the host from long double ln 2).
 struct ExpConsts {
-    double inv_l;   // 2048 / ln 2
+    float inv_l;    // 2048 / ln 2, rounded to FP32 (the index is formed in FP32)
     double l;       // ln 2 / 2048, rounded to nearest
 };
 
@@ -47,6 +56,31 @@ constexpr double EXP_X_MAX = 709.7;
 
 __device__ __forceinline__ int64_t bits_of(double x) { return __double_as_longlong(x); }
 
+// k within one of the integer nearest to x 2048/ln2, for |x| < 1024, with no FP64 instruction.
+// The FP32 image of x: the bit pattern shifted left by 3 puts the low 9 exponent bits and the
+// top 23 mantissa bits in the upper word; subtracting 384 from those 9 bits turns a double
+// exponent e in [897, 1033] into the float exponent e - 896 (mod 512, with the float's sign bit
+// left clear), and |x| below 2^-126 becomes 0.  Then k = rn(x' 2048/ln2 + 1.5 2^23) - 1.5 2^23,
+// read off the sum's bit pattern (|x' 2048/ln2| < 2^22).
+__device__ __forceinline__ int exp_index(double x, float inv_l)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned y = (__funnelshift_l(lo, hi, 3) - (384u << 23)) | (hi & 0x80000000u);
+    const float xf = (hi & 0x7fffffffu) >= (897u << 20) ? __uint_as_float(y) : 0.0f;
+    return __float_as_int(fmaf(xf, inv_l, 12582912.0f)) - 0x4B400000;
+}
+
+// (double)k, exact for |k| < 2^31, from k's bits: the leading one of |k| shifted to bit 31 and
+// then to bit 20 of the high word, where it adds one to the biased exponent 1053 - clz(|k|).
+__device__ __forceinline__ double dbl_of_int(int k)
+{
+    const unsigned a = (unsigned)abs(k);
+    const int lz = __clz(a);
+    const unsigned m = a << (lz & 31);
+    const unsigned hi = (((unsigned)(1053 - lz) << 20) + (m >> 11)) | ((unsigned)k & 0x80000000u);
+    return a ? __hiloint2double((int)hi, (int)(m << 21)) : 0.0;
+}
+
 // exp(x).  tab = [hi, lo] pairs in shared memory.
 __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ tab, const ExpConsts& k)
 {
@@ -55,10 +89,8 @@ __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ 
     const bool under = (uint64_t)b > (uint64_t)bits_of(EXP_X_MIN);  // negative and below the range
     const bool over = b > bits_of(EXP_X_MAX);                         // positive and above the range
     const double xs = (under | over) ? 0.0 : x;
-    const double t = fma(xs, k.inv_l, EXP_SHIFTER);
-    const int n = __double2loint(t);
-    const double kd = t - EXP_SHIFTER;
-    const double r = fma(kd, -k.l, xs);
+    const int n = exp_index(xs, k.inv_l);
+    const double r = fma(dbl_of_int(n), -k.l, xs);
     const double p = fma(fma(r, 1.0 / 6.0, 0.5), r * r, r);  // e^r - 1
     // 2^(j/2048) e^r in [0.99, 2.01): the correctly rounded T_hi alone keeps the result
     // within about one ulp (the lo part matters only for expm1's cancellation).
@@ -78,10 +110,8 @@ __device__ __forceinline__ double expm1_tab(double u, const double2* __restrict_
     const bool under = (uint64_t)b > (uint64_t)bits_of(EXP_X_MIN);
     const bool over = b > bits_of(EXP_X_MAX);
     const double us = (under | over) ? 0.0 : u;
-    const double t = fma(us, k.inv_l, EXP_SHIFTER);
-    const int n = __double2loint(t);
-    const double kd = t - EXP_SHIFTER;
-    const double r = fma(kd, -k.l, us);
+    const int n = exp_index(us, k.inv_l);
+    const double r = fma(dbl_of_int(n), -k.l, us);
     // To r^4 here: near the first table steps the result is as small as ~1.7e-4, so the
     // truncation must be small relative to r, not to 1 (r^5/120 / r < 1e-17).
     const double p = fma(fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5), r * r, r);
