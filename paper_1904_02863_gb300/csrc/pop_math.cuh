@@ -10,8 +10,7 @@
 // x is written as (2048 m + j) ln2/2048 + r with |r| <= ln2/4096, so
 // exp(x) = 2^m 2^(j/2048) e^r; 2^(j/2048) comes from a 2048-entry table held as
 // hi + lo doubles (built on the host in extended precision), e^r - 1 from its
-// Taylor series to r^3 for exp (truncation r^4/24 < 4e-17 of a result near 1)
-// and to r^4 for expm1 (whose result can be as small as r).
+// Taylor series.
 //
 // The index k = m 2048 + j, the integer nearest to x 2048/ln2, is found off the FP64
 // pipe: an FP32 image of x (its top 24 significant bits, assembled from the bit
@@ -19,10 +18,15 @@
 // kd = (double)k assembled from k's bits.  The FP32 rounding leaves k within one of
 // the nearest integer: |x 2048/ln2 - k| <= 0.5 + |x| 5.3e-4 (the image's truncation,
 // 2^-23, and fl32(2048/ln2), 2^-24, relative), so |r| <= 0.51 ln2/2048 for |x| <= 20
-// and 0.88 ln2/2048 at the ends of the range.  The exp series' truncation r^4/24 stays
-// below 5e-17 relative for |x| <= 20 (3.4e-17 with exact rounding) and 3.3e-16 at
-// |x| = 709; expm1's, r^4/120 relative to the result, below 7e-17.  Only the
-// reduction's fma and the series remain on the FP64 pipe.
+// and 0.88 ln2/2048 (3e-4) at the ends of the range.
+//
+// The series e^r - 1 = r + r^2 q is carried one term further than that |r| needs
+// (exp: q to r^2/24, truncation r^5/120 < 3e-20; expm1: q to r^3/120), and q, which
+// lies within 5e-5 of 1/2, is formed off the FP64 pipe too: its tail in FP32 (an
+// FP32 pair for expm1, whose result can be as small as r), turned into a fixed-point
+// integer and added to the bit pattern of 1/2.  What stays on the FP64 pipe is the
+// reduction's fma, r^2, the fma r + r^2 q and the table step: 4 operations for exp,
+// 6 for expm1.
 //
 // The reduction r = x - kd l takes one fma with l = fl(ln2/2048), not Tang's
 // two-part constant.  l carries the relative error of fl(ln 2), 3.35e-17, so r
@@ -56,18 +60,52 @@ constexpr double EXP_X_MAX = 709.7;
 
 __device__ __forceinline__ int64_t bits_of(double x) { return __double_as_longlong(x); }
 
-// k within one of the integer nearest to x 2048/ln2, for |x| < 1024, with no FP64 instruction.
-// The FP32 image of x: the bit pattern shifted left by 3 puts the low 9 exponent bits and the
-// top 23 mantissa bits in the upper word; subtracting 384 from those 9 bits turns a double
-// exponent e in [897, 1033] into the float exponent e - 896 (mod 512, with the float's sign bit
-// left clear), and |x| below 2^-126 becomes 0.  Then k = rn(x' 2048/ln2 + 1.5 2^23) - 1.5 2^23,
-// read off the sum's bit pattern (|x' 2048/ln2| < 2^22).
-__device__ __forceinline__ int exp_index(double x, float inv_l)
+// The FP32 image of x for 2^-126 <= |x| < 1024: its top 24 significant bits (truncated), with
+// no FP64 instruction; smaller |x| gives 0.  The bit pattern shifted left by 3 puts the low 9
+// exponent bits and the top 23 mantissa bits in the upper word; subtracting 384 from those 9 bits
+// turns a double exponent e in [897, 1033] into the float exponent e - 896 (mod 512, with the
+// float's sign bit left clear).
+__device__ __forceinline__ float f32_image(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const unsigned y = (__funnelshift_l(lo, hi, 3) - (384u << 23)) | (hi & 0x80000000u);
-    const float xf = (hi & 0x7fffffffu) >= (897u << 20) ? __uint_as_float(y) : 0.0f;
-    return __float_as_int(fmaf(xf, inv_l, 12582912.0f)) - 0x4B400000;
+    return (hi & 0x7fffffffu) >= (897u << 20) ? __uint_as_float(y) : 0.0f;
+}
+
+// The rest of x after its image, x - f32_image(x), rounded to FP32: the low 29 mantissa bits
+// scaled by 2^(e - 1075); 0 where that scale is below the FP32 normal range (|x| < 2^-74).
+__device__ __forceinline__ float f32_image_rest(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const float v = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((e - 948u) << 23));
+    return e >= 949u ? __uint_as_float(__float_as_uint(v) | (hi & 0x80000000u)) : 0.0f;
+}
+
+// k within one of the integer nearest to x 2048/ln2, for |x| < 1024, with no FP64 instruction:
+// k = rn(x' 2048/ln2 + 1.5 2^23) - 1.5 2^23 with x' = f32_image(x), read off the sum's bit
+// pattern (|x' 2048/ln2| < 2^22).
+__device__ __forceinline__ int exp_index(double x, float inv_l)
+{
+    return __float_as_int(fmaf(f32_image(x), inv_l, 12582912.0f)) - 0x4B400000;
+}
+
+// v 2^53 rounded toward zero, for |v| < 2^-10, from v's bits (integer operations); FP32
+// subnormals give 0.
+__device__ __forceinline__ long long fx53(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    const int sh = (int)((b >> 23) & 0xffu) - 97;  // |v| 2^53 = m 2^sh
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const long long q = sh >= 0 ? m << (sh & 63) : (sh > -24 ? m >> ((-sh) & 31) : 0ll);
+    return (b >> 31) ? -q : q;
+}
+
+// The double 1/2 + D 2^-53, exactly, for |D| < 2^50, from its bits: above 1/2 the ulp is 2^-53,
+// below it 2^-54, so a negative D moves the pattern twice as far (and borrows the exponent).
+__device__ __forceinline__ double half_plus(long long D)
+{
+    return __longlong_as_double((1022ll << 52) + (D >= 0 ? D : 2 * D));
 }
 
 // (double)k, exact for |k| < 2^31, from k's bits: the leading one of |k| shifted to bit 31 and
@@ -91,7 +129,13 @@ __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ 
     const double xs = (under | over) ? 0.0 : x;
     const int n = exp_index(xs, k.inv_l);
     const double r = fma(dbl_of_int(n), -k.l, xs);
-    const double p = fma(fma(r, 1.0 / 6.0, 0.5), r * r, r);  // e^r - 1
+    // e^r - 1 = r + r^2 q, q = 1/2 + r/6 + r^2/24 (truncation r^5/120 < 3e-20).  q's error enters
+    // the result as r^2 times it (r^2 <= 9e-8), so its tail r/6 + r^2/24 (< 5e-5) is evaluated in
+    // FP32 from r's top 24 bits (error below 2e-11, i.e. below 2e-18 of the result) and q is
+    // assembled from bits.
+    const float rh = f32_image(r);
+    const double q = half_plus(fx53(__fmul_rn(rh, fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f))));
+    const double p = fma(r * r, q, r);  // e^r - 1
     // 2^(j/2048) e^r in [0.99, 2.01): the correctly rounded T_hi alone keeps the result
     // within about one ulp (the lo part matters only for expm1's cancellation).
     const double th = tab[n & (EXP_TABLE_SIZE - 1)].x;
@@ -112,9 +156,20 @@ __device__ __forceinline__ double expm1_tab(double u, const double2* __restrict_
     const double us = (under | over) ? 0.0 : u;
     const int n = exp_index(us, k.inv_l);
     const double r = fma(dbl_of_int(n), -k.l, us);
-    // To r^4 here: near the first table steps the result is as small as ~1.7e-4, so the
-    // truncation must be small relative to r, not to 1 (r^5/120 / r < 1e-17).
-    const double p = fma(fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5), r * r, r);
+    // e^r - 1 = r + r^2 q with q = 1/2 + r/6 + r^2/24 + r^3/120 (truncation r^6/720, below 1e-24
+    // of the result).  The result can be as small as r, so q's error enters relative to it as
+    // |r| times that error: q is wanted to about 3e-14.  r/6 is taken as an FP32 pair (r's two
+    // FP32 parts times the two parts of 1/6, with the product's exact error), the rest
+    // (< 4e-9) in FP32 from r's top part; q = 1/2 + their sum, assembled from bits (error below
+    // 2^-52 + 1e-15 of the tail, i.e. under 1e-18 of the result relative).
+    const float rh = f32_image(r), rl = f32_image_rest(r);
+    const float a = __fmul_rn(rh, 0.16666667163372039795f);
+    float t = fmaf(rh, 0.16666667163372039795f, -a);                // rh c6_hi - a, exact
+    t = fmaf(rh, -4.9670538793e-9f, t);                                // + rh c6_lo
+    t = fmaf(rl, 0.16666667163372039795f, t);                        // + rl c6_hi
+    t = fmaf(__fmul_rn(rh, rh), fmaf(rh, 1.0f / 120.0f, 1.0f / 24.0f), t);
+    const double q = half_plus(fx53(a) + fx53(t));
+    const double p = fma(r * r, q, r);
     const double2 tj = tab[n & (EXP_TABLE_SIZE - 1)];
     const int m = n >> EXP_TABLE_BITS;
     const double s = __hiloint2double(__double2hiint(tj.x) + (int)((unsigned)m << 20), __double2loint(tj.x));
