@@ -50,8 +50,15 @@ struct alignas(16) LamF64 {
     double t0;           // (1 - xi_t) / 4
     double gs;           // 1 / (sqrt2 sigpp): the Gaussian exponent is -y^2, y = fma(m1, gs, gc)
     double gc;           // -mpp gs
+    // The mass mixture with the larger of its two constants factored out into the tilt term:
+    // w = [e^(aE - alpha ln m1) + rmix e^(aE - y^2)] (t0m + e^(ctm - dc/(2 sigma_t^2))) / den when
+    // cpl >= cg (mix_swap 0), the two exponentials' roles exchanged otherwise; cmax = max(cpl, cg).
+    double rmix;         // e^(min(cpl, cg) - cmax), in [0, 1]
+    double t0m;          // e^cmax t0
+    double ctm;          // ct + cmax
     int32_t beta_m1;     // beta == -1: q normalisation is ln(m1/mmin)
     int32_t valid;
+    int32_t mix_swap;    // cg > cpl: rmix scales the power-law exponential
 };
 
 // Per-Lambda constants of the FP32 weight (base-2 units).

@@ -221,6 +221,11 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     c.t0 = 0.25 * (1.0 - xit);
     c.gs = 1.0 / (SQRT2 * sig);
     c.gc = -mu * c.gs;
+    const double cmax = fmax(c.cpl, c.cg);
+    c.mix_swap = c.cg > c.cpl;
+    c.rmix = exp(fmin(c.cpl, c.cg) - cmax);
+    c.t0m = exp(cmax) * c.t0;
+    c.ctm = c.ct + cmax;
     c.beta_m1 = beta_m1;
     c.valid = 1;
     c64[k] = c;

@@ -11,7 +11,8 @@
 // (Lambda, chunk) — no atomics, bit-reproducible.
 //
 // w(theta) = [exp(aE + cpl - alpha ln m1) + exp(aE + cg - (m1-mu)^2/(2 sig^2))]
-//            * [(1-xi_t)/4 + exp(ct - dc/(2 sig_t^2))] / |expm1((1+beta) ln(mmin/m1))|
+//            * [(1-xi_t)/4 + exp(ct - dc/(2 sig_t^2))] / |expm1((1+beta) ln(mmin/m1))|,
+// evaluated with max(cpl, cg) moved into the tilt factor (LamF64::rmix, t0m, ctm)
 // with aE = -ln pi + beta ln q + (alpha_chi-1)(ln a1 + ln a2) + (beta_chi-1)(ln(1-a1) + ln(1-a2))
 //          [+ (kappa-1) ln(1+z)], and every Lambda-only factor folded into cpl, cg, ct.
 #include <math.h>
@@ -57,13 +58,17 @@ __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c
     aE = fma(c.ac, x.sa, aE);
     aE = fma(c.bc, x.sb, aE);
     if (HAS_Z) aE = fma(c.km1, x.lz1, aE);
-    const double e1 = exp_tab(fma(c.nalpha, x.lm1, aE + c.cpl), tab, kc);
+    // The mass mixture (1-lam) C_pl m1^-alpha + lam C_g N(m1) with the larger of its two
+    // constants (cpl, cg in logs) moved into the tilt factor: e1 + rmix e2 (or e2 + rmix e1),
+    // rmix <= 1, so neither exponential needs its constant added (2 FP64 ops fewer).
+    const double e1 = exp_tab(fma(c.nalpha, x.lm1, aE), tab, kc);
     // Gaussian exponent -(m1 - mu)^2 / (2 sig^2) = -y^2 with y = (m1 - mu) / (sqrt2 sig) formed
     // by one fma from per-Lambda constants (3 FP64 ops instead of 4).  The rounding of
     // gc = -mu gs shifts y by at most |mu gs| 1.1e-16, so the exponent by 2|y| |mu gs| 1.1e-16
     // absolute: of the order of the roundings of the subtract-and-square form at the same y.
     const double y = fma(x.m1, c.gs, c.gc);
-    const double e2 = exp_tab(fma(-y, y, aE + c.cg), tab, kc);
+    const double e2 = exp_tab(fma(-y, y, aE), tab, kc);
+    const double mix = fma(c.rmix, c.mix_swap ? e1 : e2, c.mix_swap ? e2 : e1);
     // u = kq ln(mmin/m1) for the q normalisation, one fma with kq ln mmin folded into a
     // per-Lambda constant (kq = 1 + beta, or 1 for beta = -1, whose normalisation is
     // ln(m1/mmin) = -u).  Within ~3% of the lower edge the log difference would cancel,
@@ -72,8 +77,8 @@ __device__ __forceinline__ double weight_f64(const F64Sample& x, const LamF64& c
     double u = fma(-c.kq, x.lm1, c.kqlmmin);
     if (llabs(x.m1b - c.mmin_bits) < NEAR_EDGE_BITS) u = c.kq * log1p_near0(x.invm1 * (c.mmin - x.m1));
     const double den = c.beta_m1 ? -u : fabs(expm1_tab(u, tab, kc));
-    const double tt = c.t0 + exp_tab(fma(c.nht, x.dc, c.ct), tab, kc);
-    return (e1 + e2) * tt * rcp_pos(den);
+    const double tt = c.t0m + exp_tab(fma(c.nht, x.dc, c.ctm), tab, kc);
+    return mix * tt * rcp_pos(den);
 }
 
 // Support: mmin < m1 <= mmax and fl64(q m1) >= mmin, compared on bit patterns
