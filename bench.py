@@ -38,13 +38,13 @@ METRIC = "ln L(Lambda) evals/s at 1000 events x 4096 samples + 1e6 inj"
 WORKLOAD = "f64_catalog_1000x4096_inj1e7"
 
 # Algorithmic FP64-pipe operations per (sample, Lambda) pair of the weight
-# kernel: 13 add/mul/fma + 3 exp (4 each) + 1 expm1 (6) + 1 reciprocal (3);
+# kernel: 13 add/mul/fma + 3 exp (2 each) + 1 expm1 (6) + 1 reciprocal (3);
 # +1 fma for the squared weight on injection pairs.  (The exponentials' table
-# index and the tail of their series coefficient are formed in FP32 and integer
-# operations, off the FP64 pipe; the mass mixture's larger constant sits in the
-# tilt factor, so neither mass exponent adds its own.)
-FP64_OPS_PER_PAIR = 34
-FP64_OPS_PER_INJ_PAIR = 35
+# index, exp's table value times 1 + (e^r - 1 - r) and expm1's series coefficient
+# are formed in FP32 and integer operations, off the FP64 pipe; the mass mixture's
+# larger constant sits in the tilt factor, so neither mass exponent adds its own.)
+FP64_OPS_PER_PAIR = 28
+FP64_OPS_PER_INJ_PAIR = 29
 # GB300: 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2070 MHz
 # over 152 SMs); peak op rate = 2 * SMs * clock.
 FP64_LANES_PER_SM = 2
@@ -433,9 +433,9 @@ def grid_form(B, like, lam, dev_lam, outs, args, world, stream):
 # split into its power-law and peak parts (3 exp, 1 expm1, 1 reciprocal and their FMAs), the
 # 11-12 score terms and the 14 sums, with the loop-invariant terms hoisted: the DFMA + DADD + DMUL
 # count per in-support pair of the ncu capture in profiles/grad_weight_catalog100x4096_K16_full.md
-# (105), less the FP64 operations that the 3 exp (3 each) and the expm1 (4) no longer spend on
-# their table index and series coefficient: 92.
-FP64_OPS_PER_GRAD_PAIR = 92
+# (105), less the FP64 operations that the 3 exp (5 each) and the expm1 (4) no longer spend on
+# the FP64 pipe: 86.
+FP64_OPS_PER_GRAD_PAIR = 86
 
 
 def grad_form(B, like, lam, args, world, n_pairs):

@@ -20,13 +20,17 @@
 // 2^-23, and fl32(2048/ln2), 2^-24, relative), so |r| <= 0.51 ln2/2048 for |x| <= 20
 // and 0.88 ln2/2048 (3e-4) at the ends of the range.
 //
-// The series e^r - 1 = r + r^2 q is carried one term further than that |r| needs
-// (exp: q to r^2/24, truncation r^5/120 < 3e-20; expm1: q to r^3/120), and q, which
-// lies within 5e-5 of 1/2, is formed off the FP64 pipe too: its tail in FP32 (an
-// FP32 pair for expm1, whose result can be as small as r), turned into a fixed-point
-// integer and added to the bit pattern of 1/2.  What stays on the FP64 pipe is the
-// reduction's fma, r^2, the fma r + r^2 q and the table step: 4 operations for exp,
-// 6 for expm1.
+// exp takes k near floor(x 2048/ln2) instead (r in [-0.44, 1.44] ln2/2048) and never forms
+// e^r - 1 in FP64: the table value times 1 + c, c = e^r - 1 - r, lies in [1, 2), so T_hi + T_lo +
+// T_hi c is T_hi's bit pattern plus an integer that FP32 arithmetic and integer operations
+// give, and exp(x) = 2^m fma(T_hi, r, that): 2 FP64 operations, within one ulp (exp_t2).
+//
+// expm1 keeps the nearest k (so that k = 0 and the result is e^r - 1 itself for |u| below
+// ln2/4096) and the series e^r - 1 = r + r^2 q, q = 1/2 + r/6 + r^2/24 + r^3/120 (truncation
+// r^6/720): q lies within 5e-5 of 1/2, so its tail is formed in FP32 (an FP32 pair, since the
+// result can be as small as r), turned into a fixed-point integer and added to the bit pattern
+// of 1/2.  What stays on the FP64 pipe is the reduction's fma, r^2, the fma r + r^2 q and the
+// reconstruction: 6 operations.
 //
 // The reduction r = x - kd l takes one fma with l = fl(ln2/2048), not Tang's
 // two-part constant.  l carries the relative error of fl(ln 2), 3.35e-17, so r
@@ -90,12 +94,22 @@ __device__ __forceinline__ int exp_index(double x, float inv_l)
     return __float_as_int(fmaf(f32_image(x), inv_l, 12582912.0f)) - 0x4B400000;
 }
 
-// v 2^53 rounded toward zero, for |v| < 2^-10, from v's bits (integer operations); FP32
+// The same for floor(x 2048/ln2): k = rn(v) with v = fl32(x' 2048/ln2 - 1/2).  With
+// e = 5.3e-4 |x| + 1/16 (the image's and 2048/ln2's FP32 errors, and v's rounding for
+// |v| < 2^21), x 2048/ln2 - k lies in [-e, 1 + e].
+__device__ __forceinline__ int exp_index_floor(double x, float inv_l)
+{
+    const float v = fmaf(f32_image(x), inv_l, -0.5f);
+    return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000;
+}
+
+// v 2^P rounded toward zero, for |v 2^P| < 2^62, from v's bits (integer operations); FP32
 // subnormals give 0.
-__device__ __forceinline__ long long fx53(float v)
+template <int P>
+__device__ __forceinline__ long long fx(float v)
 {
     const unsigned b = __float_as_uint(v);
-    const int sh = (int)((b >> 23) & 0xffu) - 97;  // |v| 2^53 = m 2^sh
+    const int sh = (int)((b >> 23) & 0xffu) - 150 + P;  // |v| 2^P = m 2^sh
     const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
     const long long q = sh >= 0 ? m << (sh & 63) : (sh > -24 ? m >> ((-sh) & 31) : 0ll);
     return (b >> 31) ? -q : q;
@@ -119,7 +133,39 @@ __device__ __forceinline__ double dbl_of_int(int k)
     return a ? __hiloint2double((int)hi, (int)(m << 21)) : 0.0;
 }
 
-// exp(x).  tab = [hi, lo] pairs in shared memory.
+// T2 = T_hi + T_lo + T_hi c with c = e^r - 1 - r, to within half a unit of 2^-52 plus 2^-8 of
+// one, for T_hi in [1, 2^(2047/2048)] and |r| <= 1.5 ln2/2048.  T2 lies in [1, 2) (c < 1.3e-7),
+// so it is T_hi's bit pattern plus round((T_lo + T_hi c) 2^52), and no FP64 instruction forms it:
+// c = r^2 (1/2 + r/6 + r^2/24) (truncation r^5/120 < 3e-19) from r's two FP32 parts (r^2 as an
+// FP32 pair with the square's exact error; r/6 + r^2/24 in FP32, whose error enters c at 2^-22 of
+// r^2/6), then (T_lo + T_hi c) 2^60 as an FP32 pair from T_hi's two FP32 parts, each part turned
+// into an integer and the sum rounded to units of 2^-52 (the pair's error is below 2^-37 of it,
+// a few units of 2^-60).
+__device__ __forceinline__ double exp_t2(double th, double tl, double r)
+{
+    const float rh = f32_image(r), rl = f32_image_rest(r);
+    const float sh = __fmul_rn(rh, rh);
+    const float sl = fmaf(2.0f * rh, rl, fmaf(rh, rh, -sh));                  // r^2 = sh + sl
+    const float d = __fmul_rn(rh, fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f));       // r/6 + r^2/24
+    const float ch = __fmul_rn(sh, 0x1p59f);                                   // c 2^60 = ch + cl
+    const float cl = __fmul_rn(fmaf(sh, d, 0.5f * sl), 0x1p60f);
+    const float tf = f32_image(th), tr = f32_image_rest(th);                   // T_hi = tf + tr
+    const float ph = __fmul_rn(tf, ch);                                        // (T_lo + T_hi c) 2^60
+    float pl = fmaf(tf, ch, -ph);                                              //   = ph + pl
+    pl = fmaf(tr, ch, pl);
+    pl = fmaf(tf, cl, pl);
+    pl = fmaf(f32_image(tl), 0x1p60f, pl);
+    const long long F = (fx<0>(ph) + fx<0>(pl) + 128) >> 8;
+    return __longlong_as_double(__double_as_longlong(th) + F);
+}
+
+// exp(x).  tab = [hi, lo] pairs in shared memory.  k is taken near floor(x 2048/ln2), so that
+// r = x - k ln2/2048 lies in [-e, 1 + e] ln2/2048 (exp_index_floor) and the result 2^m T e^r
+// has T e^r in [1, 2.001) except when j = 0 and r < 0.  With T2 from exp_t2 the result is
+// fma(T_hi, r, T2) 2^m: 2 FP64 operations with the reduction's fma.  Error: T2's half unit of
+// 2^-52 and the fma's rounding, at most one ulp of a result in [1, 2) (1.5 in the rare j = 0,
+// r < 0 case, whose result lies in [1 - 2e-4, 1)); the table's own rounding enters only through
+// T_hi r, below 2^-64.
 __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ tab, const ExpConsts& k)
 {
     // Range tests on bit patterns (integer pipe): x < EXP_X_MIN or x > EXP_X_MAX (or -inf/+inf).
@@ -127,19 +173,10 @@ __device__ __forceinline__ double exp_tab(double x, const double2* __restrict__ 
     const bool under = (uint64_t)b > (uint64_t)bits_of(EXP_X_MIN);  // negative and below the range
     const bool over = b > bits_of(EXP_X_MAX);                         // positive and above the range
     const double xs = (under | over) ? 0.0 : x;
-    const int n = exp_index(xs, k.inv_l);
+    const int n = exp_index_floor(xs, k.inv_l);
     const double r = fma(dbl_of_int(n), -k.l, xs);
-    // e^r - 1 = r + r^2 q, q = 1/2 + r/6 + r^2/24 (truncation r^5/120 < 3e-20).  q's error enters
-    // the result as r^2 times it (r^2 <= 9e-8), so its tail r/6 + r^2/24 (< 5e-5) is evaluated in
-    // FP32 from r's top 24 bits (error below 2e-11, i.e. below 2e-18 of the result) and q is
-    // assembled from bits.
-    const float rh = f32_image(r);
-    const double q = half_plus(fx53(__fmul_rn(rh, fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f))));
-    const double p = fma(r * r, q, r);  // e^r - 1
-    // 2^(j/2048) e^r in [0.99, 2.01): the correctly rounded T_hi alone keeps the result
-    // within about one ulp (the lo part matters only for expm1's cancellation).
-    const double th = tab[n & (EXP_TABLE_SIZE - 1)].x;
-    const double res = fma(th, p, th);
+    const double2 T = tab[n & (EXP_TABLE_SIZE - 1)];
+    const double res = fma(T.x, r, exp_t2(T.x, T.y, r));
     const int m = n >> EXP_TABLE_BITS;                       // arithmetic shift: floor
     const double scaled = __hiloint2double(__double2hiint(res) + (int)((unsigned)m << 20), __double2loint(res));
     return under ? 0.0 : (over ? __longlong_as_double(0x7ff0000000000000LL) : scaled);
@@ -168,7 +205,7 @@ __device__ __forceinline__ double expm1_tab(double u, const double2* __restrict_
     t = fmaf(rh, -4.9670538793e-9f, t);                                // + rh c6_lo
     t = fmaf(rl, 0.16666667163372039795f, t);                        // + rl c6_hi
     t = fmaf(__fmul_rn(rh, rh), fmaf(rh, 1.0f / 120.0f, 1.0f / 24.0f), t);
-    const double q = half_plus(fx53(a) + fx53(t));
+    const double q = half_plus(fx<53>(a) + fx<53>(t));
     const double p = fma(r * r, q, r);
     const double2 tj = tab[n & (EXP_TABLE_SIZE - 1)];
     const int m = n >> EXP_TABLE_BITS;
