@@ -73,9 +73,9 @@ _PEAKS = _measured_peaks()
 BF16_PEAK_TFLOPS = float(_PEAKS.get("bf16_tflops_sustained") or 1700.0)
 BF16_PEAK_BASIS = "of measured (sustained)" if _PEAKS.get("bf16_tflops_sustained") else "of fallback (sustained)"
 # DRAM bytes per (sample or injection) unit of one weight_f64 launch, from the ncu capture in
-# profiles/weight_f64_catalog400x4096_K64_full.md (153.78 MB / 2,077,126 units); a launch
+# profiles/weight_f64_catalog400x4096_K64_full.md (153.90 MB / 2,077,126 units); a launch
 # reads every chunk from DRAM once, so traffic scales with the units.
-F64_DRAM_BYTES_PER_UNIT = 153.78e6 / 2077126
+F64_DRAM_BYTES_PER_UNIT = 153.90e6 / 2077126
 
 
 def in_support_pairs(theta, lam):
