@@ -4,7 +4,11 @@ CUDA's own exp (torch on the GPU), and against their error bounds.
 
 The exponentials reduce their argument with one constant, fl(ln2/2048), whose
 relative error (that of fl(ln 2), 3.35e-17) adds |x| 3.35e-17 relative error to
-exp(x): at most 0.31 |x| ulp on top of the table method's 2 ulp."""
+exp(x): at most 0.31 |x| ulp on top of the table method's 2 ulp.  exp takes its
+table index near floor(x 2048/ln2) from FP32 arithmetic and assembles
+T_hi (1 + e^r - 1 - r) + T_lo from bits, which bounds it by one ulp for a result
+in [1, 2) times a power of two, and 1.5 ulp just below a power of two (table
+entry 0 with r < 0); libm adds up to half an ulp of its own."""
 import numpy as np
 import pytest
 
@@ -79,3 +83,26 @@ def test_reciprocal_correct_to_half_ulp_bound(ctx):
     x = np.concatenate([10 ** rng.uniform(-300, 300, 200000), rng.uniform(1e-3, 10, 100000)])
     y = B.pop_math_check(ctx, 2, x)
     assert np.max(ulps(y, 1.0 / x)) <= 1.0
+
+
+def test_exp_at_the_index_switches_and_range_ends(ctx):
+    """Arguments within a few ulp of multiples of ln2/2048 (where the floor index changes), of
+    multiples of ln2 (table entry 0, whose r can be slightly negative: results just below a
+    power of two), and near both ends of the range."""
+    from paper_1904_02863_gb300 import binding as B
+    rng = np.random.default_rng(6)
+    step = np.log(2) / 2048
+    ks = np.concatenate([np.arange(-3000, 3000), rng.integers(-2_088_000, 2_096_000, 20000)])
+    base = ks * step
+    base = base[(base > -706.9) & (base < 709.6)]
+    eps = np.array([-1e-9, -1e-12, -1e-15, 0.0, 1e-15, 1e-12, 1e-9])
+    x = (base[:, None] * (1.0 + eps[None, :]) + eps[None, :]).ravel()
+    m = np.arange(-1019, 1024) * np.log(2)
+    m = m[(m > -706.9) & (m < 709.6)]
+    x = np.concatenate([x, m, np.nextafter(m, -np.inf), np.nextafter(m, np.inf), m - 1e-13, m + 1e-13,
+                        np.linspace(709.0, 709.69, 2000), np.linspace(-706.99, -706.0, 2000)])
+    y = B.pop_math_check(ctx, 0, x)
+    e = ulps(y, np.exp(x))
+    assert (e <= 2.0 + 0.31 * np.abs(x)).all(), np.max(e - 0.31 * np.abs(x))
+    small = np.abs(x) <= 1.0
+    assert np.max(e[small]) <= 2.0
