@@ -293,6 +293,8 @@ int pop_last_kernel_ms(pop_ctx* ctx, double* weight_ms, double* total_ms);
  * float-float value, returning hi + lo: 3 = exp (0 below x = -87), 4 = expm1
  * (Taylor series below |x| = 1/16, Tang's table above), 5 = reciprocal, 6 =
  * square, 7 = the exact square of the FP32 high part (packed FMA error term).
+ * fn 8 = ln x (the finalise's per-event log: Tang's table-driven logarithm with
+ * a 129-entry table for positive normal x, the library's log elsewhere).
  * The test suite checks them against libm and CUDA's functions. */
 int pop_math_check(pop_ctx* ctx, int fn, int64_t n, const double* x, double* y, int mem);
 

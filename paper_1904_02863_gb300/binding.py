@@ -343,8 +343,9 @@ def pop_pipe_rates(device=0):
 
 
 def pop_math_check(ctx, fn, x):
-    """The FP64 kernel's exp (0), expm1 (1) or reciprocal (2), or the float-float kernel's exp (3),
-    expm1 (4), reciprocal (5), square (6) and exact FP32 hi-part square (7), evaluated on the GPU."""
+    """The FP64 kernel's exp (0), expm1 (1) or reciprocal (2), the float-float kernel's exp (3),
+    expm1 (4), reciprocal (5), square (6) and exact FP32 hi-part square (7), or the finalise's
+    ln (8), evaluated on the GPU."""
     xa = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(xa)
     _check(ctx, load_library().pop_math_check(ctx, int(fn), xa.size, xa.ctypes.data_as(ctypes.c_void_p),

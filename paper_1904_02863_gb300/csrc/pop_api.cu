@@ -125,6 +125,8 @@ struct pop_ctx {
     DevBuf d_queue;          // the weight kernels' work-item counter
     cudaEvent_t ev_t0 = nullptr, ev_w0 = nullptr, ev_w1 = nullptr, ev_t1 = nullptr;
     DevBuf d_exptab;         // 2^(j/2048) as (hi, lo) for the FP64 exponentials
+    DevBuf d_logtab;         // log_tab's table (the finalise's per-event logs)
+    LogConsts logc{};
     DevBuf d_ztab;           // redshift trapezoid nodes (ln(1 + z_i), w_i z_i^2)
     ExpConsts expc{};
     DevBuf d_fftab;          // 2^(j/2048) as FP32 (hi, lo) for the float-float exponentials
@@ -458,7 +460,7 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
                        n_items, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                        c->k_cap, c->d_lnL.as<double>(), c->d_lnxi.as<double>(), c->d_neff.as<double>(),
                        c->d_flags.as<uint32_t>(), c->stream, sx, use_grid ? c->grid->xi.as<double>() : nullptr,
-                       c->d_parts.as<double>()),
+                       c->d_parts.as<double>(), c->d_logtab.as<LogEntry>(), c->logc),
        "finalise");
     CK(cudaEventRecordWithFlags(c->ev_t1, c->stream, rec), "event");
     return POP_OK;
@@ -527,6 +529,22 @@ void build_exp_table(double2* tab, ExpConsts* kc)
     kc->l = (double)(ln2 / EXP_TABLE_SIZE);
 }
 
+// log_tab's table: F_j = 1 + j/128, 1/F_j rounded, ln F_j = hi + lo with hi rounded to the grid
+// of 2^-43, and ln 2 split the same way, all from long double arithmetic.
+void build_log_table(LogEntry* tab, LogConsts* k)
+{
+    auto grid43 = [](long double v) { return (double)(ldexpl(nearbyintl(ldexpl(v, 43)), -43)); };
+    for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
+        const long double F = 1.0L + (long double)j / 128.0L;
+        const long double lnF = logl(F);
+        const double h = grid43(lnF);
+        tab[j] = LogEntry{(double)(1.0L / F), h, (double)(lnF - (long double)h)};
+    }
+    const long double ln2 = logl(2.0L);
+    k->l_hi = grid43(ln2);
+    k->l_lo = (double)(ln2 - (long double)k->l_hi);
+}
+
 }  // namespace pop
 
 // Context accessors for the surrogate entry points (pop_surrogate.cu).
@@ -564,7 +582,7 @@ extern "C" {
 int pop_math_check(pop_ctx* c, int fn, int64_t n, const double* x, double* y, int mem)
 {
     if (!c) return POP_EINVAL;
-    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y)) || !valid_mem(mem))
+    if (fn < 0 || fn > 8 || n < 0 || (n > 0 && (!x || !y)) || !valid_mem(mem))
         return fail(c, POP_EINVAL, "pop_math_check: bad arguments");
     if (n == 0) return POP_OK;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -578,8 +596,10 @@ int pop_math_check(pop_ctx* c, int fn, int64_t n, const double* x, double* y, in
         dx = bx.as<double>();
         dy = by.as<double>();
     }
-    if (fn <= 2)
-        CK(launch_math_check(fn, n, dx, dy, c->d_exptab.as<double2>(), c->expc, c->stream), "math_check");
+    if (fn <= 2 || fn == 8)
+        CK(launch_math_check(fn, n, dx, dy, c->d_exptab.as<double2>(), c->expc, c->d_logtab.as<LogEntry>(), c->logc,
+                             c->stream),
+           "math_check");
     else
         CK(launch_ff_math_check(fn, n, dx, dy, c->d_fftab.as<float2>(), c->ffk, c->stream), "ff_math_check");
     if (mem == POP_MEM_HOST) {
@@ -660,6 +680,11 @@ int pop_create(pop_ctx** out, int device, void* stream)
         e = c->d_exptab.alloc(sizeof(double2) * EXP_TABLE_SIZE);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d_exptab.p, tab.data(), sizeof(double2) * EXP_TABLE_SIZE, cudaMemcpyHostToDevice);
+        std::vector<LogEntry> ltab(LOG_TABLE_SIZE);
+        build_log_table(ltab.data(), &c->logc);
+        if (e == cudaSuccess) e = c->d_logtab.alloc(sizeof(LogEntry) * LOG_TABLE_SIZE);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_logtab.p, ltab.data(), sizeof(LogEntry) * LOG_TABLE_SIZE, cudaMemcpyHostToDevice);
         std::vector<double2> ztab(REDSHIFT_NODES);
         build_z_table(ztab.data());
         if (e == cudaSuccess) e = c->d_ztab.alloc(sizeof(double2) * REDSHIFT_NODES);

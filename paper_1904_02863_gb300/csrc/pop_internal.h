@@ -146,9 +146,11 @@ cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj
                               const double2* exptab, ExpConsts kc, unsigned long long* queue, cudaStream_t s);
 // Evaluates the FP64 weight kernel's exp (fn 0), expm1 (fn 1) or reciprocal (fn 2) on x[n].
 cudaError_t launch_math_check(int fn, int64_t n, const double* x, double* y, const double2* exptab, ExpConsts kc,
-                              cudaStream_t s);
+                              const LogEntry* logtab, LogConsts logc, cudaStream_t s);
 // Host: the 2^(j/2048) table (hi, lo) and the reduction constants, in extended precision.
 void build_exp_table(double2* tab, ExpConsts* kc);
+// log_tab's table and constants, from long double arithmetic.
+void build_log_table(LogEntry* tab, LogConsts* k);
 // Selection term from the surrogate (all NULL when the Monte Carlo xi is used for every Lambda):
 // need_mc[k] = 1 keeps the Monte Carlo xi for Lambda k, else ln xi = lnxi[k], N_eff = neff[k].
 struct SurrogateXi {
@@ -192,7 +194,9 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
                             double* lnL, double* lnxi, double* neff, uint32_t* flags, cudaStream_t s,
                             SurrogateXi sx = SurrogateXi{nullptr, nullptr, nullptr},
                             const double* grid_xi = nullptr,  // xi per Lambda from the grid (N_eff = +inf)
-                            double* parts = nullptr);         // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2
+                            double* parts = nullptr,          // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2
+                            const LogEntry* logtab = nullptr,  // table of log_tab (NULL: the library's log)
+                            LogConsts logc = LogConsts{0.0, 0.0});
 
 // Gradient of ln L (pop_grad.cu): per-Lambda constants (lam_grad_bytes() each), the
 // weight-and-derivative sums per (chunk, Lambda) ([K][n_chunks][13] doubles, plus the

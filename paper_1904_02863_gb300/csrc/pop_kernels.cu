@@ -281,7 +281,8 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
                 const int32_t* __restrict__ ecb, const int64_t* __restrict__ off, int64_t n_events,
                 int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw, const LamF64* __restrict__ lam,
                 const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags,
-                SurrogateXi sx, const double* __restrict__ grid_xi, double* __restrict__ parts)
+                SurrogateXi sx, const double* __restrict__ grid_xi, double* __restrict__ parts,
+                const LogEntry* __restrict__ logtab, LogConsts logc)
 {
     __shared__ double sh[FIN_THREADS / 32];
     const int64_t k = blockIdx.x;
@@ -305,8 +306,14 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
     for (int64_t i = threadIdx.x; i < n_events; i += FIN_THREADS) {
         double S = 0.0;
         for (int32_t c = ecb[i]; c < ecb[i + 1]; ++c) S += pk[c];
-        if (S == 0.0) zero = 1.0;
-        else s_ln += log(S / (double)(off[i + 1] - off[i]));
+        if (S == 0.0) {
+            zero = 1.0;
+        } else {
+            // ln(S/n): with the table, S times the Newton reciprocal of n (within 1.5 ulp of S/n)
+            // into log_pos (8 FP64 operations against the division's and the library log's dozens).
+            const double nd = (double)(off[i + 1] - off[i]);
+            s_ln += logtab ? log_pos(S * rcp_pos(nd), logtab, logc) : log(S / nd);
+        }
     }
     const int32_t n_inj = n_chunks - n_ev_chunks;
     const double* p2 = part2 + k * (int64_t)n_inj;
@@ -438,11 +445,12 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
                             int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
                             const LamF64* lam, const int64_t* dK, int64_t K_cap, double* lnL, double* lnxi,
                             double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx, const double* grid_xi,
-                            double* parts)
+                            double* parts, const LogEntry* logtab, LogConsts logc)
 {
     if (K_cap <= 0) return cudaSuccess;
     finalise_kernel<<<(unsigned)K_cap, FIN_THREADS, 0, s>>>(part, part2, ecb, off, n_events, n_chunks, n_ev_chunks,
-                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx, grid_xi, parts);
+                                                            n_draw, lam, dK, lnL, lnxi, neff, flags, sx, grid_xi, parts,
+                                                            logtab, logc);
     return cudaGetLastError();
 }
 

@@ -215,6 +215,64 @@ __device__ __forceinline__ double expm1_tab(double u, const double2* __restrict_
     return under ? -1.0 : (over ? __longlong_as_double(0x7ff0000000000000LL) : res);
 }
 
+// ln x for positive normal finite x, after P. T. P. Tang, "Table-driven implementation of the
+// logarithm function in IEEE floating-point arithmetic", ACM TOMS 16 (1990) 378-400:
+// x = 2^e m, m in [1, 2), F = 1 + j/128 the nearest such point (j = 0..128), f = m - F exact
+// (|f| <= 2^-8), and ln x = e ln2 + ln F + log1p(z) with z = f (1/F) (|z| <= 2^-8; exact for
+// j = 0 and 128).  ln2 and ln F are hi + lo pairs whose hi parts lie on the grid of 2^-43, so
+// e L_hi + lnF_hi is exact for |e| < 1100.  log1p(z) = z - z^2 q, q = 1/2 - z/3 + z^2/4 - z^3/5 +
+// z^4/6 - z^5/7 (truncation z^8/8, below 2^-59 of the result): q's error enters relative to the
+// result as |z| times it, so q is wanted to about 2^-46 and, lying within 0.0013 of 1/2, is
+// assembled from bits like expm1's coefficient: -z/3 and z^2/4 as FP32 pairs (z's two FP32
+// parts, the products' exact errors and the two parts of 1/3), the rest in FP32.  8 FP64
+// operations: f, z, z^2, the fma z - z^2 q, the two table fmas and two additions.  Error: within
+// about one ulp (z's own rounding, 2^-52 of |z|, matters most where the result is a few times
+// |z|, next to x = 1 +- 2^-8).
+constexpr int LOG_TABLE_SIZE = 129;  // F_j = 1 + j/128, j = 0..128
+
+struct LogEntry {
+    double inv_f;  // 1/F_j, rounded
+    double ln_hi;  // ln F_j on the grid of 2^-43
+    double ln_lo;  // ln F_j - ln_hi, rounded
+};
+
+struct LogConsts {
+    double l_hi, l_lo;  // ln 2 = l_hi + l_lo, l_hi on the grid of 2^-43
+};
+
+__device__ __forceinline__ double log_tab(double x, const LogEntry* __restrict__ tab, const LogConsts& k)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)(hi >> 20) - 1023;
+    const unsigned j = ((((hi & 0x000fffffu) >> 12) + 1u) >> 1);  // round((m - 1) 128), 0..128
+    const double m = __hiloint2double((int)((hi & 0x000fffffu) | 0x3ff00000u), (int)lo);
+    const double f = m - __hiloint2double((int)(0x3ff00000u + (j << 13)), 0);
+    const double z = f * __ldg(&tab[j].inv_f);
+    const float zh = f32_image(z), zl = f32_image_rest(z);
+    const float a = __fmul_rn(-zh, 0.3333333432674407959f);                  // -z/3 = a + t (pair)
+    float t = fmaf(-zh, 0.3333333432674407959f, -a);
+    t = fmaf(-zh, -9.9341077586e-9f, t);
+    t = fmaf(-zl, 0.3333333432674407959f, t);
+    const float sh = __fmul_rn(zh, zh);                                       // z^2 = sh + sl
+    const float sl = fmaf(2.0f * zh, zl, fmaf(zh, zh, -sh));
+    t = fmaf(0.25f, sl, t);
+    t = fmaf(__fmul_rn(sh, zh), fmaf(fmaf(zh, -1.0f / 7.0f, 1.0f / 6.0f), zh, -0.2f), t);
+    const double q = half_plus(fx<53>(a) + fx<53>(0.25f * sh) + fx<53>(t));
+    const double l1p = fma(-(z * z), q, z);
+    const double ed = dbl_of_int(e);
+    const double A = fma(ed, k.l_hi, __ldg(&tab[j].ln_hi));
+    const double B = fma(ed, k.l_lo, __ldg(&tab[j].ln_lo));
+    return A + (l1p + B);
+}
+
+// ln x for any x: log_tab for positive normal finite x, the library's log otherwise (0, subnormal,
+// infinite, negative or NaN arguments).
+__device__ __forceinline__ double log_pos(double x, const LogEntry* __restrict__ tab, const LogConsts& k)
+{
+    const long long b = __double_as_longlong(x);
+    return (b >= 0x0010000000000000LL && b < 0x7ff0000000000000LL) ? log_tab(x, tab, k) : log(x);
+}
+
 // |bits(m1) - bits(mmin)| below 2^46 means m1/mmin - 1 is below ~2^-6: there
 // ln(mmin/m1) is taken as log1p((mmin - m1)/m1) by the series below, since the
 // difference of the two logs would cancel.

@@ -240,23 +240,25 @@ cudaError_t launch_weight_f64(const Tiling& t, int grid, FeatF64 ev, FeatF64 inj
 namespace {
 
 __global__ void math_check_kernel(int fn, int64_t n, const double* __restrict__ x, double* __restrict__ y,
-                                  const double2* __restrict__ exptab, ExpConsts kc)
+                                  const double2* __restrict__ exptab, ExpConsts kc,
+                                  const LogEntry* __restrict__ logtab, LogConsts logc)
 {
     extern __shared__ double2 stab[];
     load_table<256>(stab, exptab);
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = fn == 0 ? exp_tab(x[i], stab, kc) : (fn == 1 ? expm1_tab(x[i], stab, kc) : rcp_pos(x[i]));
+        y[i] = fn == 0 ? exp_tab(x[i], stab, kc)
+                       : (fn == 1 ? expm1_tab(x[i], stab, kc) : (fn == 2 ? rcp_pos(x[i]) : log_pos(x[i], logtab, logc)));
 }
 
 }  // namespace
 
 cudaError_t launch_math_check(int fn, int64_t n, const double* x, double* y, const double2* exptab, ExpConsts kc,
-                              cudaStream_t s)
+                              const LogEntry* logtab, LogConsts logc, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
-    math_check_kernel<<<(unsigned)blocks, 256, WEIGHT_F64_DYN_SMEM, s>>>(fn, n, x, y, exptab, kc);
+    math_check_kernel<<<(unsigned)blocks, 256, WEIGHT_F64_DYN_SMEM, s>>>(fn, n, x, y, exptab, kc, logtab, logc);
     return cudaGetLastError();
 }
 

@@ -106,3 +106,26 @@ def test_exp_at_the_index_switches_and_range_ends(ctx):
     assert (e <= 2.0 + 0.31 * np.abs(x)).all(), np.max(e - 0.31 * np.abs(x))
     small = np.abs(x) <= 1.0
     assert np.max(e[small]) <= 2.0
+
+
+def test_log_against_libm(ctx):
+    """The finalise's ln x (Tang's table-driven logarithm, 129 entries) within 2 ulp of libm, with
+    the library's log for zero, subnormal, infinite and negative arguments."""
+    from paper_1904_02863_gb300 import binding as B
+    rng = np.random.default_rng(9)
+    x = np.concatenate([10.0 ** rng.uniform(-307, 308, 200000), rng.uniform(0.25, 4.0, 100000),
+                        1.0 + rng.uniform(-2.0 ** -6, 2.0 ** -6, 100000),
+                        1.0 + np.array([2.0 ** -8, -2.0 ** -8, 2.0 ** -9, -2.0 ** -9, 1e-12, -1e-12, 2.0 ** -52]),
+                        [np.nextafter(1.0, 0.0), 1.0, 2.0, 0.5, 4096.0, 1.0 / 3.0],
+                        2.0 ** np.arange(-1022.0, 1024.0) * (1.0 + 2.0 ** -8)])
+    y = B.pop_math_check(ctx, 8, x)
+    ref = np.log(x)
+    nz = ref != 0.0
+    e = ulps(y[nz], ref[nz])
+    assert e.max() <= 2.0 and e.mean() < 0.4, (e.max(), e.mean())
+    assert (y[~nz] == 0.0).all()
+    special = np.array([0.0, 5e-324, 1e-310, np.inf, -1.0, np.nan])
+    ys = B.pop_math_check(ctx, 8, special)
+    with np.errstate(divide="ignore"):
+        np.testing.assert_allclose(ys[:4], np.log(special[:4]), rtol=1e-15)
+    assert np.isnan(ys[4]) and np.isnan(ys[5])
