@@ -98,6 +98,7 @@ struct pop_ctx {
     SampleSet ev, inj;
     std::vector<int64_t> h_offsets;
     DevBuf d_offsets;        // int64 [N+1]
+    DevBuf d_inv_n;          // double [N]: 1/n_i
     int64_t n_draw = 0;
 
     // Work chunks: event chunks first, then injection chunks.
@@ -460,7 +461,7 @@ int enqueue_pipeline(pop_ctx* c, int mode, int n_params, int grid, bool capturin
                        n_items, c->n_ev_chunks, c->n_draw, c->d_c64.as<LamF64>(), c->d_K.as<int64_t>(),
                        c->k_cap, c->d_lnL.as<double>(), c->d_lnxi.as<double>(), c->d_neff.as<double>(),
                        c->d_flags.as<uint32_t>(), c->stream, sx, use_grid ? c->grid->xi.as<double>() : nullptr,
-                       c->d_parts.as<double>(), c->d_logtab.as<LogEntry>(), c->logc),
+                       c->d_parts.as<double>(), c->d_logtab.as<LogEntry>(), c->logc, c->d_inv_n.as<double>()),
        "finalise");
     CK(cudaEventRecordWithFlags(c->ev_t1, c->stream, rec), "event");
     return POP_OK;
@@ -761,13 +762,18 @@ int pop_load_events(pop_ctx* c, int64_t n_events, const int64_t* offsets, int n_
     int rc = pack_samples(c, n, n_dims, theta, prior, storage, mem, s, "pop_load_events",
                           std::vector<int64_t>(offsets, offsets + n_events + 1));
     if (rc != POP_OK) return rc;
-    DevBuf doff;
+    DevBuf doff, dinv;
+    std::vector<double> inv(n_events);  // 1/n_i, correctly rounded, for the finalise
+    for (int64_t i = 0; i < n_events; ++i) inv[i] = 1.0 / (double)(offsets[i + 1] - offsets[i]);
     CK(doff.alloc(sizeof(int64_t) * (n_events + 1)), "cudaMalloc(offsets)");
+    CK(dinv.alloc(sizeof(double) * std::max<int64_t>(n_events, 1)), "cudaMalloc(1/n)");
     CK(cudaMemcpyAsync(doff.p, offsets, sizeof(int64_t) * (n_events + 1), cudaMemcpyHostToDevice, c->stream),
        "copy offsets");
+    CK(cudaMemcpyAsync(dinv.p, inv.data(), sizeof(double) * n_events, cudaMemcpyHostToDevice, c->stream), "copy 1/n");
     CK(cudaStreamSynchronize(c->stream), "sync");
     c->ev.swap(s);
     c->d_offsets.swap(doff);
+    c->d_inv_n.swap(dinv);
     c->h_offsets.assign(offsets, offsets + n_events + 1);
     if (c->inj.n && c->inj.n_dims != n_dims) {  // stale injections of another layout
         SampleSet none;

@@ -196,7 +196,8 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
                             const double* grid_xi = nullptr,  // xi per Lambda from the grid (N_eff = +inf)
                             double* parts = nullptr,          // [K][3]: sum_i ln(S_i/n_i), sum w, sum w^2
                             const LogEntry* logtab = nullptr,  // table of log_tab (NULL: the library's log)
-                            LogConsts logc = LogConsts{0.0, 0.0});
+                            LogConsts logc = LogConsts{0.0, 0.0},
+                            const double* inv_n = nullptr);   // 1/n_i [N] (NULL: formed in the kernel)
 
 // Gradient of ln L (pop_grad.cu): per-Lambda constants (lam_grad_bytes() each), the
 // weight-and-derivative sums per (chunk, Lambda) ([K][n_chunks][13] doubles, plus the

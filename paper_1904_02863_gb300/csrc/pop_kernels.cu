@@ -144,24 +144,65 @@ __global__ void zint_kernel(const double* __restrict__ lambda, const int64_t* __
     if (lane == 0) zint[k] = zs * (2.0 / (Z_NODES - 1));
 }
 
-// Per-Lambda constants, one thread per Lambda (the special functions of a warp's 32 Lambda
-// share each FP64 instruction); zint from zint_kernel when the model has redshift.
-__global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
-                                LamF64* __restrict__ c64, LamF32* __restrict__ c32, const double* __restrict__ zint)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= *dK) return;
-    const double* L = lambda + k * n_params;
-    const bool has_z = n_params == 12;
-    const double zs = has_z ? zint[k] : 0.0;
+// Per-Lambda constants, 32 Lambda per block of 4 warps, lane = Lambda: the special functions
+// of a warp's 32 Lambda share each FP64 instruction (an FP64 warp instruction costs the same for
+// one lane or 32), and the block's 4 warps, on the SM's 4 schedulers, split them: warps 1-3 take
+// the lgamma and erf terms, warp 0 the logs meanwhile, then combines.  zint from zint_kernel when
+// the model has redshift.
+constexpr int PRO_THREADS = 128;
 
-    bool valid = true;
-    for (int p = 0; p < n_params; ++p) valid = valid && finite_d(L[p]);
-    const double alpha = L[P_ALPHA], beta = L[P_BETA], mmin = L[P_MMIN], mmax = L[P_MMAX];
-    const double lam = L[P_LAM], mu = L[P_MPP], sig = L[P_SIGPP], ach = L[P_ACHI], bch = L[P_BCHI];
-    const double xit = L[P_XIT], sigt = L[P_SIGT];
+__global__ void __launch_bounds__(PRO_THREADS)
+prologue_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
+                LamF64* __restrict__ c64, LamF32* __restrict__ c32, const double* __restrict__ zint)
+{
+    __shared__ double s_lb[32], s_lab[32], s_cg[32], s_ct[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t k = blockIdx.x * 32LL + lane;
+    const bool live = k < *dK;
+    const double* L = lambda + (live ? k : 0) * n_params;
+    const bool has_z = n_params == 12;
+
+    bool valid = live;
+    for (int p = 0; p < n_params && live; ++p) valid = valid && finite_d(L[p]);
+    // Lanes past K or with bad rows evaluate the special functions at 1 (their results unused).
+    const double one = 1.0;
+    const double alpha = valid ? L[P_ALPHA] : one, beta = valid ? L[P_BETA] : one;
+    const double mmin = valid ? L[P_MMIN] : one, mmax = valid ? L[P_MMAX] : 2.0;
+    const double lam = valid ? L[P_LAM] : 0.5, mu = valid ? L[P_MPP] : one, sig = valid ? L[P_SIGPP] : one;
+    const double ach = valid ? L[P_ACHI] : one, bch = valid ? L[P_BCHI] : one;
+    const double xit = valid ? L[P_XIT] : 0.5, sigt = valid ? L[P_SIGT] : one;
     valid = valid && mmin > 0.0 && mmin < mmax && lam >= 0.0 && lam <= 1.0 && sig > 0.0 && sigt > 0.0 &&
             ach > 0.0 && bch > 0.0 && xit >= 0.0 && xit <= 1.0;
+    double lmmin = 0.0, ln_cpl = 0.0, ln_qn = 0.0, ln_iz = 0.0, l1lam = 0.0, l2mmin = 0.0;
+    const double b1 = 1.0 + beta;
+    const int beta_m1 = b1 == 0.0;
+    if (w == 1) {
+        s_lb[lane] = lgamma(ach) + lgamma(bch);
+    } else if (w == 2) {
+        s_lab[lane] = lgamma(ach + bch);
+        // Tilt: C_t = 1 / (sigma_t sqrt(2 pi) * erf(sqrt2 / sigma_t) / 2); ct = ln(xi_t C_t^2).
+        s_ct[lane] = log(xit) - 2.0 * log(sigt * SQRT2PI * 0.5 * erf(SQRT2 / sigt));
+    } else if (w == 3) {
+        // Truncated Gaussian on [mmin, mmax]: C_g = 1 / (sigma sqrt(2 pi) Z_m).
+        const double zm = 0.5 * (erf((mmax - mu) / (SQRT2 * sig)) - erf((mmin - mu) / (SQRT2 * sig)));
+        s_cg[lane] = log(lam) - log(sig * SQRT2PI * zm);
+    } else {
+        lmmin = log(mmin);
+        const double lmmax = log(mmax);
+        // Power law: C_pl = (1-alpha) / (mmax^(1-alpha) - mmin^(1-alpha)), in logs.
+        if (alpha == 1.0) {
+            ln_cpl = -log(lmmax - lmmin);
+        } else {
+            const double oma = 1.0 - alpha;
+            ln_cpl = log(fabs(oma)) - oma * lmmin - log(fabs(expm1(oma * (lmmax - lmmin))));
+        }
+        ln_qn = beta_m1 ? 0.0 : log(fabs(b1));
+        ln_iz = has_z && live ? log(zint[k]) : 0.0;
+        l1lam = log1p(-lam);
+        l2mmin = log2(mmin);
+    }
+    __syncthreads();  // the one barrier: warps 1-3 have written their terms
+    if (w != 0 || !live) return;
 
     LamF64 c;
     LamF32 f;
@@ -179,31 +220,14 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
         c32[k] = f;
         return;
     }
-    const double lmmin = log(mmin), lmmax = log(mmax);
-    // Power law: C_pl = (1-alpha) / (mmax^(1-alpha) - mmin^(1-alpha)), in logs.
-    double ln_cpl;
-    if (alpha == 1.0) {
-        ln_cpl = -log(lmmax - lmmin);
-    } else {
-        const double oma = 1.0 - alpha;
-        ln_cpl = log(fabs(oma)) - oma * lmmin - log(fabs(expm1(oma * (lmmax - lmmin))));
-    }
-    // Truncated Gaussian on [mmin, mmax]: C_g = 1 / (sigma sqrt(2 pi) Z_m).
-    const double zm = 0.5 * (erf((mmax - mu) / (SQRT2 * sig)) - erf((mmin - mu) / (SQRT2 * sig)));
-    const double ln_cg = log(lam) - log(sig * SQRT2PI * zm);
-    const double ln_beta = lgamma(ach) + lgamma(bch) - lgamma(ach + bch);
-    const double b1 = 1.0 + beta;
-    const int beta_m1 = b1 == 0.0;
-    const double ln_qn = beta_m1 ? 0.0 : log(fabs(b1));
-    const double ln_iz = has_z ? log(zs) : 0.0;
+    const double ln_beta = s_lb[lane] - s_lab[lane];
     const double common = ln_qn - 2.0 * ln_beta - ln_iz;
-    // Tilt: C_t = 1 / (sigma_t sqrt(2 pi) * erf(sqrt2 / sigma_t) / 2).
-    const double ln_ct = -log(sigt * SQRT2PI * 0.5 * erf(SQRT2 / sigt));
+    const double ln_cg = s_cg[lane];
 
     c.mmin_bits = dbits(mmin);
     c.mmax_bits = dbits(mmax);
     c.nalpha = -alpha;
-    c.cpl = common + log1p(-lam) + ln_cpl;
+    c.cpl = common + l1lam + ln_cpl;
     c.mu = mu;
     c.nh = -0.5 / (sig * sig);
     c.cg = common + ln_cg;
@@ -217,7 +241,7 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     c.kq = beta_m1 ? 1.0 : b1;
     c.kqlmmin = c.kq * lmmin;
     c.nht = -0.5 / (sigt * sigt);
-    c.ct = log(xit) + 2.0 * ln_ct;
+    c.ct = s_ct[lane];
     c.t0 = 0.25 * (1.0 - xit);
     c.gs = 1.0 / (SQRT2 * sig);
     c.gc = -mu * c.gs;
@@ -246,7 +270,6 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     f.bc = (float)c.bc;
     f.km1 = (float)c.km1;
     const double b1f = beta_m1 ? 1.0 : b1;
-    const double l2mmin = log2(mmin);
     f.lmmin = (float)l2mmin;
     f.b1 = (float)b1f;
     f.nb1 = (float)-b1f;
@@ -259,20 +282,6 @@ __global__ void prologue_kernel(const double* __restrict__ lambda, const int64_t
     c32[k] = f;
 }
 
-// Deterministic block sum (fixed shuffle tree, then warps in order).
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int i = 0; i < NT / 32; ++i) s += sh[i];
-    return s;
-}
-
 constexpr int FIN_THREADS = 256;
 
 // ln L = sum_i ln(S_i / n_i) - N ln xi, plus ln xi, N_eff and flags.
@@ -282,9 +291,9 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
                 int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw, const LamF64* __restrict__ lam,
                 const int64_t* __restrict__ dK, double* lnL, double* lnxi, double* neff, uint32_t* flags,
                 SurrogateXi sx, const double* __restrict__ grid_xi, double* __restrict__ parts,
-                const LogEntry* __restrict__ logtab, LogConsts logc)
+                const LogEntry* __restrict__ logtab, LogConsts logc, const double* __restrict__ inv_n)
 {
-    __shared__ double sh[FIN_THREADS / 32];
+    __shared__ double sh[FIN_THREADS / 32][3];
     const int64_t k = blockIdx.x;
     if (k >= *dK) return;
     if (!lam[k].valid) {
@@ -302,17 +311,19 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
         return;
     }
     const double* pk = part + k * (int64_t)n_chunks;
-    double s_ln = 0.0, zero = 0.0;
+    double s_ln = 0.0;
+    int zero = 0;
     for (int64_t i = threadIdx.x; i < n_events; i += FIN_THREADS) {
         double S = 0.0;
         for (int32_t c = ecb[i]; c < ecb[i + 1]; ++c) S += pk[c];
         if (S == 0.0) {
-            zero = 1.0;
+            zero = 1;
+        } else if (logtab) {
+            // ln(S/n) as log_pos(S (1/n)) (within 1 ulp of S/n; 8 FP64 operations against the
+            // division's and the library log's dozens), 1/n from the table or a Newton step.
+            s_ln += log_pos(S * (inv_n ? inv_n[i] : rcp_pos((double)(off[i + 1] - off[i]))), logtab, logc);
         } else {
-            // ln(S/n): with the table, S times the Newton reciprocal of n (within 1.5 ulp of S/n)
-            // into log_pos (8 FP64 operations against the division's and the library log's dozens).
-            const double nd = (double)(off[i + 1] - off[i]);
-            s_ln += logtab ? log_pos(S * rcp_pos(nd), logtab, logc) : log(S / nd);
+            s_ln += log(S / (double)(off[i + 1] - off[i]));
         }
     }
     const int32_t n_inj = n_chunks - n_ev_chunks;
@@ -322,13 +333,31 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
         sw += pk[n_ev_chunks + c];
         sw2 += p2[c];
     }
-    s_ln = block_sum<FIN_THREADS>(s_ln, sh);
-    zero = block_sum<FIN_THREADS>(zero, sh);
-    sw = block_sum<FIN_THREADS>(sw, sh);
-    sw2 = block_sum<FIN_THREADS>(sw2, sh);
+    // One fixed-order reduction of the three sums: the shuffle tree in the warps that hold any
+    // item (an FP64 warp instruction costs the same with idle lanes), the warps' partials added
+    // in order by three lanes of warp 0; the zero-event flag by the barrier's OR.
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v[3] = {s_ln, sw, sw2};
+    if ((int64_t)w * 32 < max(n_events, (int64_t)n_inj)) {  // warp-uniform; later warps hold zeros
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sh[w][q] = v[q];
+    const int any_zero = __syncthreads_or(zero);
+    if (w != 0) return;
+    double tot = 0.0;
+    if (lane < 3)
+        for (int u = 0; u < FIN_THREADS / 32; ++u) tot += sh[u][lane];
+    s_ln = __shfl_sync(0xffffffffu, tot, 0);
+    sw = __shfl_sync(0xffffffffu, tot, 1);
+    sw2 = __shfl_sync(0xffffffffu, tot, 2);
+    const double zero_any = any_zero ? 1.0 : 0.0;
     if (threadIdx.x != 0) return;
     if (parts) {  // the additive parts: event log-sum, injection sum w and sum w^2
-        parts[3 * k] = zero > 0.0 ? -INFINITY : s_ln;
+        parts[3 * k] = zero_any > 0.0 ? -INFINITY : s_ln;
         parts[3 * k + 1] = sw;
         parts[3 * k + 2] = sw2;
     }
@@ -338,7 +367,7 @@ finalise_kernel(const double* __restrict__ part, const double* __restrict__ part
     const double var = sw2 / (nd * nd) - xi * xi / nd;
     double ne = var > 0.0 ? xi * xi / var : INFINITY;
     double out, lx;
-    if (zero > 0.0) fl |= POP_FLAG_ZERO_EVENT;
+    if (zero_any > 0.0) fl |= POP_FLAG_ZERO_EVENT;
     if (grid_xi) {  // selection term from the grid: no Monte Carlo variance
         xi = grid_xi[k];
         ne = INFINITY;
@@ -428,8 +457,8 @@ cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_c
         if (!zint) return cudaErrorInvalidValue;
         zint_kernel<<<(unsigned)((K_cap * 32 + 255) / 256), 256, 0, s>>>(lambda, dK, n_params, ztab, exptab, kc, zint);
     }
-    // Blocks of one warp, so that a small batch still spreads over many SMs.
-    prologue_kernel<<<(unsigned)((K_cap + 31) / 32), 32, 0, s>>>(lambda, dK, n_params, c64, c32, zint);
+    // 32 Lambda per block (4 warps), so that a small batch still spreads over many SMs.
+    prologue_kernel<<<(unsigned)((K_cap + 31) / 32), PRO_THREADS, 0, s>>>(lambda, dK, n_params, c64, c32, zint);
     return cudaGetLastError();
 }
 
@@ -445,12 +474,12 @@ cudaError_t launch_finalise(const double* part, const double* part2, const int32
                             int64_t n_events, int32_t n_chunks, int32_t n_ev_chunks, int64_t n_draw,
                             const LamF64* lam, const int64_t* dK, int64_t K_cap, double* lnL, double* lnxi,
                             double* neff, uint32_t* flags, cudaStream_t s, SurrogateXi sx, const double* grid_xi,
-                            double* parts, const LogEntry* logtab, LogConsts logc)
+                            double* parts, const LogEntry* logtab, LogConsts logc, const double* inv_n)
 {
     if (K_cap <= 0) return cudaSuccess;
     finalise_kernel<<<(unsigned)K_cap, FIN_THREADS, 0, s>>>(part, part2, ecb, off, n_events, n_chunks, n_ev_chunks,
                                                             n_draw, lam, dK, lnL, lnxi, neff, flags, sx, grid_xi, parts,
-                                                            logtab, logc);
+                                                            logtab, logc, inv_n);
     return cudaGetLastError();
 }
 
