@@ -539,8 +539,10 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot)
     return (warp ? warp_tot[warp - 1] : 0) + x - v;
 }
 
-// order[0, K): the Lambda by increasing mmin (1024 equal bins over the batch's range,
-// invalid Lambda last).  order[K_cap, K_cap + K): the same with the Lambda that need the
+// order[0, K): the Lambda by increasing mmin (1024 bins, equal in the bit pattern of mmin, which
+// orders positive doubles like their values, over the batch's range; invalid Lambda last).  The
+// range and the bins use integer operations only (an FP64 min/max loop over the warps' partials
+// on every thread took most of this kernel's time).  order[K_cap, K_cap + K): the same with the Lambda that need the
 // Monte Carlo xi (need_mc[k] != 0) first; *n_mc = their number (K without need_mc).  The order
 // within a bin is arbitrary: it only decides which lane evaluates which Lambda.
 __global__ void __launch_bounds__(ORDER_THREADS)
@@ -548,22 +550,23 @@ lam_order_kernel(const LamF32* __restrict__ lam, const int64_t* __restrict__ dK,
                  int64_t K_cap, int32_t* __restrict__ order, int32_t* __restrict__ n_mc)
 {
     __shared__ int h_ev[ORDER_BINS], h_inj[2 * ORDER_BINS], warp_tot[32];
-    __shared__ double s_lo[32], s_hi[32];
+    __shared__ long long s_lo[32], s_hi[32];
+    constexpr long long INF_BITS = 0x7ff0000000000000LL;  // +inf: an invalid Lambda's mmin
     const int K = (int)*dK;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double lo = INFINITY, hi = -INFINITY;
+    long long lo = INF_BITS, hi = 0;
     int cnt = 0;
     for (int k = threadIdx.x; k < K; k += ORDER_THREADS) {
-        const double m = __longlong_as_double(lam[k].mmin_bits);
-        if (m < INFINITY) {
-            lo = fmin(lo, m);
-            hi = fmax(hi, m);
+        const long long m = lam[k].mmin_bits;
+        if (m < INF_BITS) {
+            lo = min(lo, m);
+            hi = max(hi, m);
         }
         cnt += (need_mc == nullptr || need_mc[k]) ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     if (lane == 0) {
@@ -578,15 +581,18 @@ lam_order_kernel(const LamF32* __restrict__ lam, const int64_t* __restrict__ dK,
     hi = s_hi[0];
     cnt = 0;
     for (int w = 0; w < ORDER_THREADS / 32; ++w) {
-        lo = fmin(lo, s_lo[w]);
-        hi = fmax(hi, s_hi[w]);
+        lo = min(lo, s_lo[w]);
+        hi = max(hi, s_hi[w]);
         cnt += warp_tot[w];
     }
-    const double scale = hi > lo ? ORDER_BINS / (hi - lo) : 0.0;
+    // bin = floor((m - lo) 1024 / (range + 1)) on the bit patterns, both shifted to 20 bits.
+    const unsigned long long range = hi > lo ? (unsigned long long)(hi - lo) : 0ull;
+    const int sh = (range >> 20) ? 44 - __clzll((long long)range) : 0;
+    const unsigned den = (unsigned)(range >> sh) + 1u;
     auto bin = [&](int k) {
-        const double m = __longlong_as_double(lam[k].mmin_bits);
-        if (!(m < INFINITY)) return ORDER_BINS - 1;
-        return min(ORDER_BINS - 1, (int)((m - lo) * scale));
+        const long long m = lam[k].mmin_bits;
+        if (m >= INF_BITS) return ORDER_BINS - 1;
+        return min(ORDER_BINS - 1, (int)(((unsigned)((unsigned long long)(m - lo) >> sh) * ORDER_BINS) / den));
     };
     for (int k = threadIdx.x; k < K; k += ORDER_THREADS) {
         const int b = bin(k);
