@@ -115,33 +115,42 @@ __global__ void pack_f32_kernel(const double* __restrict__ theta, const double* 
 __device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
 
 // Redshift normalisation per Lambda, I(kappa) = trapezoid of (1+z)^(kappa-1) z^2 on
-// z_k = 2k/1023: one warp per Lambda, the lanes share the 1024 nodes.  With ztab (node i:
+// z_k = 2k/1023: one block of 4 warps per Lambda, the threads share the 1024 nodes (a warp per
+// Lambda left each scheduler under two warps to hide the exponentials' latency).  With ztab (node i:
 // ln(1 + z_i) and its trapezoid weight times z_i^2) each node costs one table-driven
 // exponential; without it (callers that hold no tables) the logarithm and exponential are
 // evaluated directly.
-__global__ void zint_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
-                            const double2* __restrict__ ztab, const double2* __restrict__ exptab, ExpConsts kc,
-                            double* __restrict__ zint)
+constexpr int ZINT_THREADS = 128;
+static_assert(ZINT_THREADS == 128, "the block's four warp partials are added in order below");
+
+__global__ void __launch_bounds__(ZINT_THREADS)
+zint_kernel(const double* __restrict__ lambda, const int64_t* __restrict__ dK, int n_params,
+            const double2* __restrict__ ztab, const double2* __restrict__ exptab, ExpConsts kc,
+            double* __restrict__ zint)
 {
-    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= *dK) return;
+    __shared__ double s_part[ZINT_THREADS / 32];
+    const int64_t k = blockIdx.x;
+    if (k >= *dK) return;  // the same for the whole block
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const double km1 = lambda[k * n_params + P_KAPPA] - 1.0;
     double zs = 0.0;
     if (ztab) {
-        for (int i = lane; i < Z_NODES; i += 32) {
+        for (int i = threadIdx.x; i < Z_NODES; i += ZINT_THREADS) {
             const double2 t = ztab[i];
             zs = fma(t.y, exp_tab(km1 * t.x, exptab, kc), zs);
         }
     } else {
-        for (int i = lane; i < Z_NODES; i += 32) {
+        for (int i = threadIdx.x; i < Z_NODES; i += ZINT_THREADS) {
             double z = 2.0 * i / (Z_NODES - 1);
             double f = exp(km1 * log1p(z)) * z * z;
             zs += (i == 0 || i == Z_NODES - 1) ? 0.5 * f : f;
         }
     }
     for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
-    if (lane == 0) zint[k] = zs * (2.0 / (Z_NODES - 1));
+    if (lane == 0) s_part[w] = zs;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        zint[k] = (((s_part[0] + s_part[1]) + s_part[2]) + s_part[3]) * (2.0 / (Z_NODES - 1));
 }
 
 // Per-Lambda constants, 32 Lambda per block of 4 warps, lane = Lambda: the special functions
@@ -455,7 +464,7 @@ cudaError_t launch_prologue(const double* lambda, const int64_t* dK, int64_t K_c
     if (K_cap <= 0) return cudaSuccess;
     if (n_params == 12) {
         if (!zint) return cudaErrorInvalidValue;
-        zint_kernel<<<(unsigned)((K_cap * 32 + 255) / 256), 256, 0, s>>>(lambda, dK, n_params, ztab, exptab, kc, zint);
+        zint_kernel<<<(unsigned)K_cap, ZINT_THREADS, 0, s>>>(lambda, dK, n_params, ztab, exptab, kc, zint);
     }
     // 32 Lambda per block (4 warps), so that a small batch still spreads over many SMs.
     prologue_kernel<<<(unsigned)((K_cap + 31) / 32), PRO_THREADS, 0, s>>>(lambda, dK, n_params, c64, c32, zint);
